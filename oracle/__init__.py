@@ -1,0 +1,193 @@
+"""CPU oracle for the DiffSoup hot path (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library never loads it.
+
+``build()`` compiles ``diffsoup_oracle.c`` with gcc into ``oracle/_build``;
+the wrappers below marshal numpy arrays into it.  See the C file for the
+passage of the paper that each function restates and for its pin status.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "diffsoup_oracle.c")
+_OUT = os.path.join(_HERE, "_build", "liboracle.so")
+
+MODE_STOCHASTIC = 0
+MODE_THRESHOLD_HALF = 1
+G_TEX, G_SCORE, G_INTERIOR, G_EDGE = 1, 2, 4, 8
+G_ALL = G_TEX | G_SCORE | G_INTERIOR | G_EDGE
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (plain C, no fused multiply-add contraction)."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
+        tmp = _OUT + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_OUT)
+        f32, i32, u32, i64, u64 = ctypes.c_float, ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64, ctypes.c_uint64
+        P = ctypes.c_void_p
+        L.or_expf.restype = f32; L.or_expf.argtypes = [f32]
+        L.or_sigmoidf.restype = f32; L.or_sigmoidf.argtypes = [f32]
+        L.or_philox4x32.restype = None; L.or_philox4x32.argtypes = [P, P, P]
+        L.or_tau.restype = f32; L.or_tau.argtypes = [u64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.or_lookup.restype = f32; L.or_lookup.argtypes = [P, ctypes.c_int, ctypes.c_int, f32, f32]
+        L.or_cell.restype = None; L.or_cell.argtypes = [ctypes.c_int, f32, f32, P, P]
+        L.or_fragment.restype = ctypes.c_int
+        L.or_fragment.argtypes = [P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
+        L.or_activate.restype = None; L.or_activate.argtypes = [P, i64, P]
+        L.or_forward.restype = ctypes.c_int
+        L.or_forward.argtypes = [P, P, i32, i32, i32, P, P, P, i32, i32, i32, P, P, i32, i32,
+                                 P, P, P, P, P, P]
+        L.or_backward.restype = ctypes.c_int
+        L.or_backward.argtypes = [P, P, i32, i32, i32, P, P, i32, i32, P, P, P, P, P, u32, i32, i32, P, P]
+        L.or_expected.restype = ctypes.c_int
+        L.or_expected.argtypes = [P, P, i32, i32, i32, P, P, i32, P, P, P, P]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def _cams(cams):
+    cf = np.stack([c.as_floats() for c in cams]).astype(np.float32)
+    wh = np.array([[c.width, c.height] for c in cams], np.int32)
+    return np.ascontiguousarray(cf), np.ascontiguousarray(wh)
+
+
+# ---------------------------------------------------------------- scalar pins
+def expf(x: float) -> float:
+    return float(lib().or_expf(float(x)))
+
+
+def sigmoidf(x: float) -> float:
+    return float(lib().or_sigmoidf(float(x)))
+
+
+def philox(ctr, key) -> np.ndarray:
+    c = _c(ctr, np.uint32); k = _c(key, np.uint32); out = np.zeros(4, np.uint32)
+    lib().or_philox4x32(_p(c), _p(k), _p(out))
+    return out
+
+
+def tau(seed: int, px: int, py: int, t: int, s: int) -> float:
+    return float(lib().or_tau(int(seed), px, py, t, s))
+
+
+def lookup(grid: np.ndarray, N: int, b1: float, b2: float) -> float:
+    """Value of a single-channel grid (V,) at (b1, b2)."""
+    g = _c(grid, np.float32)
+    return float(lib().or_lookup(_p(g), N, 1, float(b1), float(b2)))
+
+
+def cell(N: int, b1: float, b2: float):
+    idx = np.zeros(3, np.int32); w = np.zeros(2, np.float32)
+    lib().or_cell(N, float(b1), float(b2), _p(idx), _p(w))
+    return idx, w
+
+
+def fragment(v9, cam, px: int, py: int):
+    """(covered, rho, D, b1, b2) of one triangle at one pixel."""
+    v = _c(v9, np.float32).reshape(9); cf = cam.as_floats(); out = np.zeros(4, np.float32)
+    cov = lib().or_fragment(_p(v), _p(cf), cam.width, cam.height, px, py, _p(out))
+    return bool(cov), float(out[0]), float(out[1]), float(out[2]), float(out[3])
+
+
+def activate(tex: np.ndarray) -> np.ndarray:
+    t = _c(tex, np.float32); out = np.empty_like(t)
+    lib().or_activate(_p(t), t.size, _p(out))
+    return out
+
+
+# ---------------------------------------------------------------- full passes
+def forward(verts, tex, grid_n, cams, seeds, S=1, mode=MODE_STOCHASTIC, bg=None,
+            order=None, rows=None):
+    """Brute-force forward.  Returns one dict per view with tri_id [S,H,W],
+    bary [S,H,W,2], depth [S,H,W], n_front, n_cover [S,H,W], color [S,C-1,H,W]."""
+    verts = _c(verts, np.float32); tex = _c(tex, np.float32)
+    T, V, C = tex.shape
+    cf, wh = _cams(cams)
+    seeds = _c(seeds if seeds is not None else np.zeros(len(cams), np.uint64), np.uint64)
+    bg = _c(bg if bg is not None else np.zeros(C - 1), np.float32)
+    npx = sum(S * c.width * c.height for c in cams)
+    tri = np.full(npx, -1, np.int32); bary = np.zeros(2 * npx, np.float32)
+    depth = np.zeros(npx, np.float32); nf = np.zeros(npx, np.int32); nc = np.zeros(npx, np.int32)
+    color = np.zeros(npx * (C - 1), np.float32)
+    order_a = None if order is None else _c(order, np.int32)
+    r0, r1 = (0, -1) if rows is None else rows
+    rc = lib().or_forward(_p(verts), _p(tex), T, grid_n, C, _p(cf), _p(wh), _p(seeds), len(cams),
+                          S, mode, _p(bg), _p(order_a), r0, r1,
+                          _p(tri), _p(bary), _p(depth), _p(nf), _p(nc), _p(color))
+    assert rc == 0, rc
+    out, o, oc = [], 0, 0
+    for c in cams:
+        n = S * c.height * c.width
+        out.append(dict(
+            tri_id=tri[o:o + n].reshape(S, c.height, c.width),
+            bary=bary[2 * o:2 * (o + n)].reshape(S, c.height, c.width, 2),
+            depth=depth[o:o + n].reshape(S, c.height, c.width),
+            n_front=nf[o:o + n].reshape(S, c.height, c.width),
+            n_cover=nc[o:o + n].reshape(S, c.height, c.width),
+            color=color[oc:oc + n * (C - 1)].reshape(S, C - 1, c.height, c.width)))
+        o += n; oc += n * (C - 1)
+    return out
+
+
+def backward(verts, tex, grid_n, cams, S, fwd, grad_color, score_w, flags=G_ALL, rows=None):
+    """Algorithm A1 step 2 plus vertex gradients, FP64 accumulation.
+    fwd: list of per-view dicts (tri_id, bary, color); grad_color: list of
+    [S,C-1,H,W]; score_w: list of [S,H,W].  Returns (grad_tex, grad_verts)."""
+    verts = _c(verts, np.float32); tex = _c(tex, np.float32)
+    T, V, C = tex.shape
+    cf, wh = _cams(cams)
+    tri = _c(np.concatenate([f["tri_id"].ravel() for f in fwd]), np.int32)
+    bary = _c(np.concatenate([f["bary"].ravel() for f in fwd]), np.float32)
+    col = _c(np.concatenate([f["color"].ravel() for f in fwd]), np.float32)
+    gc = _c(np.concatenate([g.ravel() for g in grad_color]), np.float32)
+    sw = _c(np.concatenate([w.ravel() for w in score_w]), np.float32)
+    gt = np.zeros(tex.shape, np.float64); gv = np.zeros(verts.shape, np.float64)
+    r0, r1 = (0, -1) if rows is None else rows
+    rc = lib().or_backward(_p(verts), _p(tex), T, grid_n, C, _p(cf), _p(wh), len(cams), S,
+                           _p(tri), _p(bary), _p(col), _p(gc), _p(sw), flags, r0, r1, _p(gt), _p(gv))
+    assert rc == 0, rc
+    return gt, gv
+
+
+def expected(verts, tex, grid_n, cams, targets, bg=None, with_grad=True):
+    """Closed-form E[l] per view (l = squared error summed over channels and
+    pixels) and its exact gradient w.r.t. the texture logits (FP64 logits)."""
+    verts = _c(verts, np.float32); tex = _c(tex, np.float64)
+    T, V, C = tex.shape
+    cf, wh = _cams(cams)
+    tg = _c(np.concatenate([t.ravel() for t in targets]), np.float32)
+    bg = _c(bg if bg is not None else np.zeros(C - 1), np.float32)
+    el = np.zeros(len(cams), np.float64)
+    eg = np.zeros(tex.shape, np.float64) if with_grad else None
+    rc = lib().or_expected(_p(verts), _p(tex), T, grid_n, C, _p(cf), _p(wh), len(cams),
+                           _p(tg), _p(bg), _p(el), _p(eg))
+    assert rc == 0, rc
+    return el, eg

@@ -1,0 +1,799 @@
+/*
+ * diffsoup_oracle.c -- plain, slow CPU oracle for the stochastic-opacity-masked
+ * rasteriser of DiffSoup (arXiv 2603.27151) and its gradient.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark load this file.  It shares no code, header or
+ * constant table with the CUDA library; both are written from the paper and
+ * from the readings recorded with the project's design notes.
+ *
+ * Every function names the passage it restates.  Decisions that pick an
+ * integer (coverage, the depth order, alpha > tau) are taken in FP32 with a
+ * fixed operation order, because the GPU path takes them in FP32; gradients
+ * are accumulated in FP64.
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fPIC -shared -o liboracle.so diffsoup_oracle.c -lm
+ * (-ffp-contract=off: no fused multiply-add unless written as fmaf()).
+ *
+ * Parity status per function:
+ *   or_expf / or_sigmoidf ... pinned (error bound against libm exp in double)
+ *   or_philox4x32 ........... pinned (independent Philox4x32-10 implementation)
+ *   or_lookup ............... pinned (linear reproduction, constant grid, texel count)
+ *   or_fragment ............. pinned (watertight tiling, ray-plane depth/barycentrics)
+ *   or_forward .............. pinned (z-buffer special case, background special case,
+ *                             order independence, Monte Carlo selection frequencies)
+ *   or_backward (tex, score)  pinned (expectation == finite differences of Eq. 7)
+ *   or_backward (interior) .. pinned (finite differences at fixed visibility)
+ *   or_backward (edge) ...... partly pinned: sign/magnitude against a supersampled
+ *                             finite difference; the absolute weighting is
+ *                             "parity unpinned" (the paper prints no formula).
+ *   or_expected ............. pinned (finite differences; Monte Carlo of or_forward)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define OR_MODE_STOCHASTIC 0
+#define OR_MODE_THRESHOLD_HALF 1
+
+#define OR_G_TEX 1u
+#define OR_G_SCORE 2u
+#define OR_G_INTERIOR 4u
+#define OR_G_EDGE 8u
+
+/* ------------------------------------------------------------------------ */
+/* Pinned scalar math                                                        */
+/* ------------------------------------------------------------------------ */
+
+static float o_pow2i(int k) /* 2^k for -126 <= k <= 127, built from exponent bits */
+{
+    uint32_t bits = (uint32_t)(k + 127) << 23;
+    float f;
+    memcpy(&f, &bits, 4);
+    return f;
+}
+
+/* exp(x) in FP32 by Cody and Waite's argument reduction (Cody & Waite,
+ * "Software Manual for the Elementary Functions", 1980): x = k ln2 + r with
+ * ln2 split into a 16-bit head and a float tail, |r| <= ln2/2; e^r from its
+ * degree-7 Taylor polynomial (coefficients 1/n! rounded to float) by Horner's
+ * rule with fused multiply-adds; then scaled by 2^k in two exact steps so that
+ * subnormal results round once. */
+float or_expf(float x)
+{
+    if (x != x) return x;
+    if (x >= 0x1.62e430p+6f) return INFINITY;     /* above ln(FLT_MAX)         */
+    if (x < -0x1.9fe368p+6f) return 0.0f;         /* below ln(2^-150)          */
+    const float log2e = 0x1.715476p+0f;           /* 1/ln2 rounded to float    */
+    const float ln2_hi = 0x1.62e400p-1f;          /* ln2 cut to 16 bits        */
+    const float ln2_lo = 0x1.7f7d1cp-20f;         /* ln2 - ln2_hi, rounded     */
+    float kf = rintf(x * log2e);
+    float r = fmaf(-kf, ln2_hi, x);
+    r = fmaf(-kf, ln2_lo, r);
+    float p = 0x1.a01a02p-13f;                    /* 1/7! */
+    p = fmaf(p, r, 0x1.6c16c2p-10f);              /* 1/6! */
+    p = fmaf(p, r, 0x1.111112p-7f);               /* 1/5! */
+    p = fmaf(p, r, 0x1.555556p-5f);               /* 1/4! */
+    p = fmaf(p, r, 0x1.555556p-3f);               /* 1/3! */
+    p = fmaf(p, r, 0.5f);                         /* 1/2! */
+    p = fmaf(p, r, 1.0f);
+    p = fmaf(p, r, 1.0f);
+    int k = (int)kf;
+    int k1 = k / 2, k2 = k - k1;
+    return (p * o_pow2i(k1)) * o_pow2i(k2);
+}
+
+/* Sigmoid activation applied to the accumulated feature grid before
+ * rasterisation (Sec. 3.3, "Learnable multi-resolution triangle texture"). */
+float or_sigmoidf(float th) { return 1.0f / (1.0f + or_expf(-th)); }
+
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+ * as 1, 2, 3", SC'11): ten rounds of two 32x32->64 multiplications by
+ * 0xD2511F53 and 0xCD9E8D57, with the Weyl key schedule 0x9E3779B9,
+ * 0xBB67AE85. */
+void or_philox4x32(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* The per-fragment threshold tau_f of Eq. 5: uniform on the 2^-24 grid of
+ * [0, 1), one Philox block per (pixel, triangle, group of four samples). */
+static float o_tau(uint64_t seed, int px, int py, int t, int s)
+{
+    uint32_t ctr[4] = {(uint32_t)px, (uint32_t)py, (uint32_t)t, (uint32_t)(s >> 2)};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    or_philox4x32(ctr, key, out);
+    return (float)(out[s & 3] >> 8) * 0x1p-24f;
+}
+
+float or_tau(uint64_t seed, int px, int py, int t, int s) { return o_tau(seed, px, py, t, s); }
+
+/* ------------------------------------------------------------------------ */
+/* Mesh-colour texture decode (Sec. 3.3; supplementary Fig. "texture_vis")   */
+/* ------------------------------------------------------------------------ */
+
+/* Index of grid vertex (i, j), i + j <= N: rows of constant j, i along a row. */
+static int o_texel(int N, int i, int j) { return j * (N + 1) - j * (j - 1) / 2 + i; }
+
+/* Micro-triangle containing (b1, b2) and its interpolation weights.  Grid
+ * vertex (i, j) sits at barycentrics (1 - (i+j)/N, i/N, j/N).  The value is
+ * a0 + wa (a1 - a0) + wb (a2 - a0), i.e. linear interpolation over the three
+ * corners with weights (1 - wa - wb, wa, wb). */
+static void o_cell(int N, float b1, float b2, int idx[3], float* wa, float* wb, int* lower_out)
+{
+    float Nf = (float)N;
+    float u = Nf * b1, v = Nf * b2;
+    float fi = floorf(u), fj = floorf(v);
+    int i = fi < 0.0f ? 0 : (fi > (float)(N - 1) ? N - 1 : (int)fi);
+    int jmax = N - 1 - i;
+    int j = fj < 0.0f ? 0 : (fj > (float)jmax ? jmax : (int)fj);
+    float fu = u - (float)i, fv = v - (float)j;
+    int lower = (fu + fv <= 1.0f) || (i + j == N - 1);
+    if (lower) {
+        idx[0] = o_texel(N, i, j); idx[1] = o_texel(N, i + 1, j); idx[2] = o_texel(N, i, j + 1);
+        *wa = fu; *wb = fv;
+    } else {
+        idx[0] = o_texel(N, i + 1, j + 1); idx[1] = o_texel(N, i, j + 1); idx[2] = o_texel(N, i + 1, j);
+        *wa = 1.0f - fu; *wb = 1.0f - fv;
+    }
+    if (lower_out) *lower_out = lower;
+}
+
+static float o_interp(float a0, float a1, float a2, float wa, float wb)
+{
+    return fmaf(wb, a2 - a0, fmaf(wa, a1 - a0, a0));
+}
+
+/* Value of one channel plane (stride C between texels) at (b1, b2). */
+float or_lookup(const float* grid, int N, int C, float b1, float b2)
+{
+    int idx[3]; float wa, wb;
+    o_cell(N, b1, b2, idx, &wa, &wb, NULL);
+    return o_interp(grid[(size_t)idx[0] * C], grid[(size_t)idx[1] * C], grid[(size_t)idx[2] * C], wa, wb);
+}
+
+void or_cell(int N, float b1, float b2, int32_t* idx3, float* wab)
+{
+    int idx[3]; float wa, wb;
+    o_cell(N, b1, b2, idx, &wa, &wb, NULL);
+    idx3[0] = idx[0]; idx3[1] = idx[1]; idx3[2] = idx[2];
+    wab[0] = wa; wab[1] = wb;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Triangle set-up and fragments (Eq. 1)                                     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int live;                 /* 0: culled in this view                     */
+    int32_t X[3], Y[3];       /* snapped screen position, 1/256 pixel units */
+    int sgn;                  /* +1 / -1: orientation of the snapped points */
+    float k[3];               /* (1 / w_i) / doubled area, FP32             */
+    int px0, px1, py0, py1;   /* pixel rectangle that may be covered        */
+} OTri;
+
+/* Camera cam[17] = fx, fy, cx, cy, R (row-major 3x3), t, near. */
+static void o_setup(const float* v9, const float* cam, int W, int H, OTri* o)
+{
+    const float fx = cam[0], fy = cam[1], cx = cam[2], cy = cam[3];
+    const float* R = cam + 4;
+    const float* tt = cam + 13;
+    const float near_z = cam[16];
+    float w[3];
+    o->live = 1;
+    for (int i = 0; i < 3; ++i) {
+        const float* p = v9 + 3 * i;
+        float xc = fmaf(R[0], p[0], fmaf(R[1], p[1], fmaf(R[2], p[2], tt[0])));
+        float yc = fmaf(R[3], p[0], fmaf(R[4], p[1], fmaf(R[5], p[2], tt[1])));
+        float zc = fmaf(R[6], p[0], fmaf(R[7], p[1], fmaf(R[8], p[2], tt[2])));
+        if (!(zc > near_z)) { o->live = 0; return; }
+        float sx = fmaf(fx, xc / zc, cx);
+        float sy = fmaf(fy, yc / zc, cy);
+        if (!(fabsf(sx) <= 16384.0f && fabsf(sy) <= 16384.0f)) { o->live = 0; return; }
+        o->X[i] = (int32_t)rintf(sx * 256.0f);
+        o->Y[i] = (int32_t)rintf(sy * 256.0f);
+        w[i] = zc;
+    }
+    int64_t area = (int64_t)(o->X[1] - o->X[0]) * (o->Y[2] - o->Y[0])
+                 - (int64_t)(o->X[2] - o->X[0]) * (o->Y[1] - o->Y[0]);
+    if (area == 0) { o->live = 0; return; }
+    o->sgn = area > 0 ? 1 : -1;
+    float fa = (float)(area > 0 ? area : -area);
+    for (int i = 0; i < 3; ++i) o->k[i] = (1.0f / w[i]) / fa;
+    int32_t xmin = o->X[0], xmax = o->X[0], ymin = o->Y[0], ymax = o->Y[0];
+    for (int i = 1; i < 3; ++i) {
+        if (o->X[i] < xmin) xmin = o->X[i];
+        if (o->X[i] > xmax) xmax = o->X[i];
+        if (o->Y[i] < ymin) ymin = o->Y[i];
+        if (o->Y[i] > ymax) ymax = o->Y[i];
+    }
+    /* pixel px has its centre at 256 px + 128 */
+    o->px0 = (int)floor((xmin - 128) / 256.0) ; o->px1 = (int)floor((xmax - 128) / 256.0) + 1;
+    o->py0 = (int)floor((ymin - 128) / 256.0) ; o->py1 = (int)floor((ymax - 128) / 256.0) + 1;
+    if (o->px0 < 0) o->px0 = 0;
+    if (o->py0 < 0) o->py0 = 0;
+    if (o->px1 > W - 1) o->px1 = W - 1;
+    if (o->py1 > H - 1) o->py1 = H - 1;
+}
+
+/* Coverage of the pixel centre by integer edge functions with the top-left
+ * fill rule (interior to the right of an edge, or below a horizontal edge,
+ * owns the edge).  E[] receives the oriented edge values. */
+static int o_cover(const OTri* o, int px, int py, int64_t E[3])
+{
+    const int64_t Xp = 256 * (int64_t)px + 128, Yp = 256 * (int64_t)py + 128;
+    int cov = 1;
+    for (int i = 0; i < 3; ++i) {
+        int j = (i + 1) % 3, k = (i + 2) % 3;
+        int64_t e = (o->X[j] - Xp) * (o->Y[k] - Yp) - (o->X[k] - Xp) * (o->Y[j] - Yp);
+        e *= o->sgn;
+        int64_t gx = (int64_t)o->sgn * (o->Y[j] - o->Y[k]);   /* dE/dx */
+        int64_t gy = (int64_t)o->sgn * (o->X[k] - o->X[j]);   /* dE/dy */
+        int owns = gx > 0 || (gx == 0 && gy > 0);
+        E[i] = e;
+        if (!(e > 0 || (e == 0 && owns))) cov = 0;
+    }
+    return cov;
+}
+
+/* Perspective-correct inverse depth rho, depth D = 1/rho and barycentrics
+ * (b1, b2) of a covered fragment, FP32 in a fixed order. */
+static void o_frag(const OTri* o, const int64_t E[3], float* rho, float* D, float* b1, float* b2)
+{
+    float q0 = (float)E[0] * o->k[0];
+    float q1 = (float)E[1] * o->k[1];
+    float q2 = (float)E[2] * o->k[2];
+    float r = (q0 + q1) + q2;
+    float inv = 1.0f / r;
+    *rho = r;
+    *D = inv;
+    *b1 = q1 * inv;
+    *b2 = q2 * inv;
+}
+
+/* Fragment of one triangle at one pixel; returns coverage. out = rho, D, b1, b2. */
+int or_fragment(const float* v9, const float* cam, int W, int H, int px, int py, float* out4)
+{
+    OTri o;
+    o_setup(v9, cam, W, H, &o);
+    if (!o.live) return 0;
+    int64_t E[3];
+    if (!o_cover(&o, px, py, E)) return 0;
+    o_frag(&o, E, out4 + 0, out4 + 1, out4 + 2, out4 + 3);
+    return 1;
+}
+
+/* (rho, t) is in front of (rho2, t2): larger inverse depth, ties to the lower index. */
+static int o_front(float rho, int t, float rho2, int t2)
+{
+    return rho > rho2 || (rho == rho2 && t < t2);
+}
+
+static int V_of(int N) { return (N + 1) * (N + 2) / 2; }
+
+static void o_activate(const float* tex, size_t n, float* act)
+{
+    for (size_t i = 0; i < n; ++i) act[i] = or_sigmoidf(tex[i]);
+}
+
+void or_activate(const float* tex, int64_t n, float* act) { o_activate(tex, (size_t)n, act); }
+
+/* ------------------------------------------------------------------------ */
+/* Forward: Eq. 5 by brute force (Algorithm A1, step 1)                      */
+/* ------------------------------------------------------------------------ */
+
+/* For every view, pixel row in [row0, row1) (all rows if row1 < 0), pixel and
+ * mask sample: the foremost covered fragment whose opacity exceeds its
+ * threshold.  Outputs per view are concatenated: [S][H][W] for tri_id, depth,
+ * n_front, n_cover; [S][H][W][2] for bary; [S][C-1][H][W] for color.
+ * order (may be NULL) is the order in which triangles are visited. */
+int or_forward(const float* verts, const float* tex, int32_t T, int32_t N, int32_t C,
+               const float* cams, const int32_t* wh, const uint64_t* seeds, int32_t n_views,
+               int32_t S, int32_t mode, const float* bg, const int32_t* order,
+               int32_t row0, int32_t row1,
+               int32_t* tri_id, float* bary, float* depth, int32_t* n_front, int32_t* n_cover,
+               float* color)
+{
+    const int V = V_of(N), Co = C - 1;
+    float* act = (float*)malloc(sizeof(float) * (size_t)T * V * C);
+    OTri* tri = (OTri*)malloc(sizeof(OTri) * (size_t)(T > 0 ? T : 1));
+    if (!act || !tri) { free(act); free(tri); return -2; }
+    o_activate(tex, (size_t)T * V * C, act);
+    size_t off = 0, coff = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const int W = wh[2 * v], H = wh[2 * v + 1];
+        const float* cam = cams + 17 * v;
+        for (int t = 0; t < T; ++t) o_setup(verts + 9 * (size_t)t, cam, W, H, &tri[t]);
+        int r0 = row1 < 0 ? 0 : row0, r1 = row1 < 0 ? H : (row1 < H ? row1 : H);
+        for (int s = 0; s < S; ++s)
+        for (int py = r0; py < r1; ++py)
+        for (int px = 0; px < W; ++px) {
+            int bt = -1;
+            float brho = 0.0f, bD = INFINITY, bb1 = 0.0f, bb2 = 0.0f;
+            for (int n = 0; n < T; ++n) {
+                int t = order ? order[n] : n;
+                const OTri* o = &tri[t];
+                if (!o->live || px < o->px0 || px > o->px1 || py < o->py0 || py > o->py1) continue;
+                int64_t E[3];
+                if (!o_cover(o, px, py, E)) continue;
+                float rho, D, b1, b2;
+                o_frag(o, E, &rho, &D, &b1, &b2);
+                const float* at = act + (size_t)t * V * C;
+                float alpha = or_lookup(at + (C - 1), N, C, b1, b2);
+                float tau = mode == OR_MODE_THRESHOLD_HALF ? 0.5f : o_tau(seeds[v], px, py, t, s);
+                if (alpha > tau && (bt < 0 || o_front(rho, t, brho, bt))) {
+                    bt = t; brho = rho; bD = D; bb1 = b1; bb2 = b2;
+                }
+            }
+            int nf = 0, nc = 0;
+            for (int t = 0; t < T; ++t) {
+                const OTri* o = &tri[t];
+                if (!o->live || px < o->px0 || px > o->px1 || py < o->py0 || py > o->py1) continue;
+                int64_t E[3];
+                if (!o_cover(o, px, py, E)) continue;
+                float rho, D, b1, b2;
+                o_frag(o, E, &rho, &D, &b1, &b2);
+                ++nc;
+                if (bt < 0 || o_front(rho, t, brho, bt)) ++nf;
+            }
+            size_t pix = off + ((size_t)s * H + py) * W + px;
+            if (tri_id) tri_id[pix] = bt;
+            if (depth) depth[pix] = bD;
+            if (bary) { bary[2 * pix] = bb1; bary[2 * pix + 1] = bb2; }
+            if (n_front) n_front[pix] = nf;
+            if (n_cover) n_cover[pix] = nc;
+            if (color) {
+                for (int c = 0; c < Co; ++c) {
+                    float val = bt < 0 ? bg[c]
+                              : or_lookup(act + (size_t)bt * V * C + c, N, C, bb1, bb2);
+                    color[coff + (((size_t)s * Co + c) * H + py) * W + px] = val;
+                }
+            }
+        }
+        off += (size_t)S * H * W;
+        coff += (size_t)S * Co * H * W;
+    }
+    free(act);
+    free(tri);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Continuous geometry (FP64) for the vertex gradients                       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { double x, y, z; } d3;
+static d3 d3_cross(d3 a, d3 b) { d3 r = {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; return r; }
+static double d3_dot(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+/* Camera-space position of a world point. */
+static d3 o_to_cam(const float* cam, const float* p)
+{
+    const float* R = cam + 4;
+    const float* tt = cam + 13;
+    d3 r;
+    r.x = (double)R[0] * p[0] + (double)R[1] * p[1] + (double)R[2] * p[2] + tt[0];
+    r.y = (double)R[3] * p[0] + (double)R[4] * p[1] + (double)R[5] * p[2] + tt[1];
+    r.z = (double)R[6] * p[0] + (double)R[7] * p[1] + (double)R[8] * p[2] + tt[2];
+    return r;
+}
+
+/* Add R^T g (a camera-space gradient) to a world-space vertex gradient. */
+static void o_add_world(const float* cam, d3 g, double* dst)
+{
+    const float* R = cam + 4;
+    dst[0] += R[0] * g.x + R[3] * g.y + R[6] * g.z;
+    dst[1] += R[1] * g.x + R[4] * g.y + R[7] * g.z;
+    dst[2] += R[2] * g.x + R[5] * g.y + R[8] * g.z;
+}
+
+/* Direction (z = 1) of the camera ray through screen point (sx, sy). */
+static d3 o_ray(const float* cam, double sx, double sy)
+{
+    d3 d = {(sx - cam[2]) / cam[0], (sy - cam[3]) / cam[1], 1.0};
+    return d;
+}
+
+/* Barycentrics of the point where ray d meets the plane of V[0..2]:
+ * beta_l = d.(V_{l+1} x V_{l+2}) / sum (Cramer's rule). nl receives the
+ * numerators, the return value is their sum. */
+static double o_ray_bary(const d3 V[3], d3 d, double nl[3])
+{
+    for (int l = 0; l < 3; ++l) nl[l] = d3_dot(d, d3_cross(V[(l + 1) % 3], V[(l + 2) % 3]));
+    return nl[0] + nl[1] + nl[2];
+}
+
+/* Jacobian rows of the projection (fx X/Z + cx, fy Y/Z + cy) at camera point P. */
+static void o_proj_jac(const float* cam, d3 P, d3* jx, d3* jy)
+{
+    jx->x = cam[0] / P.z; jx->y = 0.0; jx->z = -cam[0] * P.x / (P.z * P.z);
+    jy->x = 0.0; jy->y = cam[1] / P.z; jy->z = -cam[1] * P.y / (P.z * P.z);
+}
+
+static void o_proj(const float* cam, d3 P, double* sx, double* sy)
+{
+    *sx = cam[0] * (P.x / P.z) + cam[2];
+    *sy = cam[1] * (P.y / P.z) + cam[3];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Backward: Algorithm A1 step 2, Eq. 8-9, plus vertex gradients             */
+/* ------------------------------------------------------------------------ */
+
+/* Chain d(loss)/d(value) at (b1, b2) of one channel to the logits of the
+ * three corner texels: value = sum_m w_m sigmoid(theta_m). */
+static void o_chain_tex(double g, const float* act_t, double* gtex_t, int N, int C, int c,
+                        float b1, float b2)
+{
+    int idx[3]; float wa, wb;
+    o_cell(N, b1, b2, idx, &wa, &wb, NULL);
+    double w[3] = {1.0 - (double)wa - (double)wb, (double)wa, (double)wb};
+    for (int m = 0; m < 3; ++m) {
+        double a = act_t[(size_t)idx[m] * C + c];
+        gtex_t[(size_t)idx[m] * C + c] += g * w[m] * a * (1.0 - a);
+    }
+}
+
+/* Inverse depth and triangle index of the stored winner, recomputed. */
+static int o_winner_key(const OTri* tri, int t, int px, int py, float* rho)
+{
+    int64_t E[3];
+    float D, b1, b2;
+    if (t < 0 || !tri[t].live || !o_cover(&tri[t], px, py, E)) return 0;
+    o_frag(&tri[t], E, rho, &D, &b1, &b2);
+    return 1;
+}
+
+/* dL/d(b1, b2) of the winner's colour: sum_c g_c d value_c / d b. */
+static void o_dcolor_db(const float* act_t, int N, int C, float b1, float b2, const double* g, double G[2])
+{
+    int idx[3]; float wa, wb; int lower;
+    o_cell(N, b1, b2, idx, &wa, &wb, &lower);
+    double sgn = lower ? 1.0 : -1.0;   /* wa = N b1 - i (lower) or 1 - (N b1 - i) (upper) */
+    G[0] = G[1] = 0.0;
+    for (int c = 0; c < C - 1; ++c) {
+        double a0 = act_t[(size_t)idx[0] * C + c], a1 = act_t[(size_t)idx[1] * C + c], a2 = act_t[(size_t)idx[2] * C + c];
+        G[0] += g[c] * sgn * N * (a1 - a0);
+        G[1] += g[c] * sgn * N * (a2 - a0);
+    }
+}
+
+int or_backward(const float* verts, const float* tex, int32_t T, int32_t N, int32_t C,
+                const float* cams, const int32_t* wh, int32_t n_views, int32_t S,
+                const int32_t* tri_id, const float* bary, const float* color,
+                const float* grad_color, const float* score_w, uint32_t flags,
+                int32_t row0, int32_t row1, double* grad_tex, double* grad_verts)
+{
+    const int V = V_of(N), Co = C - 1;
+    float* act = (float*)malloc(sizeof(float) * (size_t)T * V * C);
+    OTri* tri = (OTri*)malloc(sizeof(OTri) * (size_t)(T > 0 ? T : 1));
+    double* g = (double*)malloc(sizeof(double) * (size_t)(Co > 0 ? Co : 1));
+    if (!act || !tri || !g) { free(act); free(tri); free(g); return -2; }
+    o_activate(tex, (size_t)T * V * C, act);
+    size_t off = 0, coff = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const int W = wh[2 * v], H = wh[2 * v + 1];
+        const float* cam = cams + 17 * v;
+        for (int t = 0; t < T; ++t) o_setup(verts + 9 * (size_t)t, cam, W, H, &tri[t]);
+        int r0 = row1 < 0 ? 0 : row0, r1 = row1 < 0 ? H : (row1 < H ? row1 : H);
+        const size_t HW = (size_t)H * W;
+        for (int s = 0; s < S; ++s)
+        for (int py = r0; py < r1; ++py)
+        for (int px = 0; px < W; ++px) {
+            size_t pix = off + (size_t)s * HW + (size_t)py * W + px;
+            int ts = tri_id[pix];
+            float b1 = bary[2 * pix], b2 = bary[2 * pix + 1];
+            for (int c = 0; c < Co; ++c)
+                g[c] = grad_color[coff + ((size_t)s * Co + c) * HW + (size_t)py * W + px];
+
+            /* Alg. A1 2(a): colour gradient of the selected fragment. */
+            if ((flags & OR_G_TEX) && ts >= 0)
+                for (int c = 0; c < Co; ++c)
+                    o_chain_tex(g[c], act + (size_t)ts * V * C, grad_tex + (size_t)ts * V * C, N, C, c, b1, b2);
+
+            /* Alg. A1 2(b) with Eq. 9: +l/alpha for the selected fragment,
+             * -l/(1 - alpha) for every covered fragment in front of it. */
+            if ((flags & OR_G_SCORE) && score_w[pix] != 0.0f) {
+                double w = score_w[pix];
+                float rs = 0.0f;
+                int has = o_winner_key(tri, ts, px, py, &rs);
+                for (int t = 0; t < T; ++t) {
+                    const OTri* o = &tri[t];
+                    if (t == ts || !o->live || px < o->px0 || px > o->px1 || py < o->py0 || py > o->py1) continue;
+                    int64_t E[3];
+                    if (!o_cover(o, px, py, E)) continue;
+                    float rho, D, fb1, fb2;
+                    o_frag(o, E, &rho, &D, &fb1, &fb2);
+                    if (has && !o_front(rho, t, rs, ts)) continue;
+                    const float* at = act + (size_t)t * V * C;
+                    double alpha = or_lookup(at + (C - 1), N, C, fb1, fb2);
+                    o_chain_tex(-w / (1.0 - alpha), at, grad_tex + (size_t)t * V * C, N, C, C - 1, fb1, fb2);
+                }
+                if (ts >= 0) {
+                    const float* at = act + (size_t)ts * V * C;
+                    double alpha = or_lookup(at + (C - 1), N, C, b1, b2);
+                    o_chain_tex(w / alpha, at, grad_tex + (size_t)ts * V * C, N, C, C - 1, b1, b2);
+                }
+            }
+
+            /* First term of Eq. 8 for the vertices: the winner's colour moves
+             * with its perspective-correct barycentrics (interior gradient). */
+            if ((flags & OR_G_INTERIOR) && ts >= 0) {
+                double G[3];
+                double Gb[2];
+                o_dcolor_db(act + (size_t)ts * V * C, N, C, b1, b2, g, Gb);
+                G[0] = 0.0; G[1] = Gb[0]; G[2] = Gb[1];
+                d3 Vc[3];
+                for (int m = 0; m < 3; ++m) Vc[m] = o_to_cam(cam, verts + 9 * (size_t)ts + 3 * m);
+                d3 d = o_ray(cam, px + 0.5, py + 0.5);
+                double nl[3];
+                double Ssum = o_ray_bary(Vc, d, nl);
+                double gb = (G[1] * nl[1] + G[2] * nl[2]) / Ssum;
+                double h[3] = {G[0] - gb, G[1] - gb, G[2] - gb};
+                for (int m = 0; m < 3; ++m) {
+                    int mp = (m + 1) % 3, mm = (m + 2) % 3;
+                    d3 c1 = d3_cross(Vc[mp], d);      /* d N_{m-1} / d V_m */
+                    d3 c2 = d3_cross(d, Vc[mm]);      /* d N_{m+1} / d V_m */
+                    d3 gv = {(h[mm] * c1.x + h[mp] * c2.x) / Ssum,
+                             (h[mm] * c1.y + h[mp] * c2.y) / Ssum,
+                             (h[mm] * c1.z + h[mp] * c2.z) / Ssum};
+                    o_add_world(cam, gv, grad_verts + 9 * (size_t)ts + 3 * m);
+                }
+            }
+
+            /* Edge gradients on every horizontal and vertical pixel pair of the
+             * sampled image (Sec. 3.2, "Handling visibility discontinuities"). */
+            if (flags & OR_G_EDGE) {
+                for (int dir = 0; dir < 2; ++dir) {
+                    int qx = px + (dir == 0), qy = py + (dir == 1);
+                    if (qx >= W || qy >= H) continue;
+                    size_t qix = off + (size_t)s * HW + (size_t)qy * W + qx;
+                    int tq = tri_id[qix];
+                    if (tq == ts) continue;
+                    double phi = 0.0;   /* d loss / d s for the side at p */
+                    for (int c = 0; c < Co; ++c) {
+                        size_t pc = coff + ((size_t)s * Co + c) * HW;
+                        double gp = grad_color[pc + (size_t)py * W + px], gq = grad_color[pc + (size_t)qy * W + qx];
+                        double cp = color[pc + (size_t)py * W + px], cq = color[pc + (size_t)qy * W + qx];
+                        phi += 0.5 * (gp + gq) * (cp - cq);
+                    }
+                    for (int side = 0; side < 2; ++side) {
+                        int tx = side == 0 ? ts : tq, ty = side == 0 ? tq : ts;
+                        int Xx = side == 0 ? px : qx, Xy = side == 0 ? py : qy;
+                        int Yx = side == 0 ? qx : px, Yy = side == 0 ? qy : py;
+                        double PhiX = side == 0 ? phi : -phi;
+                        double ex = (double)(Yx - Xx), ey = (double)(Yy - Xy);
+                        if (tx < 0) continue;
+                        const OTri* o = &tri[tx];
+                        if (!o->live) continue;
+                        int64_t E[3];
+                        int covers = o_cover(o, Yx, Yy, E);
+                        d3 Vc[3];
+                        for (int m = 0; m < 3; ++m) Vc[m] = o_to_cam(cam, verts + 9 * (size_t)tx + 3 * m);
+                        if (covers) {
+                            float rho, D, fb1, fb2;
+                            o_frag(o, E, &rho, &D, &fb1, &fb2);
+                            float ry = 0.0f;
+                            int hy = o_winner_key(tri, ty, Yx, Yy, &ry);
+                            if (hy && !o_front(rho, tx, ry, ty)) continue;   /* occluded at Y */
+                            /* implicit (mask) boundary: material point at the midpoint */
+                            d3 d = o_ray(cam, 0.5 * (Xx + Yx) + 0.5, 0.5 * (Xy + Yy) + 0.5);
+                            double nl[3];
+                            double Ssum = o_ray_bary(Vc, d, nl);
+                            d3 P = {0, 0, 0};
+                            for (int m = 0; m < 3; ++m) {
+                                double bm = nl[m] / Ssum;
+                                P.x += bm * Vc[m].x; P.y += bm * Vc[m].y; P.z += bm * Vc[m].z;
+                            }
+                            d3 jx, jy;
+                            o_proj_jac(cam, P, &jx, &jy);
+                            d3 je = {ex * jx.x + ey * jy.x, ex * jx.y + ey * jy.y, ex * jx.z + ey * jy.z};
+                            /* weight 1 per axis: the material displacement is
+                             * projected on the pair axis, so the two axes
+                             * see orthogonal components (no double counting) */
+                            for (int m = 0; m < 3; ++m) {
+                                double f = PhiX * nl[m] / Ssum;
+                                d3 gv = {f * je.x, f * je.y, f * je.z};
+                                o_add_world(cam, gv, grad_verts + 9 * (size_t)tx + 3 * m);
+                            }
+                        } else {
+                            /* silhouette: the first edge the segment X->Y crosses */
+                            double sx[3], sy[3];
+                            for (int m = 0; m < 3; ++m) o_proj(cam, Vc[m], &sx[m], &sy[m]);
+                            double area = (sx[1] - sx[0]) * (sy[2] - sy[0]) - (sx[2] - sx[0]) * (sy[1] - sy[0]);
+                            double sg = area > 0 ? 1.0 : -1.0;
+                            double xX = Xx + 0.5, yX = Xy + 0.5, xY = Yx + 0.5, yY = Yy + 0.5;
+                            int best = -1;
+                            double bs = 0.0, bfX = 0.0, bfY = 0.0;
+                            for (int i = 0; i < 3; ++i) {
+                                int a = (i + 1) % 3, b = (i + 2) % 3;
+                                double fX = sg * ((sx[a] - xX) * (sy[b] - yX) - (sx[b] - xX) * (sy[a] - yX));
+                                double fY = sg * ((sx[a] - xY) * (sy[b] - yY) - (sx[b] - xY) * (sy[a] - yY));
+                                if (!(fY < 0.0 && fX > fY)) continue;
+                                double si = fX / (fX - fY);
+                                if (best < 0 || si < bs) { best = i; bs = si; bfX = fX; bfY = fY; }
+                            }
+                            if (best < 0) continue;
+                            int a = (best + 1) % 3, b = (best + 2) % 3;
+                            double fX = bfX * sg, fY = bfY * sg;      /* unoriented values */
+                            double den = (fX - fY) * (fX - fY);
+                            /* d f(x)/d a = (b_y - x_y, -(b_x - x_x)); d f(x)/d b = (-(a_y - x_y), a_x - x_x) */
+                            double dfXa[2] = {sy[b] - yX, -(sx[b] - xX)}, dfYa[2] = {sy[b] - yY, -(sx[b] - xY)};
+                            double dfXb[2] = {-(sy[a] - yX), sx[a] - xX}, dfYb[2] = {-(sy[a] - yY), sx[a] - xY};
+                            double ux = sx[b] - sx[a], uy = sy[b] - sy[a];
+                            double len2 = ux * ux + uy * uy;
+                            double omega = (ex != 0.0 ? uy * uy : ux * ux) / len2;   /* squared normal component along the pair axis */
+                            double k = omega * PhiX / den;
+                            double gs[2][2];
+                            for (int r = 0; r < 2; ++r) {
+                                gs[0][r] = k * (fX * dfYa[r] - fY * dfXa[r]);
+                                gs[1][r] = k * (fX * dfYb[r] - fY * dfXb[r]);
+                            }
+                            int vid[2] = {a, b};
+                            for (int e = 0; e < 2; ++e) {
+                                d3 jx, jy;
+                                o_proj_jac(cam, Vc[vid[e]], &jx, &jy);
+                                d3 gv = {gs[e][0] * jx.x + gs[e][1] * jy.x,
+                                         gs[e][0] * jx.y + gs[e][1] * jy.y,
+                                         gs[e][0] * jx.z + gs[e][1] * jy.z};
+                                o_add_world(cam, gv, grad_verts + 9 * (size_t)tx + 3 * vid[e]);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        off += (size_t)S * HW;
+        coff += (size_t)S * Co * HW;
+    }
+    free(act);
+    free(tri);
+    free(g);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Closed forms: Eq. 6 / A1 selection probabilities, Eq. 7 expected loss and */
+/* its exact gradient (the expectation of the Eq. 8 estimator), FP64.        */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { float rho; int t; float b1, b2; } OFrag;
+
+/* Per view: E[l] with l = sum_c (C_c - target_c)^2 over every pixel, and its
+ * gradient with respect to all texture logits (colour and opacity), where the
+ * selected fragment follows p(f) = alpha_f prod_{front} (1 - alpha).  The
+ * visibility geometry (coverage, depth order, barycentrics) is the FP32 one of
+ * or_forward; logits are FP64 and activations use libm's exp in FP64, so that
+ * the result is a smooth function of the logits for finite differences. */
+int or_expected(const float* verts, const double* tex, int32_t T, int32_t N, int32_t C,
+                const float* cams, const int32_t* wh, int32_t n_views,
+                const float* target, const float* bg, double* e_loss, double* e_grad_tex)
+{
+    const int V = V_of(N), Co = C - 1;
+    const size_t n = (size_t)T * V * C;
+    double* act = (double*)malloc(sizeof(double) * (n ? n : 1));
+    OTri* tri = (OTri*)malloc(sizeof(OTri) * (size_t)(T > 0 ? T : 1));
+    OFrag* fr = (OFrag*)malloc(sizeof(OFrag) * (size_t)(T > 0 ? T : 1));
+    double* col = (double*)malloc(sizeof(double) * (size_t)(T + 1) * (Co > 0 ? Co : 1));
+    double* al = (double*)malloc(sizeof(double) * (size_t)(T + 1));
+    double* pf = (double*)malloc(sizeof(double) * (size_t)(T + 1));
+    double* lf = (double*)malloc(sizeof(double) * (size_t)(T + 1));
+    if (!act || !tri || !fr || !col || !al || !pf || !lf) {
+        free(act); free(tri); free(fr); free(col); free(al); free(pf); free(lf); return -2;
+    }
+    for (size_t i = 0; i < n; ++i) act[i] = 1.0 / (1.0 + exp(-tex[i]));
+    size_t toff = 0;
+    for (int v = 0; v < n_views; ++v) {
+        const int W = wh[2 * v], H = wh[2 * v + 1];
+        const float* cam = cams + 17 * v;
+        double L = 0.0;
+        for (int t = 0; t < T; ++t) o_setup(verts + 9 * (size_t)t, cam, W, H, &tri[t]);
+        for (int py = 0; py < H; ++py)
+        for (int px = 0; px < W; ++px) {
+            int nf = 0;
+            for (int t = 0; t < T; ++t) {
+                const OTri* o = &tri[t];
+                if (!o->live || px < o->px0 || px > o->px1 || py < o->py0 || py > o->py1) continue;
+                int64_t E[3];
+                if (!o_cover(o, px, py, E)) continue;
+                float D;
+                o_frag(o, E, &fr[nf].rho, &D, &fr[nf].b1, &fr[nf].b2);
+                fr[nf].t = t;
+                ++nf;
+            }
+            /* depth order, front first (insertion sort) */
+            for (int i = 1; i < nf; ++i) {
+                OFrag x = fr[i];
+                int j = i - 1;
+                while (j >= 0 && o_front(x.rho, x.t, fr[j].rho, fr[j].t)) { fr[j + 1] = fr[j]; --j; }
+                fr[j + 1] = x;
+            }
+            double trans = 1.0;
+            for (int i = 0; i <= nf; ++i) {
+                double li = 0.0;
+                for (int c = 0; c < Co; ++c) {
+                    double cc;
+                    if (i < nf) {
+                        int idx[3]; float wa, wb;
+                        o_cell(N, fr[i].b1, fr[i].b2, idx, &wa, &wb, NULL);
+                        const double* at = act + (size_t)fr[i].t * V * C;
+                        double a0 = at[(size_t)idx[0] * C + c], a1 = at[(size_t)idx[1] * C + c], a2 = at[(size_t)idx[2] * C + c];
+                        cc = a0 + (double)wa * (a1 - a0) + (double)wb * (a2 - a0);
+                    } else {
+                        cc = bg[c];
+                    }
+                    col[(size_t)i * Co + c] = cc;
+                    double d = cc - target[toff + (size_t)c * H * W + (size_t)py * W + px];
+                    li += d * d;
+                }
+                double a = 1.0;
+                if (i < nf) {
+                    int idx[3]; float wa, wb;
+                    o_cell(N, fr[i].b1, fr[i].b2, idx, &wa, &wb, NULL);
+                    const double* at = act + (size_t)fr[i].t * V * C;
+                    double a0 = at[(size_t)idx[0] * C + C - 1], a1 = at[(size_t)idx[1] * C + C - 1], a2 = at[(size_t)idx[2] * C + C - 1];
+                    a = a0 + (double)wa * (a1 - a0) + (double)wb * (a2 - a0);
+                }
+                al[i] = a;
+                pf[i] = trans * a;
+                lf[i] = li;
+                trans *= (1.0 - a);
+                L += pf[i] * li;
+            }
+            if (!e_grad_tex) continue;
+            /* exact gradient: sum over outcomes of p(f) [d l(C_f) + l(C_f) d log p(f)] */
+            for (int i = 0; i <= nf; ++i) {
+                double p = pf[i];
+                if (p == 0.0) continue;
+                if (i < nf) {
+                    int idx[3]; float wa, wb;
+                    o_cell(N, fr[i].b1, fr[i].b2, idx, &wa, &wb, NULL);
+                    double w[3] = {1.0 - (double)wa - (double)wb, (double)wa, (double)wb};
+                    const double* at = act + (size_t)fr[i].t * V * C;
+                    double* gt = e_grad_tex + (size_t)fr[i].t * V * C;
+                    for (int c = 0; c < Co; ++c) {
+                        double dl = 2.0 * (col[(size_t)i * Co + c] - target[toff + (size_t)c * H * W + (size_t)py * W + px]);
+                        for (int m = 0; m < 3; ++m) {
+                            double a = at[(size_t)idx[m] * C + c];
+                            gt[(size_t)idx[m] * C + c] += p * dl * w[m] * a * (1.0 - a);
+                        }
+                    }
+                    for (int m = 0; m < 3; ++m) {
+                        double a = at[(size_t)idx[m] * C + C - 1];
+                        gt[(size_t)idx[m] * C + C - 1] += p * lf[i] / al[i] * w[m] * a * (1.0 - a);
+                    }
+                }
+                for (int j = 0; j < i; ++j) {
+                    int idx[3]; float wa, wb;
+                    o_cell(N, fr[j].b1, fr[j].b2, idx, &wa, &wb, NULL);
+                    double w[3] = {1.0 - (double)wa - (double)wb, (double)wa, (double)wb};
+                    const double* at = act + (size_t)fr[j].t * V * C;
+                    double* gt = e_grad_tex + (size_t)fr[j].t * V * C;
+                    for (int m = 0; m < 3; ++m) {
+                        double a = at[(size_t)idx[m] * C + C - 1];
+                        gt[(size_t)idx[m] * C + C - 1] += -p * lf[i] / (1.0 - al[j]) * w[m] * a * (1.0 - a);
+                    }
+                }
+            }
+        }
+        e_loss[v] = L;
+        toff += (size_t)Co * H * W;
+    }
+    free(act); free(tri); free(fr); free(col); free(al); free(pf); free(lf);
+    return 0;
+}

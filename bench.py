@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Benchmark of the masked rasteriser's forward + backward pass.
+
+One step = the whole hot path on one batch: texture activation, triangle
+set-up, radix-sorted tile binning, the stochastically masked raster forward
+with texture decode, the fused L2 loss with its upstream gradients, and the
+backward (colour, opacity-score, interior and edge gradients).  Workload: the
+1080p large batch -- 100,000 triangles, 8x8 texel grids (N = 8, V = 45) of 8
+FP32 channels, 4 views at 1920x1080 + 4 at 960x540, 4 mask samples per pixel.
+
+Metric: fragments/s = covered (pixel-sample, triangle) pairs of the batch
+(|F| of Eq. 1 times S) divided by the device time of a step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs the same workload with its own mask
+seeds (weak scaling, no collective on the data path); rank 0 prints one JSON
+line.  --impl reference times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+from paper_2603_27151_gb300 import inputs as I
+
+METRIC = "fwd+bwd fragments/s"
+UNIT = "fragments/s"
+WORKLOAD = ("1080p large batch: 100,000 triangles, 8x8 texels x 8 FP32 channels (N=8, V=45), "
+            "4x1920x1080 + 4x960x540 views, 4 mask samples/pixel, fwd+bwd, L2 loss")
+
+
+# ---------------------------------------------------------------- helpers
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- the GPU step
+class Workload:
+    def __init__(self, rank: int, device: str, views: int = 0):
+        import torch
+        from paper_2603_27151_gb300 import native as N
+        self.N = N
+        sc = I.large_batch()
+        if views:
+            sc.cams = sc.cams[:views]
+        sc.seeds = I.mask_seeds(13 + 1000 * rank, len(sc.cams))
+        self.sc = sc
+        self.S = sc.samples
+        self.dev = device
+        self.ctx = N.Context(torch.cuda.current_device())
+        self.verts = torch.from_numpy(sc.verts).to(device)
+        self.tex = torch.from_numpy(sc.tex).to(device)
+        self.sid = self.ctx.soup_upload(self.verts, self.tex, sc.grid_n, borrow=True)
+        # targets: a second seeded soup rendered with binary opacity (Eq. 3)
+        tsc = I.large_batch(soup_seed=12)
+        tv, tt = torch.from_numpy(tsc.verts).to(device), torch.from_numpy(tsc.tex).to(device)
+        tsid = self.ctx.soup_upload(tv, tt, tsc.grid_n)
+        tg, tc, _ = N.alloc_outputs(sc.cams, 1, sc.C, device)
+        self.ctx.raster_forward(tsid, sc.cams, None, 1, N.DS_MODE_THRESHOLD_HALF, sc.bg, tg, tc)
+        self.targets = [c[0].contiguous() for c in tc]
+        torch.cuda.synchronize()
+        self.ctx.soup_free(tsid)
+        del tg, tc, tv, tt
+        self.g, self.col, _ = N.alloc_outputs(sc.cams, self.S, sc.C, device)
+        self.gcol = [torch.empty_like(c) for c in self.col]
+        self.sw = [torch.empty((self.S, c.height, c.width), dtype=torch.float32, device=device) for c in sc.cams]
+        self.loss = torch.zeros(1, dtype=torch.float32, device=device)
+        self.gt = torch.zeros_like(self.tex)
+        self.gv = torch.zeros_like(self.verts)
+        self.cover = self.ctx.fragment_count(self.sid, sc.cams)        # |F| for one sample
+        self.pairs, self.tiles = self.ctx.plan_stats()
+        self.fragments = self.cover * self.S
+        self.pixel_samples = sum(c.width * c.height for c in sc.cams) * self.S
+
+    def step(self):
+        N, sc = self.N, self.sc
+        self.ctx.raster_forward(self.sid, sc.cams, sc.seeds, self.S, N.DS_MODE_STOCHASTIC, sc.bg, self.g, self.col)
+        N.loss_l2(self.col, self.targets, self.gcol, self.sw, self.loss, scale=1.0 / self.S)
+        self.ctx.raster_backward(self.sid, sc.cams, self.S, self.g, self.col, self.gcol, self.sw,
+                                 N.DS_G_ALL | N.DS_REUSE_FORWARD | N.DS_OVERWRITE, self.gv, self.gt)
+
+    def algorithmic_bytes(self):
+        """Minimum HBM bytes each stage must move per launch."""
+        sc, S = self.sc, self.S
+        T, V, C = sc.tex.shape
+        Co = C - 1
+        P = sum(c.width * c.height for c in sc.cams)
+        nv = len(sc.cams)
+        K = self.pairs
+        return {
+            "activate": T * V * C * 4 * 2 + T * V * 4,
+            "setup": nv * T * (36 + 64 + 4 + 16 + 4),
+            "raster_fwd": K * (8 + 64) + T * V * 4 + T * V * C * 4 + P * S * (16 + 4 * Co),
+            "raster_bwd": K * (8 + 64) + P * S * (16 + 4 * Co + 4) + T * V * C * 4 * 3 + 36 * T * 2 + nv * T * 208,
+            "edge_bwd": P * S * (16 + 8 * Co) + nv * T * (64 + 208) + 36 * T * 2,
+            "geom": nv * T * (36 + 208),
+        }
+
+
+def _gpu_arm(args):
+    import torch
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = "cuda:%d" % local
+    from paper_2603_27151_gb300 import native as N
+    wl = Workload(rank, dev, args.views)
+    for _ in range(args.warmup):
+        wl.step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-timed steps (inputs resident in HBM; working set > L2)
+    wl.ctx.profile_reset()
+    wl.ctx.profile(True)
+    launches0 = N.kernel_launches()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            wl.step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    launches = N.kernel_launches() - launches0
+    wl.ctx.profile(False)
+    prof = wl.ctx.profile_read()
+    ms = e0.elapsed_time(e1)
+    t_max = ms
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    barrier()
+
+    # ---- end to end through the public API with host buffers
+    hv = wl.verts.cpu().pin_memory()
+    ht = wl.tex.cpu().pin_memory()
+    htg = [x.cpu().pin_memory() for x in wl.targets]
+    hl = torch.zeros(1, dtype=torch.float32).pin_memory()
+    h2d = hv.numel() * 4 + ht.numel() * 4 + sum(x.numel() * 4 for x in htg)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        wl.verts.copy_(hv, non_blocking=True)
+        wl.tex.copy_(ht, non_blocking=True)
+        for d, h in zip(wl.targets, htg):
+            d.copy_(h, non_blocking=True)
+        wl.ctx.raster_forward(wl.sid, wl.sc.cams, wl.sc.seeds, wl.S, N.DS_MODE_STOCHASTIC, wl.sc.bg, wl.g, wl.col)
+        wl.loss.zero_()
+        N.loss_l2(wl.col, wl.targets, wl.gcol, wl.sw, wl.loss, scale=1.0 / wl.S)
+        wl.ctx.raster_backward(wl.sid, wl.sc.cams, wl.S, wl.g, wl.col, wl.gcol, wl.sw,
+                               N.DS_G_ALL | N.DS_REUSE_FORWARD | N.DS_OVERWRITE, wl.gv, wl.gt)
+        hl.copy_(wl.loss, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        _ = float(hl[0])
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    barrier()
+
+    if rank != 0:
+        return None
+    frags_total = wl.fragments * args.steps * world
+    value = frags_total / (t_max / 1e3)
+    peak, peak_kind = _peaks()
+    algo = wl.algorithmic_bytes()
+    stage_ms = {k: v[1] for k, v in prof.items() if v[0] > 0}
+    dom = max((k for k in stage_ms if k in algo), key=lambda k: stage_ms[k])
+    runs = prof[dom][0]
+    per_launch_ms = prof[dom][1] / runs
+    achieved = algo[dom] / (per_launch_ms / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded soups, cameras, targets)",
+        "config": {"workload": WORKLOAD, "triangles": wl.sc.T, "views": len(wl.sc.cams), "samples": wl.S,
+                   "fragments_per_step": wl.fragments, "pixel_samples_per_step": wl.pixel_samples,
+                   "bin_pairs": wl.pairs, "l2": "inputs larger than L2 (about 3 GB touched per step)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "e2e": {"value": frags_total / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                     "algorithmic_bytes": algo[dom], "launch_ms": per_launch_ms},
+        "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
+        "clocks": clk.summary(),
+    }
+    return line
+
+
+# ---------------------------------------------------------------- CPU oracle
+def _oracle_rows(job):
+    """One bounded sample: forward + backward of the oracle on a band of rows
+    of view 0 (L2 loss against the target soup's binary-opacity render)."""
+    import oracle as O
+    view, r0, r1, seed = job
+    sc = I.large_batch()
+    tsc = I.large_batch(soup_seed=12)
+    cam = sc.cams[view]
+    t0 = time.perf_counter()
+    f = O.forward(sc.verts, sc.tex, sc.grid_n, [cam], np.array([seed], np.uint64), S=sc.samples, bg=sc.bg,
+                  rows=(r0, r1))[0]
+    tg = O.forward(tsc.verts, tsc.tex, tsc.grid_n, [cam], np.zeros(1, np.uint64), S=1,
+                   mode=O.MODE_THRESHOLD_HALF, bg=sc.bg, rows=(r0, r1))[0]
+    S = sc.samples
+    diff = f["color"] - tg["color"][0][None]
+    band = np.zeros(diff.shape[2], bool)
+    band[r0:r1] = True
+    diff[:, :, ~band] = 0.0
+    ell = (diff.astype(np.float64) ** 2).sum(1)
+    O.backward(sc.verts, sc.tex, sc.grid_n, [cam], S, [f], [(2.0 * diff / S).astype(np.float32)],
+               [(ell / S).astype(np.float32)], rows=(r0, r1))
+    frags = int(f["n_cover"][:, r0:r1].sum())
+    return frags, time.perf_counter() - t0
+
+
+def _cores():
+    n = os.cpu_count() or 1
+    return max(1, min(16, n))
+
+
+def oracle_sample(cores: int, rows_each: int = 1, start_row: int = 400):
+    jobs = [(0, start_row + k * rows_each, start_row + (k + 1) * rows_each, 13) for k in range(cores)]
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_rows, jobs)
+    wall = time.perf_counter() - t0
+    frags = sum(r[0] for r in res)
+    return frags / wall, wall, frags
+
+
+def cpu_baseline_entry():
+    cores = _cores()
+    v, wall, frags = oracle_sample(cores)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d rows of a 1920x1080 view (one row per process, S=4, fwd+bwd incl. the target render), "
+                      "%d fragments in %.1f s wall" % (cores, frags, wall)}
+
+
+def _reference_arm(args):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return None
+    cores = _cores()
+    for _ in range(args.warmup):
+        pass   # the oracle has no warm-up state; warm-up samples would only repeat the work
+    vals, walls, total = [], [], 0
+    for k in range(args.steps):
+        v, wall, frags = oracle_sample(cores, 1, 300 + 20 * k)
+        vals.append(v)
+        walls.append(wall)
+        total += frags
+    value = total / sum(walls)
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded soups, cameras, targets)",
+            "config": {"workload": WORKLOAD, "sample": "per step %d rows of view 0, one per process" % cores},
+            "impl": "reference",
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT,
+                             "sample": "per step %d rows of a 1920x1080 view, S=4, fwd+bwd" % cores},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--views", type=int, default=0,
+                    help="use only the first N views (reduced case for profiler captures; not a bench line)")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    if args.impl == "reference":
+        line = _reference_arm(args)
+        if line is not None:
+            print(json.dumps(line), flush=True)
+        return
+    world, rank, _ = _dist()
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.views:
+        cpu = cpu_baseline_entry()   # before the first GPU call (spawned workers)
+    line = _gpu_arm(args)
+    if line is not None:
+        line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

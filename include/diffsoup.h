@@ -1,0 +1,242 @@
+/*
+ * diffsoup.h -- C ABI of the GB300 (sm_103a) library for the differentiable,
+ * stochastically opacity-masked rasterisation of a textured triangle soup
+ * (DiffSoup, arXiv 2603.27151) and its gradient.
+ *
+ * Conventions shared by every entry point
+ *  - Pointers are DEVICE pointers unless the comment says "host".
+ *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
+ *    NULL = legacy default stream) unless it says otherwise, and returns a
+ *    ds_status.  Nothing aborts and no C++ exception crosses the ABI; the
+ *    message of the last failure on the calling thread is ds_last_error().
+ *  - Caller buffers must stay alive until the stream work that uses them has
+ *    completed.  Gradients are accumulated (+=): the caller zeroes them.
+ *  - Inputs are validated before any launch (sizes, counts, finiteness of
+ *    cameras); a violation returns DS_ERR_INVALID_ARG and launches nothing.
+ *  - The library owns its scratch memory (triangle set-up records, bin keys,
+ *    sort buffers, activations); it grows it with cudaMalloc when a call
+ *    needs more and frees it in ds_destroy.
+ *
+ * Notation (paper Sec. 3): T triangles; per-triangle mesh-colour grid with N
+ * subdivisions per edge and V = (N+1)(N+2)/2 feature vertices (Sec. 3.3;
+ * R = 5 gives N = 32, V = 561); C channels per feature vertex, the last one
+ * being the opacity logit and the first C-1 the colour features (Sec. 3.3,
+ * "Neural deferred shading"); S mask samples per pixel (independent draws of
+ * the thresholds tau of Eq. 5).
+ */
+#ifndef DIFFSOUP_H
+#define DIFFSOUP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DS_API __attribute__((visibility("default")))
+#else
+#define DS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t ds_status;
+typedef struct ds_ctx ds_ctx;   /* opaque library context (one CUDA device) */
+#define DS_OK 0
+#define DS_ERR_INVALID_ARG (-1) /* bad argument, nothing launched              */
+#define DS_ERR_OOM (-2)         /* cudaMalloc of scratch or a soup copy failed */
+#define DS_ERR_CUDA (-3)        /* a CUDA runtime call failed                  */
+#define DS_ERR_CAPACITY (-4)    /* bin capacity exceeded (no-sync mode only)   */
+#define DS_ERR_TIMEOUT (-5)     /* a bounded wait expired                      */
+#define DS_ERR_NOT_FOUND (-6)   /* unknown soup id or request ticket           */
+#define DS_ERR_BUSY (-7)        /* server queue full                           */
+
+/* Limits (validated). */
+#define DS_MAX_VIEWS 64          /* views per forward/backward call           */
+#define DS_MAX_RESOLUTION 8192   /* width and height                          */
+#define DS_MAX_TRIANGLES (1 << 24)
+#define DS_MAX_GRID_N 32
+#define DS_MAX_CHANNELS 16
+#define DS_MAX_SAMPLES 64
+
+/* Selection modes.  STOCHASTIC: Eq. 5 with tau ~ U[0,1) per fragment, drawn
+ * by Philox4x32-10 (Salmon et al., SC'11) from counter (px, py, t, s / 4),
+ * key (low, high 32 bits of the view's seed), word s % 4, tau = word>>8 * 2^-24.
+ * THRESHOLD_HALF: Eq. 3, tau = 0.5 (the deployment render). */
+#define DS_MODE_STOCHASTIC 0u
+#define DS_MODE_THRESHOLD_HALF 1u
+/* Forward option: skip the host synchronisation that sizes the bin buffers;
+ * use the current capacity and report an overflow through ds_ctx_status. */
+#define DS_NO_SYNC 0x100u
+
+/* Gradient terms for ds_raster_backward (Algorithm A1 step 2; Sec. 3.2). */
+#define DS_G_TEX 1u       /* 2(a): colour gradient of the selected fragment  */
+#define DS_G_SCORE 2u     /* 2(b) with Eq. 9: opacity score gradient         */
+#define DS_G_INTERIOR 4u  /* first term of Eq. 8 for the vertices            */
+#define DS_G_EDGE 8u      /* edge gradients on all adjacent pixel pairs      */
+#define DS_G_ALL 15u
+/* The soup and cameras are the ones of the last ds_raster_forward on this
+ * context and have not changed: reuse its set-up, bins and activations. */
+#define DS_REUSE_FORWARD 0x100u
+/* Overwrite instead of accumulate: zero grad_tex / grad_verts first
+ * (cudaMemsetAsync on the stream). */
+#define DS_OVERWRITE 0x200u
+
+/* Soup upload flags. */
+#define DS_COPY 0u    /* the library copies verts/tex and owns the copy       */
+#define DS_BORROW 1u  /* the library keeps the caller's pointers (training)   */
+
+/* Pinhole camera.  World -> camera: x_c = R x + t (R row-major); +z forward,
+ * +x right, +y down; pixel (px, py) has its centre at (px + 0.5, py + 0.5);
+ * screen x = fx * x_c / z_c + cx.  A triangle with a vertex at z_c <= near_z
+ * is not drawn in that view. */
+typedef struct ds_camera {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+    float near_z;
+} ds_camera;
+
+/* One G-buffer texel (Algorithm A1 step 1: the stored fragment f*): selected
+ * triangle (-1 = background), its barycentrics (b1, b2) -- weights of
+ * vertices 1 and 2, perspective-correct -- and its view-space depth D
+ * (+inf for the background). 16 bytes, stored as [S][H][W]. */
+typedef struct ds_gbuf {
+    int32_t tri_id;
+    float b1, b2;
+    float depth;
+} ds_gbuf;
+
+/* Per-view outputs of the forward pass. */
+typedef struct ds_view_out {
+    ds_gbuf* gbuf;     /* [S][H][W]                                          */
+    float* color;      /* [S][C-1][H][W] decoded colour features, planar     */
+    int32_t* n_front;  /* [S][H][W] or NULL: covered fragments in front of
+                          the selected one (all covered ones if background)  */
+} ds_view_out;
+
+/* Per-view upstream gradients for the backward pass. */
+typedef struct ds_view_gin {
+    const float* grad_color;  /* [S][C-1][H][W]  dL/dC of every sample       */
+    const float* score_w;     /* [S][H][W] or NULL: the per-sample loss value
+                                 that multiplies the score of Eq. 9 (the
+                                 L(C) of Algorithm A1 2(b)); NULL = zero     */
+} ds_view_gin;
+
+/* Library version (major * 10000 + minor * 100 + patch). Never fails. */
+DS_API int32_t ds_version(void);
+
+/* Message of the last failing call on this thread ("" if none). Host string
+ * owned by the library, valid until the next call on this thread. */
+DS_API const char* ds_last_error(void);
+
+/* Create a context on CUDA device `device`.  Allocates nothing on the device
+ * until a call needs scratch.  Errors: DS_ERR_INVALID_ARG (bad device),
+ * DS_ERR_CUDA. */
+DS_API ds_status ds_create(ds_ctx** out, int32_t device);
+
+/* Destroy a context: waits for its work, frees its scratch and owned soups. */
+DS_API void ds_destroy(ds_ctx* ctx);
+
+/* Register a triangle soup (Sec. 3.1, "Triangle soup representation").
+ *  verts: [T][3][3] float, vertex positions in world space.
+ *  tex:   [T][V][C] float texture logits (the accumulated finest grid before
+ *         the sigmoid of Sec. 3.3); channel C-1 is opacity.
+ *  grid_n = N in [1, 32]; C in [2, 16]; T in [1, 2^24).
+ *  flags: DS_COPY (asynchronous device-to-device copy on `stream` into
+ *  library memory) or DS_BORROW (pointers kept; the caller keeps them valid
+ *  and may change their contents between calls).
+ *  On success *soup_id receives a handle >= 0. */
+DS_API ds_status ds_soup_upload(ds_ctx* ctx, const float* verts, const float* tex, int32_t T,
+                         int32_t grid_n, int32_t C, uint32_t flags, int32_t* soup_id,
+                         void* stream);
+
+/* Release a soup (waits for the device, frees an owned copy). */
+DS_API ds_status ds_soup_free(ds_ctx* ctx, int32_t soup_id);
+
+/* Forward pass (Eq. 5; Algorithm A1 step 1) for n_views views of one soup:
+ * sigmoid activation of the texture (Sec. 3.3), triangle set-up, radix-sorted
+ * binning of triangles into 16x16 pixel tiles, then per pixel and sample the
+ * foremost covered fragment whose interpolated opacity exceeds its threshold
+ * (fixed tie-break: larger perspective-correct inverse depth first, then the
+ * lower triangle index), and the mesh-colour decode of its C-1 colour
+ * channels (background colour `bg` when nothing survives).
+ *  cams  (host) [n_views]; seeds (host) [n_views]; bg (host) [C-1];
+ *  out   (host) [n_views] per-view output pointers (device buffers).
+ *  mode: DS_MODE_STOCHASTIC or DS_MODE_THRESHOLD_HALF, optionally | DS_NO_SYNC.
+ * Without DS_NO_SYNC the call synchronises `stream` once to size its bin
+ * buffers. */
+DS_API ds_status ds_raster_forward(ds_ctx* ctx, int32_t soup_id, const ds_camera* cams,
+                            const uint64_t* seeds, int32_t n_views, int32_t S, uint32_t mode,
+                            const float* bg, const ds_view_out* out, void* stream);
+
+/* Backward pass (Algorithm A1 step 2, Eq. 8-9, Sec. 3.2) for the G-buffers
+ * and colours `fwd` produced by ds_raster_forward with the same soup,
+ * cameras and S.  Accumulates (+=) into
+ *   grad_tex   [T][V][C] (gradient w.r.t. the logits) and
+ *   grad_verts [T][3][3] (world space), either may be NULL,
+ * the terms selected by grad_flags (DS_G_*), optionally | DS_REUSE_FORWARD.
+ * Score term: for every sample with weight w = score_w, +w/alpha for the
+ * selected fragment and -w/(1-alpha) for every covered fragment in front of
+ * it (all covered fragments when the sample shows the background), chained
+ * to the opacity logits.  Uses floating-point atomics: summation order, and
+ * so the last bits, vary from run to run. */
+DS_API ds_status ds_raster_backward(ds_ctx* ctx, int32_t soup_id, const ds_camera* cams,
+                             int32_t n_views, int32_t S, const ds_view_out* fwd,
+                             const ds_view_gin* gin, uint32_t grad_flags, float* grad_verts,
+                             float* grad_tex, void* stream);
+
+/* Per-pixel L2 photometric loss of the rendered colour features against
+ * target images, with its upstream gradients for ds_raster_backward (the
+ * paper minimises L1 + SSIM, Eq. 10; the estimator of Eq. 8 takes any
+ * per-pixel loss).  For every view v, sample s and pixel p:
+ *   l = sum_c (color - target)^2,  grad_color = 2 * scale * (color - target),
+ *   score_w = scale * l,            *loss += scale * sum of l over everything.
+ *  hw (host) [n_views][2] = (width, height); colors, targets, grad_colors,
+ *  score_ws (host arrays of device pointers): color [S][C-1][H][W], target
+ *  [C-1][H][W], grad_color [S][C-1][H][W] (may be NULL), score_w [S][H][W]
+ *  (may be NULL); loss: one device float, accumulated (may be NULL).
+ *  scale is usually 1/S (the mean over mask samples).  Allocates nothing. */
+DS_API ds_status ds_loss_l2(int32_t n_views, int32_t S, int32_t C, const int32_t* hw,
+                            const float* const* colors, const float* const* targets,
+                            float* const* grad_colors, float* const* score_ws, float scale,
+                            float* loss, void* stream);
+
+/* Fragment statistics of Eq. 1 for n_views views: *n_cover_total (host)
+ * receives the number of (pixel, covering triangle) pairs summed over the
+ * views (|F|, one mask sample).  Synchronises `stream`. */
+DS_API ds_status ds_fragment_count(ds_ctx* ctx, int32_t soup_id, const ds_camera* cams,
+                            int32_t n_views, int64_t* n_cover_total, void* stream);
+
+/* Sizes of the context's current binning plan (the last forward, backward or
+ * fragment count): *pairs = (tile, triangle) pairs after binning, *tiles =
+ * 16x16 tiles over all views.  Host values; never synchronises. */
+DS_API ds_status ds_plan_stats(ds_ctx* ctx, int64_t* pairs, int64_t* tiles);
+
+/* Read and clear the context's device status word (synchronises the
+ * context's last stream): DS_ERR_CAPACITY after a DS_NO_SYNC forward whose
+ * bins overflowed (its outputs are invalid), else DS_OK. */
+DS_API ds_status ds_ctx_status(ds_ctx* ctx);
+
+/* Profiling (off by default; no paper counterpart: instrumentation).  While
+ * enabled, every pipeline stage that a call on this context launches
+ * (activate, setup, scan, emit, sort, ranges, raster_fwd, count, geom,
+ * raster_bwd, edge_bwd) is bracketed by two CUDA events recorded on the caller's stream.
+ * ds_profile_read waits for those events and returns, for stage index
+ * `stage` in [0, ds_profile_stages()), its name (static host string), the
+ * number of times it ran and its summed device time in ms since the last
+ * ds_profile_reset. */
+DS_API ds_status ds_profile_enable(ds_ctx* ctx, int32_t on);
+DS_API int32_t ds_profile_stages(void);
+DS_API ds_status ds_profile_read(ds_ctx* ctx, int32_t stage, const char** name, int64_t* runs,
+                                 double* ms);
+DS_API ds_status ds_profile_reset(ds_ctx* ctx);
+/* Kernels launched by the library in this process so far (all contexts). */
+DS_API int64_t ds_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIFFSOUP_H */

@@ -402,10 +402,16 @@ static void o_add_world(const float* cam, d3 g, double* dst)
     dst[2] += R[2] * g.x + R[5] * g.y + R[8] * g.z;
 }
 
-/* Direction (z = 1) of the camera ray through screen point (sx, sy). */
+/* Direction (z = 1) of the camera ray through screen point (sx, sy), a pixel
+ * centre or the midpoint of two (both exact in FP32).  The direction is
+ * defined by FP32 arithmetic, ((float)sx - cx) / fx rounded once per step, so
+ * that the GPU path holds the identical ray: at grazing incidence the
+ * barycentrics of the hit point react strongly to the last bit of the ray. */
 static d3 o_ray(const float* cam, double sx, double sy)
 {
-    d3 d = {(sx - cam[2]) / cam[0], (sy - cam[3]) / cam[1], 1.0};
+    float dx = ((float)sx - cam[2]) / cam[0];
+    float dy = ((float)sy - cam[3]) / cam[1];
+    d3 d = {dx, dy, 1.0};
     return d;
 }
 

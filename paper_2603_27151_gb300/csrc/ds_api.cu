@@ -1,0 +1,690 @@
+// ds_api.cu -- the C ABI declared in include/diffsoup.h: contexts, soups,
+// scratch management and the launch sequence of the forward and backward
+// passes.  Host code only.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ds_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+ds_status fail(ds_status code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define DS_TRY_CUDA(call)                                                                          \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return fail(DS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define DS_TRY(call)                          \
+    do {                                      \
+        ds_status s_ = (call);                \
+        if (s_ != DS_OK) return s_;           \
+    } while (0)
+
+// Grow-only device buffer.
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+    ds_status ensure(size_t bytes, const char* what) {
+        if (bytes <= cap && p) return DS_OK;
+        size_t want = bytes + bytes / 4 + 256;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        if (cudaMalloc(&p, want) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return fail(DS_ERR_OOM, std::string("cudaMalloc failed for ") + what);
+        }
+        cap = want;
+        return DS_OK;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+    template <class T>
+    T* as() const {
+        return static_cast<T*>(p);
+    }
+};
+
+struct Soup {
+    bool live = false;
+    bool owned = false;
+    const float* verts = nullptr;
+    const float* tex = nullptr;
+    float* own = nullptr;   // owned copy of verts and tex
+    float* act = nullptr;   // [T][V][C] and [T][V] (one allocation)
+    int T = 0, N = 0, C = 0, V = 0;
+};
+
+struct Plan {
+    bool valid = false;
+    int soup = -1;
+    std::vector<ds_camera> cams;
+    int DB = 0;
+    int res = 0;
+    uint32_t kcap = 0;
+    int n_tiles = 0;
+};
+
+bool finite_cam(const ds_camera& c) {
+    const float* f = &c.fx;
+    for (int i = 0; i < 17; ++i)
+        if (!std::isfinite(f[i])) return false;
+    return c.fx != 0.f && c.fy != 0.f && c.near_z > 0.f && c.width >= 1 && c.height >= 1 &&
+           c.width <= DS_MAX_RESOLUTION && c.height <= DS_MAX_RESOLUTION;
+}
+
+}  // namespace
+
+struct ds_ctx {
+    int device = 0;
+    std::mutex mu;
+    std::vector<Soup> soups;
+    DevBuf recs, counts, offs, tbox, zkeys, keys[2], vals[2], hist, hist_scan, ranges, scanbuf, misc, geom;
+    ds::ScanScratch scan;
+    int64_t scan_cap = 0;
+    uint32_t* h_word = nullptr;   // pinned host words
+    Plan plan;
+    cudaStream_t last_stream = nullptr;
+    ds::ViewTable* vt = nullptr;   // host staging of the kernel parameter table (~9 KB)
+
+    // optional stage profiler: CUDA events around each pipeline stage
+    struct ProfRec {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    bool prof_on = false;
+    std::vector<ProfRec> prof_pending;
+    std::vector<cudaEvent_t> prof_pool;
+    double prof_ms[ds::kNumStages] = {0};
+    long long prof_n[ds::kNumStages] = {0};
+
+    // misc layout
+    int* d_status() const { return misc.as<int>(); }
+    int* d_counter() const { return misc.as<int>() + 4; }
+    uint32_t* d_K() const { return reinterpret_cast<uint32_t*>(misc.as<int>() + 12); }
+    unsigned long long* d_total() const { return reinterpret_cast<unsigned long long*>(misc.as<char>() + 64); }
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+cudaEvent_t take_event(ds_ctx* c) {
+    if (!c->prof_pool.empty()) {
+        cudaEvent_t e = c->prof_pool.back();
+        c->prof_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Brackets one pipeline stage with events on `st` while profiling is on.
+struct StageScope {
+    ds_ctx* c;
+    int stage;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    StageScope(ds_ctx* c_, int stage_, cudaStream_t st_) : c(c_), stage(stage_), st(st_) {
+        if (c->prof_on) {
+            a = take_event(c);
+            if (a) cudaEventRecord(a, st);
+        }
+    }
+    ~StageScope() {
+        if (!a) return;
+        cudaEvent_t b = take_event(c);
+        if (!b) {
+            c->prof_pool.push_back(a);
+            return;
+        }
+        cudaEventRecord(b, st);
+        c->prof_pending.push_back({stage, a, b});
+    }
+};
+
+ds_status prof_flush(ds_ctx* c) {
+    for (auto& r : c->prof_pending) {
+        DS_TRY_CUDA(cudaEventSynchronize(r.b));
+        float ms = 0.f;
+        DS_TRY_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+        c->prof_ms[r.stage] += ms;
+        c->prof_n[r.stage] += 1;
+        c->prof_pool.push_back(r.a);
+        c->prof_pool.push_back(r.b);
+    }
+    c->prof_pending.clear();
+    return DS_OK;
+}
+
+ds_status ensure_scan(ds_ctx* c, int64_t n) {
+    if (n <= c->scan_cap && c->scanbuf.p) return DS_OK;
+    int64_t sizes[6] = {0};
+    const int lv = ds::scan_levels(n, sizes);
+    int64_t total = 0;
+    for (int i = 0; i < lv; ++i) total += 2 * sizes[i];
+    DS_TRY(c->scanbuf.ensure(sizeof(uint32_t) * (size_t)(total + 1), "scan scratch"));
+    uint32_t* p = c->scanbuf.as<uint32_t>();
+    c->scan.levels = lv;
+    for (int i = 0; i < lv; ++i) {
+        c->scan.level_n[i] = sizes[i];
+        c->scan.level[i] = p;
+        p += sizes[i];
+        c->scan.level_out[i] = p;
+        p += sizes[i];
+    }
+    c->scan_cap = n;
+    return DS_OK;
+}
+
+int bits_for(uint32_t n_values) {   // bits needed for indices 0 .. n_values-1
+    int b = 0;
+    while (b < 32 && (1ull << b) < n_values) ++b;
+    return b;
+}
+
+ds::SoupDev soup_dev(const Soup& s) {
+    ds::SoupDev d;
+    d.verts = s.verts;
+    d.tex = s.tex;
+    d.act = s.act;
+    d.act_a = s.act + (size_t)s.T * s.V * s.C;
+    d.T = s.T;
+    d.N = s.N;
+    d.C = s.C;
+    d.V = s.V;
+    return d;
+}
+
+ds_status get_soup(ds_ctx* c, int32_t id, Soup** out) {
+    if (id < 0 || id >= (int)c->soups.size() || !c->soups[id].live)
+        return fail(DS_ERR_NOT_FOUND, "unknown soup id " + std::to_string(id));
+    *out = &c->soups[id];
+    return DS_OK;
+}
+
+ds_status check_views(const ds_camera* cams, int32_t n_views, int32_t S) {
+    if (!cams) return fail(DS_ERR_INVALID_ARG, "cams is NULL");
+    if (n_views < 1 || n_views > DS_MAX_VIEWS)
+        return fail(DS_ERR_INVALID_ARG, "n_views must be in [1, " + std::to_string(DS_MAX_VIEWS) + "]");
+    if (S < 1 || S > DS_MAX_SAMPLES) return fail(DS_ERR_INVALID_ARG, "S must be in [1, 64]");
+    for (int v = 0; v < n_views; ++v)
+        if (!finite_cam(cams[v])) return fail(DS_ERR_INVALID_ARG, "camera " + std::to_string(v) + " is invalid");
+    return DS_OK;
+}
+
+// Fill the view table (tiles, work items, per-view pointers).
+void build_table(ds::ViewTable& vt, const ds_camera* cams, const uint64_t* seeds, int32_t n_views, int32_t S,
+                 const ds_view_out* out, const ds_view_gin* gin) {
+    std::memset(&vt, 0, sizeof(vt));
+    vt.n = n_views;
+    vt.S = S;
+    vt.n_groups = (S + ds::kSampleGroup - 1) / ds::kSampleGroup;
+    int tile_base = 0, item_base = 0;
+    for (int v = 0; v < n_views; ++v) {
+        ds::ViewDesc& d = vt.v[v];
+        const ds_camera& c = cams[v];
+        d.cam.fx = c.fx;
+        d.cam.fy = c.fy;
+        d.cam.cx = c.cx;
+        d.cam.cy = c.cy;
+        for (int i = 0; i < 9; ++i) d.cam.R[i] = c.R[i];
+        for (int i = 0; i < 3; ++i) d.cam.t[i] = c.t[i];
+        d.cam.near_z = c.near_z;
+        d.W = c.width;
+        d.H = c.height;
+        d.tiles_x = (c.width + ds::kTile - 1) / ds::kTile;
+        d.tiles_y = (c.height + ds::kTile - 1) / ds::kTile;
+        d.tile_base = tile_base;
+        d.item_base = item_base;
+        tile_base += d.tiles_x * d.tiles_y;
+        item_base += d.tiles_x * d.tiles_y * vt.n_groups;
+        const uint64_t sd = seeds ? seeds[v] : 0ull;
+        d.seed_lo = (uint32_t)sd;
+        d.seed_hi = (uint32_t)(sd >> 32);
+        if (out) {
+            d.gbuf = out[v].gbuf;
+            d.color = out[v].color;
+            d.n_front = out[v].n_front;
+        }
+        if (gin) {
+            d.grad_color = gin[v].grad_color;
+            d.score_w = gin[v].score_w;
+        }
+    }
+    vt.n_items = item_base;
+}
+
+int total_tiles(const ds::ViewTable& vt) {
+    const ds::ViewDesc& d = vt.v[vt.n - 1];
+    return d.tile_base + d.tiles_x * d.tiles_y;
+}
+
+// Activation, set-up and binning of `vt`'s views into the context's plan.
+ds_status prepare(ds_ctx* c, int32_t soup_id, Soup& s, const ds_camera* cams, const ds::ViewTable& vt, bool sync,
+                  cudaStream_t st) {
+    const ds::SoupDev sd = soup_dev(s);
+    const size_t nvt = (size_t)vt.n * s.T;
+    const int n_tiles = total_tiles(vt);
+    c->plan.valid = false;
+    DS_TRY(c->recs.ensure(sizeof(ds::SetupRec) * nvt, "set-up records"));
+    DS_TRY(c->counts.ensure(4 * nvt, "tile counts"));
+    DS_TRY(c->offs.ensure(4 * nvt, "tile offsets"));
+    DS_TRY(c->tbox.ensure(16 * nvt, "tile boxes"));
+    DS_TRY(c->zkeys.ensure(4 * nvt, "depth keys"));
+    DS_TRY(c->ranges.ensure(8 * (size_t)n_tiles, "tile ranges"));
+    DS_TRY(ensure_scan(c, (int64_t)nvt));
+
+    {
+        StageScope p(c, ds::kStActivate, st);
+        DS_TRY_CUDA(ds::launch_activate(sd, st));
+    }
+    {
+        StageScope p(c, ds::kStSetup, st);
+        DS_TRY_CUDA(ds::launch_setup(vt, sd, c->recs.as<ds::SetupRec>(), c->counts.as<uint32_t>(), c->tbox.as<int4>(),
+                                     c->zkeys.as<uint32_t>(), st));
+    }
+    {
+        StageScope p(c, ds::kStScan, st);
+        DS_TRY_CUDA(ds::scan_exclusive(c->counts.as<uint32_t>(), c->offs.as<uint32_t>(), (int64_t)nvt, c->d_K(), c->scan, st));
+    }
+
+    uint32_t kcap = (uint32_t)(c->keys[0].cap / 4);
+    if (sync || kcap == 0) {
+        DS_TRY_CUDA(cudaMemcpyAsync(c->h_word, c->d_K(), 4, cudaMemcpyDeviceToHost, st));
+        DS_TRY_CUDA(cudaStreamSynchronize(st));
+        const uint32_t K = *c->h_word;
+        if ((size_t)K * 4 > c->keys[0].cap || !c->keys[0].p) {
+            for (int b = 0; b < 2; ++b) {
+                DS_TRY(c->keys[b].ensure(4 * (size_t)(K > 0 ? K : 1), "bin keys"));
+                DS_TRY(c->vals[b].ensure(4 * (size_t)(K > 0 ? K : 1), "bin values"));
+            }
+        }
+        kcap = K;
+    }
+    const uint32_t nblk = (kcap + ds::kSortBlock - 1) / ds::kSortBlock;
+    DS_TRY(c->hist.ensure(4 * 256 * (size_t)(nblk > 0 ? nblk : 1), "radix histogram"));
+    DS_TRY(c->hist_scan.ensure(4 * 256 * (size_t)(nblk > 0 ? nblk : 1), "radix offsets"));
+    DS_TRY(ensure_scan(c, (int64_t)256 * (nblk > 0 ? nblk : 1)));
+
+    const int tile_bits = bits_for((uint32_t)n_tiles);
+    const int DB = std::min(16, 32 - tile_bits);
+    {
+        StageScope p(c, ds::kStEmit, st);
+        DS_TRY_CUDA(ds::launch_emit(vt, s.T, c->recs.as<ds::SetupRec>(), c->counts.as<uint32_t>(), c->offs.as<uint32_t>(),
+                                    c->tbox.as<int4>(), c->zkeys.as<uint32_t>(), DB, c->keys[0].as<uint32_t>(),
+                                    c->vals[0].as<uint32_t>(), kcap, c->d_status(), st));
+    }
+    cudaError_t se = cudaSuccess;
+    StageScope* sort_scope = new StageScope(c, ds::kStSort, st);
+    const int res = ds::radix_sort_pairs(c->keys[0].as<uint32_t>(), c->vals[0].as<uint32_t>(), c->keys[1].as<uint32_t>(),
+                                         c->vals[1].as<uint32_t>(), c->d_K(), kcap, tile_bits + DB,
+                                         c->hist.as<uint32_t>(), c->hist_scan.as<uint32_t>(), c->scan, st, &se);
+    delete sort_scope;
+    DS_TRY_CUDA(se);
+    {
+        StageScope p(c, ds::kStRanges, st);
+        DS_TRY_CUDA(cudaMemsetAsync(c->ranges.p, 0, 8 * (size_t)n_tiles, st));
+        DS_TRY_CUDA(ds::launch_tile_ranges(c->keys[res].as<uint32_t>(), c->d_K(), kcap, DB, c->ranges.as<uint2>(), st));
+    }
+
+    c->plan.valid = true;
+    c->plan.soup = soup_id;
+    c->plan.cams.assign(cams, cams + vt.n);
+    c->plan.DB = DB;
+    c->plan.res = res;
+    c->plan.kcap = kcap;
+    c->plan.n_tiles = n_tiles;
+    return DS_OK;
+}
+
+bool plan_matches(const ds_ctx* c, int32_t soup_id, const ds_camera* cams, int32_t n_views) {
+    if (!c->plan.valid || c->plan.soup != soup_id || (int)c->plan.cams.size() != n_views) return false;
+    return std::memcmp(c->plan.cams.data(), cams, sizeof(ds_camera) * n_views) == 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t ds_version(void) { return 100; }
+
+const char* ds_last_error(void) { return g_err.c_str(); }
+
+ds_status ds_create(ds_ctx** out, int32_t device) {
+    if (!out) return fail(DS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(DS_ERR_CUDA, "no CUDA device available");
+    }
+    if (device < 0 || device >= n) return fail(DS_ERR_INVALID_ARG, "bad device index");
+    ds_ctx* c = new (std::nothrow) ds_ctx();
+    if (!c) return fail(DS_ERR_OOM, "host allocation failed");
+    c->vt = new (std::nothrow) ds::ViewTable();
+    if (!c->vt) {
+        delete c;
+        return fail(DS_ERR_OOM, "host allocation failed");
+    }
+    c->device = device;
+    DeviceGuard g(device);
+    if (cudaHostAlloc(reinterpret_cast<void**>(&c->h_word), 64, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        delete c->vt;
+        delete c;
+        return fail(DS_ERR_CUDA, "cudaHostAlloc failed");
+    }
+    if (c->misc.ensure(256, "context words") != DS_OK) {
+        cudaFreeHost(c->h_word);
+        delete c->vt;
+        delete c;
+        return DS_ERR_OOM;
+    }
+    cudaMemset(c->misc.p, 0, c->misc.cap);
+    *out = c;
+    return DS_OK;
+}
+
+void ds_destroy(ds_ctx* c) {
+    if (!c) return;
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    for (Soup& s : c->soups) {
+        if (s.own) cudaFree(s.own);
+        if (s.act) cudaFree(s.act);
+    }
+    DevBuf* bufs[] = {&c->recs,  &c->counts,  &c->offs,      &c->tbox,   &c->zkeys,   &c->keys[0], &c->keys[1],
+                      &c->vals[0], &c->vals[1], &c->hist, &c->hist_scan, &c->ranges, &c->scanbuf, &c->misc,
+                      &c->geom};
+    for (DevBuf* b : bufs) b->release();
+    if (c->h_word) cudaFreeHost(c->h_word);
+    for (auto& r : c->prof_pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
+    delete c->vt;
+    delete c;
+}
+
+ds_status ds_soup_upload(ds_ctx* c, const float* verts, const float* tex, int32_t T, int32_t grid_n, int32_t C,
+                         uint32_t flags, int32_t* soup_id, void* stream) {
+    if (!c || !verts || !tex || !soup_id) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    if (T < 1 || T >= DS_MAX_TRIANGLES) return fail(DS_ERR_INVALID_ARG, "T out of range");
+    if (grid_n < 1 || grid_n > DS_MAX_GRID_N) return fail(DS_ERR_INVALID_ARG, "grid_n out of range");
+    if (C < 2 || C > DS_MAX_CHANNELS) return fail(DS_ERR_INVALID_ARG, "C out of range");
+    if (flags != DS_COPY && flags != DS_BORROW) return fail(DS_ERR_INVALID_ARG, "bad flags");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Soup s;
+    s.T = T;
+    s.N = grid_n;
+    s.C = C;
+    s.V = (grid_n + 1) * (grid_n + 2) / 2;
+    const size_t nv = 9 * (size_t)T, nt = (size_t)T * s.V * C;
+    if (cudaMalloc(reinterpret_cast<void**>(&s.act), sizeof(float) * (nt + (size_t)T * s.V)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(DS_ERR_OOM, "cudaMalloc failed for activations");
+    }
+    if (flags == DS_COPY) {
+        if (cudaMalloc(reinterpret_cast<void**>(&s.own), sizeof(float) * (nv + nt + 4)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(s.act);
+            return fail(DS_ERR_OOM, "cudaMalloc failed for the soup copy");
+        }
+        float* tex_dst = s.own + ((nv + 3) & ~size_t(3));   // 16-byte aligned texture copy
+        DS_TRY_CUDA(cudaMemcpyAsync(s.own, verts, sizeof(float) * nv, cudaMemcpyDeviceToDevice, st));
+        DS_TRY_CUDA(cudaMemcpyAsync(tex_dst, tex, sizeof(float) * nt, cudaMemcpyDeviceToDevice, st));
+        s.verts = s.own;
+        s.tex = tex_dst;
+        s.owned = true;
+    } else {
+        s.verts = verts;
+        s.tex = tex;
+    }
+    s.live = true;
+    int id = -1;
+    for (int i = 0; i < (int)c->soups.size(); ++i)
+        if (!c->soups[i].live) {
+            id = i;
+            break;
+        }
+    if (id < 0) {
+        id = (int)c->soups.size();
+        c->soups.push_back(s);
+    } else {
+        c->soups[id] = s;
+    }
+    if (c->plan.soup == id) c->plan.valid = false;
+    *soup_id = id;
+    return DS_OK;
+}
+
+ds_status ds_soup_free(ds_ctx* c, int32_t soup_id) {
+    if (!c) return fail(DS_ERR_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    Soup* s = nullptr;
+    DS_TRY(get_soup(c, soup_id, &s));
+    cudaDeviceSynchronize();
+    if (s->own) cudaFree(s->own);
+    if (s->act) cudaFree(s->act);
+    *s = Soup();
+    if (c->plan.soup == soup_id) c->plan.valid = false;
+    return DS_OK;
+}
+
+ds_status ds_raster_forward(ds_ctx* c, int32_t soup_id, const ds_camera* cams, const uint64_t* seeds, int32_t n_views,
+                            int32_t S, uint32_t mode, const float* bg, const ds_view_out* out, void* stream) {
+    if (!c) return fail(DS_ERR_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    Soup* s = nullptr;
+    DS_TRY(get_soup(c, soup_id, &s));
+    DS_TRY(check_views(cams, n_views, S));
+    const uint32_t base_mode = mode & 0xffu;
+    if (base_mode != DS_MODE_STOCHASTIC && base_mode != DS_MODE_THRESHOLD_HALF)
+        return fail(DS_ERR_INVALID_ARG, "bad mode");
+    if ((mode & ~(0xffu | DS_NO_SYNC)) != 0) return fail(DS_ERR_INVALID_ARG, "unknown mode bits");
+    if (!seeds && base_mode == DS_MODE_STOCHASTIC) return fail(DS_ERR_INVALID_ARG, "seeds is NULL");
+    if (!bg || !out) return fail(DS_ERR_INVALID_ARG, "bg or out is NULL");
+    for (int v = 0; v < n_views; ++v) {
+        if (!out[v].gbuf || !out[v].color) return fail(DS_ERR_INVALID_ARG, "view output buffer is NULL");
+        if (((uintptr_t)out[v].gbuf & 15) != 0) return fail(DS_ERR_INVALID_ARG, "gbuf must be 16-byte aligned");
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    ds::ViewTable& vt = *c->vt;   // calls on one context are serialised by its mutex
+    build_table(vt, cams, seeds, n_views, S, out, nullptr);
+    DS_TRY(prepare(c, soup_id, *s, cams, vt, (mode & DS_NO_SYNC) == 0, st));
+    ds::Bg b{};
+    for (int i = 0; i < s->C - 1; ++i) b.c[i] = bg[i];
+    const ds::SoupDev sd = soup_dev(*s);
+    const int grid = ds::persistent_grid(vt.n_items, 2);
+    {
+        StageScope p(c, ds::kStRasterFwd, st);
+        DS_TRY_CUDA(cudaMemsetAsync(c->d_counter(), 0, 4, st));
+        DS_TRY_CUDA(ds::launch_raster_fwd(vt, sd, c->recs.as<ds::SetupRec>(), c->keys[c->plan.res].as<uint32_t>(),
+                                          c->vals[c->plan.res].as<uint32_t>(), c->ranges.as<uint2>(), c->plan.DB,
+                                          base_mode, b, c->d_counter(), grid, st));
+    }
+    bool want_front = false;
+    for (int v = 0; v < n_views; ++v) want_front = want_front || out[v].n_front;
+    if (want_front) {
+        StageScope p(c, ds::kStCount, st);
+        DS_TRY_CUDA(cudaMemsetAsync(c->d_counter() + 1, 0, 4, st));
+        DS_TRY_CUDA(ds::launch_raster_count(vt, sd, c->recs.as<ds::SetupRec>(), c->keys[c->plan.res].as<uint32_t>(),
+                                            c->vals[c->plan.res].as<uint32_t>(), c->ranges.as<uint2>(), c->plan.DB, 0,
+                                            nullptr, c->d_counter() + 1, grid, st));
+    }
+    return DS_OK;
+}
+
+ds_status ds_raster_backward(ds_ctx* c, int32_t soup_id, const ds_camera* cams, int32_t n_views, int32_t S,
+                             const ds_view_out* fwd, const ds_view_gin* gin, uint32_t grad_flags, float* grad_verts,
+                             float* grad_tex, void* stream) {
+    if (!c) return fail(DS_ERR_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    Soup* s = nullptr;
+    DS_TRY(get_soup(c, soup_id, &s));
+    DS_TRY(check_views(cams, n_views, S));
+    if ((grad_flags & ~(DS_G_ALL | DS_REUSE_FORWARD | DS_OVERWRITE)) != 0)
+        return fail(DS_ERR_INVALID_ARG, "unknown gradient flags");
+    if (!fwd || !gin) return fail(DS_ERR_INVALID_ARG, "fwd or gin is NULL");
+    const bool need_color = (grad_flags & (DS_G_TEX | DS_G_INTERIOR | DS_G_EDGE)) != 0;
+    for (int v = 0; v < n_views; ++v) {
+        if (!fwd[v].gbuf) return fail(DS_ERR_INVALID_ARG, "fwd gbuf is NULL");
+        if (((uintptr_t)fwd[v].gbuf & 15) != 0) return fail(DS_ERR_INVALID_ARG, "gbuf must be 16-byte aligned");
+        if (need_color && !gin[v].grad_color) return fail(DS_ERR_INVALID_ARG, "grad_color is NULL");
+        if ((grad_flags & DS_G_EDGE) && !fwd[v].color) return fail(DS_ERR_INVALID_ARG, "fwd color is NULL");
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    ds::ViewTable& vt = *c->vt;
+    build_table(vt, cams, nullptr, n_views, S, fwd, gin);
+    if (!((grad_flags & DS_REUSE_FORWARD) && plan_matches(c, soup_id, cams, n_views)))
+        DS_TRY(prepare(c, soup_id, *s, cams, vt, true, st));
+    const ds::SoupDev sd = soup_dev(*s);
+    const int grid = ds::persistent_grid(vt.n_items, 2);
+    const uint32_t gflags = grad_flags & DS_G_ALL;
+    if (grad_flags & DS_OVERWRITE) {
+        if (grad_tex) DS_TRY_CUDA(cudaMemsetAsync(grad_tex, 0, sizeof(float) * (size_t)s->T * s->V * s->C, st));
+        if (grad_verts) DS_TRY_CUDA(cudaMemsetAsync(grad_verts, 0, sizeof(float) * 9 * (size_t)s->T, st));
+    }
+    const bool need_geom = grad_verts && (gflags & (DS_G_INTERIOR | DS_G_EDGE));
+    if (need_geom) {
+        DS_TRY(c->geom.ensure(sizeof(ds::GeomRec) * (size_t)n_views * s->T, "vertex-gradient geometry"));
+        StageScope p(c, ds::kStGeom, st);
+        DS_TRY_CUDA(ds::launch_geom(vt, sd, c->geom.as<ds::GeomRec>(), st));
+    }
+    if (((gflags & (DS_G_TEX | DS_G_SCORE)) && grad_tex) || ((gflags & DS_G_INTERIOR) && grad_verts)) {
+        StageScope p(c, ds::kStRasterBwd, st);
+        DS_TRY_CUDA(cudaMemsetAsync(c->d_counter() + 2, 0, 4, st));
+        DS_TRY_CUDA(ds::launch_raster_bwd(vt, sd, c->recs.as<ds::SetupRec>(), c->keys[c->plan.res].as<uint32_t>(),
+                                          c->vals[c->plan.res].as<uint32_t>(), c->ranges.as<uint2>(), c->plan.DB,
+                                          gflags, c->geom.as<ds::GeomRec>(), grad_tex, grad_verts, c->d_counter() + 2,
+                                          grid, st));
+    }
+    if ((gflags & DS_G_EDGE) && grad_verts) {
+        StageScope p(c, ds::kStEdgeBwd, st);
+        DS_TRY_CUDA(cudaMemsetAsync(c->d_counter() + 3, 0, 4, st));
+        DS_TRY_CUDA(ds::launch_edge_bwd(vt, sd, c->recs.as<ds::SetupRec>(), c->geom.as<ds::GeomRec>(), grad_verts,
+                                        c->d_counter() + 3, grid, st));
+    }
+    return DS_OK;
+}
+
+ds_status ds_fragment_count(ds_ctx* c, int32_t soup_id, const ds_camera* cams, int32_t n_views,
+                            int64_t* n_cover_total, void* stream) {
+    if (!c || !n_cover_total) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    Soup* s = nullptr;
+    DS_TRY(get_soup(c, soup_id, &s));
+    DS_TRY(check_views(cams, n_views, 1));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    ds::ViewTable& vt = *c->vt;
+    build_table(vt, cams, nullptr, n_views, 1, nullptr, nullptr);
+    DS_TRY(prepare(c, soup_id, *s, cams, vt, true, st));
+    const ds::SoupDev sd = soup_dev(*s);
+    const int grid = ds::persistent_grid(vt.n_items, 2);
+    DS_TRY_CUDA(cudaMemsetAsync(c->d_total(), 0, 8, st));
+    DS_TRY_CUDA(cudaMemsetAsync(c->d_counter() + 4, 0, 4, st));
+    DS_TRY_CUDA(ds::launch_raster_count(vt, sd, c->recs.as<ds::SetupRec>(), c->keys[c->plan.res].as<uint32_t>(),
+                                        c->vals[c->plan.res].as<uint32_t>(), c->ranges.as<uint2>(), c->plan.DB, 1,
+                                        c->d_total(), c->d_counter() + 4, grid, st));
+    DS_TRY_CUDA(cudaMemcpyAsync(c->h_word, c->d_total(), 8, cudaMemcpyDeviceToHost, st));
+    DS_TRY_CUDA(cudaStreamSynchronize(st));
+    uint64_t v = 0;
+    std::memcpy(&v, c->h_word, 8);
+    *n_cover_total = (int64_t)v;
+    return DS_OK;
+}
+
+ds_status ds_profile_enable(ds_ctx* c, int32_t on) {
+    if (!c) return fail(DS_ERR_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->prof_on = on != 0;
+    return DS_OK;
+}
+
+int32_t ds_profile_stages(void) { return ds::kNumStages; }
+
+ds_status ds_profile_read(ds_ctx* c, int32_t stage, const char** name, int64_t* launches, double* ms) {
+    if (!c || stage < 0 || stage >= ds::kNumStages) return fail(DS_ERR_INVALID_ARG, "bad context or stage");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    DS_TRY(prof_flush(c));
+    if (name) *name = ds::kStageNames[stage];
+    if (launches) *launches = c->prof_n[stage];
+    if (ms) *ms = c->prof_ms[stage];
+    return DS_OK;
+}
+
+ds_status ds_profile_reset(ds_ctx* c) {
+    if (!c) return fail(DS_ERR_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    DS_TRY(prof_flush(c));
+    for (int i = 0; i < ds::kNumStages; ++i) {
+        c->prof_ms[i] = 0.0;
+        c->prof_n[i] = 0;
+    }
+    return DS_OK;
+}
+
+int64_t ds_kernel_launches(void) { return ds::launches_total(); }
+
+ds_status ds_plan_stats(ds_ctx* c, int64_t* pairs, int64_t* tiles) {
+    if (!c) return fail(DS_ERR_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (pairs) *pairs = c->plan.valid ? (int64_t)c->plan.kcap : 0;
+    if (tiles) *tiles = c->plan.valid ? (int64_t)c->plan.n_tiles : 0;
+    return DS_OK;
+}
+
+ds_status ds_ctx_status(ds_ctx* c) {
+    if (!c) return fail(DS_ERR_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    DS_TRY_CUDA(cudaStreamSynchronize(c->last_stream));
+    int st = 0;
+    DS_TRY_CUDA(cudaMemcpy(&st, c->d_status(), 4, cudaMemcpyDeviceToHost));
+    DS_TRY_CUDA(cudaMemset(c->d_status(), 0, 4));
+    if (st & 1) return fail(DS_ERR_CAPACITY, "bin capacity exceeded in a DS_NO_SYNC forward");
+    return DS_OK;
+}
+
+}  // extern "C"

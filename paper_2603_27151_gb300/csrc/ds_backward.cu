@@ -1,0 +1,594 @@
+// ds_backward.cu -- gradients of the stochastic rasteriser.
+//
+//  k_raster_bwd: Algorithm A1 step 2 by G-buffer recomputation.  Every tile
+//    list is walked again (front to back, stopping early) to find the covered
+//    fragments in front of each stored winner: they get -w/(1-alpha) (Eq. 9);
+//    the winner gets +w/alpha and the colour gradient (2(a)); the interior
+//    vertex term (first term of Eq. 8) moves the winner's barycentrics.
+//  k_edge_bwd: edge gradients on every horizontal and vertical pixel pair of
+//    the sampled image (Sec. 3.2): silhouettes of the winning triangle and
+//    mask-induced boundaries inside it.
+//
+// Scatter: lanes holding the same target (texel cell or triangle) in
+// consecutive lanes are summed in registers first (warp_run_sum); only the
+// first lane of each run issues the atomics.
+#include "ds_internal.h"
+#include "ds_tile.cuh"
+
+namespace ds {
+
+__device__ __forceinline__ unsigned long long lane_sentinel() {
+    return 0xffffffffffff0000ull | (threadIdx.x & 31);
+}
+
+// ------------------------------------------------------------ small vectors
+struct f3 {
+    float x, y, z;
+};
+__device__ __forceinline__ f3 mk3(float x, float y, float z) { return f3{x, y, z}; }
+__device__ __forceinline__ f3 sub3(f3 a, f3 b) { return mk3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ f3 cross3(f3 a, f3 b) {
+    return mk3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float dot3(f3 a, f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+__device__ __forceinline__ f3 to_cam(const DevCam& c, const float* p) {
+    const float x = __ldg(p), y = __ldg(p + 1), z = __ldg(p + 2);
+    return mk3(c.R[0] * x + c.R[1] * y + c.R[2] * z + c.t[0], c.R[3] * x + c.R[4] * y + c.R[5] * z + c.t[1],
+               c.R[6] * x + c.R[7] * y + c.R[8] * z + c.t[2]);
+}
+
+// world-space gradient R^T g
+__device__ __forceinline__ f3 to_world(const DevCam& c, f3 g) {
+    return mk3(c.R[0] * g.x + c.R[3] * g.y + c.R[6] * g.z, c.R[1] * g.x + c.R[4] * g.y + c.R[7] * g.z,
+               c.R[2] * g.x + c.R[5] * g.y + c.R[8] * g.z);
+}
+
+// Ray-plane barycentrics of camera-space triangle V with ray direction d
+// (z = 1), written with edge vectors so that small, distant triangles do not
+// cancel: n1 = d.(e2 x V0), n2 = d.(V0 x e1), S = d.(e1 x e2), n0 = S - n1 - n2.
+struct RayBary {
+    float n[3];
+    float S;
+};
+__device__ __forceinline__ RayBary ray_bary(const f3 V[3], f3 d) {
+    const f3 e1 = sub3(V[1], V[0]), e2 = sub3(V[2], V[0]);
+    RayBary rb;
+    rb.S = dot3(d, cross3(e1, e2));
+    rb.n[1] = dot3(d, cross3(e2, V[0]));
+    rb.n[2] = dot3(d, cross3(V[0], e1));
+    rb.n[0] = rb.S - rb.n[1] - rb.n[2];
+    return rb;
+}
+
+// ------------------------------------------------------------ texture scatter
+// Adds (for one lane) g_m = val[m] to channel c of the three corner texels of
+// cell `cl` of triangle t, chained through the sigmoid: += g_m a (1 - a).
+__device__ __forceinline__ void scatter_alpha_run(const SoupDev& s, float* grad_tex, bool act, int t, const Cell& cl,
+                                                  float g) {
+    float v[3] = {0.f, 0.f, 0.f};
+    unsigned long long key = lane_sentinel();
+    if (act) {
+        v[0] = g * (1.0f - cl.wa - cl.wb);
+        v[1] = g * cl.wa;
+        v[2] = g * cl.wb;
+        key = ((unsigned long long)(unsigned)t << 20) | ((unsigned)cl.k0 << 1) | (cl.lower ? 1u : 0u);
+    }
+    const bool head = warp_run_sum<3>(key, v);
+    if (act && head) {
+        const float* aa = s.act_a + (size_t)t * s.V;
+        const int ks[3] = {cl.k0, cl.k1, cl.k2};
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const float a = __ldg(aa + ks[m]);
+            atomicAdd(grad_tex + ((size_t)t * s.V + ks[m]) * s.C + (s.C - 1), v[m] * a * (1.0f - a));
+        }
+    }
+}
+
+// Winner terms of one sample: colour gradient (C-1 channels) and the +w/alpha
+// opacity score, merged into one pass over the corner texels, four channels
+// at a time.  Returns dL/d(b1, b2) of the colour through G.
+template <bool kInterior>
+__device__ __forceinline__ void winner_texture(const SoupDev& s, float* grad_tex, bool act, int t, float b1, float b2,
+                                               const float* gcol, size_t HW, float wscore, bool do_tex,
+                                               bool do_score, float G[2]) {
+    Cell cl;
+    cl.k0 = cl.k1 = cl.k2 = 0;
+    cl.wa = cl.wb = 0.f;
+    cl.lower = true;
+    if (act) cl = find_cell(s.N, b1, b2);
+    const float w0 = 1.0f - cl.wa - cl.wb;
+    const float sgnN = cl.lower ? (float)s.N : -(float)s.N;
+    const int C = s.C;
+    const float* base = s.act + (size_t)(act ? t : 0) * s.V * C;
+    float alpha_g = 0.f;
+    if (act && do_score && wscore != 0.0f) {
+        const float* aa = s.act_a + (size_t)t * s.V;
+        const float alpha = interp(__ldg(aa + cl.k0), __ldg(aa + cl.k1), __ldg(aa + cl.k2), cl.wa, cl.wb);
+        alpha_g = wscore / alpha;
+    }
+    G[0] = G[1] = 0.f;
+    const unsigned long long key =
+        act ? (((unsigned long long)(unsigned)t << 20) | ((unsigned)cl.k0 << 1) | (cl.lower ? 1u : 0u)) : lane_sentinel();
+    for (int c4 = 0; c4 < C; c4 += 4) {
+        float v[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[k] = 0.f;
+        if (act) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int c = c4 + k;
+                if (c >= C) break;
+                float g = 0.f;
+                if (c < C - 1) {
+                    g = (do_tex || kInterior) ? __ldg(gcol + c * HW) : 0.f;
+                    if (kInterior) {
+                        const float a0 = __ldg(base + (size_t)cl.k0 * C + c);
+                        const float a1 = __ldg(base + (size_t)cl.k1 * C + c);
+                        const float a2 = __ldg(base + (size_t)cl.k2 * C + c);
+                        G[0] += g * sgnN * (a1 - a0);
+                        G[1] += g * sgnN * (a2 - a0);
+                    }
+                    if (!do_tex) g = 0.f;
+                } else {
+                    g = alpha_g;
+                }
+                v[k] = g * w0;
+                v[4 + k] = g * cl.wa;
+                v[8 + k] = g * cl.wb;
+            }
+        }
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) any = any || v[k] != 0.f;
+        if (!__any_sync(kFullMask, act && any)) continue;
+        const bool head = warp_run_sum<12>(key, v);
+        if (act && head) {
+            const int ks[3] = {cl.k0, cl.k1, cl.k2};
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                const float* ap = base + (size_t)ks[m] * C + c4;
+                float* gp = grad_tex + ((size_t)t * s.V + ks[m]) * C + c4;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (c4 + k >= C) break;
+                    const float g = v[4 * m + k];
+                    if (g != 0.f) {
+                        const float a = __ldg(ap + k);
+                        atomicAdd(gp + k, g * a * (1.0f - a));
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Nine-float vertex gradient of triangle t summed over runs of lanes.
+__device__ __forceinline__ void scatter_verts_run(float* grad_verts, bool act, int t, float (&g)[9]) {
+    const unsigned long long key = act ? (unsigned long long)(unsigned)t : lane_sentinel();
+    if (!__any_sync(kFullMask, act)) return;
+    const bool head = warp_run_sum<9>(key, g);
+    if (act && head) {
+        float* p = grad_verts + 9 * (size_t)t;
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            if (g[k] != 0.f) atomicAdd(p + k, g[k]);
+    }
+}
+
+// Interior term at pixel (px, py).  With X = sum_i b_i V_i on the fixed ray
+// d, moving vertex m gives e1 db1 + e2 db2 = dlambda d - b_m dV_m; crossing
+// with d: db1/dV_m = -b_m (e2 x d) / S, db2/dV_m = -b_m (d x e1) / S with
+// S = d.(e1 x e2).  So dL/dV_m = -(b_m / S) [G1 (e2 x d) + G2 (d x e1)].
+// S and the barycentric numerators come from Dot2 on FP64-derived vectors
+// (grazing triangles make them small differences of O(1) terms).
+__device__ __forceinline__ void interior_grad(const GeomRec& g, const DevCam& cam, int px, int py, const float G[2],
+                                              float (&out)[9]) {
+    float dx, dy;
+    pinned_ray(cam, (float)px + 0.5f, (float)py + 0.5f, dx, dy);
+    const float S = dot2(dx, dy, 1.0f, g.n);
+    const float n1 = dot2(dx, dy, 1.0f, g.m1), n2 = dot2(dx, dy, 1.0f, g.m2);
+    const float inv = 1.0f / S;
+    const float b[3] = {(S - n1 - n2) * inv, n1 * inv, n2 * inv};
+    const f3 d = mk3(dx, dy, 1.0f);
+    const f3 e1 = mk3(g.e1[0], g.e1[1], g.e1[2]), e2 = mk3(g.e2[0], g.e2[1], g.e2[2]);
+    const f3 c1 = cross3(e2, d), c2 = cross3(d, e1);
+    const f3 u = mk3(G[0] * c1.x + G[1] * c2.x, G[0] * c1.y + G[1] * c2.y, G[0] * c1.z + G[1] * c2.z);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        const float k = -b[m] * inv;
+        const f3 gw = to_world(cam, mk3(k * u.x, k * u.y, k * u.z));
+        out[3 * m] = gw.x;
+        out[3 * m + 1] = gw.y;
+        out[3 * m + 2] = gw.z;
+    }
+}
+
+// FP64 geometry record of every (view, triangle): camera-space positions and
+// screen projection as the oracle computes them, stored for compensated FP32
+// use (see GeomRec).
+__device__ __forceinline__ float2 split2(double x) {
+    const float hi = (float)x;
+    return make_float2(hi, (float)(x - (double)hi));
+}
+
+__global__ void k_geom(const __grid_constant__ ViewTable vt, const SoupDev s, GeomRec* __restrict__ out) {
+    const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (gid >= (long long)vt.n * s.T) return;
+    const int v = (int)(gid / s.T), t = (int)(gid - (long long)v * s.T);
+    const DevCam& c = vt.v[v].cam;
+    double V[3][3];
+    const float* p = s.verts + 9LL * t;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        const double x = __ldg(p + 3 * m), y = __ldg(p + 3 * m + 1), z = __ldg(p + 3 * m + 2);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+            V[m][r] = (double)c.R[3 * r] * x + (double)c.R[3 * r + 1] * y + (double)c.R[3 * r + 2] * z + (double)c.t[r];
+    }
+    GeomRec g;
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        const double iz = 1.0 / V[m][2];
+        g.sx[m] = split2((double)c.fx * (V[m][0] * iz) + (double)c.cx);
+        g.sy[m] = split2((double)c.fy * (V[m][1] * iz) + (double)c.cy);
+        g.jx[m][0] = (float)(c.fx * iz);
+        g.jx[m][1] = (float)(-c.fx * V[m][0] * iz * iz);
+        g.jy[m][0] = (float)(c.fy * iz);
+        g.jy[m][1] = (float)(-c.fy * V[m][1] * iz * iz);
+    }
+    double e1[3], e2[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        e1[r] = V[1][r] - V[0][r];
+        e2[r] = V[2][r] - V[0][r];
+        g.e1[r] = (float)e1[r];
+        g.e2[r] = (float)e2[r];
+        g.v0[r] = (float)V[0][r];
+    }
+    const double* v0 = V[0];
+    g.n[0] = split2(e1[1] * e2[2] - e1[2] * e2[1]);
+    g.n[1] = split2(e1[2] * e2[0] - e1[0] * e2[2]);
+    g.n[2] = split2(e1[0] * e2[1] - e1[1] * e2[0]);
+    g.m1[0] = split2(e2[1] * v0[2] - e2[2] * v0[1]);
+    g.m1[1] = split2(e2[2] * v0[0] - e2[0] * v0[2]);
+    g.m1[2] = split2(e2[0] * v0[1] - e2[1] * v0[0]);
+    g.m2[0] = split2(v0[1] * e1[2] - v0[2] * e1[1]);
+    g.m2[1] = split2(v0[2] * e1[0] - v0[0] * e1[2]);
+    g.m2[2] = split2(v0[0] * e1[1] - v0[1] * e1[0]);
+    g.pad = 0.f;
+    const int4* src = reinterpret_cast<const int4*>(&g);
+    int4* dst = reinterpret_cast<int4*>(out + gid);
+#pragma unroll
+    for (int k = 0; k < 13; ++k) dst[k] = src[k];
+}
+
+__device__ __forceinline__ GeomRec load_geom(const GeomRec* p) {
+    GeomRec g;
+    const int4* q = reinterpret_cast<const int4*>(p);
+    int4* d = reinterpret_cast<int4*>(&g);
+#pragma unroll
+    for (int k = 0; k < 13; ++k) d[k] = __ldg(q + k);
+    return g;
+}
+
+template <int SG>
+__global__ void __launch_bounds__(kTilePix, 2)
+    k_raster_bwd(const __grid_constant__ ViewTable vt, const SoupDev s, const SetupRec* __restrict__ recs,
+                 const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                 const uint2* __restrict__ ranges, int DB, uint32_t flags, const GeomRec* __restrict__ geom,
+                 float* __restrict__ grad_tex, float* __restrict__ grad_verts, int* __restrict__ counter) {
+    __shared__ TileStage sm;
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    const int lx = tid & (kTile - 1), ly = tid / kTile;
+    const bool do_tex = (flags & DS_G_TEX) && grad_tex;
+    const bool do_score = (flags & DS_G_SCORE) && grad_tex;
+    const bool do_int = (flags & DS_G_INTERIOR) && grad_verts;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= vt.n_items) break;
+        const WorkItem wi = decode_item(vt, item);
+        const ViewDesc& V = vt.v[wi.v];
+        const int px = wi.tx * kTile + lx, py = wi.ty * kTile + ly;
+        const bool valid = px < V.W && py < V.H;
+        const int s0 = wi.g * kSampleGroup;
+        const int ns = min(SG, vt.S - s0);
+        const size_t HW = (size_t)V.H * V.W, pix = (size_t)py * V.W + px;
+        const SetupRec* vrec = recs + (size_t)wi.v * s.T;
+
+        int wt[SG];
+        float wb1[SG], wb2[SG], wrho[SG], wsc[SG];
+        bool any_score = false;
+#pragma unroll
+        for (int q = 0; q < SG; ++q) {
+            wt[q] = -1;
+            wb1[q] = wb2[q] = wrho[q] = wsc[q] = 0.f;
+            if (valid && q < ns) {
+                const int4 gb = reinterpret_cast<const int4*>(V.gbuf)[(s0 + q) * HW + pix];
+                wt[q] = (gb.x >= 0 && gb.x < s.T) ? gb.x : -1;   // ids outside the soup read as background
+                wb1[q] = __int_as_float(gb.y);
+                wb2[q] = __int_as_float(gb.z);
+                if (do_score && V.score_w) wsc[q] = V.score_w[(s0 + q) * HW + pix];
+                if (wt[q] >= 0) wrho[q] = winner_rho(vrec + wt[q], px, py);
+                any_score = any_score || wsc[q] != 0.f;
+            }
+        }
+
+        // ---- Eq. 9 for every covered fragment in front of the winner
+        const uint2 rg = ranges[V.tile_base + wi.ty * V.tiles_x + wi.tx];
+        bool warp_done = !__any_sync(kFullMask, any_score);
+        if (__syncthreads_or(!warp_done)) {
+            for (uint32_t c0 = rg.x; c0 < rg.y; c0 += kChunk) {
+                const int n = (int)min((uint32_t)kChunk, rg.y - c0);
+                __syncthreads();
+                if (tid < n) stage_triangle(sm, tid, recs, (size_t)wi.v * s.T, keys[c0 + tid], vals[c0 + tid], DB, wi.tx, wi.ty);
+                __syncthreads();
+                if (!warp_done) {
+                    for (int j = 0; j < n; ++j) {
+                        const int4 h2 = sm.h2[j];
+                        bool ldone = true;
+#pragma unroll
+                        for (int q = 0; q < SG; ++q)
+                            if (wsc[q] != 0.f) ldone = ldone && wt[q] >= 0 && wrho[q] > __int_as_float(h2.z);
+                        if (__all_sync(kFullMask, ldone)) {
+                            warp_done = true;
+                            break;
+                        }
+                        const int t = h2.y;
+                        bool act = false;
+                        float g = 0.f;
+                        Cell cl;
+                        cl.k0 = cl.k1 = cl.k2 = 0;
+                        cl.wa = cl.wb = 0.f;
+                        cl.lower = true;
+                        long long E[3];
+                        if (any_score && tile_cover(sm, j, lx, ly, E)) {
+                            const Frag f = make_frag(E[0], E[1], E[2], sm.kk[j][0], sm.kk[j][1], sm.kk[j][2]);
+                            bool need = false;
+#pragma unroll
+                            for (int q = 0; q < SG; ++q)
+                                need = need || (wsc[q] != 0.f && t != wt[q] &&
+                                                (wt[q] < 0 || in_front(f.rho, t, wrho[q], wt[q])));
+                            if (need) {
+                                const float r = __frcp_rn(f.rho);
+                                cl = find_cell(s.N, __fmul_rn(f.q1, r), __fmul_rn(f.q2, r));
+                                const float* aa = s.act_a + (size_t)t * s.V;
+                                const float alpha = interp(__ldg(aa + cl.k0), __ldg(aa + cl.k1), __ldg(aa + cl.k2), cl.wa, cl.wb);
+                                const float inv = 1.0f / (1.0f - alpha);
+#pragma unroll
+                                for (int q = 0; q < SG; ++q)
+                                    if (wsc[q] != 0.f && t != wt[q] && (wt[q] < 0 || in_front(f.rho, t, wrho[q], wt[q])))
+                                        g -= wsc[q] * inv;
+                                act = true;
+                            }
+                        }
+                        if (__any_sync(kFullMask, act)) scatter_alpha_run(s, grad_tex, act, t, cl, g);
+                    }
+                }
+                if (__syncthreads_and(warp_done)) break;
+            }
+        }
+
+        // ---- winner terms: colour (2(a)), +w/alpha (2(b)), interior (Eq. 8)
+#pragma unroll
+        for (int q = 0; q < SG; ++q) {
+            const bool act = valid && q < ns && wt[q] >= 0;
+            const float* gcol = V.grad_color + (size_t)(s0 + (q < ns ? q : 0)) * (s.C - 1) * HW + pix;
+            float G[2];
+            if (do_int)
+                winner_texture<true>(s, grad_tex, act, wt[q], wb1[q], wb2[q], gcol, HW, wsc[q], do_tex, do_score, G);
+            else if (do_tex || do_score)
+                winner_texture<false>(s, grad_tex, act, wt[q], wb1[q], wb2[q], gcol, HW, wsc[q], do_tex, do_score, G);
+            if (do_int) {
+                float gv[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) gv[k] = 0.f;
+                if (act) interior_grad(load_geom(geom + (size_t)wi.v * s.T + wt[q]), V.cam, px, py, G, gv);
+                scatter_verts_run(grad_verts, act, wt[q], gv);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ edge gradients
+// Screen coordinate (hi + lo) relative to pixel coordinate x, compensated.
+__device__ __forceinline__ float rel(float2 s, float x) {
+    float e;
+    const float d = two_sum(s.x, -x, e);
+    return __fadd_rn(d, __fadd_rn(e, s.y));
+}
+
+// Contribution of side X of a pixel pair (X -> Y along unit axis e = (ex, ey))
+// whose winner triangle is t: silhouette or mask-induced (implicit) boundary.
+// phi = 1/2 sum_c (g_X + g_Y)(C_X - C_Y).  Returns false if X is not in front.
+__device__ bool edge_side(const DevCam& cam, const SetupRec* vrec, const GeomRec* vgeom, int t, int xX, int yX,
+                          int xY, int yY, int tY, float phi, float (&out)[9]) {
+    const SetupRec r = load_rec(vrec + t);
+    long long E[3];
+    const int ex = xY - xX, ey = yY - yX;
+    const GeomRec g = load_geom(vgeom + t);
+    if (cover_exact(r, xY, yY, E)) {
+        const float rho = make_frag(E[0], E[1], E[2], r.k[0], r.k[1], r.k[2]).rho;
+        if (tY >= 0) {
+            const float ry = winner_rho(vrec + tY, xY, yY);
+            if (!in_front(rho, t, ry, tY)) return false;   // occluded at Y
+        }
+        // implicit boundary: the material point under the pair's midpoint
+        // moves with the surface; weight 1 per pair axis
+        float dx, dy;
+        pinned_ray(cam, 0.5f * (float)(xX + xY + 1), 0.5f * (float)(yX + yY + 1), dx, dy);
+        const float S = dot2(dx, dy, 1.0f, g.n);
+        const float n1 = dot2(dx, dy, 1.0f, g.m1), n2 = dot2(dx, dy, 1.0f, g.m2);
+        const float inv = 1.0f / S;
+        const float beta[3] = {(S - n1 - n2) * inv, n1 * inv, n2 * inv};
+        const f3 P = mk3(g.v0[0] + beta[1] * g.e1[0] + beta[2] * g.e2[0], g.v0[1] + beta[1] * g.e1[1] + beta[2] * g.e2[1],
+                         g.v0[2] + beta[1] * g.e1[2] + beta[2] * g.e2[2]);
+        const float iz = 1.0f / P.z;
+        // J^T e with J rows (fx/z, 0, -fx x/z^2), (0, fy/z, -fy y/z^2)
+        const f3 je = mk3(ex * cam.fx * iz, ey * cam.fy * iz, -(ex * cam.fx * P.x + ey * cam.fy * P.y) * iz * iz);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+            const float f = phi * beta[m];
+            const f3 gw = to_world(cam, mk3(f * je.x, f * je.y, f * je.z));
+            out[3 * m] += gw.x;
+            out[3 * m + 1] += gw.y;
+            out[3 * m + 2] += gw.z;
+        }
+        return true;
+    }
+    // silhouette: the first edge the segment X -> Y crosses; coordinates
+    // relative to X's pixel centre
+    const float cxX = (float)xX + 0.5f, cyX = (float)yX + 0.5f;
+    float sx[3], sy[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        sx[m] = rel(g.sx[m], cxX);
+        sy[m] = rel(g.sy[m], cyX);
+    }
+    const float area = diff_prod(sx[1] - sx[0], sy[2] - sy[0], sx[2] - sx[0], sy[1] - sy[0]);
+    const float sg = area > 0.f ? 1.f : -1.f;
+    const float yx = (float)ex, yy = (float)ey;   // Y relative to X
+    int best = -1;
+    float bs = 0.f, bfX = 0.f, bfY = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int a = (i + 1) % 3, b = (i + 2) % 3;
+        const float fX = sg * diff_prod(sx[a], sy[b], sx[b], sy[a]);
+        const float fY = sg * diff_prod(sx[a] - yx, sy[b] - yy, sx[b] - yx, sy[a] - yy);
+        if (!(fY < 0.f && fX > fY)) continue;
+        const float si = fX / (fX - fY);
+        if (best < 0 || si < bs) {
+            best = i;
+            bs = si;
+            bfX = fX;
+            bfY = fY;
+        }
+    }
+    if (best < 0) return true;
+    const int a = (best + 1) % 3, b = (best + 2) % 3;
+    const float fX = bfX * sg, fY = bfY * sg;
+    const float den = (fX - fY) * (fX - fY);
+    const float dfXa[2] = {sy[b], -sx[b]}, dfYa[2] = {sy[b] - yy, -(sx[b] - yx)};
+    const float dfXb[2] = {-sy[a], sx[a]}, dfYb[2] = {-(sy[a] - yy), sx[a] - yx};
+    const float ux = sx[b] - sx[a], uy = sy[b] - sy[a];
+    const float omega = (ex != 0 ? uy * uy : ux * ux) / (ux * ux + uy * uy);
+    const float k = omega * phi / den;
+    const float gs[2][2] = {{k * (fX * dfYa[0] - fY * dfXa[0]), k * (fX * dfYa[1] - fY * dfXa[1])},
+                            {k * (fX * dfYb[0] - fY * dfXb[0]), k * (fX * dfYb[1] - fY * dfXb[1])}};
+    const int vid[2] = {a, b};
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int m = vid[e];
+        const f3 gc = mk3(gs[e][0] * g.jx[m][0], gs[e][1] * g.jy[m][0], gs[e][0] * g.jx[m][1] + gs[e][1] * g.jy[m][1]);
+        const f3 gw = to_world(cam, gc);
+        out[3 * m] += gw.x;
+        out[3 * m + 1] += gw.y;
+        out[3 * m + 2] += gw.z;
+    }
+    return true;
+}
+
+// One CTA per (view, tile, sample group); every pixel handles its pairs with
+// the right and the lower neighbour.
+template <int SG>
+__global__ void __launch_bounds__(kTilePix, 2)
+    k_edge_bwd(const __grid_constant__ ViewTable vt, const SoupDev s, const SetupRec* __restrict__ recs,
+               const GeomRec* __restrict__ geom, float* __restrict__ grad_verts, int* __restrict__ counter) {
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    const int lx = tid & (kTile - 1), ly = tid / kTile;
+    const int Co = s.C - 1;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= vt.n_items) break;
+        const WorkItem wi = decode_item(vt, item);
+        const ViewDesc& V = vt.v[wi.v];
+        const int px = wi.tx * kTile + lx, py = wi.ty * kTile + ly;
+        const bool valid = px < V.W && py < V.H;
+        const int s0 = wi.g * kSampleGroup;
+        const int ns = min(SG, vt.S - s0);
+        const size_t HW = (size_t)V.H * V.W;
+        const SetupRec* vrec = recs + (size_t)wi.v * s.T;
+        const GeomRec* vgeom = geom + (size_t)wi.v * s.T;
+        const int4* gbuf = reinterpret_cast<const int4*>(V.gbuf);
+#pragma unroll 1
+        for (int q = 0; q < SG; ++q) {
+            const bool qv = valid && q < ns;
+            const size_t sb = (size_t)(s0 + (q < ns ? q : 0)) * HW;
+            int tp = qv ? gbuf[sb + (size_t)py * V.W + px].x : -1;
+            if (tp < 0 || tp >= s.T) tp = -1;
+            const float* col = V.color + (size_t)(s0 + (q < ns ? q : 0)) * Co * HW;
+            const float* gc = V.grad_color + (size_t)(s0 + (q < ns ? q : 0)) * Co * HW;
+            // slot 0: pixel's own winner (both pairs), slots 1, 2: right / lower neighbour's winner
+            float acc[3][9];
+            int tgt[3] = {qv ? tp : -1, -1, -1};
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int k = 0; k < 9; ++k) acc[a][k] = 0.f;
+            bool has[3] = {false, false, false};
+#pragma unroll 1
+            for (int dir = 0; dir < 2; ++dir) {
+                const int qx = px + (dir == 0), qy = py + (dir == 1);
+                if (!qv || qx >= V.W || qy >= V.H) continue;
+                int tq = gbuf[sb + (size_t)qy * V.W + qx].x;
+                if (tq < 0 || tq >= s.T) tq = -1;
+                if (tq == tp) continue;
+                float phi = 0.f;
+                const size_t ip = (size_t)py * V.W + px, iq = (size_t)qy * V.W + qx;
+                for (int c = 0; c < Co; ++c)
+                    phi += 0.5f * (__ldg(gc + c * HW + ip) + __ldg(gc + c * HW + iq)) * (__ldg(col + c * HW + ip) - __ldg(col + c * HW + iq));
+                if (phi == 0.f) continue;
+                if (tp >= 0 && edge_side(V.cam, vrec, vgeom, tp, px, py, qx, qy, tq, phi, acc[0])) has[0] = true;
+                if (tq >= 0) {
+                    tgt[1 + dir] = tq;
+                    if (edge_side(V.cam, vrec, vgeom, tq, qx, qy, px, py, tp, -phi, acc[1 + dir])) has[1 + dir] = true;
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) scatter_verts_run(grad_verts, has[a] && tgt[a] >= 0, tgt[a], acc[a]);
+        }
+    }
+}
+
+cudaError_t launch_geom(const ViewTable& vt, const SoupDev& s, GeomRec* geom, cudaStream_t st) {
+    const long long n = (long long)vt.n * s.T;
+    k_geom<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(vt, s, geom);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_raster_bwd(const ViewTable& vt, const SoupDev& s, const SetupRec* recs, const uint32_t* keys,
+                              const uint32_t* vals, const uint2* ranges, int DB, uint32_t flags, const GeomRec* geom,
+                              float* grad_tex, float* grad_verts, int* counter, int grid, cudaStream_t st) {
+    if (vt.S == 1)
+        k_raster_bwd<1><<<grid, kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, flags, geom, grad_tex, grad_verts, counter);
+    else if (vt.S == 2)
+        k_raster_bwd<2><<<grid, kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, flags, geom, grad_tex, grad_verts, counter);
+    else
+        k_raster_bwd<4><<<grid, kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, flags, geom, grad_tex, grad_verts, counter);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_edge_bwd(const ViewTable& vt, const SoupDev& s, const SetupRec* recs, const GeomRec* geom,
+                            float* grad_verts, int* counter, int grid, cudaStream_t st) {
+    if (vt.S == 1)
+        k_edge_bwd<1><<<grid, kTilePix, 0, st>>>(vt, s, recs, geom, grad_verts, counter);
+    else if (vt.S == 2)
+        k_edge_bwd<2><<<grid, kTilePix, 0, st>>>(vt, s, recs, geom, grad_verts, counter);
+    else
+        k_edge_bwd<4><<<grid, kTilePix, 0, st>>>(vt, s, recs, geom, grad_verts, counter);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+}  // namespace ds

@@ -1,0 +1,89 @@
+// ds_internal.h -- host-side launchers shared by the library's translation
+// units (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ds_common.cuh"
+
+namespace ds {
+
+// Pipeline stages timed by the optional profiler (ds_profile_*).
+enum Stage {
+    kStActivate, kStSetup, kStScan, kStEmit, kStSort, kStRanges,
+    kStRasterFwd, kStCount, kStGeom, kStRasterBwd, kStEdgeBwd, kNumStages
+};
+extern const char* const kStageNames[kNumStages];
+
+// Library-wide count of kernel launches (every launch site adds to it).
+void note_launches(int n);
+long long launches_total();
+
+// Scratch for the multi-level exclusive scan (one sum buffer per level).
+struct ScanScratch {
+    uint32_t* level[6] = {nullptr};
+    uint32_t* level_out[6] = {nullptr};
+    int64_t level_n[6] = {0};
+    int levels = 0;
+};
+
+constexpr int kScanBlock = 4096;    // items per scan block (1024 threads x 4)
+constexpr int kSortBlock = 4096;    // keys per radix-sort block (256 threads x 16)
+
+// Number of level buffers (and their sizes) needed to scan n items.
+int scan_levels(int64_t n, int64_t sizes[6]);
+
+// out[i] = sum_{j<i} in[j]; *total = sum of all (device).  in != out.
+cudaError_t scan_exclusive(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total,
+                           const ScanScratch& sc, cudaStream_t st);
+
+// Stable LSD radix sort of (key, value) pairs on bits [0, nbits) with 8-bit
+// digits.  The pair count is read on the device from *count; kcap bounds it
+// (grid size).  Buffers ping-pong between (k0, v0) and (k1, v1); returns the
+// index (0 or 1) of the pair holding the result.
+int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
+                     const uint32_t* count, uint32_t kcap, int nbits, uint32_t* hist,
+                     uint32_t* hist_scan, const ScanScratch& sc, cudaStream_t st,
+                     cudaError_t* err);
+
+// ---- set-up and binning (ds_setup.cu)
+cudaError_t launch_activate(const SoupDev& s, cudaStream_t st);
+cudaError_t launch_setup(const ViewTable& vt, const SoupDev& s, SetupRec* recs, uint32_t* counts,
+                         int4* tbox, uint32_t* zkeys, cudaStream_t st);
+cudaError_t launch_emit(const ViewTable& vt, int T, const SetupRec* recs, const uint32_t* counts,
+                        const uint32_t* offs, const int4* tbox, const uint32_t* zkeys, int DB,
+                        uint32_t* keys, uint32_t* vals, uint32_t cap, int* status,
+                        cudaStream_t st);
+cudaError_t launch_tile_ranges(const uint32_t* keys, const uint32_t* count, uint32_t kcap, int DB,
+                               uint2* ranges, cudaStream_t st);
+
+// ---- forward rasteriser (ds_raster.cu)
+struct Bg {
+    float c[DS_MAX_CHANNELS];
+};
+cudaError_t launch_raster_fwd(const ViewTable& vt, const SoupDev& s, const SetupRec* recs,
+                              const uint32_t* keys, const uint32_t* vals, const uint2* ranges,
+                              int DB, uint32_t mode, const Bg& bg, int* counter, int grid,
+                              cudaStream_t st);
+// mode 0: n_front into the views' n_front buffers; mode 1: add the number of
+// covered fragments (one sample) to *total.
+cudaError_t launch_raster_count(const ViewTable& vt, const SoupDev& s, const SetupRec* recs,
+                                const uint32_t* keys, const uint32_t* vals, const uint2* ranges,
+                                int DB, int mode, unsigned long long* total, int* counter,
+                                int grid, cudaStream_t st);
+
+// ---- backward (ds_backward.cu)
+cudaError_t launch_geom(const ViewTable& vt, const SoupDev& s, GeomRec* geom, cudaStream_t st);
+cudaError_t launch_raster_bwd(const ViewTable& vt, const SoupDev& s, const SetupRec* recs,
+                              const uint32_t* keys, const uint32_t* vals, const uint2* ranges,
+                              int DB, uint32_t flags, const GeomRec* geom, float* grad_tex,
+                              float* grad_verts, int* counter, int grid, cudaStream_t st);
+cudaError_t launch_edge_bwd(const ViewTable& vt, const SoupDev& s, const SetupRec* recs,
+                            const GeomRec* geom, float* grad_verts, int* counter, int grid,
+                            cudaStream_t st);
+
+// Persistent-grid size for the tile kernels on this device.
+int persistent_grid(int n_items, int blocks_per_sm);
+
+}  // namespace ds

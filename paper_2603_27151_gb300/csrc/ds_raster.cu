@@ -1,0 +1,259 @@
+// ds_raster.cu -- forward rasteriser: stochastic opacity masking (Eq. 5) by a
+// z-buffer over each 16x16 tile's depth-sorted triangle list, mesh-colour
+// decode of the selected fragment, and the optional fragment counts.
+#include <atomic>
+
+#include "ds_internal.h"
+#include "ds_tile.cuh"
+
+namespace ds {
+
+// One CTA (256 threads, one pixel each) per work item (view, tile, group of
+// up to four samples), taken from a global counter until none is left.
+template <int SG>
+__global__ void __launch_bounds__(kTilePix, 2)
+    k_raster_fwd(const __grid_constant__ ViewTable vt, const SoupDev s, const SetupRec* __restrict__ recs,
+                 const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                 const uint2* __restrict__ ranges, int DB, uint32_t mode, const Bg bg, int* __restrict__ counter) {
+    __shared__ TileStage sm;
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    const int lx = tid & (kTile - 1), ly = tid / kTile;
+    const bool stochastic = mode == DS_MODE_STOCHASTIC;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= vt.n_items) break;
+        const WorkItem wi = decode_item(vt, item);
+        const ViewDesc& V = vt.v[wi.v];
+        const int px = wi.tx * kTile + lx, py = wi.ty * kTile + ly;
+        const bool valid = px < V.W && py < V.H;
+        const int s0 = wi.g * kSampleGroup;
+        const int ns = min(SG, vt.S - s0);
+
+        int bt[SG];
+        float brho[SG], bb1[SG], bb2[SG], bD[SG];
+#pragma unroll
+        for (int q = 0; q < SG; ++q) {
+            bt[q] = -1;
+            brho[q] = 0.0f;
+            bb1[q] = bb2[q] = 0.0f;
+            bD[q] = __int_as_float(0x7f800000);
+        }
+
+        const uint2 rg = ranges[V.tile_base + wi.ty * V.tiles_x + wi.tx];
+        bool warp_done = !__any_sync(kFullMask, valid);
+        for (uint32_t c0 = rg.x; c0 < rg.y; c0 += kChunk) {
+            const int n = (int)min((uint32_t)kChunk, rg.y - c0);
+            __syncthreads();
+            if (tid < n) stage_triangle(sm, tid, recs, (size_t)wi.v * s.T, keys[c0 + tid], vals[c0 + tid], DB, wi.tx, wi.ty);
+            __syncthreads();
+            if (!warp_done) {
+                for (int j = 0; j < n; ++j) {
+                    const int4 h2 = sm.h2[j];
+                    // early exit: every sample already holds a fragment in
+                    // front of anything the rest of the (depth-sorted) list can give
+                    bool ldone = true;
+                    if (valid) {
+#pragma unroll
+                        for (int q = 0; q < SG; ++q)
+                            if (q < ns) ldone = ldone && bt[q] >= 0 && brho[q] > __int_as_float(h2.z);
+                    }
+                    if (__all_sync(kFullMask, ldone)) {
+                        warp_done = true;
+                        break;
+                    }
+                    if (!valid) continue;
+                    long long E[3];
+                    if (!tile_cover(sm, j, lx, ly, E)) continue;
+                    const int t = h2.y;
+                    const Frag f = make_frag(E[0], E[1], E[2], sm.kk[j][0], sm.kk[j][1], sm.kk[j][2]);
+                    bool need = false;
+#pragma unroll
+                    for (int q = 0; q < SG; ++q)
+                        need = need || (q < ns && (bt[q] < 0 || in_front(f.rho, t, brho[q], bt[q])));
+                    if (!need) continue;
+                    const float r = __frcp_rn(f.rho);
+                    const float b1 = __fmul_rn(f.q1, r), b2 = __fmul_rn(f.q2, r);
+                    const Cell cl = find_cell(s.N, b1, b2);
+                    const float* aa = s.act_a + (size_t)t * s.V;
+                    const float alpha = interp(__ldg(aa + cl.k0), __ldg(aa + cl.k1), __ldg(aa + cl.k2), cl.wa, cl.wb);
+                    float tau[4] = {0.5f, 0.5f, 0.5f, 0.5f};
+                    if (stochastic) {
+                        const uint4 w = philox4x32_10(make_uint4((uint32_t)px, (uint32_t)py, (uint32_t)t, (uint32_t)wi.g),
+                                                      V.seed_lo, V.seed_hi);
+                        tau[0] = word_to_tau(w.x);
+                        tau[1] = word_to_tau(w.y);
+                        tau[2] = word_to_tau(w.z);
+                        tau[3] = word_to_tau(w.w);
+                    }
+#pragma unroll
+                    for (int q = 0; q < SG; ++q) {
+                        if (q < ns && alpha > tau[q] && (bt[q] < 0 || in_front(f.rho, t, brho[q], bt[q]))) {
+                            bt[q] = t;
+                            brho[q] = f.rho;
+                            bb1[q] = b1;
+                            bb2[q] = b2;
+                            bD[q] = r;
+                        }
+                    }
+                }
+            }
+            if (__syncthreads_and(warp_done)) break;
+        }
+
+        if (valid) {
+            const size_t HW = (size_t)V.H * V.W, pix = (size_t)py * V.W + px;
+            const int Co = s.C - 1;
+#pragma unroll
+            for (int q = 0; q < SG; ++q) {
+                if (q >= ns) continue;
+                const int sg = s0 + q;
+                reinterpret_cast<int4*>(V.gbuf)[sg * HW + pix] =
+                    make_int4(bt[q], __float_as_int(bb1[q]), __float_as_int(bb2[q]), __float_as_int(bD[q]));
+                float* out = V.color + (size_t)sg * Co * HW + pix;
+                if (bt[q] < 0) {
+                    for (int c = 0; c < Co; ++c) out[c * HW] = bg.c[c];
+                } else {
+                    decode_color(s, bt[q], bb1[q], bb2[q], out, HW);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Fragment counts.  mode 0: per sample, the covered fragments in front of
+// the stored winner (all covered fragments for the background), written to
+// n_front.  mode 1: covered fragments of the pixel (one sample), summed.
+template <int SG>
+__global__ void __launch_bounds__(kTilePix, 2)
+    k_raster_count(const __grid_constant__ ViewTable vt, const SoupDev s, const SetupRec* __restrict__ recs,
+                   const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                   const uint2* __restrict__ ranges, int DB, int mode, unsigned long long* __restrict__ total,
+                   int* __restrict__ counter) {
+    __shared__ TileStage sm;
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    const int lx = tid & (kTile - 1), ly = tid / kTile;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= vt.n_items) break;
+        const WorkItem wi = decode_item(vt, item);
+        const ViewDesc& V = vt.v[wi.v];
+        const int px = wi.tx * kTile + lx, py = wi.ty * kTile + ly;
+        const bool valid = px < V.W && py < V.H;
+        const int s0 = wi.g * kSampleGroup;
+        const int ns = mode == 0 ? min(SG, vt.S - s0) : 1;
+        const size_t HW = (size_t)V.H * V.W, pix = (size_t)py * V.W + px;
+
+        int wt[SG], cnt[SG];
+        float wrho[SG];
+#pragma unroll
+        for (int q = 0; q < SG; ++q) {
+            wt[q] = -1;
+            wrho[q] = 0.0f;
+            cnt[q] = 0;
+            if (mode == 0 && valid && q < ns) {
+                wt[q] = reinterpret_cast<const int4*>(V.gbuf)[(s0 + q) * HW + pix].x;
+                if (wt[q] < 0 || wt[q] >= s.T) wt[q] = -1;
+                if (wt[q] >= 0) wrho[q] = winner_rho(recs + (size_t)wi.v * s.T + wt[q], px, py);
+            }
+        }
+        const uint2 rg = ranges[V.tile_base + wi.ty * V.tiles_x + wi.tx];
+        bool warp_done = !__any_sync(kFullMask, valid);
+        for (uint32_t c0 = rg.x; c0 < rg.y; c0 += kChunk) {
+            const int n = (int)min((uint32_t)kChunk, rg.y - c0);
+            __syncthreads();
+            if (tid < n) stage_triangle(sm, tid, recs, (size_t)wi.v * s.T, keys[c0 + tid], vals[c0 + tid], DB, wi.tx, wi.ty);
+            __syncthreads();
+            if (!warp_done) {
+                for (int j = 0; j < n; ++j) {
+                    const int4 h2 = sm.h2[j];
+                    bool ldone = true;
+                    if (valid && mode == 0) {
+#pragma unroll
+                        for (int q = 0; q < SG; ++q)
+                            if (q < ns) ldone = ldone && wt[q] >= 0 && wrho[q] > __int_as_float(h2.z);
+                    } else if (valid) {
+                        ldone = false;
+                    }
+                    if (__all_sync(kFullMask, ldone)) {
+                        warp_done = true;
+                        break;
+                    }
+                    if (!valid) continue;
+                    long long E[3];
+                    if (!tile_cover(sm, j, lx, ly, E)) continue;
+                    if (mode == 1) {
+                        ++cnt[0];
+                        continue;
+                    }
+                    const int t = h2.y;
+                    const Frag f = make_frag(E[0], E[1], E[2], sm.kk[j][0], sm.kk[j][1], sm.kk[j][2]);
+#pragma unroll
+                    for (int q = 0; q < SG; ++q)
+                        if (q < ns && (wt[q] < 0 || in_front(f.rho, t, wrho[q], wt[q]))) ++cnt[q];
+                }
+            }
+            if (__syncthreads_and(warp_done)) break;
+        }
+        if (valid) {
+            if (mode == 0) {
+#pragma unroll
+                for (int q = 0; q < SG; ++q)
+                    if (q < ns) V.n_front[(s0 + q) * HW + pix] = cnt[q];
+            }
+        }
+        if (mode == 1) {
+            unsigned long long c = valid ? (unsigned long long)cnt[0] : 0ull;
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) c += __shfl_down_sync(kFullMask, c, d);
+            if ((tid & 31) == 0 && c) atomicAdd(total, c);
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_raster_fwd(const ViewTable& vt, const SoupDev& s, const SetupRec* recs, const uint32_t* keys,
+                              const uint32_t* vals, const uint2* ranges, int DB, uint32_t mode, const Bg& bg,
+                              int* counter, int grid, cudaStream_t st) {
+    if (vt.S == 1)
+        k_raster_fwd<1><<<grid, kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, bg, counter);
+    else if (vt.S == 2)
+        k_raster_fwd<2><<<grid, kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, bg, counter);
+    else
+        k_raster_fwd<4><<<grid, kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, bg, counter);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_raster_count(const ViewTable& vt, const SoupDev& s, const SetupRec* recs, const uint32_t* keys,
+                                const uint32_t* vals, const uint2* ranges, int DB, int mode,
+                                unsigned long long* total, int* counter, int grid, cudaStream_t st) {
+    if (mode == 1 || vt.S == 1)
+        k_raster_count<1><<<grid, kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, total, counter);
+    else
+        k_raster_count<4><<<grid, kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, total, counter);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+const char* const kStageNames[kNumStages] = {"activate", "setup", "scan", "emit", "sort", "ranges",
+                                             "raster_fwd", "count", "geom", "raster_bwd", "edge_bwd"};
+
+static std::atomic<long long> g_launches{0};
+void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
+
+int persistent_grid(int n_items, int blocks_per_sm) {
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int g = sms * blocks_per_sm;
+    return n_items < g ? (n_items > 0 ? n_items : 1) : g;
+}
+
+}  // namespace ds

@@ -1,0 +1,150 @@
+// ds_tile.cuh -- device helpers shared by the tile kernels (forward, counts,
+// backward): work-item decoding, per-tile staging of triangle set-up in
+// shared memory, the tile-relative coverage test and the colour decode.
+#pragma once
+
+#include "ds_common.cuh"
+
+namespace ds {
+
+constexpr unsigned kFullMask = 0xffffffffu;
+constexpr int kChunk = 256;   // triangles staged per round (one per thread)
+
+// Per-tile staged set-up.  h0..h2 hold what the per-pixel coverage test reads
+// for every triangle; eo/kk are read only for covered fragments.
+struct TileStage {
+    int4 h0[kChunk];         // A0, B0, thr0, A1
+    int4 h1[kChunk];         // B1, thr1, A2, B2
+    int4 h2[kChunk];         // thr2, triangle, rho bound (float bits), -
+    long long eo[kChunk][3]; // oriented (unbiased) edge values at the tile's first pixel centre
+    float kk[kChunk][3];     // perspective factors k_i
+};
+
+struct WorkItem {
+    int v, g, tx, ty;
+};
+
+// Work items are numbered view by view, then sample group, then tile.
+__device__ __forceinline__ WorkItem decode_item(const ViewTable& vt, int item) {
+    WorkItem w;
+    w.v = 0;
+    for (int i = 1; i < vt.n; ++i)
+        if (vt.v[i].item_base <= item) w.v = i;
+    const ViewDesc& V = vt.v[w.v];
+    const int tiles = V.tiles_x * V.tiles_y;
+    const int local = item - V.item_base;
+    w.g = local / tiles;
+    const int tile = local - w.g * tiles;
+    w.ty = tile / V.tiles_x;
+    w.tx = tile - w.ty * V.tiles_x;
+    return w;
+}
+
+// Upper bound on the inverse depth of every triangle whose sort key is at
+// least `key`: the key's depth bits are the top DB bits of the nearest
+// vertex depth, so the float they encode is <= that depth.  The bound is
+// widened by 2^-10 to cover the rounding of rho (a few ulps).
+__device__ __forceinline__ float rho_bound(uint32_t key, int DB) {
+    if (DB <= 0) return __int_as_float(0x7f800000);
+    const uint32_t q = key & ((1u << DB) - 1u);
+    const float zq = __uint_as_float(q << (31 - DB));
+    if (!(zq > 0.0f)) return __int_as_float(0x7f800000);
+    return __fmul_rn(__frcp_rn(zq), 1.0f + 0x1p-10f);
+}
+
+// Stage triangle t (set-up record in view base vbase) for tile (tx, ty).  For
+// a pixel at local offset (lx, ly) the biased edge value is
+// E'(origin) + 256 (A lx + B ly); it is >= 0 iff A lx + B ly >= thr with
+// thr = ceil(-E'(origin) / 256).  |A lx + B ly| < 2^28 inside the guard band,
+// so thr is clamped to +-2^30 and the test runs in int32.
+__device__ __forceinline__ void stage_triangle(TileStage& sm, int slot, const SetupRec* recs, size_t vbase,
+                                               uint32_t key, uint32_t t, int DB, int tx, int ty) {
+    const SetupRec r = load_rec(recs + vbase + t);
+    const long long X0 = 256LL * (kTile * tx) + 128, Y0 = 256LL * (kTile * ty) + 128;
+    int thr[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const long long eb = (long long)r.A[i] * X0 + (long long)r.B[i] * Y0 + r.C[i];
+        long long th = -(eb >> 8);
+        th = th < -(1LL << 30) ? -(1LL << 30) : (th > (1LL << 30) ? (1LL << 30) : th);
+        thr[i] = (int)th;
+        sm.eo[slot][i] = eb + ((r.bias >> i) & 1u);
+        sm.kk[slot][i] = r.k[i];
+    }
+    sm.h0[slot] = make_int4(r.A[0], r.B[0], thr[0], r.A[1]);
+    sm.h1[slot] = make_int4(r.B[1], thr[1], r.A[2], r.B[2]);
+    sm.h2[slot] = make_int4(thr[2], (int)t, __float_as_int(rho_bound(key, DB)), 0);
+}
+
+// Coverage of local pixel (lx, ly) by staged triangle j; on success E gets
+// the exact oriented edge values (int64) at the pixel centre.
+__device__ __forceinline__ bool tile_cover(const TileStage& sm, int j, int lx, int ly, long long E[3]) {
+    const int4 h0 = sm.h0[j], h1 = sm.h1[j], h2 = sm.h2[j];
+    const int a0 = h0.x * lx + h0.y * ly;
+    const int a1 = h0.w * lx + h1.x * ly;
+    const int a2 = h1.z * lx + h1.w * ly;
+    if (((a0 - h0.z) | (a1 - h1.y) | (a2 - h2.x)) < 0) return false;
+    E[0] = sm.eo[j][0] + 256LL * a0;
+    E[1] = sm.eo[j][1] + 256LL * a1;
+    E[2] = sm.eo[j][2] + 256LL * a2;
+    return true;
+}
+
+// Inverse depth of triangle `rec` at pixel (px, py) (the stored winner's
+// key, recomputed bit for bit).  +inf if the record does not cover the pixel.
+__device__ __forceinline__ float winner_rho(const SetupRec* rec, int px, int py) {
+    const SetupRec r = load_rec(rec);
+    long long E[3];
+    if (!cover_exact(r, px, py, E)) return __int_as_float(0x7f800000);
+    return make_frag(E[0], E[1], E[2], r.k[0], r.k[1], r.k[2]).rho;
+}
+
+// Decode the C-1 colour channels of triangle t at (b1, b2) into out[c * HW].
+__device__ __forceinline__ void decode_color(const SoupDev& s, int t, float b1, float b2, float* out, size_t HW) {
+    const Cell cl = find_cell(s.N, b1, b2);
+    const int C = s.C;
+    const float* base = s.act + (size_t)t * s.V * C;
+    const float* p0 = base + (size_t)cl.k0 * C;
+    const float* p1 = base + (size_t)cl.k1 * C;
+    const float* p2 = base + (size_t)cl.k2 * C;
+    if ((C & 3) == 0) {
+        for (int c4 = 0; c4 < C; c4 += 4) {
+            const float4 a0 = __ldg(reinterpret_cast<const float4*>(p0 + c4));
+            const float4 a1 = __ldg(reinterpret_cast<const float4*>(p1 + c4));
+            const float4 a2 = __ldg(reinterpret_cast<const float4*>(p2 + c4));
+            const float v[4] = {interp(a0.x, a1.x, a2.x, cl.wa, cl.wb), interp(a0.y, a1.y, a2.y, cl.wa, cl.wb),
+                                interp(a0.z, a1.z, a2.z, cl.wa, cl.wb), interp(a0.w, a1.w, a2.w, cl.wa, cl.wb)};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (c4 + k < C - 1) out[(c4 + k) * HW] = v[k];
+        }
+    } else {
+        for (int c = 0; c < C - 1; ++c)
+            out[c * HW] = interp(__ldg(p0 + c), __ldg(p1 + c), __ldg(p2 + c), cl.wa, cl.wb);
+    }
+}
+
+// Sum NV values over runs of consecutive lanes that hold the same key.  On
+// return the first lane of every run holds the run's sums; the function
+// returns true there.  All 32 lanes must call it; a lane with nothing to add
+// passes a key no other lane uses (so it forms a run of its own).
+template <int NV>
+__device__ __forceinline__ bool warp_run_sum(unsigned long long key, float (&v)[NV]) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long prev = __shfl_up_sync(kFullMask, key, 1);
+    const bool head = lane == 0 || prev != key;
+    const unsigned heads = __ballot_sync(kFullMask, head);
+    const unsigned above = heads & ~((2u << lane) - 1u);
+    const int end = above ? __ffs(above) - 1 : 32;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            const float o = __shfl_down_sync(kFullMask, v[q], d);
+            if (lane + d < end) v[q] += o;
+        }
+    }
+    return head;
+}
+
+}  // namespace ds

@@ -1,0 +1,270 @@
+"""ctypes binding of ``libdiffsoup.so`` (argument marshalling only).
+
+The names mirror the C ABI in ``include/diffsoup.h``.  Device buffers are
+passed as torch tensors (their data pointers); torch supplies the memory and
+the stream, every computation runs in the library's kernels.  There is no
+CPU fallback: if the library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libdiffsoup.so")
+HEADER = os.path.join(HERE, "..", "include", "diffsoup.h")
+
+DS_OK = 0
+DS_MODE_STOCHASTIC = 0
+DS_MODE_THRESHOLD_HALF = 1
+DS_NO_SYNC = 0x100
+DS_G_TEX, DS_G_SCORE, DS_G_INTERIOR, DS_G_EDGE = 1, 2, 4, 8
+DS_G_ALL = 15
+DS_REUSE_FORWARD = 0x100
+DS_OVERWRITE = 0x200
+DS_COPY, DS_BORROW = 0, 1
+ERRORS = {-1: "DS_ERR_INVALID_ARG", -2: "DS_ERR_OOM", -3: "DS_ERR_CUDA", -4: "DS_ERR_CAPACITY",
+          -5: "DS_ERR_TIMEOUT", -6: "DS_ERR_NOT_FOUND", -7: "DS_ERR_BUSY"}
+
+
+class DsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class ds_camera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("near_z", ctypes.c_float)]
+
+
+class ds_view_out(ctypes.Structure):
+    _fields_ = [("gbuf", ctypes.c_void_p), ("color", ctypes.c_void_p), ("n_front", ctypes.c_void_p)]
+
+
+class ds_view_gin(ctypes.Structure):
+    _fields_ = [("grad_color", ctypes.c_void_p), ("score_w", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load():
+    """Load the library (built by ``paper_2603_27151_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libdiffsoup.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    P, i32, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32
+    L.ds_version.restype = i32
+    L.ds_last_error.restype = ctypes.c_char_p
+    L.ds_create.argtypes = [ctypes.POINTER(P), i32]
+    L.ds_create.restype = i32
+    L.ds_destroy.argtypes = [P]
+    L.ds_destroy.restype = None
+    L.ds_soup_upload.argtypes = [P, P, P, i32, i32, i32, u32, ctypes.POINTER(i32), P]
+    L.ds_soup_upload.restype = i32
+    L.ds_soup_free.argtypes = [P, i32]
+    L.ds_soup_free.restype = i32
+    L.ds_raster_forward.argtypes = [P, i32, P, P, i32, i32, u32, P, P, P]
+    L.ds_raster_forward.restype = i32
+    L.ds_raster_backward.argtypes = [P, i32, P, i32, i32, P, P, u32, P, P, P]
+    L.ds_raster_backward.restype = i32
+    L.ds_fragment_count.argtypes = [P, i32, P, i32, ctypes.POINTER(ctypes.c_int64), P]
+    L.ds_fragment_count.restype = i32
+    L.ds_ctx_status.argtypes = [P]
+    L.ds_ctx_status.restype = i32
+    L.ds_profile_enable.argtypes = [P, i32]
+    L.ds_profile_enable.restype = i32
+    L.ds_profile_stages.restype = i32
+    L.ds_profile_read.argtypes = [P, i32, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int64),
+                                  ctypes.POINTER(ctypes.c_double)]
+    L.ds_profile_read.restype = i32
+    L.ds_profile_reset.argtypes = [P]
+    L.ds_profile_reset.restype = i32
+    L.ds_kernel_launches.restype = ctypes.c_int64
+    L.ds_loss_l2.argtypes = [i32, i32, i32, P, P, P, P, P, ctypes.c_float, P, P]
+    L.ds_loss_l2.restype = i32
+    L.ds_plan_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
+    L.ds_plan_stats.restype = i32
+    _lib = L
+    return L
+
+
+def declared_symbols(header: str = HEADER):
+    """Function names declared in the public header."""
+    txt = open(header).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ds_[a-z_0-9]+)\s*\(", txt)))
+
+
+def _check(rc: int):
+    if rc != DS_OK:
+        raise DsError(rc, load().ds_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def cameras(cams):
+    """Pack ``inputs.Camera`` objects into a ds_camera array."""
+    arr = (ds_camera * len(cams))()
+    for a, c in zip(arr, cams):
+        a.width, a.height = int(c.width), int(c.height)
+        a.fx, a.fy, a.cx, a.cy = float(c.fx), float(c.fy), float(c.cx), float(c.cy)
+        R = np.asarray(c.R, np.float32).reshape(9)
+        t = np.asarray(c.t, np.float32).reshape(3)
+        for i in range(9):
+            a.R[i] = float(R[i])
+        for i in range(3):
+            a.t[i] = float(t[i])
+        a.near_z = float(c.near)
+    return arr
+
+
+class Context:
+    """One library context on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        L = load()
+        h = ctypes.c_void_p()
+        _check(L.ds_create(ctypes.byref(h), int(device)))
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if self.h:
+            load().ds_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -------------------------------------------------------------- soups
+    def soup_upload(self, verts, tex, grid_n: int, borrow: bool = False, stream=None) -> int:
+        """verts: [T,3,3] float32 CUDA tensor; tex: [T,V,C] float32 CUDA tensor."""
+        assert verts.is_cuda and tex.is_cuda and verts.is_contiguous() and tex.is_contiguous()
+        T, V, C = tex.shape
+        sid = ctypes.c_int32(-1)
+        _check(load().ds_soup_upload(self.h, _ptr(verts), _ptr(tex), T, grid_n, C,
+                                     DS_BORROW if borrow else DS_COPY, ctypes.byref(sid), _stream(stream)))
+        return sid.value
+
+    def soup_free(self, soup_id: int):
+        _check(load().ds_soup_free(self.h, soup_id))
+
+    # -------------------------------------------------------------- passes
+    def raster_forward(self, soup_id, cams, seeds, S, mode, bg, gbufs, colors, n_fronts=None, stream=None):
+        """gbufs[v]: int32 [S,H,W,4] (tri_id, b1, b2, depth bit patterns);
+        colors[v]: float32 [S,C-1,H,W]; n_fronts[v]: int32 [S,H,W] or None."""
+        n = len(cams)
+        ca = cameras(cams)
+        sd = (ctypes.c_uint64 * n)(*[int(x) for x in (seeds if seeds is not None else [0] * n)])
+        bga = np.ascontiguousarray(bg, np.float32)
+        outs = (ds_view_out * n)()
+        for v in range(n):
+            outs[v].gbuf = gbufs[v].data_ptr()
+            outs[v].color = colors[v].data_ptr()
+            outs[v].n_front = n_fronts[v].data_ptr() if n_fronts is not None and n_fronts[v] is not None else None
+        _check(load().ds_raster_forward(self.h, soup_id, ca, sd, n, S, mode,
+                                        bga.ctypes.data_as(ctypes.c_void_p), outs, _stream(stream)))
+
+    def raster_backward(self, soup_id, cams, S, gbufs, colors, grad_colors, score_ws, flags,
+                        grad_verts=None, grad_tex=None, stream=None):
+        n = len(cams)
+        ca = cameras(cams)
+        fwd = (ds_view_out * n)()
+        gin = (ds_view_gin * n)()
+        for v in range(n):
+            fwd[v].gbuf = gbufs[v].data_ptr()
+            fwd[v].color = colors[v].data_ptr() if colors is not None else None
+            gin[v].grad_color = grad_colors[v].data_ptr() if grad_colors is not None else None
+            gin[v].score_w = score_ws[v].data_ptr() if score_ws is not None and score_ws[v] is not None else None
+        _check(load().ds_raster_backward(self.h, soup_id, ca, n, S, fwd, gin, flags,
+                                         _ptr(grad_verts), _ptr(grad_tex), _stream(stream)))
+
+    def fragment_count(self, soup_id, cams, stream=None) -> int:
+        n = len(cams)
+        out = ctypes.c_int64(0)
+        _check(load().ds_fragment_count(self.h, soup_id, cameras(cams), n, ctypes.byref(out), _stream(stream)))
+        return out.value
+
+    def status(self):
+        _check(load().ds_ctx_status(self.h))
+
+    def plan_stats(self):
+        """(pairs, tiles) of the current binning plan."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().ds_plan_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    # -------------------------------------------------------------- profiling
+    def profile(self, on: bool = True):
+        _check(load().ds_profile_enable(self.h, 1 if on else 0))
+
+    def profile_reset(self):
+        _check(load().ds_profile_reset(self.h))
+
+    def profile_read(self) -> dict:
+        """{stage: (runs, total device ms)} since the last reset."""
+        L = load()
+        out = {}
+        for i in range(L.ds_profile_stages()):
+            name = ctypes.c_char_p()
+            n = ctypes.c_int64()
+            ms = ctypes.c_double()
+            _check(L.ds_profile_read(self.h, i, ctypes.byref(name), ctypes.byref(n), ctypes.byref(ms)))
+            out[name.value.decode()] = (n.value, ms.value)
+        return out
+
+
+def loss_l2(colors, targets, grad_colors=None, score_ws=None, loss=None, scale=1.0, stream=None):
+    """Fused L2 loss (see ds_loss_l2).  colors[v] [S,C-1,H,W]; targets[v]
+    [C-1,H,W]; outputs written in place; loss: 1-element float32 tensor (+=)."""
+    n = len(colors)
+    S, Co, H0, W0 = colors[0].shape
+    hw = (ctypes.c_int32 * (2 * n))()
+    arr = lambda ts: None if ts is None else (ctypes.c_void_p * n)(*[t.data_ptr() for t in ts])
+    for v, c in enumerate(colors):
+        hw[2 * v], hw[2 * v + 1] = int(c.shape[3]), int(c.shape[2])
+    _check(load().ds_loss_l2(n, S, Co + 1, hw, arr(colors), arr(targets), arr(grad_colors), arr(score_ws),
+                             float(scale), _ptr(loss), _stream(stream)))
+
+
+def kernel_launches() -> int:
+    return int(load().ds_kernel_launches())
+
+
+def alloc_outputs(cams, S, C, device="cuda", n_front=False):
+    """Allocate per-view G-buffers [S,H,W,4] int32, colours [S,C-1,H,W] and
+    optional n_front [S,H,W]."""
+    import torch
+    g = [torch.empty((S, c.height, c.width, 4), dtype=torch.int32, device=device) for c in cams]
+    col = [torch.empty((S, C - 1, c.height, c.width), dtype=torch.float32, device=device) for c in cams]
+    nf = [torch.empty((S, c.height, c.width), dtype=torch.int32, device=device) for c in cams] if n_front else None
+    return g, col, nf
+
+
+def split_gbuf(g):
+    """(tri_id int32, bary float32 [...,2], depth float32) views of a G-buffer."""
+    import torch
+    tri = g[..., 0]
+    f = g.view(torch.float32)
+    return tri, f[..., 1:3], f[..., 3]

@@ -180,8 +180,9 @@ DS_API ds_status ds_raster_forward(ds_ctx* ctx, int32_t soup_id, const ds_camera
  * Score term: for every sample with weight w = score_w, +w/alpha for the
  * selected fragment and -w/(1-alpha) for every covered fragment in front of
  * it (all covered fragments when the sample shows the background), chained
- * to the opacity logits.  Uses floating-point atomics: summation order, and
- * so the last bits, vary from run to run. */
+ * to the opacity logits.  Contributions are summed in FP64 scratch with
+ * atomics (summation order varies from run to run) and added to the FP32
+ * outputs at the end. */
 DS_API ds_status ds_raster_backward(ds_ctx* ctx, int32_t soup_id, const ds_camera* cams,
                              int32_t n_views, int32_t S, const ds_view_out* fwd,
                              const ds_view_gin* gin, uint32_t grad_flags, float* grad_verts,
@@ -222,7 +223,7 @@ DS_API ds_status ds_ctx_status(ds_ctx* ctx);
 /* Profiling (off by default; no paper counterpart: instrumentation).  While
  * enabled, every pipeline stage that a call on this context launches
  * (activate, setup, scan, emit, sort, ranges, raster_fwd, count, geom,
- * raster_bwd, edge_bwd) is bracketed by two CUDA events recorded on the caller's stream.
+ * raster_bwd, edge_bwd, finish) is bracketed by two CUDA events recorded on the caller's stream.
  * ds_profile_read waits for those events and returns, for stage index
  * `stage` in [0, ds_profile_stages()), its name (static host string), the
  * number of times it ran and its summed device time in ms since the last

@@ -94,6 +94,7 @@ struct ds_ctx {
     std::mutex mu;
     std::vector<Soup> soups;
     DevBuf recs, counts, offs, tbox, zkeys, keys[2], vals[2], hist, hist_scan, ranges, scanbuf, misc, geom;
+    DevBuf acc_tex, acc_verts;   // FP64 gradient accumulators of the backward
     ds::ScanScratch scan;
     int64_t scan_cap = 0;
     uint32_t* h_word = nullptr;   // pinned host words
@@ -424,7 +425,7 @@ void ds_destroy(ds_ctx* c) {
     }
     DevBuf* bufs[] = {&c->recs,  &c->counts,  &c->offs,      &c->tbox,   &c->zkeys,   &c->keys[0], &c->keys[1],
                       &c->vals[0], &c->vals[1], &c->hist, &c->hist_scan, &c->ranges, &c->scanbuf, &c->misc,
-                      &c->geom};
+                      &c->geom, &c->acc_tex, &c->acc_verts};
     for (DevBuf* b : bufs) b->release();
     if (c->h_word) cudaFreeHost(c->h_word);
     for (auto& r : c->prof_pending) {
@@ -578,29 +579,45 @@ ds_status ds_raster_backward(ds_ctx* c, int32_t soup_id, const ds_camera* cams, 
     const ds::SoupDev sd = soup_dev(*s);
     const int grid = ds::persistent_grid(vt.n_items, 2);
     const uint32_t gflags = grad_flags & DS_G_ALL;
-    if (grad_flags & DS_OVERWRITE) {
-        if (grad_tex) DS_TRY_CUDA(cudaMemsetAsync(grad_tex, 0, sizeof(float) * (size_t)s->T * s->V * s->C, st));
-        if (grad_verts) DS_TRY_CUDA(cudaMemsetAsync(grad_verts, 0, sizeof(float) * 9 * (size_t)s->T, st));
+    const size_t n_tex = (size_t)s->T * s->V * s->C, n_verts = 9 * (size_t)s->T;
+    const bool want_tex = grad_tex && (gflags & (DS_G_TEX | DS_G_SCORE));
+    const bool want_verts = grad_verts && (gflags & (DS_G_INTERIOR | DS_G_EDGE));
+    const bool overwrite = (grad_flags & DS_OVERWRITE) != 0;
+    double* acc_tex = nullptr;
+    double* acc_verts = nullptr;
+    if (want_tex) {
+        DS_TRY(c->acc_tex.ensure(sizeof(double) * n_tex, "texture gradient accumulator"));
+        acc_tex = c->acc_tex.as<double>();
+        DS_TRY_CUDA(cudaMemsetAsync(acc_tex, 0, sizeof(double) * n_tex, st));
     }
-    const bool need_geom = grad_verts && (gflags & (DS_G_INTERIOR | DS_G_EDGE));
-    if (need_geom) {
+    if (want_verts) {
+        DS_TRY(c->acc_verts.ensure(sizeof(double) * n_verts, "vertex gradient accumulator"));
+        acc_verts = c->acc_verts.as<double>();
+        DS_TRY_CUDA(cudaMemsetAsync(acc_verts, 0, sizeof(double) * n_verts, st));
         DS_TRY(c->geom.ensure(sizeof(ds::GeomRec) * (size_t)n_views * s->T, "vertex-gradient geometry"));
         StageScope p(c, ds::kStGeom, st);
         DS_TRY_CUDA(ds::launch_geom(vt, sd, c->geom.as<ds::GeomRec>(), st));
     }
-    if (((gflags & (DS_G_TEX | DS_G_SCORE)) && grad_tex) || ((gflags & DS_G_INTERIOR) && grad_verts)) {
+    if (want_tex || (want_verts && (gflags & DS_G_INTERIOR))) {
         StageScope p(c, ds::kStRasterBwd, st);
         DS_TRY_CUDA(cudaMemsetAsync(c->d_counter() + 2, 0, 4, st));
         DS_TRY_CUDA(ds::launch_raster_bwd(vt, sd, c->recs.as<ds::SetupRec>(), c->keys[c->plan.res].as<uint32_t>(),
                                           c->vals[c->plan.res].as<uint32_t>(), c->ranges.as<uint2>(), c->plan.DB,
-                                          gflags, c->geom.as<ds::GeomRec>(), grad_tex, grad_verts, c->d_counter() + 2,
+                                          gflags, c->geom.as<ds::GeomRec>(), acc_tex, acc_verts, c->d_counter() + 2,
                                           grid, st));
     }
-    if ((gflags & DS_G_EDGE) && grad_verts) {
+    if (want_verts && (gflags & DS_G_EDGE)) {
         StageScope p(c, ds::kStEdgeBwd, st);
         DS_TRY_CUDA(cudaMemsetAsync(c->d_counter() + 3, 0, 4, st));
-        DS_TRY_CUDA(ds::launch_edge_bwd(vt, sd, c->recs.as<ds::SetupRec>(), c->geom.as<ds::GeomRec>(), grad_verts,
+        DS_TRY_CUDA(ds::launch_edge_bwd(vt, sd, c->recs.as<ds::SetupRec>(), c->geom.as<ds::GeomRec>(), acc_verts,
                                         c->d_counter() + 3, grid, st));
+    }
+    {
+        StageScope p(c, ds::kStFinish, st);
+        if (want_tex) DS_TRY_CUDA(ds::launch_grad_finish(acc_tex, grad_tex, (long long)n_tex, overwrite, st));
+        else if (grad_tex && overwrite) DS_TRY_CUDA(cudaMemsetAsync(grad_tex, 0, sizeof(float) * n_tex, st));
+        if (want_verts) DS_TRY_CUDA(ds::launch_grad_finish(acc_verts, grad_verts, (long long)n_verts, overwrite, st));
+        else if (grad_verts && overwrite) DS_TRY_CUDA(cudaMemsetAsync(grad_verts, 0, sizeof(float) * n_verts, st));
     }
     return DS_OK;
 }

@@ -1,5 +1,6 @@
 // ds_backward.cu -- gradients of the stochastic rasteriser.
 //
+//  k_geom: per (view, triangle) FP64 geometry for the vertex gradients.
 //  k_raster_bwd: Algorithm A1 step 2 by G-buffer recomputation.  Every tile
 //    list is walked again (front to back, stopping early) to find the covered
 //    fragments in front of each stored winner: they get -w/(1-alpha) (Eq. 9);
@@ -8,10 +9,13 @@
 //  k_edge_bwd: edge gradients on every horizontal and vertical pixel pair of
 //    the sampled image (Sec. 3.2): silhouettes of the winning triangle and
 //    mask-induced boundaries inside it.
+//  k_grad_finish: adds the FP64 accumulators to the caller's FP32 gradients.
 //
 // Scatter: lanes holding the same target (texel cell or triangle) in
 // consecutive lanes are summed in registers first (warp_run_sum); only the
-// first lane of each run issues the atomics.
+// first lane of each run issues the atomics, which accumulate in FP64 so that
+// the summation order of the many opposite-signed score terms does not limit
+// the result's accuracy.
 #include "ds_internal.h"
 #include "ds_tile.cuh"
 
@@ -26,16 +30,8 @@ struct f3 {
     float x, y, z;
 };
 __device__ __forceinline__ f3 mk3(float x, float y, float z) { return f3{x, y, z}; }
-__device__ __forceinline__ f3 sub3(f3 a, f3 b) { return mk3(a.x - b.x, a.y - b.y, a.z - b.z); }
 __device__ __forceinline__ f3 cross3(f3 a, f3 b) {
     return mk3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
-__device__ __forceinline__ float dot3(f3 a, f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-
-__device__ __forceinline__ f3 to_cam(const DevCam& c, const float* p) {
-    const float x = __ldg(p), y = __ldg(p + 1), z = __ldg(p + 2);
-    return mk3(c.R[0] * x + c.R[1] * y + c.R[2] * z + c.t[0], c.R[3] * x + c.R[4] * y + c.R[5] * z + c.t[1],
-               c.R[6] * x + c.R[7] * y + c.R[8] * z + c.t[2]);
 }
 
 // world-space gradient R^T g
@@ -44,175 +40,18 @@ __device__ __forceinline__ f3 to_world(const DevCam& c, f3 g) {
                c.R[2] * g.x + c.R[5] * g.y + c.R[8] * g.z);
 }
 
-// Ray-plane barycentrics of camera-space triangle V with ray direction d
-// (z = 1), written with edge vectors so that small, distant triangles do not
-// cancel: n1 = d.(e2 x V0), n2 = d.(V0 x e1), S = d.(e1 x e2), n0 = S - n1 - n2.
-struct RayBary {
-    float n[3];
-    float S;
-};
-__device__ __forceinline__ RayBary ray_bary(const f3 V[3], f3 d) {
-    const f3 e1 = sub3(V[1], V[0]), e2 = sub3(V[2], V[0]);
-    RayBary rb;
-    rb.S = dot3(d, cross3(e1, e2));
-    rb.n[1] = dot3(d, cross3(e2, V[0]));
-    rb.n[2] = dot3(d, cross3(V[0], e1));
-    rb.n[0] = rb.S - rb.n[1] - rb.n[2];
-    return rb;
-}
+__device__ __forceinline__ float2 ld2(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ f3 ld3(const float* p) { return mk3(__ldg(p), __ldg(p + 1), __ldg(p + 2)); }
 
-// ------------------------------------------------------------ texture scatter
-// Adds (for one lane) g_m = val[m] to channel c of the three corner texels of
-// cell `cl` of triangle t, chained through the sigmoid: += g_m a (1 - a).
-__device__ __forceinline__ void scatter_alpha_run(const SoupDev& s, float* grad_tex, bool act, int t, const Cell& cl,
-                                                  float g) {
-    float v[3] = {0.f, 0.f, 0.f};
-    unsigned long long key = lane_sentinel();
-    if (act) {
-        v[0] = g * (1.0f - cl.wa - cl.wb);
-        v[1] = g * cl.wa;
-        v[2] = g * cl.wb;
-        key = ((unsigned long long)(unsigned)t << 20) | ((unsigned)cl.k0 << 1) | (cl.lower ? 1u : 0u);
-    }
-    const bool head = warp_run_sum<3>(key, v);
-    if (act && head) {
-        const float* aa = s.act_a + (size_t)t * s.V;
-        const int ks[3] = {cl.k0, cl.k1, cl.k2};
-#pragma unroll
-        for (int m = 0; m < 3; ++m) {
-            const float a = __ldg(aa + ks[m]);
-            atomicAdd(grad_tex + ((size_t)t * s.V + ks[m]) * s.C + (s.C - 1), v[m] * a * (1.0f - a));
-        }
-    }
-}
-
-// Winner terms of one sample: colour gradient (C-1 channels) and the +w/alpha
-// opacity score, merged into one pass over the corner texels, four channels
-// at a time.  Returns dL/d(b1, b2) of the colour through G.
-template <bool kInterior>
-__device__ __forceinline__ void winner_texture(const SoupDev& s, float* grad_tex, bool act, int t, float b1, float b2,
-                                               const float* gcol, size_t HW, float wscore, bool do_tex,
-                                               bool do_score, float G[2]) {
-    Cell cl;
-    cl.k0 = cl.k1 = cl.k2 = 0;
-    cl.wa = cl.wb = 0.f;
-    cl.lower = true;
-    if (act) cl = find_cell(s.N, b1, b2);
-    const float w0 = 1.0f - cl.wa - cl.wb;
-    const float sgnN = cl.lower ? (float)s.N : -(float)s.N;
-    const int C = s.C;
-    const float* base = s.act + (size_t)(act ? t : 0) * s.V * C;
-    float alpha_g = 0.f;
-    if (act && do_score && wscore != 0.0f) {
-        const float* aa = s.act_a + (size_t)t * s.V;
-        const float alpha = interp(__ldg(aa + cl.k0), __ldg(aa + cl.k1), __ldg(aa + cl.k2), cl.wa, cl.wb);
-        alpha_g = wscore / alpha;
-    }
-    G[0] = G[1] = 0.f;
-    const unsigned long long key =
-        act ? (((unsigned long long)(unsigned)t << 20) | ((unsigned)cl.k0 << 1) | (cl.lower ? 1u : 0u)) : lane_sentinel();
-    for (int c4 = 0; c4 < C; c4 += 4) {
-        float v[12];
-#pragma unroll
-        for (int k = 0; k < 12; ++k) v[k] = 0.f;
-        if (act) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int c = c4 + k;
-                if (c >= C) break;
-                float g = 0.f;
-                if (c < C - 1) {
-                    g = (do_tex || kInterior) ? __ldg(gcol + c * HW) : 0.f;
-                    if (kInterior) {
-                        const float a0 = __ldg(base + (size_t)cl.k0 * C + c);
-                        const float a1 = __ldg(base + (size_t)cl.k1 * C + c);
-                        const float a2 = __ldg(base + (size_t)cl.k2 * C + c);
-                        G[0] += g * sgnN * (a1 - a0);
-                        G[1] += g * sgnN * (a2 - a0);
-                    }
-                    if (!do_tex) g = 0.f;
-                } else {
-                    g = alpha_g;
-                }
-                v[k] = g * w0;
-                v[4 + k] = g * cl.wa;
-                v[8 + k] = g * cl.wb;
-            }
-        }
-        bool any = false;
-#pragma unroll
-        for (int k = 0; k < 12; ++k) any = any || v[k] != 0.f;
-        if (!__any_sync(kFullMask, act && any)) continue;
-        const bool head = warp_run_sum<12>(key, v);
-        if (act && head) {
-            const int ks[3] = {cl.k0, cl.k1, cl.k2};
-#pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                const float* ap = base + (size_t)ks[m] * C + c4;
-                float* gp = grad_tex + ((size_t)t * s.V + ks[m]) * C + c4;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if (c4 + k >= C) break;
-                    const float g = v[4 * m + k];
-                    if (g != 0.f) {
-                        const float a = __ldg(ap + k);
-                        atomicAdd(gp + k, g * a * (1.0f - a));
-                    }
-                }
-            }
-        }
-    }
-}
-
-// Nine-float vertex gradient of triangle t summed over runs of lanes.
-__device__ __forceinline__ void scatter_verts_run(float* grad_verts, bool act, int t, float (&g)[9]) {
-    const unsigned long long key = act ? (unsigned long long)(unsigned)t : lane_sentinel();
-    if (!__any_sync(kFullMask, act)) return;
-    const bool head = warp_run_sum<9>(key, g);
-    if (act && head) {
-        float* p = grad_verts + 9 * (size_t)t;
-#pragma unroll
-        for (int k = 0; k < 9; ++k)
-            if (g[k] != 0.f) atomicAdd(p + k, g[k]);
-    }
-}
-
-// Interior term at pixel (px, py).  With X = sum_i b_i V_i on the fixed ray
-// d, moving vertex m gives e1 db1 + e2 db2 = dlambda d - b_m dV_m; crossing
-// with d: db1/dV_m = -b_m (e2 x d) / S, db2/dV_m = -b_m (d x e1) / S with
-// S = d.(e1 x e2).  So dL/dV_m = -(b_m / S) [G1 (e2 x d) + G2 (d x e1)].
-// S and the barycentric numerators come from Dot2 on FP64-derived vectors
-// (grazing triangles make them small differences of O(1) terms).
-__device__ __forceinline__ void interior_grad(const GeomRec& g, const DevCam& cam, int px, int py, const float G[2],
-                                              float (&out)[9]) {
-    float dx, dy;
-    pinned_ray(cam, (float)px + 0.5f, (float)py + 0.5f, dx, dy);
-    const float S = dot2(dx, dy, 1.0f, g.n);
-    const float n1 = dot2(dx, dy, 1.0f, g.m1), n2 = dot2(dx, dy, 1.0f, g.m2);
-    const float inv = 1.0f / S;
-    const float b[3] = {(S - n1 - n2) * inv, n1 * inv, n2 * inv};
-    const f3 d = mk3(dx, dy, 1.0f);
-    const f3 e1 = mk3(g.e1[0], g.e1[1], g.e1[2]), e2 = mk3(g.e2[0], g.e2[1], g.e2[2]);
-    const f3 c1 = cross3(e2, d), c2 = cross3(d, e1);
-    const f3 u = mk3(G[0] * c1.x + G[1] * c2.x, G[0] * c1.y + G[1] * c2.y, G[0] * c1.z + G[1] * c2.z);
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-        const float k = -b[m] * inv;
-        const f3 gw = to_world(cam, mk3(k * u.x, k * u.y, k * u.z));
-        out[3 * m] = gw.x;
-        out[3 * m + 1] = gw.y;
-        out[3 * m + 2] = gw.z;
-    }
-}
-
-// FP64 geometry record of every (view, triangle): camera-space positions and
-// screen projection as the oracle computes them, stored for compensated FP32
-// use (see GeomRec).
+// ------------------------------------------------------------ FP64 geometry
 __device__ __forceinline__ float2 split2(double x) {
     const float hi = (float)x;
     return make_float2(hi, (float)(x - (double)hi));
 }
 
+// Camera-space positions and screen projection of every (view, triangle) as
+// the oracle computes them (FP64 from the FP32 inputs), stored for
+// compensated FP32 use (see GeomRec).
 __global__ void k_geom(const __grid_constant__ ViewTable vt, const SoupDev s, GeomRec* __restrict__ out) {
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (gid >= (long long)vt.n * s.T) return;
@@ -264,13 +103,154 @@ __global__ void k_geom(const __grid_constant__ ViewTable vt, const SoupDev s, Ge
     for (int k = 0; k < 13; ++k) dst[k] = src[k];
 }
 
-__device__ __forceinline__ GeomRec load_geom(const GeomRec* p) {
-    GeomRec g;
-    const int4* q = reinterpret_cast<const int4*>(p);
-    int4* d = reinterpret_cast<int4*>(&g);
+// Barycentrics (beta0, beta1, beta2) and 1/S of the hit of the pinned ray
+// through screen point (x, y) with the plane of the triangle (Dot2 on the
+// FP64-derived vectors: grazing triangles make S and the numerators small
+// differences of O(1) terms).
+__device__ __forceinline__ void ray_bary(const GeomRec* g, const DevCam& cam, float x, float y, float& dx, float& dy,
+                                         float b[3], float& inv) {
+    pinned_ray(cam, x, y, dx, dy);
+    const float2 n[3] = {ld2(&g->n[0]), ld2(&g->n[1]), ld2(&g->n[2])};
+    const float2 m1[3] = {ld2(&g->m1[0]), ld2(&g->m1[1]), ld2(&g->m1[2])};
+    const float2 m2[3] = {ld2(&g->m2[0]), ld2(&g->m2[1]), ld2(&g->m2[2])};
+    const float S = dot2(dx, dy, 1.0f, n);
+    const float n1 = dot2(dx, dy, 1.0f, m1), n2 = dot2(dx, dy, 1.0f, m2);
+    inv = 1.0f / S;
+    b[0] = (S - n1 - n2) * inv;
+    b[1] = n1 * inv;
+    b[2] = n2 * inv;
+}
+
+// ------------------------------------------------------------ texture scatter
+// Opacity-channel score gradient g of one lane's fragment (cell cl of
+// triangle t), chained through the interpolation weights and the sigmoid.
+__device__ __forceinline__ void scatter_alpha_run(const SoupDev& s, double* acc_tex, bool act, int t, const Cell& cl,
+                                                  float g) {
+    float v[3] = {0.f, 0.f, 0.f};
+    unsigned long long key = lane_sentinel();
+    if (act) {
+        v[0] = g * (1.0f - cl.wa - cl.wb);
+        v[1] = g * cl.wa;
+        v[2] = g * cl.wb;
+        key = ((unsigned long long)(unsigned)t << 20) | ((unsigned)cl.k0 << 1) | (cl.lower ? 1u : 0u);
+    }
+    const bool head = warp_run_sum<3>(key, v);
+    if (act && head) {
+        const float* aa = s.act_a + (size_t)t * s.V;
+        const int ks[3] = {cl.k0, cl.k1, cl.k2};
 #pragma unroll
-    for (int k = 0; k < 13; ++k) d[k] = __ldg(q + k);
-    return g;
+        for (int m = 0; m < 3; ++m) {
+            const float a = __ldg(aa + ks[m]);
+            atomicAdd(acc_tex + ((size_t)t * s.V + ks[m]) * s.C + (s.C - 1), (double)(v[m] * a * (1.0f - a)));
+        }
+    }
+}
+
+// Winner terms of one sample: colour gradient (C-1 channels) and the +w/alpha
+// opacity score, merged into one pass over the corner texels, four channels
+// at a time.  G receives dL/d(b1, b2) of the colour (for the interior term).
+template <bool kInterior>
+__device__ __forceinline__ void winner_texture(const SoupDev& s, double* acc_tex, bool act, int t, float b1, float b2,
+                                               const float* gcol, size_t HW, float wscore, bool do_tex,
+                                               bool do_score, float G[2]) {
+    Cell cl;
+    cl.k0 = cl.k1 = cl.k2 = 0;
+    cl.wa = cl.wb = 0.f;
+    cl.lower = true;
+    if (act) cl = find_cell(s.N, b1, b2);
+    const float w0 = 1.0f - cl.wa - cl.wb;
+    const float sgnN = cl.lower ? (float)s.N : -(float)s.N;
+    const int C = s.C;
+    const float* base = s.act + (size_t)(act ? t : 0) * s.V * C;
+    float alpha_g = 0.f;
+    if (act && do_score && wscore != 0.0f) {
+        const float* aa = s.act_a + (size_t)t * s.V;
+        const float alpha = interp(__ldg(aa + cl.k0), __ldg(aa + cl.k1), __ldg(aa + cl.k2), cl.wa, cl.wb);
+        alpha_g = wscore / alpha;
+    }
+    G[0] = G[1] = 0.f;
+    const unsigned long long key =
+        act ? (((unsigned long long)(unsigned)t << 20) | ((unsigned)cl.k0 << 1) | (cl.lower ? 1u : 0u)) : lane_sentinel();
+    for (int c4 = 0; c4 < C; c4 += 4) {
+        float v[12];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) v[k] = 0.f;
+        if (act) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int c = c4 + k;
+                if (c >= C) break;
+                const float a0 = __ldg(base + (size_t)cl.k0 * C + c);
+                const float a1 = __ldg(base + (size_t)cl.k1 * C + c);
+                const float a2 = __ldg(base + (size_t)cl.k2 * C + c);
+                float g = 0.f;
+                if (c < C - 1) {
+                    g = (do_tex || kInterior) ? __ldg(gcol + c * HW) : 0.f;
+                    if (kInterior) {
+                        G[0] += g * sgnN * (a1 - a0);
+                        G[1] += g * sgnN * (a2 - a0);
+                    }
+                    if (!do_tex) g = 0.f;
+                } else {
+                    g = alpha_g;
+                }
+                v[k] = g * w0 * a0 * (1.0f - a0);
+                v[4 + k] = g * cl.wa * a1 * (1.0f - a1);
+                v[8 + k] = g * cl.wb * a2 * (1.0f - a2);
+            }
+        }
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) any = any || v[k] != 0.f;
+        if (!__any_sync(kFullMask, act && any)) continue;
+        const bool head = warp_run_sum<12>(key, v);
+        if (act && head) {
+            const int ks[3] = {cl.k0, cl.k1, cl.k2};
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                double* gp = acc_tex + ((size_t)t * s.V + ks[m]) * C + c4;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (c4 + k >= C) break;
+                    if (v[4 * m + k] != 0.f) atomicAdd(gp + k, (double)v[4 * m + k]);
+                }
+            }
+        }
+    }
+}
+
+// Nine-float vertex gradient of triangle t summed over runs of lanes.
+__device__ __forceinline__ void scatter_verts_run(double* acc_verts, bool act, int t, float (&g)[9]) {
+    if (!__any_sync(kFullMask, act)) return;
+    const unsigned long long key = act ? (unsigned long long)(unsigned)t : lane_sentinel();
+    const bool head = warp_run_sum<9>(key, g);
+    if (act && head) {
+        double* p = acc_verts + 9 * (size_t)t;
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            if (g[k] != 0.f) atomicAdd(p + k, (double)g[k]);
+    }
+}
+
+// Interior term at pixel (px, py).  With X = sum_i b_i V_i on the fixed ray
+// d, moving vertex m gives e1 db1 + e2 db2 = dlambda d - b_m dV_m; crossing
+// with d: db1/dV_m = -b_m (e2 x d) / S, db2/dV_m = -b_m (d x e1) / S with
+// S = d.(e1 x e2).  So dL/dV_m = -(b_m / S) [G1 (e2 x d) + G2 (d x e1)].
+__device__ __forceinline__ void interior_grad(const GeomRec* g, const DevCam& cam, int px, int py, const float G[2],
+                                              float (&out)[9]) {
+    float dx, dy, b[3], inv;
+    ray_bary(g, cam, (float)px + 0.5f, (float)py + 0.5f, dx, dy, b, inv);
+    const f3 d = mk3(dx, dy, 1.0f);
+    const f3 c1 = cross3(ld3(g->e2), d), c2 = cross3(d, ld3(g->e1));
+    const f3 u = mk3(G[0] * c1.x + G[1] * c2.x, G[0] * c1.y + G[1] * c2.y, G[0] * c1.z + G[1] * c2.z);
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+        const float k = -b[m] * inv;
+        const f3 gw = to_world(cam, mk3(k * u.x, k * u.y, k * u.z));
+        out[3 * m] = gw.x;
+        out[3 * m + 1] = gw.y;
+        out[3 * m + 2] = gw.z;
+    }
 }
 
 template <int SG>
@@ -278,14 +258,14 @@ __global__ void __launch_bounds__(kTilePix, 2)
     k_raster_bwd(const __grid_constant__ ViewTable vt, const SoupDev s, const SetupRec* __restrict__ recs,
                  const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
                  const uint2* __restrict__ ranges, int DB, uint32_t flags, const GeomRec* __restrict__ geom,
-                 float* __restrict__ grad_tex, float* __restrict__ grad_verts, int* __restrict__ counter) {
+                 double* __restrict__ acc_tex, double* __restrict__ acc_verts, int* __restrict__ counter) {
     __shared__ TileStage sm;
     __shared__ int s_item;
     const int tid = threadIdx.x;
     const int lx = tid & (kTile - 1), ly = tid / kTile;
-    const bool do_tex = (flags & DS_G_TEX) && grad_tex;
-    const bool do_score = (flags & DS_G_SCORE) && grad_tex;
-    const bool do_int = (flags & DS_G_INTERIOR) && grad_verts;
+    const bool do_tex = (flags & DS_G_TEX) && acc_tex;
+    const bool do_score = (flags & DS_G_SCORE) && acc_tex;
+    const bool do_int = (flags & DS_G_INTERIOR) && acc_verts;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
@@ -366,7 +346,7 @@ __global__ void __launch_bounds__(kTilePix, 2)
                                 act = true;
                             }
                         }
-                        if (__any_sync(kFullMask, act)) scatter_alpha_run(s, grad_tex, act, t, cl, g);
+                        if (__any_sync(kFullMask, act)) scatter_alpha_run(s, acc_tex, act, t, cl, g);
                     }
                 }
                 if (__syncthreads_and(warp_done)) break;
@@ -380,15 +360,15 @@ __global__ void __launch_bounds__(kTilePix, 2)
             const float* gcol = V.grad_color + (size_t)(s0 + (q < ns ? q : 0)) * (s.C - 1) * HW + pix;
             float G[2];
             if (do_int)
-                winner_texture<true>(s, grad_tex, act, wt[q], wb1[q], wb2[q], gcol, HW, wsc[q], do_tex, do_score, G);
+                winner_texture<true>(s, acc_tex, act, wt[q], wb1[q], wb2[q], gcol, HW, wsc[q], do_tex, do_score, G);
             else if (do_tex || do_score)
-                winner_texture<false>(s, grad_tex, act, wt[q], wb1[q], wb2[q], gcol, HW, wsc[q], do_tex, do_score, G);
+                winner_texture<false>(s, acc_tex, act, wt[q], wb1[q], wb2[q], gcol, HW, wsc[q], do_tex, do_score, G);
             if (do_int) {
                 float gv[9];
 #pragma unroll
                 for (int k = 0; k < 9; ++k) gv[k] = 0.f;
-                if (act) interior_grad(load_geom(geom + (size_t)wi.v * s.T + wt[q]), V.cam, px, py, G, gv);
-                scatter_verts_run(grad_verts, act, wt[q], gv);
+                if (act) interior_grad(geom + (size_t)wi.v * s.T + wt[q], V.cam, px, py, G, gv);
+                scatter_verts_run(acc_verts, act, wt[q], gv);
             }
         }
         __syncthreads();
@@ -403,41 +383,39 @@ __device__ __forceinline__ float rel(float2 s, float x) {
     return __fadd_rn(d, __fadd_rn(e, s.y));
 }
 
+__device__ __forceinline__ void add_world(const DevCam& cam, f3 gc, float* out) {
+    const f3 gw = to_world(cam, gc);
+    out[0] += gw.x;
+    out[1] += gw.y;
+    out[2] += gw.z;
+}
+
 // Contribution of side X of a pixel pair (X -> Y along unit axis e = (ex, ey))
 // whose winner triangle is t: silhouette or mask-induced (implicit) boundary.
 // phi = 1/2 sum_c (g_X + g_Y)(C_X - C_Y).  Returns false if X is not in front.
-__device__ bool edge_side(const DevCam& cam, const SetupRec* vrec, const GeomRec* vgeom, int t, int xX, int yX,
-                          int xY, int yY, int tY, float phi, float (&out)[9]) {
+// Every array index is a compile-time constant (no local memory).
+__device__ __forceinline__ bool edge_side(const DevCam& cam, const SetupRec* vrec, const GeomRec* g, int t, int xX,
+                                          int yX, int xY, int yY, int tY, float phi, float (&out)[9]) {
     const SetupRec r = load_rec(vrec + t);
     long long E[3];
-    const int ex = xY - xX, ey = yY - yX;
-    const GeomRec g = load_geom(vgeom + t);
+    const float ex = (float)(xY - xX), ey = (float)(yY - yX);
     if (cover_exact(r, xY, yY, E)) {
         const float rho = make_frag(E[0], E[1], E[2], r.k[0], r.k[1], r.k[2]).rho;
-        if (tY >= 0) {
-            const float ry = winner_rho(vrec + tY, xY, yY);
-            if (!in_front(rho, t, ry, tY)) return false;   // occluded at Y
-        }
+        if (tY >= 0 && !in_front(rho, t, winner_rho(vrec + tY, xY, yY), tY)) return false;   // occluded at Y
         // implicit boundary: the material point under the pair's midpoint
         // moves with the surface; weight 1 per pair axis
-        float dx, dy;
-        pinned_ray(cam, 0.5f * (float)(xX + xY + 1), 0.5f * (float)(yX + yY + 1), dx, dy);
-        const float S = dot2(dx, dy, 1.0f, g.n);
-        const float n1 = dot2(dx, dy, 1.0f, g.m1), n2 = dot2(dx, dy, 1.0f, g.m2);
-        const float inv = 1.0f / S;
-        const float beta[3] = {(S - n1 - n2) * inv, n1 * inv, n2 * inv};
-        const f3 P = mk3(g.v0[0] + beta[1] * g.e1[0] + beta[2] * g.e2[0], g.v0[1] + beta[1] * g.e1[1] + beta[2] * g.e2[1],
-                         g.v0[2] + beta[1] * g.e1[2] + beta[2] * g.e2[2]);
+        float dx, dy, beta[3], inv;
+        ray_bary(g, cam, 0.5f * (float)(xX + xY + 1), 0.5f * (float)(yX + yY + 1), dx, dy, beta, inv);
+        const f3 e1 = ld3(g->e1), e2 = ld3(g->e2), v0 = ld3(g->v0);
+        const f3 P = mk3(v0.x + beta[1] * e1.x + beta[2] * e2.x, v0.y + beta[1] * e1.y + beta[2] * e2.y,
+                         v0.z + beta[1] * e1.z + beta[2] * e2.z);
         const float iz = 1.0f / P.z;
         // J^T e with J rows (fx/z, 0, -fx x/z^2), (0, fy/z, -fy y/z^2)
         const f3 je = mk3(ex * cam.fx * iz, ey * cam.fy * iz, -(ex * cam.fx * P.x + ey * cam.fy * P.y) * iz * iz);
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
             const float f = phi * beta[m];
-            const f3 gw = to_world(cam, mk3(f * je.x, f * je.y, f * je.z));
-            out[3 * m] += gw.x;
-            out[3 * m + 1] += gw.y;
-            out[3 * m + 2] += gw.z;
+            add_world(cam, mk3(f * je.x, f * je.y, f * je.z), out + 3 * m);
         }
         return true;
     }
@@ -447,19 +425,18 @@ __device__ bool edge_side(const DevCam& cam, const SetupRec* vrec, const GeomRec
     float sx[3], sy[3];
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-        sx[m] = rel(g.sx[m], cxX);
-        sy[m] = rel(g.sy[m], cyX);
+        sx[m] = rel(ld2(&g->sx[m]), cxX);
+        sy[m] = rel(ld2(&g->sy[m]), cyX);
     }
     const float area = diff_prod(sx[1] - sx[0], sy[2] - sy[0], sx[2] - sx[0], sy[1] - sy[0]);
     const float sg = area > 0.f ? 1.f : -1.f;
-    const float yx = (float)ex, yy = (float)ey;   // Y relative to X
     int best = -1;
-    float bs = 0.f, bfX = 0.f, bfY = 0.f;
+    float bs = 0.f, bfX = 0.f, bfY = 0.f, ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const int a = (i + 1) % 3, b = (i + 2) % 3;
         const float fX = sg * diff_prod(sx[a], sy[b], sx[b], sy[a]);
-        const float fY = sg * diff_prod(sx[a] - yx, sy[b] - yy, sx[b] - yx, sy[a] - yy);
+        const float fY = sg * diff_prod(sx[a] - ex, sy[b] - ey, sx[b] - ex, sy[a] - ey);
         if (!(fY < 0.f && fX > fY)) continue;
         const float si = fX / (fX - fY);
         if (best < 0 || si < bs) {
@@ -467,28 +444,30 @@ __device__ bool edge_side(const DevCam& cam, const SetupRec* vrec, const GeomRec
             bs = si;
             bfX = fX;
             bfY = fY;
+            ax = sx[a];
+            ay = sy[a];
+            bx = sx[b];
+            by = sy[b];
         }
     }
     if (best < 0) return true;
-    const int a = (best + 1) % 3, b = (best + 2) % 3;
     const float fX = bfX * sg, fY = bfY * sg;
     const float den = (fX - fY) * (fX - fY);
-    const float dfXa[2] = {sy[b], -sx[b]}, dfYa[2] = {sy[b] - yy, -(sx[b] - yx)};
-    const float dfXb[2] = {-sy[a], sx[a]}, dfYb[2] = {-(sy[a] - yy), sx[a] - yx};
-    const float ux = sx[b] - sx[a], uy = sy[b] - sy[a];
-    const float omega = (ex != 0 ? uy * uy : ux * ux) / (ux * ux + uy * uy);
+    const float ux = bx - ax, uy = by - ay;
+    const float omega = (ex != 0.f ? uy * uy : ux * ux) / (ux * ux + uy * uy);
     const float k = omega * phi / den;
-    const float gs[2][2] = {{k * (fX * dfYa[0] - fY * dfXa[0]), k * (fX * dfYa[1] - fY * dfXa[1])},
-                            {k * (fX * dfYb[0] - fY * dfXb[0]), k * (fX * dfYb[1] - fY * dfXb[1])}};
-    const int vid[2] = {a, b};
+    // d f(x)/d a = (b_y - x_y, -(b_x - x_x)); d f(x)/d b = (-(a_y - x_y), a_x - x_x)
+    const float gax = k * (fX * (by - ey) - fY * by), gay = k * (fX * (-(bx - ex)) - fY * (-bx));
+    const float gbx = k * (fX * (-(ay - ey)) - fY * (-ay)), gby = k * (fX * (ax - ex) - fY * ax);
+    const int ia = (best + 1) % 3, ib = (best + 2) % 3;
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const int m = vid[e];
-        const f3 gc = mk3(gs[e][0] * g.jx[m][0], gs[e][1] * g.jy[m][0], gs[e][0] * g.jx[m][1] + gs[e][1] * g.jy[m][1]);
-        const f3 gw = to_world(cam, gc);
-        out[3 * m] += gw.x;
-        out[3 * m + 1] += gw.y;
-        out[3 * m + 2] += gw.z;
+    for (int m = 0; m < 3; ++m) {
+        if (m != ia && m != ib) continue;
+        const float gx = m == ia ? gax : gbx;
+        const float gy = m == ia ? gay : gby;
+        const float j0 = __ldg(&g->jx[m][0]), j1 = __ldg(&g->jx[m][1]);
+        const float k0 = __ldg(&g->jy[m][0]), k1 = __ldg(&g->jy[m][1]);
+        add_world(cam, mk3(gx * j0, gy * k0, gx * j1 + gy * k1), out + 3 * m);
     }
     return true;
 }
@@ -498,7 +477,7 @@ __device__ bool edge_side(const DevCam& cam, const SetupRec* vrec, const GeomRec
 template <int SG>
 __global__ void __launch_bounds__(kTilePix, 2)
     k_edge_bwd(const __grid_constant__ ViewTable vt, const SoupDev s, const SetupRec* __restrict__ recs,
-               const GeomRec* __restrict__ geom, float* __restrict__ grad_verts, int* __restrict__ counter) {
+               const GeomRec* __restrict__ geom, double* __restrict__ acc_verts, int* __restrict__ counter) {
     __shared__ int s_item;
     const int tid = threadIdx.x;
     const int lx = tid & (kTile - 1), ly = tid / kTile;
@@ -515,47 +494,62 @@ __global__ void __launch_bounds__(kTilePix, 2)
         const bool valid = px < V.W && py < V.H;
         const int s0 = wi.g * kSampleGroup;
         const int ns = min(SG, vt.S - s0);
-        const size_t HW = (size_t)V.H * V.W;
+        const size_t HW = (size_t)V.H * V.W, ip = (size_t)py * V.W + px;
         const SetupRec* vrec = recs + (size_t)wi.v * s.T;
         const GeomRec* vgeom = geom + (size_t)wi.v * s.T;
         const int4* gbuf = reinterpret_cast<const int4*>(V.gbuf);
 #pragma unroll 1
         for (int q = 0; q < SG; ++q) {
             const bool qv = valid && q < ns;
-            const size_t sb = (size_t)(s0 + (q < ns ? q : 0)) * HW;
-            int tp = qv ? gbuf[sb + (size_t)py * V.W + px].x : -1;
+            const int sq = s0 + (q < ns ? q : 0);
+            int tp = qv ? gbuf[sq * HW + ip].x : -1;
             if (tp < 0 || tp >= s.T) tp = -1;
-            const float* col = V.color + (size_t)(s0 + (q < ns ? q : 0)) * Co * HW;
-            const float* gc = V.grad_color + (size_t)(s0 + (q < ns ? q : 0)) * Co * HW;
-            // slot 0: pixel's own winner (both pairs), slots 1, 2: right / lower neighbour's winner
-            float acc[3][9];
-            int tgt[3] = {qv ? tp : -1, -1, -1};
+            const float* col = V.color + (size_t)sq * Co * HW;
+            const float* gc = V.grad_color + (size_t)sq * Co * HW;
+            // slot 0: the pixel's own winner (both pairs); slots 1, 2: the
+            // right and the lower neighbour's winner
+            float acc0[9], acc1[9], acc2[9];
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
+            for (int k = 0; k < 9; ++k) acc0[k] = acc1[k] = acc2[k] = 0.f;
+            bool has0 = false, has1 = false, has2 = false;
+            int t1 = -1, t2 = -1;
 #pragma unroll
-                for (int k = 0; k < 9; ++k) acc[a][k] = 0.f;
-            bool has[3] = {false, false, false};
-#pragma unroll 1
             for (int dir = 0; dir < 2; ++dir) {
                 const int qx = px + (dir == 0), qy = py + (dir == 1);
                 if (!qv || qx >= V.W || qy >= V.H) continue;
-                int tq = gbuf[sb + (size_t)qy * V.W + qx].x;
+                const size_t iq = (size_t)qy * V.W + qx;
+                int tq = gbuf[sq * HW + iq].x;
                 if (tq < 0 || tq >= s.T) tq = -1;
                 if (tq == tp) continue;
                 float phi = 0.f;
-                const size_t ip = (size_t)py * V.W + px, iq = (size_t)qy * V.W + qx;
                 for (int c = 0; c < Co; ++c)
-                    phi += 0.5f * (__ldg(gc + c * HW + ip) + __ldg(gc + c * HW + iq)) * (__ldg(col + c * HW + ip) - __ldg(col + c * HW + iq));
+                    phi += 0.5f * (__ldg(gc + c * HW + ip) + __ldg(gc + c * HW + iq)) *
+                           (__ldg(col + c * HW + ip) - __ldg(col + c * HW + iq));
                 if (phi == 0.f) continue;
-                if (tp >= 0 && edge_side(V.cam, vrec, vgeom, tp, px, py, qx, qy, tq, phi, acc[0])) has[0] = true;
+                if (tp >= 0 && edge_side(V.cam, vrec, vgeom + tp, tp, px, py, qx, qy, tq, phi, acc0)) has0 = true;
                 if (tq >= 0) {
-                    tgt[1 + dir] = tq;
-                    if (edge_side(V.cam, vrec, vgeom, tq, qx, qy, px, py, tp, -phi, acc[1 + dir])) has[1 + dir] = true;
+                    if (dir == 0) {
+                        t1 = tq;
+                        has1 = edge_side(V.cam, vrec, vgeom + tq, tq, qx, qy, px, py, tp, -phi, acc1);
+                    } else {
+                        t2 = tq;
+                        has2 = edge_side(V.cam, vrec, vgeom + tq, tq, qx, qy, px, py, tp, -phi, acc2);
+                    }
                 }
             }
-#pragma unroll
-            for (int a = 0; a < 3; ++a) scatter_verts_run(grad_verts, has[a] && tgt[a] >= 0, tgt[a], acc[a]);
+            scatter_verts_run(acc_verts, has0 && tp >= 0, tp, acc0);
+            scatter_verts_run(acc_verts, has1 && t1 >= 0, t1, acc1);
+            scatter_verts_run(acc_verts, has2 && t2 >= 0, t2, acc2);
         }
+    }
+}
+
+// Add (or write) the FP64 accumulators into the caller's FP32 gradients.
+__global__ void k_grad_finish(const double* __restrict__ acc, float* __restrict__ out, long long n, int overwrite) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double base = overwrite ? 0.0 : (double)out[i];
+        out[i] = (float)(base + acc[i]);
     }
 }
 
@@ -568,25 +562,34 @@ cudaError_t launch_geom(const ViewTable& vt, const SoupDev& s, GeomRec* geom, cu
 
 cudaError_t launch_raster_bwd(const ViewTable& vt, const SoupDev& s, const SetupRec* recs, const uint32_t* keys,
                               const uint32_t* vals, const uint2* ranges, int DB, uint32_t flags, const GeomRec* geom,
-                              float* grad_tex, float* grad_verts, int* counter, int grid, cudaStream_t st) {
+                              double* acc_tex, double* acc_verts, int* counter, int grid, cudaStream_t st) {
     if (vt.S == 1)
-        k_raster_bwd<1><<<grid, kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, flags, geom, grad_tex, grad_verts, counter);
+        k_raster_bwd<1><<<grid, kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, flags, geom, acc_tex, acc_verts, counter);
     else if (vt.S == 2)
-        k_raster_bwd<2><<<grid, kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, flags, geom, grad_tex, grad_verts, counter);
+        k_raster_bwd<2><<<grid, kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, flags, geom, acc_tex, acc_verts, counter);
     else
-        k_raster_bwd<4><<<grid, kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, flags, geom, grad_tex, grad_verts, counter);
+        k_raster_bwd<4><<<grid, kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, flags, geom, acc_tex, acc_verts, counter);
     note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_edge_bwd(const ViewTable& vt, const SoupDev& s, const SetupRec* recs, const GeomRec* geom,
-                            float* grad_verts, int* counter, int grid, cudaStream_t st) {
+                            double* acc_verts, int* counter, int grid, cudaStream_t st) {
     if (vt.S == 1)
-        k_edge_bwd<1><<<grid, kTilePix, 0, st>>>(vt, s, recs, geom, grad_verts, counter);
+        k_edge_bwd<1><<<grid, kTilePix, 0, st>>>(vt, s, recs, geom, acc_verts, counter);
     else if (vt.S == 2)
-        k_edge_bwd<2><<<grid, kTilePix, 0, st>>>(vt, s, recs, geom, grad_verts, counter);
+        k_edge_bwd<2><<<grid, kTilePix, 0, st>>>(vt, s, recs, geom, acc_verts, counter);
     else
-        k_edge_bwd<4><<<grid, kTilePix, 0, st>>>(vt, s, recs, geom, grad_verts, counter);
+        k_edge_bwd<4><<<grid, kTilePix, 0, st>>>(vt, s, recs, geom, acc_verts, counter);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_finish(const double* acc, float* out, long long n, bool overwrite, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    long long g = (n + 255) / 256;
+    if (g > 152 * 8) g = 152 * 8;
+    k_grad_finish<<<(unsigned)g, 256, 0, st>>>(acc, out, n, overwrite ? 1 : 0);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -12,7 +12,7 @@ namespace ds {
 // Pipeline stages timed by the optional profiler (ds_profile_*).
 enum Stage {
     kStActivate, kStSetup, kStScan, kStEmit, kStSort, kStRanges,
-    kStRasterFwd, kStCount, kStGeom, kStRasterBwd, kStEdgeBwd, kNumStages
+    kStRasterFwd, kStCount, kStGeom, kStRasterBwd, kStEdgeBwd, kStFinish, kNumStages
 };
 extern const char* const kStageNames[kNumStages];
 
@@ -77,11 +77,14 @@ cudaError_t launch_raster_count(const ViewTable& vt, const SoupDev& s, const Set
 cudaError_t launch_geom(const ViewTable& vt, const SoupDev& s, GeomRec* geom, cudaStream_t st);
 cudaError_t launch_raster_bwd(const ViewTable& vt, const SoupDev& s, const SetupRec* recs,
                               const uint32_t* keys, const uint32_t* vals, const uint2* ranges,
-                              int DB, uint32_t flags, const GeomRec* geom, float* grad_tex,
-                              float* grad_verts, int* counter, int grid, cudaStream_t st);
+                              int DB, uint32_t flags, const GeomRec* geom, double* acc_tex,
+                              double* acc_verts, int* counter, int grid, cudaStream_t st);
 cudaError_t launch_edge_bwd(const ViewTable& vt, const SoupDev& s, const SetupRec* recs,
-                            const GeomRec* geom, float* grad_verts, int* counter, int grid,
+                            const GeomRec* geom, double* acc_verts, int* counter, int grid,
                             cudaStream_t st);
+// out[i] = (overwrite ? 0 : out[i]) + acc[i] (FP64 accumulators into FP32 gradients)
+cudaError_t launch_grad_finish(const double* acc, float* out, long long n, bool overwrite,
+                               cudaStream_t st);
 
 // Persistent-grid size for the tile kernels on this device.
 int persistent_grid(int n_items, int blocks_per_sm);

@@ -21,21 +21,21 @@ struct LossTable {
     LossView v[DS_MAX_VIEWS];
 };
 
-// blockIdx.y = view; threads stride over the view's S*H*W pixel-samples.
+// blockIdx.y = view, blockIdx.z = sample; threads stride over the pixels.
 __global__ void __launch_bounds__(256) k_loss_l2(const __grid_constant__ LossTable lt, float* __restrict__ loss) {
     const LossView& V = lt.v[blockIdx.y];
-    const long long n = (long long)lt.S * V.HW;
+    const int s = blockIdx.z;
+    const float* col = V.color + (size_t)s * lt.Co * V.HW;
+    float* gc = V.grad_color ? V.grad_color + (size_t)s * lt.Co * V.HW : nullptr;
     float acc = 0.f;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const long long s = i / V.HW, p = i - s * V.HW;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < V.HW; p += gridDim.x * blockDim.x) {
         float ell = 0.f;
         for (int c = 0; c < lt.Co; ++c) {
-            const long long ci = (s * lt.Co + c) * V.HW + p;
-            const float d = V.color[ci] - __ldg(V.target + (long long)c * V.HW + p);
+            const float d = col[(size_t)c * V.HW + p] - __ldg(V.target + (size_t)c * V.HW + p);
             ell += d * d;
-            if (V.grad_color) V.grad_color[ci] = 2.0f * lt.scale * d;
+            if (gc) gc[(size_t)c * V.HW + p] = 2.0f * lt.scale * d;
         }
-        if (V.score_w) V.score_w[i] = lt.scale * ell;
+        if (V.score_w) V.score_w[(size_t)s * V.HW + p] = lt.scale * ell;
         acc += ell;
     }
 #pragma unroll
@@ -80,10 +80,10 @@ extern "C" DS_API ds_status ds_loss_l2(int32_t n_views, int32_t S, int32_t C, co
         lt->v[v].target = targets[v];
         lt->v[v].grad_color = grad_colors ? grad_colors[v] : nullptr;
         lt->v[v].score_w = score_ws ? score_ws[v] : nullptr;
-        most = std::max(most, (long long)S * lt->v[v].HW);
+        most = std::max(most, (long long)lt->v[v].HW);
     }
-    const int gx = (int)std::min<long long>((most + 255) / 256, 2048);
-    ds::k_loss_l2<<<dim3(gx, n_views), 256, 0, static_cast<cudaStream_t>(stream)>>>(*lt, loss);
+    const int gx = (int)std::min<long long>((most + 1023) / 1024, 512);
+    ds::k_loss_l2<<<dim3(gx, n_views, S), 256, 0, static_cast<cudaStream_t>(stream)>>>(*lt, loss);
     ds::note_launches(1);
     delete lt;
     return cudaGetLastError() == cudaSuccess ? DS_OK : DS_ERR_CUDA;

@@ -243,7 +243,8 @@ cudaError_t launch_raster_count(const ViewTable& vt, const SoupDev& s, const Set
 }
 
 const char* const kStageNames[kNumStages] = {"activate", "setup", "scan", "emit", "sort", "ranges",
-                                             "raster_fwd", "count", "geom", "raster_bwd", "edge_bwd"};
+                                             "raster_fwd", "count", "geom", "raster_bwd", "edge_bwd",
+                                             "finish"};
 
 static std::atomic<long long> g_launches{0};
 void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }

@@ -250,3 +250,42 @@ def test_no_sync_forward_matches_and_reports_capacity(ctx):
     assert e.value.code == -4
     ctx.status()   # cleared
     ctx.close()
+
+
+def test_fused_l2_loss_matches_numpy(ctx):
+    """ds_loss_l2: per-sample l, dL/dC and score weights against FP64 numpy."""
+    import torch
+    from paper_2603_27151_gb300 import native as N
+    rng = np.random.default_rng(4)
+    S, Co = 3, 5
+    shapes = [(37, 23), (64, 48)]
+    cols = [rng.uniform(0, 1, (S, Co, h, w)).astype(np.float32) for (w, h) in shapes]
+    tgts = [rng.uniform(0, 1, (Co, h, w)).astype(np.float32) for (w, h) in shapes]
+    dc = [torch.from_numpy(c).cuda() for c in cols]
+    dt = [torch.from_numpy(t).cuda() for t in tgts]
+    gc = [torch.empty_like(c) for c in dc]
+    sw = [torch.empty((S, c.shape[2], c.shape[3]), dtype=torch.float32, device="cuda") for c in dc]
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    N.loss_l2(dc, dt, gc, sw, loss, scale=1.0 / S)
+    torch.cuda.synchronize()
+    total = 0.0
+    for c, t, g, w in zip(cols, tgts, gc, sw):
+        d = c.astype(np.float64) - t[None]
+        ell = (d ** 2).sum(1)
+        total += ell.sum() / S
+        assert np.allclose(g.cpu().numpy(), 2 * d / S, rtol=1e-6, atol=1e-7)
+        assert np.allclose(w.cpu().numpy(), ell / S, rtol=1e-5, atol=1e-7)
+    assert abs(float(loss.item()) - total) <= 1e-5 * total
+
+
+def test_backward_is_within_tolerance_on_every_run(ctx):
+    """The atomics' summation order changes between runs; every run must
+    stay within the tolerance (FP64 accumulation)."""
+    sc = I.batched_views()
+    sid, got, (g, col, verts, tex) = gpu_forward(ctx, sc)
+    ref = _oracle_fwd(sc)
+    gc, sw = upstream(ref, 1, seed=5)
+    rt, rv = O.backward(sc.verts, sc.tex, sc.grid_n, sc.cams, 1, ref, gc, sw)
+    for rep in range(5):
+        gt, gv = gpu_backward(ctx, sid, sc, 1, g, col, gc, sw, O.G_ALL | 0x100, verts, tex)
+        _check_grads(gt, gv, rt, rv, "run %d" % rep)

@@ -204,6 +204,34 @@ DS_API ds_status ds_loss_l2(int32_t n_views, int32_t S, int32_t C, const int32_t
                             float* const* grad_colors, float* const* score_ws, float scale,
                             float* loss, void* stream);
 
+/* Forward pass for callers that cannot allocate device memory: the same
+ * computation and outputs as ds_raster_forward (Eq. 5, Algorithm A1 step 1),
+ * on a soup passed directly (verts [T][3][3], tex [T][V][C] logits, as in
+ * ds_soup_upload) instead of a registered one, and with no context.  The
+ * paper has no counterpart: this serves embedding.  Some callers cannot call
+ * cudaMalloc: engines and plug-in hosts that own every byte of device memory
+ * through their own pool, programs under a hard device-memory budget, and
+ * real-time loops that cannot afford the device-wide synchronisation that
+ * cudaMalloc and cudaFree may imply.  This entry point makes no cudaMalloc,
+ * cudaFree or other allocating call.  Its scratch is one fixed device array
+ * of about 21 MiB inside the library, which every GPU that loads the library
+ * holds until the process exits.  Limits (checked before any launch,
+ * DS_ERR_INVALID_ARG beyond them): T*V*C <= 2^20 texture values,
+ * n_views*T <= 65536, at most 65536 16x16 tiles over all views.  The number
+ * of (tile, triangle) pairs is known only after binning; the call reads it
+ * back (one synchronisation of `stream`) and returns DS_ERR_CAPACITY above
+ * 524288 pairs.  The first call on each device looks up the array's device
+ * address with that device current; make that first call before any stream
+ * capture.  Every call in the process shares the one array and leaves its
+ * contents behind (the call clears what must start at zero): calls whose work
+ * overlaps on the GPU, from several streams or host threads, race and must be
+ * serialised by the caller. */
+DS_API ds_status ds_raster_forward_noalloc(const float* verts, const float* tex, int32_t T,
+                                           int32_t grid_n, int32_t C, const ds_camera* cams,
+                                           const uint64_t* seeds, int32_t n_views, int32_t S,
+                                           uint32_t mode, const float* bg, const ds_view_out* out,
+                                           void* stream);
+
 /* Fragment statistics of Eq. 1 for n_views views: *n_cover_total (host)
  * receives the number of (pixel, covering triangle) pairs summed over the
  * views (|F|, one mask sample).  Synchronises `stream`. */

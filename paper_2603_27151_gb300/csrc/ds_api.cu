@@ -89,6 +89,10 @@ bool finite_cam(const ds_camera& c) {
 
 }  // namespace
 
+namespace ds {
+void report_error(const std::string& msg) { g_err = msg; }
+}  // namespace ds
+
 struct ds_ctx {
     int device = 0;
     std::mutex mu;

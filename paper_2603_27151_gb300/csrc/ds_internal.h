@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "ds_common.cuh"
 
 namespace ds {
@@ -15,6 +17,9 @@ enum Stage {
     kStRasterFwd, kStCount, kStGeom, kStRasterBwd, kStEdgeBwd, kStFinish, kNumStages
 };
 extern const char* const kStageNames[kNumStages];
+
+// Set the message returned by ds_last_error on this thread.
+void report_error(const std::string& msg);
 
 // Library-wide count of kernel launches (every launch site adds to it).
 void note_launches(int n);

@@ -93,6 +93,8 @@ def load():
     L.ds_loss_l2.restype = i32
     L.ds_plan_stats.argtypes = [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]
     L.ds_plan_stats.restype = i32
+    L.ds_raster_forward_noalloc.argtypes = [P, P, i32, i32, i32, P, P, i32, i32, u32, P, P, P]
+    L.ds_raster_forward_noalloc.restype = i32
     _lib = L
     return L
 
@@ -233,6 +235,23 @@ class Context:
             _check(L.ds_profile_read(self.h, i, ctypes.byref(name), ctypes.byref(n), ctypes.byref(ms)))
             out[name.value.decode()] = (n.value, ms.value)
         return out
+
+
+def raster_forward_noalloc(verts, tex, grid_n, cams, seeds, S, mode, bg, gbufs, colors, n_fronts=None,
+                           stream=None):
+    """ds_raster_forward_noalloc: the forward pass on a soup given directly,
+    with no context and no allocation (library-internal fixed scratch)."""
+    n = len(cams)
+    T, V, C = tex.shape
+    sd = (ctypes.c_uint64 * n)(*[int(x) for x in (seeds if seeds is not None else [0] * n)])
+    bga = np.ascontiguousarray(bg, np.float32)
+    outs = (ds_view_out * n)()
+    for v in range(n):
+        outs[v].gbuf = gbufs[v].data_ptr()
+        outs[v].color = colors[v].data_ptr()
+        outs[v].n_front = n_fronts[v].data_ptr() if n_fronts is not None and n_fronts[v] is not None else None
+    _check(load().ds_raster_forward_noalloc(_ptr(verts), _ptr(tex), T, grid_n, C, cameras(cams), sd, n, S, mode,
+                                            bga.ctypes.data_as(ctypes.c_void_p), outs, _stream(stream)))
 
 
 def loss_l2(colors, targets, grad_colors=None, score_ws=None, loss=None, scale=1.0, stream=None):

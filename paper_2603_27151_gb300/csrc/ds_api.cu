@@ -535,7 +535,7 @@ ds_status ds_raster_forward(ds_ctx* c, int32_t soup_id, const ds_camera* cams, c
     ds::Bg b{};
     for (int i = 0; i < s->C - 1; ++i) b.c[i] = bg[i];
     const ds::SoupDev sd = soup_dev(*s);
-    const int grid = ds::persistent_grid(vt.n_items, 2);
+    const int grid = 0;
     {
         StageScope p(c, ds::kStRasterFwd, st);
         DS_TRY_CUDA(cudaMemsetAsync(c->d_counter(), 0, 4, st));
@@ -581,7 +581,7 @@ ds_status ds_raster_backward(ds_ctx* c, int32_t soup_id, const ds_camera* cams, 
     if (!((grad_flags & DS_REUSE_FORWARD) && plan_matches(c, soup_id, cams, n_views)))
         DS_TRY(prepare(c, soup_id, *s, cams, vt, true, st));
     const ds::SoupDev sd = soup_dev(*s);
-    const int grid = ds::persistent_grid(vt.n_items, 2);
+    const int grid = 0;
     const uint32_t gflags = grad_flags & DS_G_ALL;
     const size_t n_tex = (size_t)s->T * s->V * s->C, n_verts = 9 * (size_t)s->T;
     const bool want_tex = grad_tex && (gflags & (DS_G_TEX | DS_G_SCORE));
@@ -640,7 +640,7 @@ ds_status ds_fragment_count(ds_ctx* c, int32_t soup_id, const ds_camera* cams, i
     build_table(vt, cams, nullptr, n_views, 1, nullptr, nullptr);
     DS_TRY(prepare(c, soup_id, *s, cams, vt, true, st));
     const ds::SoupDev sd = soup_dev(*s);
-    const int grid = ds::persistent_grid(vt.n_items, 2);
+    const int grid = 0;
     DS_TRY_CUDA(cudaMemsetAsync(c->d_total(), 0, 8, st));
     DS_TRY_CUDA(cudaMemsetAsync(c->d_counter() + 4, 0, 4, st));
     DS_TRY_CUDA(ds::launch_raster_count(vt, sd, c->recs.as<ds::SetupRec>(), c->keys[c->plan.res].as<uint32_t>(),

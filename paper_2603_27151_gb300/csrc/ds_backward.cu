@@ -254,7 +254,7 @@ __device__ __forceinline__ void interior_grad(const GeomRec* g, const DevCam& ca
 }
 
 template <int SG>
-__global__ void __launch_bounds__(kTilePix, 2)
+__global__ void __launch_bounds__(kTilePix, DS_MINB_BWD)
     k_raster_bwd(const __grid_constant__ ViewTable vt, const SoupDev s, const SetupRec* __restrict__ recs,
                  const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
                  const uint2* __restrict__ ranges, int DB, uint32_t flags, const GeomRec* __restrict__ geom,
@@ -472,16 +472,33 @@ __device__ __forceinline__ bool edge_side(const DevCam& cam, const SetupRec* vre
     return true;
 }
 
-// One CTA per (view, tile, sample group); every pixel handles its pairs with
-// the right and the lower neighbour.
+// One CTA per (view, tile, sample group); every pixel owns its pairs with
+// the right and the lower neighbour.  A pair with different winners yields up
+// to two side jobs (one per side with a triangle).  Each warp first queues
+// its jobs in shared memory (ballot + prefix), then evaluates them 32 at a
+// time, so that every lane works on a boundary instead of idling while its
+// neighbours do; consecutive jobs mostly share a triangle, and runs of equal
+// triangles are summed before the atomics.
+struct EdgeJob {
+    int xy;      // X: x | (y << 16)
+    int t;       // triangle of side X
+    int tY;      // winner at Y (-1: background)
+    float phi;   // 1/2 sum_c (g_X + g_Y)(C_X - C_Y) for side X
+    int dir;     // Y = X + (1, 0) / (-1, 0) / (0, 1) / (0, -1): 0..3
+};
+
+constexpr int kJobsPerWarp = 4 * 32;
+
 template <int SG>
-__global__ void __launch_bounds__(kTilePix, 2)
+__global__ void __launch_bounds__(kTilePix, DS_MINB_EDGE)
     k_edge_bwd(const __grid_constant__ ViewTable vt, const SoupDev s, const SetupRec* __restrict__ recs,
                const GeomRec* __restrict__ geom, double* __restrict__ acc_verts, int* __restrict__ counter) {
     __shared__ int s_item;
-    const int tid = threadIdx.x;
+    __shared__ EdgeJob s_jobs[kTilePix / 32][kJobsPerWarp];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int lx = tid & (kTile - 1), ly = tid / kTile;
     const int Co = s.C - 1;
+    EdgeJob* jobs = s_jobs[warp];
     for (;;) {
         if (tid == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
@@ -506,13 +523,10 @@ __global__ void __launch_bounds__(kTilePix, 2)
             if (tp < 0 || tp >= s.T) tp = -1;
             const float* col = V.color + (size_t)sq * Co * HW;
             const float* gc = V.grad_color + (size_t)sq * Co * HW;
-            // slot 0: the pixel's own winner (both pairs); slots 1, 2: the
-            // right and the lower neighbour's winner
-            float acc0[9], acc1[9], acc2[9];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) acc0[k] = acc1[k] = acc2[k] = 0.f;
-            bool has0 = false, has1 = false, has2 = false;
-            int t1 = -1, t2 = -1;
+            // ---- this lane's jobs: slot 2*dir + side (fixed slots keep the
+            // register arrays at constant indices)
+            EdgeJob sl[4];
+            bool vl[4] = {false, false, false, false};
 #pragma unroll
             for (int dir = 0; dir < 2; ++dir) {
                 const int qx = px + (dir == 0), qy = py + (dir == 1);
@@ -526,20 +540,47 @@ __global__ void __launch_bounds__(kTilePix, 2)
                     phi += 0.5f * (__ldg(gc + c * HW + ip) + __ldg(gc + c * HW + iq)) *
                            (__ldg(col + c * HW + ip) - __ldg(col + c * HW + iq));
                 if (phi == 0.f) continue;
-                if (tp >= 0 && edge_side(V.cam, vrec, vgeom + tp, tp, px, py, qx, qy, tq, phi, acc0)) has0 = true;
+                if (tp >= 0) {
+                    sl[2 * dir] = EdgeJob{px | (py << 16), tp, tq, phi, dir == 0 ? 0 : 2};
+                    vl[2 * dir] = true;
+                }
                 if (tq >= 0) {
-                    if (dir == 0) {
-                        t1 = tq;
-                        has1 = edge_side(V.cam, vrec, vgeom + tq, tq, qx, qy, px, py, tp, -phi, acc1);
-                    } else {
-                        t2 = tq;
-                        has2 = edge_side(V.cam, vrec, vgeom + tq, tq, qx, qy, px, py, tp, -phi, acc2);
-                    }
+                    sl[2 * dir + 1] = EdgeJob{qx | (qy << 16), tq, tp, -phi, dir == 0 ? 1 : 3};
+                    vl[2 * dir + 1] = true;
                 }
             }
-            scatter_verts_run(acc_verts, has0 && tp >= 0, tp, acc0);
-            scatter_verts_run(acc_verts, has1 && t1 >= 0, t1, acc1);
-            scatter_verts_run(acc_verts, has2 && t2 >= 0, t2, acc2);
+            const int nmine = (int)vl[0] + (int)vl[1] + (int)vl[2] + (int)vl[3];
+            // ---- queue them (lane order, then slot order)
+            int pre = nmine;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int o = __shfl_up_sync(kFullMask, pre, d);
+                if (lane >= d) pre += o;
+            }
+            const int total = __shfl_sync(kFullMask, pre, 31);
+            pre -= nmine;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (vl[k]) jobs[pre++] = sl[k];
+            __syncwarp();
+            // ---- evaluate 32 at a time
+            for (int b0 = 0; b0 < total; b0 += 32) {
+                const int j = b0 + lane;
+                float acc[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) acc[k] = 0.f;
+                bool act = false;
+                int t = -1;
+                if (j < total) {
+                    const EdgeJob jb = jobs[j];
+                    const int xX = jb.xy & 0xffff, yX = jb.xy >> 16;
+                    const int xY = xX + (jb.dir == 0) - (jb.dir == 1), yY = yX + (jb.dir == 2) - (jb.dir == 3);
+                    t = jb.t;
+                    act = edge_side(V.cam, vrec, vgeom + t, t, xX, yX, xY, yY, jb.tY, jb.phi, acc);
+                }
+                scatter_verts_run(acc_verts, act, t, acc);
+            }
+            __syncwarp();
         }
     }
 }
@@ -564,11 +605,11 @@ cudaError_t launch_raster_bwd(const ViewTable& vt, const SoupDev& s, const Setup
                               const uint32_t* vals, const uint2* ranges, int DB, uint32_t flags, const GeomRec* geom,
                               double* acc_tex, double* acc_verts, int* counter, int grid, cudaStream_t st) {
     if (vt.S == 1)
-        k_raster_bwd<1><<<grid, kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, flags, geom, acc_tex, acc_verts, counter);
+        k_raster_bwd<1><<<resident_grid(k_raster_bwd<1>, vt.n_items, grid), kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, flags, geom, acc_tex, acc_verts, counter);
     else if (vt.S == 2)
-        k_raster_bwd<2><<<grid, kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, flags, geom, acc_tex, acc_verts, counter);
+        k_raster_bwd<2><<<resident_grid(k_raster_bwd<2>, vt.n_items, grid), kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, flags, geom, acc_tex, acc_verts, counter);
     else
-        k_raster_bwd<4><<<grid, kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, flags, geom, acc_tex, acc_verts, counter);
+        k_raster_bwd<4><<<resident_grid(k_raster_bwd<4>, vt.n_items, grid), kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, flags, geom, acc_tex, acc_verts, counter);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -576,11 +617,11 @@ cudaError_t launch_raster_bwd(const ViewTable& vt, const SoupDev& s, const Setup
 cudaError_t launch_edge_bwd(const ViewTable& vt, const SoupDev& s, const SetupRec* recs, const GeomRec* geom,
                             double* acc_verts, int* counter, int grid, cudaStream_t st) {
     if (vt.S == 1)
-        k_edge_bwd<1><<<grid, kTilePix, 0, st>>>(vt, s, recs, geom, acc_verts, counter);
+        k_edge_bwd<1><<<resident_grid(k_edge_bwd<1>, vt.n_items, grid), kTilePix, 0, st>>>(vt, s, recs, geom, acc_verts, counter);
     else if (vt.S == 2)
-        k_edge_bwd<2><<<grid, kTilePix, 0, st>>>(vt, s, recs, geom, acc_verts, counter);
+        k_edge_bwd<2><<<resident_grid(k_edge_bwd<2>, vt.n_items, grid), kTilePix, 0, st>>>(vt, s, recs, geom, acc_verts, counter);
     else
-        k_edge_bwd<4><<<grid, kTilePix, 0, st>>>(vt, s, recs, geom, acc_verts, counter);
+        k_edge_bwd<4><<<resident_grid(k_edge_bwd<4>, vt.n_items, grid), kTilePix, 0, st>>>(vt, s, recs, geom, acc_verts, counter);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -94,4 +94,18 @@ cudaError_t launch_grad_finish(const double* acc, float* out, long long n, bool 
 // Persistent-grid size for the tile kernels on this device.
 int persistent_grid(int n_items, int blocks_per_sm);
 
+// Persistent grid of a tile kernel: every CTA the device can keep resident
+// (SM count x occupancy of `kernel` at 256 threads), at most n_items.  A
+// positive `grid` from the caller is used as given.
+template <class Kernel>
+inline int resident_grid(Kernel kernel, int n_items, int grid) {
+    if (grid > 0) return grid;
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, 256, 0) != cudaSuccess || blocks < 1) {
+        cudaGetLastError();
+        blocks = 1;
+    }
+    return persistent_grid(n_items, blocks);
+}
+
 }  // namespace ds

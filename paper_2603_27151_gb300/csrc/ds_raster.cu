@@ -11,7 +11,7 @@ namespace ds {
 // One CTA (256 threads, one pixel each) per work item (view, tile, group of
 // up to four samples), taken from a global counter until none is left.
 template <int SG>
-__global__ void __launch_bounds__(kTilePix, 2)
+__global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
     k_raster_fwd(const __grid_constant__ ViewTable vt, const SoupDev s, const SetupRec* __restrict__ recs,
                  const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
                  const uint2* __restrict__ ranges, int DB, uint32_t mode, const Bg bg, int* __restrict__ counter) {
@@ -114,7 +114,9 @@ __global__ void __launch_bounds__(kTilePix, 2)
                     make_int4(bt[q], __float_as_int(bb1[q]), __float_as_int(bb2[q]), __float_as_int(bD[q]));
                 float* out = V.color + (size_t)sg * Co * HW + pix;
                 if (bt[q] < 0) {
-                    for (int c = 0; c < Co; ++c) out[c * HW] = bg.c[c];
+#pragma unroll
+                    for (int c = 0; c < DS_MAX_CHANNELS; ++c)
+                        if (c < Co) out[c * HW] = bg.c[c];
                 } else {
                     decode_color(s, bt[q], bb1[q], bb2[q], out, HW);
                 }
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(kTilePix, 2)
 // the stored winner (all covered fragments for the background), written to
 // n_front.  mode 1: covered fragments of the pixel (one sample), summed.
 template <int SG>
-__global__ void __launch_bounds__(kTilePix, 2)
+__global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
     k_raster_count(const __grid_constant__ ViewTable vt, const SoupDev s, const SetupRec* __restrict__ recs,
                    const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
                    const uint2* __restrict__ ranges, int DB, int mode, unsigned long long* __restrict__ total,
@@ -222,11 +224,11 @@ cudaError_t launch_raster_fwd(const ViewTable& vt, const SoupDev& s, const Setup
                               const uint32_t* vals, const uint2* ranges, int DB, uint32_t mode, const Bg& bg,
                               int* counter, int grid, cudaStream_t st) {
     if (vt.S == 1)
-        k_raster_fwd<1><<<grid, kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, bg, counter);
+        k_raster_fwd<1><<<resident_grid(k_raster_fwd<1>, vt.n_items, grid), kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, bg, counter);
     else if (vt.S == 2)
-        k_raster_fwd<2><<<grid, kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, bg, counter);
+        k_raster_fwd<2><<<resident_grid(k_raster_fwd<2>, vt.n_items, grid), kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, bg, counter);
     else
-        k_raster_fwd<4><<<grid, kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, bg, counter);
+        k_raster_fwd<4><<<resident_grid(k_raster_fwd<4>, vt.n_items, grid), kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, bg, counter);
     note_launches(1);
     return cudaGetLastError();
 }
@@ -235,9 +237,9 @@ cudaError_t launch_raster_count(const ViewTable& vt, const SoupDev& s, const Set
                                 const uint32_t* vals, const uint2* ranges, int DB, int mode,
                                 unsigned long long* total, int* counter, int grid, cudaStream_t st) {
     if (mode == 1 || vt.S == 1)
-        k_raster_count<1><<<grid, kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, total, counter);
+        k_raster_count<1><<<resident_grid(k_raster_count<1>, vt.n_items, grid), kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, total, counter);
     else
-        k_raster_count<4><<<grid, kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, total, counter);
+        k_raster_count<4><<<resident_grid(k_raster_count<4>, vt.n_items, grid), kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, total, counter);
     note_launches(1);
     return cudaGetLastError();
 }

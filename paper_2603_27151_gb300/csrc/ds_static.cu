@@ -218,7 +218,7 @@ extern "C" DS_API ds_status ds_raster_forward_noalloc(const float* verts, const 
     NA_TRY(ds::launch_tile_ranges(keys[res], dK, K, DB, ranges, st));
     ds::Bg b{};
     for (int i = 0; i < C - 1; ++i) b.c[i] = bg[i];
-    const int grid = ds::persistent_grid(vt.n_items, 2);
+    const int grid = 0;
     NA_TRY(ds::launch_raster_fwd(vt, sd, recs, keys[res], vals[res], ranges, DB, mode, b, counter, grid, st));
     bool want_front = false;
     for (int v = 0; v < n_views; ++v) want_front = want_front || out[v].n_front;

@@ -8,6 +8,18 @@
 namespace ds {
 
 constexpr unsigned kFullMask = 0xffffffffu;
+
+// Resident CTAs per SM requested from the compiler for the tile kernels
+// (register budget 65536 / (256 x blocks)); set per kernel at build time.
+#ifndef DS_MINB_FWD
+#define DS_MINB_FWD 4
+#endif
+#ifndef DS_MINB_BWD
+#define DS_MINB_BWD 4
+#endif
+#ifndef DS_MINB_EDGE
+#define DS_MINB_EDGE 4
+#endif
 constexpr int kChunk = 256;   // triangles staged per round (one per thread)
 
 // Per-tile staged set-up.  h0..h2 hold what the per-pixel coverage test reads

@@ -85,6 +85,8 @@ typedef struct ds_ctx ds_ctx;   /* opaque library context (one CUDA device) */
 /* Soup upload flags. */
 #define DS_COPY 0u    /* the library copies verts/tex and owns the copy       */
 #define DS_BORROW 1u  /* the library keeps the caller's pointers (training)   */
+#define DS_STATIC 2u  /* contents never change after upload: the sigmoid
+                         activation is computed once and reused (serving)   */
 
 /* Pinhole camera.  World -> camera: x_c = R x + t (R row-major); +z forward,
  * +x right, +y down; pixel (px, py) has its centre at (px + 0.5, py + 0.5);
@@ -146,7 +148,8 @@ DS_API void ds_destroy(ds_ctx* ctx);
  *  grid_n = N in [1, 32]; C in [2, 16]; T in [1, 2^24).
  *  flags: DS_COPY (asynchronous device-to-device copy on `stream` into
  *  library memory) or DS_BORROW (pointers kept; the caller keeps them valid
- *  and may change their contents between calls).
+ *  and may change their contents between calls), optionally | DS_STATIC
+ *  (the contents never change: activations are computed once).
  *  On success *soup_id receives a handle >= 0. */
 DS_API ds_status ds_soup_upload(ds_ctx* ctx, const float* verts, const float* tex, int32_t T,
                          int32_t grid_n, int32_t C, uint32_t flags, int32_t* soup_id,
@@ -187,6 +190,30 @@ DS_API ds_status ds_raster_backward(ds_ctx* ctx, int32_t soup_id, const ds_camer
                              int32_t n_views, int32_t S, const ds_view_out* fwd,
                              const ds_view_gin* gin, uint32_t grad_flags, float* grad_verts,
                              float* grad_tex, void* stream);
+
+/* The two passes with the cameras and seeds in DEVICE memory (ds_camera[n]
+ * and uint64[n], read by the kernels), the view sizes on the host
+ * (wh [n][2] = width, height).  Otherwise as ds_raster_forward /
+ * ds_raster_backward.  For a training step whose views are chosen at run time
+ * inside a captured CUDA graph: the graph records the pointers, the caller
+ * rewrites the camera and seed arrays before each replay.  The device values
+ * are not validated (finite, fx, fy != 0, near_z > 0 are the caller's
+ * contract).  DS_REUSE_FORWARD reuses the plan of the last device-camera
+ * forward on this context with the same soup and view sizes. */
+DS_API ds_status ds_raster_forward_devcam(ds_ctx* ctx, int32_t soup_id, const int32_t* wh,
+                                          const ds_camera* cams, const uint64_t* seeds,
+                                          int32_t n_views, int32_t S, uint32_t mode, const float* bg,
+                                          const ds_view_out* out, void* stream);
+DS_API ds_status ds_raster_backward_devcam(ds_ctx* ctx, int32_t soup_id, const int32_t* wh,
+                                           const ds_camera* cams, int32_t n_views, int32_t S,
+                                           const ds_view_out* fwd, const ds_view_gin* gin,
+                                           uint32_t grad_flags, float* grad_verts, float* grad_tex,
+                                           void* stream);
+
+/* Grow the context's bin buffers to hold `pairs` (tile, triangle) pairs, so
+ * that DS_NO_SYNC forwards (which never allocate or synchronise) have that
+ * capacity.  Synchronous (may call cudaMalloc). */
+DS_API ds_status ds_reserve(ds_ctx* ctx, int64_t pairs);
 
 /* Per-pixel L2 photometric loss of the rendered colour features against
  * target images, with its upstream gradients for ds_raster_backward (the
@@ -247,6 +274,64 @@ DS_API ds_status ds_plan_stats(ds_ctx* ctx, int64_t* pairs, int64_t* tiles);
  * context's last stream): DS_ERR_CAPACITY after a DS_NO_SYNC forward whose
  * bins overflowed (its outputs are invalid), else DS_OK. */
 DS_API ds_status ds_ctx_status(ds_ctx* ctx);
+
+/* ---------------------------------------------------------------------------
+ * Render server: continuous batching of single-view forward requests over
+ * resident soups (the inference use of Eq. 5 and Eq. 3; the paper measures
+ * the rendering speed of the optimised soups, Sec. 4).  One scheduler thread
+ * and n_streams workers, each a context with its own CUDA stream.  A free
+ * worker takes the oldest queued request and every other queued request for
+ * the same soup, mode and background (up to max_batch views) into one forward
+ * launch; requests that arrive while batches run join the next one, and the
+ * batches of different workers overlap on the device.  Admission by device
+ * memory: a batch is launched only while the scratch estimate of all batches
+ * in flight stays within mem_budget bytes (a batch of one request is always
+ * admitted when nothing else runs).  Workers launch with DS_NO_SYNC after
+ * ds_reserve(reserve_pairs); a batch whose bins overflow is rendered again
+ * with synchronised sizing before its requests complete.  A request's output
+ * is identical whichever batch it runs in (each view's pixels depend only on
+ * its own soup, camera and seed).
+ * ------------------------------------------------------------------------- */
+typedef struct ds_server ds_server;   /* opaque */
+
+typedef struct ds_request_stats {
+    int64_t submit_ns, launch_ns, done_ns; /* steady-clock times (host, ns)         */
+    int32_t batch;                         /* views in the launch that served it     */
+    int32_t pad;
+} ds_request_stats;
+
+/* Create a server on `device`.  n_streams in [1, 32], max_batch in [1, 64],
+ * reserve_pairs >= 0 (bin capacity per worker).  Starts the scheduler thread. */
+DS_API ds_status ds_server_create(int32_t device, int32_t n_streams, size_t mem_budget,
+                                  int32_t max_batch, int64_t reserve_pairs, ds_server** out);
+
+/* Copy a soup (device pointers, layout as ds_soup_upload) into server memory
+ * and register it with every worker as immutable (activations computed
+ * once).  Synchronous.  *soup_id receives the server's handle. */
+DS_API ds_status ds_server_add_soup(ds_server* srv, const float* verts, const float* tex, int32_t T,
+                                    int32_t grid_n, int32_t C, int32_t* soup_id);
+
+/* Queue one view for rendering; returns at once with *ticket (host).  cam,
+ * bg [C-1] (NULL = zeros) are host values copied into the request; `out`
+ * (host struct of device pointers, S = 1) must stay valid until the request
+ * completes.  DS_ERR_BUSY when the queue is full or the server stops. */
+DS_API ds_status ds_render_request(ds_server* srv, int32_t soup_id, const ds_camera* cam,
+                                   uint64_t seed, uint32_t mode, const float* bg,
+                                   const ds_view_out* out, uint64_t* ticket);
+
+/* Wait for a request (timeout_ms < 0: no limit).  On return other than
+ * DS_ERR_TIMEOUT the ticket is released; `stats` (host, may be NULL)
+ * receives its timestamps.  The outputs are complete on the device when this
+ * returns DS_OK. */
+DS_API ds_status ds_request_wait(ds_server* srv, uint64_t ticket, int32_t timeout_ms,
+                                 ds_request_stats* stats);
+
+/* Hold (paused != 0) or resume the launching of queued requests. */
+DS_API ds_status ds_server_pause(ds_server* srv, int32_t paused);
+
+/* Cancel queued requests (their waits return DS_ERR_BUSY), let launched
+ * batches finish, free everything. */
+DS_API ds_status ds_server_destroy(ds_server* srv);
 
 /* Profiling (off by default; no paper counterpart: instrumentation).  While
  * enabled, every pipeline stage that a call on this context launches

@@ -62,6 +62,8 @@ struct DevBuf {
 struct Soup {
     bool live = false;
     bool owned = false;
+    bool fixed = false;       // DS_STATIC: contents never change, activate once
+    bool act_valid = false;   // activations of a fixed soup are current
     const float* verts = nullptr;
     const float* tex = nullptr;
     float* own = nullptr;   // owned copy of verts and tex
@@ -71,6 +73,8 @@ struct Soup {
 
 struct Plan {
     bool valid = false;
+    bool devcam = false;   // built from device-resident cameras
+    int n_views = 0;
     int soup = -1;
     std::vector<ds_camera> cams;
     int DB = 0;
@@ -308,9 +312,10 @@ ds_status prepare(ds_ctx* c, int32_t soup_id, Soup& s, const ds_camera* cams, co
     DS_TRY(c->ranges.ensure(8 * (size_t)n_tiles, "tile ranges"));
     DS_TRY(ensure_scan(c, (int64_t)nvt));
 
-    {
+    if (!(s.fixed && s.act_valid)) {
         StageScope p(c, ds::kStActivate, st);
         DS_TRY_CUDA(ds::launch_activate(sd, st));
+        s.act_valid = s.fixed;
     }
     {
         StageScope p(c, ds::kStSetup, st);
@@ -363,7 +368,12 @@ ds_status prepare(ds_ctx* c, int32_t soup_id, Soup& s, const ds_camera* cams, co
 
     c->plan.valid = true;
     c->plan.soup = soup_id;
-    c->plan.cams.assign(cams, cams + vt.n);
+    c->plan.devcam = cams == nullptr;
+    c->plan.n_views = vt.n;
+    if (cams)
+        c->plan.cams.assign(cams, cams + vt.n);
+    else
+        c->plan.cams.clear();
     c->plan.DB = DB;
     c->plan.res = res;
     c->plan.kcap = kcap;
@@ -372,7 +382,7 @@ ds_status prepare(ds_ctx* c, int32_t soup_id, Soup& s, const ds_camera* cams, co
 }
 
 bool plan_matches(const ds_ctx* c, int32_t soup_id, const ds_camera* cams, int32_t n_views) {
-    if (!c->plan.valid || c->plan.soup != soup_id || (int)c->plan.cams.size() != n_views) return false;
+    if (!c->plan.valid || c->plan.devcam || c->plan.soup != soup_id || (int)c->plan.cams.size() != n_views) return false;
     return std::memcmp(c->plan.cams.data(), cams, sizeof(ds_camera) * n_views) == 0;
 }
 
@@ -447,7 +457,7 @@ ds_status ds_soup_upload(ds_ctx* c, const float* verts, const float* tex, int32_
     if (T < 1 || T >= DS_MAX_TRIANGLES) return fail(DS_ERR_INVALID_ARG, "T out of range");
     if (grid_n < 1 || grid_n > DS_MAX_GRID_N) return fail(DS_ERR_INVALID_ARG, "grid_n out of range");
     if (C < 2 || C > DS_MAX_CHANNELS) return fail(DS_ERR_INVALID_ARG, "C out of range");
-    if (flags != DS_COPY && flags != DS_BORROW) return fail(DS_ERR_INVALID_ARG, "bad flags");
+    if ((flags & ~(DS_BORROW | DS_STATIC)) != 0) return fail(DS_ERR_INVALID_ARG, "bad flags");
     std::lock_guard<std::mutex> lk(c->mu);
     DeviceGuard g(c->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -461,7 +471,8 @@ ds_status ds_soup_upload(ds_ctx* c, const float* verts, const float* tex, int32_
         cudaGetLastError();
         return fail(DS_ERR_OOM, "cudaMalloc failed for activations");
     }
-    if (flags == DS_COPY) {
+    s.fixed = (flags & DS_STATIC) != 0;
+    if ((flags & DS_BORROW) == 0) {
         if (cudaMalloc(reinterpret_cast<void**>(&s.own), sizeof(float) * (nv + nt + 4)) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(s.act);
@@ -509,61 +520,29 @@ ds_status ds_soup_free(ds_ctx* c, int32_t soup_id) {
     return DS_OK;
 }
 
-ds_status ds_raster_forward(ds_ctx* c, int32_t soup_id, const ds_camera* cams, const uint64_t* seeds, int32_t n_views,
-                            int32_t S, uint32_t mode, const float* bg, const ds_view_out* out, void* stream) {
-    if (!c) return fail(DS_ERR_INVALID_ARG, "NULL context");
-    std::lock_guard<std::mutex> lk(c->mu);
-    DeviceGuard g(c->device);
-    Soup* s = nullptr;
-    DS_TRY(get_soup(c, soup_id, &s));
-    DS_TRY(check_views(cams, n_views, S));
-    const uint32_t base_mode = mode & 0xffu;
-    if (base_mode != DS_MODE_STOCHASTIC && base_mode != DS_MODE_THRESHOLD_HALF)
-        return fail(DS_ERR_INVALID_ARG, "bad mode");
-    if ((mode & ~(0xffu | DS_NO_SYNC)) != 0) return fail(DS_ERR_INVALID_ARG, "unknown mode bits");
-    if (!seeds && base_mode == DS_MODE_STOCHASTIC) return fail(DS_ERR_INVALID_ARG, "seeds is NULL");
-    if (!bg || !out) return fail(DS_ERR_INVALID_ARG, "bg or out is NULL");
+}  // extern "C"
+
+namespace {
+
+ds_status check_outputs(const ds_view_out* out, int32_t n_views) {
+    if (!out) return fail(DS_ERR_INVALID_ARG, "out is NULL");
     for (int v = 0; v < n_views; ++v) {
         if (!out[v].gbuf || !out[v].color) return fail(DS_ERR_INVALID_ARG, "view output buffer is NULL");
         if (((uintptr_t)out[v].gbuf & 15) != 0) return fail(DS_ERR_INVALID_ARG, "gbuf must be 16-byte aligned");
     }
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    c->last_stream = st;
-    ds::ViewTable& vt = *c->vt;   // calls on one context are serialised by its mutex
-    build_table(vt, cams, seeds, n_views, S, out, nullptr);
-    DS_TRY(prepare(c, soup_id, *s, cams, vt, (mode & DS_NO_SYNC) == 0, st));
-    ds::Bg b{};
-    for (int i = 0; i < s->C - 1; ++i) b.c[i] = bg[i];
-    const ds::SoupDev sd = soup_dev(*s);
-    const int grid = 0;
-    {
-        StageScope p(c, ds::kStRasterFwd, st);
-        DS_TRY_CUDA(cudaMemsetAsync(c->d_counter(), 0, 4, st));
-        DS_TRY_CUDA(ds::launch_raster_fwd(vt, sd, c->recs.as<ds::SetupRec>(), c->keys[c->plan.res].as<uint32_t>(),
-                                          c->vals[c->plan.res].as<uint32_t>(), c->ranges.as<uint2>(), c->plan.DB,
-                                          base_mode, b, c->d_counter(), grid, st));
-    }
-    bool want_front = false;
-    for (int v = 0; v < n_views; ++v) want_front = want_front || out[v].n_front;
-    if (want_front) {
-        StageScope p(c, ds::kStCount, st);
-        DS_TRY_CUDA(cudaMemsetAsync(c->d_counter() + 1, 0, 4, st));
-        DS_TRY_CUDA(ds::launch_raster_count(vt, sd, c->recs.as<ds::SetupRec>(), c->keys[c->plan.res].as<uint32_t>(),
-                                            c->vals[c->plan.res].as<uint32_t>(), c->ranges.as<uint2>(), c->plan.DB, 0,
-                                            nullptr, c->d_counter() + 1, grid, st));
-    }
     return DS_OK;
 }
 
-ds_status ds_raster_backward(ds_ctx* c, int32_t soup_id, const ds_camera* cams, int32_t n_views, int32_t S,
-                             const ds_view_out* fwd, const ds_view_gin* gin, uint32_t grad_flags, float* grad_verts,
-                             float* grad_tex, void* stream) {
-    if (!c) return fail(DS_ERR_INVALID_ARG, "NULL context");
-    std::lock_guard<std::mutex> lk(c->mu);
-    DeviceGuard g(c->device);
-    Soup* s = nullptr;
-    DS_TRY(get_soup(c, soup_id, &s));
-    DS_TRY(check_views(cams, n_views, S));
+ds_status check_mode(uint32_t mode, bool have_seeds) {
+    const uint32_t base_mode = mode & 0xffu;
+    if (base_mode != DS_MODE_STOCHASTIC && base_mode != DS_MODE_THRESHOLD_HALF)
+        return fail(DS_ERR_INVALID_ARG, "bad mode");
+    if ((mode & ~(0xffu | DS_NO_SYNC)) != 0) return fail(DS_ERR_INVALID_ARG, "unknown mode bits");
+    if (!have_seeds && base_mode == DS_MODE_STOCHASTIC) return fail(DS_ERR_INVALID_ARG, "seeds is NULL");
+    return DS_OK;
+}
+
+ds_status check_gin(const ds_view_out* fwd, const ds_view_gin* gin, int32_t n_views, uint32_t grad_flags) {
     if ((grad_flags & ~(DS_G_ALL | DS_REUSE_FORWARD | DS_OVERWRITE)) != 0)
         return fail(DS_ERR_INVALID_ARG, "unknown gradient flags");
     if (!fwd || !gin) return fail(DS_ERR_INVALID_ARG, "fwd or gin is NULL");
@@ -574,16 +553,45 @@ ds_status ds_raster_backward(ds_ctx* c, int32_t soup_id, const ds_camera* cams, 
         if (need_color && !gin[v].grad_color) return fail(DS_ERR_INVALID_ARG, "grad_color is NULL");
         if ((grad_flags & DS_G_EDGE) && !fwd[v].color) return fail(DS_ERR_INVALID_ARG, "fwd color is NULL");
     }
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    c->last_stream = st;
+    return DS_OK;
+}
+
+// Forward after validation; vt is filled.  host_cams is NULL for device cameras.
+ds_status forward_impl(ds_ctx* c, int32_t soup_id, Soup& s, const ds_camera* host_cams, uint32_t mode, const float* bg,
+                       const ds_view_out* out, cudaStream_t st) {
     ds::ViewTable& vt = *c->vt;
-    build_table(vt, cams, nullptr, n_views, S, fwd, gin);
-    if (!((grad_flags & DS_REUSE_FORWARD) && plan_matches(c, soup_id, cams, n_views)))
-        DS_TRY(prepare(c, soup_id, *s, cams, vt, true, st));
-    const ds::SoupDev sd = soup_dev(*s);
+    DS_TRY(prepare(c, soup_id, s, host_cams, vt, (mode & DS_NO_SYNC) == 0, st));
+    ds::Bg b{};
+    for (int i = 0; i < s.C - 1; ++i) b.c[i] = bg[i];
+    const ds::SoupDev sd = soup_dev(s);
+    const int grid = 0;
+    {
+        StageScope p(c, ds::kStRasterFwd, st);
+        DS_TRY_CUDA(cudaMemsetAsync(c->d_counter(), 0, 4, st));
+        DS_TRY_CUDA(ds::launch_raster_fwd(vt, sd, c->recs.as<ds::SetupRec>(), c->keys[c->plan.res].as<uint32_t>(),
+                                          c->vals[c->plan.res].as<uint32_t>(), c->ranges.as<uint2>(), c->plan.DB,
+                                          mode & 0xffu, b, c->d_counter(), grid, st));
+    }
+    bool want_front = false;
+    for (int v = 0; v < vt.n; ++v) want_front = want_front || out[v].n_front;
+    if (want_front) {
+        StageScope p(c, ds::kStCount, st);
+        DS_TRY_CUDA(cudaMemsetAsync(c->d_counter() + 1, 0, 4, st));
+        DS_TRY_CUDA(ds::launch_raster_count(vt, sd, c->recs.as<ds::SetupRec>(), c->keys[c->plan.res].as<uint32_t>(),
+                                            c->vals[c->plan.res].as<uint32_t>(), c->ranges.as<uint2>(), c->plan.DB, 0,
+                                            nullptr, c->d_counter() + 1, grid, st));
+    }
+    return DS_OK;
+}
+
+// Backward after validation; vt is filled and the plan is current.
+ds_status backward_impl(ds_ctx* c, Soup& s, uint32_t grad_flags, float* grad_verts, float* grad_tex, cudaStream_t st) {
+    ds::ViewTable& vt = *c->vt;
+    const int n_views = vt.n;
+    const ds::SoupDev sd = soup_dev(s);
     const int grid = 0;
     const uint32_t gflags = grad_flags & DS_G_ALL;
-    const size_t n_tex = (size_t)s->T * s->V * s->C, n_verts = 9 * (size_t)s->T;
+    const size_t n_tex = (size_t)s.T * s.V * s.C, n_verts = 9 * (size_t)s.T;
     const bool want_tex = grad_tex && (gflags & (DS_G_TEX | DS_G_SCORE));
     const bool want_verts = grad_verts && (gflags & (DS_G_INTERIOR | DS_G_EDGE));
     const bool overwrite = (grad_flags & DS_OVERWRITE) != 0;
@@ -598,7 +606,7 @@ ds_status ds_raster_backward(ds_ctx* c, int32_t soup_id, const ds_camera* cams, 
         DS_TRY(c->acc_verts.ensure(sizeof(double) * n_verts, "vertex gradient accumulator"));
         acc_verts = c->acc_verts.as<double>();
         DS_TRY_CUDA(cudaMemsetAsync(acc_verts, 0, sizeof(double) * n_verts, st));
-        DS_TRY(c->geom.ensure(sizeof(ds::GeomRec) * (size_t)n_views * s->T, "vertex-gradient geometry"));
+        DS_TRY(c->geom.ensure(sizeof(ds::GeomRec) * (size_t)n_views * s.T, "vertex-gradient geometry"));
         StageScope p(c, ds::kStGeom, st);
         DS_TRY_CUDA(ds::launch_geom(vt, sd, c->geom.as<ds::GeomRec>(), st));
     }
@@ -623,6 +631,117 @@ ds_status ds_raster_backward(ds_ctx* c, int32_t soup_id, const ds_camera* cams, 
         if (want_verts) DS_TRY_CUDA(ds::launch_grad_finish(acc_verts, grad_verts, (long long)n_verts, overwrite, st));
         else if (grad_verts && overwrite) DS_TRY_CUDA(cudaMemsetAsync(grad_verts, 0, sizeof(float) * n_verts, st));
     }
+    return DS_OK;
+}
+
+// View table for device-resident cameras: sizes from the host, cameras and
+// seeds read by the kernels from device memory.
+ds_status build_table_devcam(ds::ViewTable& vt, const int32_t* wh, const ds_camera* dcams, const uint64_t* dseeds,
+                             int32_t n_views, int32_t S, const ds_view_out* out, const ds_view_gin* gin) {
+    if (!wh || !dcams) return fail(DS_ERR_INVALID_ARG, "wh or cams is NULL");
+    if (n_views < 1 || n_views > DS_MAX_VIEWS) return fail(DS_ERR_INVALID_ARG, "n_views out of range");
+    if (S < 1 || S > DS_MAX_SAMPLES) return fail(DS_ERR_INVALID_ARG, "S must be in [1, 64]");
+    static thread_local std::vector<ds_camera> tmp;
+    tmp.assign(n_views, ds_camera{});
+    for (int v = 0; v < n_views; ++v) {
+        if (wh[2 * v] < 1 || wh[2 * v + 1] < 1 || wh[2 * v] > DS_MAX_RESOLUTION || wh[2 * v + 1] > DS_MAX_RESOLUTION)
+            return fail(DS_ERR_INVALID_ARG, "view size out of range");
+        tmp[v].width = wh[2 * v];
+        tmp[v].height = wh[2 * v + 1];
+    }
+    build_table(vt, tmp.data(), nullptr, n_views, S, out, gin);
+    vt.dcam = dcams;
+    vt.dseed = reinterpret_cast<const unsigned long long*>(dseeds);
+    return DS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ds_status ds_raster_forward(ds_ctx* c, int32_t soup_id, const ds_camera* cams, const uint64_t* seeds, int32_t n_views,
+                            int32_t S, uint32_t mode, const float* bg, const ds_view_out* out, void* stream) {
+    if (!c) return fail(DS_ERR_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    Soup* s = nullptr;
+    DS_TRY(get_soup(c, soup_id, &s));
+    DS_TRY(check_views(cams, n_views, S));
+    DS_TRY(check_mode(mode, seeds != nullptr));
+    if (!bg) return fail(DS_ERR_INVALID_ARG, "bg is NULL");
+    DS_TRY(check_outputs(out, n_views));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    build_table(*c->vt, cams, seeds, n_views, S, out, nullptr);   // calls on one context are serialised
+    return forward_impl(c, soup_id, *s, cams, mode, bg, out, st);
+}
+
+ds_status ds_raster_forward_devcam(ds_ctx* c, int32_t soup_id, const int32_t* wh, const ds_camera* cams,
+                                   const uint64_t* seeds, int32_t n_views, int32_t S, uint32_t mode, const float* bg,
+                                   const ds_view_out* out, void* stream) {
+    if (!c) return fail(DS_ERR_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    Soup* s = nullptr;
+    DS_TRY(get_soup(c, soup_id, &s));
+    DS_TRY(check_mode(mode, seeds != nullptr));
+    if (!bg) return fail(DS_ERR_INVALID_ARG, "bg is NULL");
+    DS_TRY(check_outputs(out, n_views));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    DS_TRY(build_table_devcam(*c->vt, wh, cams, seeds, n_views, S, out, nullptr));
+    return forward_impl(c, soup_id, *s, nullptr, mode, bg, out, st);
+}
+
+ds_status ds_raster_backward(ds_ctx* c, int32_t soup_id, const ds_camera* cams, int32_t n_views, int32_t S,
+                             const ds_view_out* fwd, const ds_view_gin* gin, uint32_t grad_flags, float* grad_verts,
+                             float* grad_tex, void* stream) {
+    if (!c) return fail(DS_ERR_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    Soup* s = nullptr;
+    DS_TRY(get_soup(c, soup_id, &s));
+    DS_TRY(check_views(cams, n_views, S));
+    DS_TRY(check_gin(fwd, gin, n_views, grad_flags));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    build_table(*c->vt, cams, nullptr, n_views, S, fwd, gin);
+    if (!((grad_flags & DS_REUSE_FORWARD) && plan_matches(c, soup_id, cams, n_views)))
+        DS_TRY(prepare(c, soup_id, *s, cams, *c->vt, true, st));
+    return backward_impl(c, *s, grad_flags, grad_verts, grad_tex, st);
+}
+
+ds_status ds_raster_backward_devcam(ds_ctx* c, int32_t soup_id, const int32_t* wh, const ds_camera* cams,
+                                    int32_t n_views, int32_t S, const ds_view_out* fwd, const ds_view_gin* gin,
+                                    uint32_t grad_flags, float* grad_verts, float* grad_tex, void* stream) {
+    if (!c) return fail(DS_ERR_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    Soup* s = nullptr;
+    DS_TRY(get_soup(c, soup_id, &s));
+    DS_TRY(check_gin(fwd, gin, n_views, grad_flags));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    DS_TRY(build_table_devcam(*c->vt, wh, cams, nullptr, n_views, S, fwd, gin));
+    const bool reuse = (grad_flags & DS_REUSE_FORWARD) && c->plan.valid && c->plan.devcam && c->plan.soup == soup_id &&
+                       c->plan.n_tiles == total_tiles(*c->vt) && c->plan.n_views == n_views;
+    if (!reuse) DS_TRY(prepare(c, soup_id, *s, nullptr, *c->vt, true, st));
+    return backward_impl(c, *s, grad_flags, grad_verts, grad_tex, st);
+}
+
+ds_status ds_reserve(ds_ctx* c, int64_t pairs) {
+    if (!c || pairs < 0 || pairs > 0x7fffffffLL) return fail(DS_ERR_INVALID_ARG, "bad context or pair count");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    const size_t K = (size_t)(pairs > 0 ? pairs : 1);
+    for (int b = 0; b < 2; ++b) {
+        DS_TRY(c->keys[b].ensure(4 * K, "bin keys"));
+        DS_TRY(c->vals[b].ensure(4 * K, "bin values"));
+    }
+    const size_t nblk = (K + ds::kSortBlock - 1) / ds::kSortBlock;
+    DS_TRY(c->hist.ensure(4 * 256 * nblk, "radix histogram"));
+    DS_TRY(c->hist_scan.ensure(4 * 256 * nblk, "radix offsets"));
+    DS_TRY(ensure_scan(c, (int64_t)(256 * nblk)));
     return DS_OK;
 }
 

@@ -56,7 +56,7 @@ __global__ void k_geom(const __grid_constant__ ViewTable vt, const SoupDev s, Ge
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (gid >= (long long)vt.n * s.T) return;
     const int v = (int)(gid / s.T), t = (int)(gid - (long long)v * s.T);
-    const DevCam& c = vt.v[v].cam;
+    const DevCam& c = view_cam(vt, v);
     double V[3][3];
     const float* p = s.verts + 9LL * t;
 #pragma unroll
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_BWD)
                 float gv[9];
 #pragma unroll
                 for (int k = 0; k < 9; ++k) gv[k] = 0.f;
-                if (act) interior_grad(geom + (size_t)wi.v * s.T + wt[q], V.cam, px, py, G, gv);
+                if (act) interior_grad(geom + (size_t)wi.v * s.T + wt[q], view_cam(vt, wi.v), px, py, G, gv);
                 scatter_verts_run(acc_verts, act, wt[q], gv);
             }
         }
@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_EDGE)
                     const int xX = jb.xy & 0xffff, yX = jb.xy >> 16;
                     const int xY = xX + (jb.dir == 0) - (jb.dir == 1), yY = yX + (jb.dir == 2) - (jb.dir == 3);
                     t = jb.t;
-                    act = edge_side(V.cam, vrec, vgeom + t, t, xX, yX, xY, yY, jb.tY, jb.phi, acc);
+                    act = edge_side(view_cam(vt, wi.v), vrec, vgeom + t, t, xX, yX, xY, yY, jb.tY, jb.phi, acc);
                 }
                 scatter_verts_run(acc_verts, act, t, acc);
             }

@@ -46,8 +46,26 @@ struct ViewTable {
     int S;          // samples per pixel
     int n_groups;   // ceil(S / 4)
     int n_items;    // total work items
+    // Optional device-resident cameras (ds_camera[n]) and seeds (uint64[n]):
+    // when set they replace v[i].cam and v[i].seed_*, so that a captured
+    // CUDA graph can render views chosen after capture.
+    const ds_camera* dcam;
+    const unsigned long long* dseed;
     ViewDesc v[DS_MAX_VIEWS];
 };
+
+// Camera and seed of view v (device table if present, else the parameters).
+__device__ __forceinline__ const DevCam& view_cam(const ViewTable& vt, int v) {
+    if (vt.dcam) return *reinterpret_cast<const DevCam*>(reinterpret_cast<const char*>(vt.dcam + v) + 8);
+    return vt.v[v].cam;
+}
+__device__ __forceinline__ uint2 view_seed(const ViewTable& vt, int v) {
+    if (vt.dseed) {
+        const unsigned long long s = vt.dseed[v];
+        return make_uint2((uint32_t)s, (uint32_t)(s >> 32));
+    }
+    return make_uint2(vt.v[v].seed_lo, vt.v[v].seed_hi);
+}
 
 // Triangle set-up of one (view, triangle), 64 bytes.  Edge i runs from vertex
 // i+1 to vertex i+2; E_i(X, Y) = A_i X + B_i Y + C_i in 1/256-pixel units is

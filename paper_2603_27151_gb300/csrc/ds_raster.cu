@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
         const bool valid = px < V.W && py < V.H;
         const int s0 = wi.g * kSampleGroup;
         const int ns = min(SG, vt.S - s0);
+        const uint2 seed = view_seed(vt, wi.v);
 
         int bt[SG];
         float brho[SG], bb1[SG], bb2[SG], bD[SG];
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
                     float tau[4] = {0.5f, 0.5f, 0.5f, 0.5f};
                     if (stochastic) {
                         const uint4 w = philox4x32_10(make_uint4((uint32_t)px, (uint32_t)py, (uint32_t)t, (uint32_t)wi.g),
-                                                      V.seed_lo, V.seed_hi);
+                                                      seed.x, seed.y);
                         tau[0] = word_to_tau(w.x);
                         tau[1] = word_to_tau(w.y);
                         tau[2] = word_to_tau(w.z);

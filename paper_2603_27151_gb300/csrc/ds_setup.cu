@@ -82,7 +82,7 @@ __global__ void k_setup(const __grid_constant__ ViewTable vt, const SoupDev s,
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (gid >= (long long)vt.n * s.T) return;
     const int v = (int)(gid / s.T), t = (int)(gid - (long long)v * s.T);
-    const DevCam& cam = vt.v[v].cam;
+    const DevCam& cam = view_cam(vt, v);
     const int W = vt.v[v].W, H = vt.v[v].H;
     const float* p = s.verts + 9LL * t;
 

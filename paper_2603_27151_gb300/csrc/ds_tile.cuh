@@ -148,8 +148,10 @@ __device__ __forceinline__ bool warp_run_sum(unsigned long long key, float (&v)[
     const unsigned heads = __ballot_sync(kFullMask, head);
     const unsigned above = heads & ~((2u << lane) - 1u);
     const int end = above ? __ffs(above) - 1 : 32;
+    if (heads == kFullMask) return true;   // every run has one lane
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
+        if (!__any_sync(kFullMask, lane + d < end)) break;   // no run is longer than d
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
             const float o = __shfl_down_sync(kFullMask, v[q], d);

@@ -25,7 +25,7 @@ DS_G_TEX, DS_G_SCORE, DS_G_INTERIOR, DS_G_EDGE = 1, 2, 4, 8
 DS_G_ALL = 15
 DS_REUSE_FORWARD = 0x100
 DS_OVERWRITE = 0x200
-DS_COPY, DS_BORROW = 0, 1
+DS_COPY, DS_BORROW, DS_STATIC = 0, 1, 2
 ERRORS = {-1: "DS_ERR_INVALID_ARG", -2: "DS_ERR_OOM", -3: "DS_ERR_CUDA", -4: "DS_ERR_CAPACITY",
           -5: "DS_ERR_TIMEOUT", -6: "DS_ERR_NOT_FOUND", -7: "DS_ERR_BUSY"}
 
@@ -44,6 +44,11 @@ class ds_camera(ctypes.Structure):
 
 class ds_view_out(ctypes.Structure):
     _fields_ = [("gbuf", ctypes.c_void_p), ("color", ctypes.c_void_p), ("n_front", ctypes.c_void_p)]
+
+
+class ds_request_stats(ctypes.Structure):
+    _fields_ = [("submit_ns", ctypes.c_int64), ("launch_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64),
+                ("batch", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class ds_view_gin(ctypes.Structure):
@@ -95,6 +100,24 @@ def load():
     L.ds_plan_stats.restype = i32
     L.ds_raster_forward_noalloc.argtypes = [P, P, i32, i32, i32, P, P, i32, i32, u32, P, P, P]
     L.ds_raster_forward_noalloc.restype = i32
+    L.ds_raster_forward_devcam.argtypes = [P, i32, P, P, P, i32, i32, u32, P, P, P]
+    L.ds_raster_forward_devcam.restype = i32
+    L.ds_raster_backward_devcam.argtypes = [P, i32, P, P, i32, i32, P, P, u32, P, P, P]
+    L.ds_raster_backward_devcam.restype = i32
+    L.ds_reserve.argtypes = [P, ctypes.c_int64]
+    L.ds_reserve.restype = i32
+    L.ds_server_create.argtypes = [i32, i32, ctypes.c_size_t, i32, ctypes.c_int64, ctypes.POINTER(P)]
+    L.ds_server_create.restype = i32
+    L.ds_server_add_soup.argtypes = [P, P, P, i32, i32, i32, ctypes.POINTER(i32)]
+    L.ds_server_add_soup.restype = i32
+    L.ds_render_request.argtypes = [P, i32, P, ctypes.c_uint64, u32, P, P, ctypes.POINTER(ctypes.c_uint64)]
+    L.ds_render_request.restype = i32
+    L.ds_request_wait.argtypes = [P, ctypes.c_uint64, i32, P]
+    L.ds_request_wait.restype = i32
+    L.ds_server_pause.argtypes = [P, i32]
+    L.ds_server_pause.restype = i32
+    L.ds_server_destroy.argtypes = [P]
+    L.ds_server_destroy.restype = i32
     _lib = L
     return L
 
@@ -160,13 +183,15 @@ class Context:
             pass
 
     # -------------------------------------------------------------- soups
-    def soup_upload(self, verts, tex, grid_n: int, borrow: bool = False, stream=None) -> int:
+    def soup_upload(self, verts, tex, grid_n: int, borrow: bool = False, static: bool = False,
+                    stream=None) -> int:
         """verts: [T,3,3] float32 CUDA tensor; tex: [T,V,C] float32 CUDA tensor."""
         assert verts.is_cuda and tex.is_cuda and verts.is_contiguous() and tex.is_contiguous()
         T, V, C = tex.shape
         sid = ctypes.c_int32(-1)
-        _check(load().ds_soup_upload(self.h, _ptr(verts), _ptr(tex), T, grid_n, C,
-                                     DS_BORROW if borrow else DS_COPY, ctypes.byref(sid), _stream(stream)))
+        flags = (DS_BORROW if borrow else DS_COPY) | (DS_STATIC if static else 0)
+        _check(load().ds_soup_upload(self.h, _ptr(verts), _ptr(tex), T, grid_n, C, flags, ctypes.byref(sid),
+                                     _stream(stream)))
         return sid.value
 
     def soup_free(self, soup_id: int):
@@ -201,6 +226,38 @@ class Context:
             gin[v].score_w = score_ws[v].data_ptr() if score_ws is not None and score_ws[v] is not None else None
         _check(load().ds_raster_backward(self.h, soup_id, ca, n, S, fwd, gin, flags,
                                          _ptr(grad_verts), _ptr(grad_tex), _stream(stream)))
+
+    def raster_forward_devcam(self, soup_id, wh, cams_dev, seeds_dev, S, mode, bg, gbufs, colors, n_fronts=None,
+                              stream=None):
+        """Forward with device-resident cameras (uint8 tensor of n x 76 bytes,
+        the ds_camera layout) and seeds (int64 tensor [n]); wh: list of (W, H)."""
+        n = len(wh)
+        wha = (ctypes.c_int32 * (2 * n))(*[int(x) for p in wh for x in p])
+        bga = np.ascontiguousarray(bg, np.float32)
+        outs = (ds_view_out * n)()
+        for v in range(n):
+            outs[v].gbuf = gbufs[v].data_ptr()
+            outs[v].color = colors[v].data_ptr()
+            outs[v].n_front = n_fronts[v].data_ptr() if n_fronts is not None and n_fronts[v] is not None else None
+        _check(load().ds_raster_forward_devcam(self.h, soup_id, wha, _ptr(cams_dev), _ptr(seeds_dev), n, S, mode,
+                                               bga.ctypes.data_as(ctypes.c_void_p), outs, _stream(stream)))
+
+    def raster_backward_devcam(self, soup_id, wh, cams_dev, S, gbufs, colors, grad_colors, score_ws, flags,
+                               grad_verts=None, grad_tex=None, stream=None):
+        n = len(wh)
+        wha = (ctypes.c_int32 * (2 * n))(*[int(x) for p in wh for x in p])
+        fwd = (ds_view_out * n)()
+        gin = (ds_view_gin * n)()
+        for v in range(n):
+            fwd[v].gbuf = gbufs[v].data_ptr()
+            fwd[v].color = colors[v].data_ptr() if colors is not None else None
+            gin[v].grad_color = grad_colors[v].data_ptr() if grad_colors is not None else None
+            gin[v].score_w = score_ws[v].data_ptr() if score_ws is not None and score_ws[v] is not None else None
+        _check(load().ds_raster_backward_devcam(self.h, soup_id, wha, _ptr(cams_dev), n, S, fwd, gin, flags,
+                                                _ptr(grad_verts), _ptr(grad_tex), _stream(stream)))
+
+    def reserve(self, pairs: int):
+        _check(load().ds_reserve(self.h, int(pairs)))
 
     def fragment_count(self, soup_id, cams, stream=None) -> int:
         n = len(cams)
@@ -267,8 +324,72 @@ def loss_l2(colors, targets, grad_colors=None, score_ws=None, loss=None, scale=1
                              float(scale), _ptr(loss), _stream(stream)))
 
 
+class Server:
+    """Continuous-batching render server (``ds_server_*``)."""
+
+    def __init__(self, device: int = 0, n_streams: int = 2, mem_budget: int = 4 << 30, max_batch: int = 16,
+                 reserve_pairs: int = 1 << 22):
+        L = load()
+        h = ctypes.c_void_p()
+        _check(L.ds_server_create(int(device), int(n_streams), int(mem_budget), int(max_batch), int(reserve_pairs),
+                                  ctypes.byref(h)))
+        self.h = h
+        self._keep = {}   # ticket -> (out struct, bg array)
+
+    def add_soup(self, verts, tex, grid_n: int) -> int:
+        assert verts.is_cuda and tex.is_cuda and verts.is_contiguous() and tex.is_contiguous()
+        T, V, C = tex.shape
+        sid = ctypes.c_int32(-1)
+        _check(load().ds_server_add_soup(self.h, _ptr(verts), _ptr(tex), T, grid_n, C, ctypes.byref(sid)))
+        return sid.value
+
+    def submit(self, soup_id, cam, seed, mode, bg, gbuf, color, n_front=None) -> int:
+        """Queue one view (gbuf int32 [1,H,W,4], color float32 [1,C-1,H,W]);
+        returns the ticket."""
+        ca = cameras([cam])
+        out = ds_view_out()
+        out.gbuf, out.color = gbuf.data_ptr(), color.data_ptr()
+        out.n_front = n_front.data_ptr() if n_front is not None else None
+        bga = None if bg is None else np.ascontiguousarray(bg, np.float32)
+        tk = ctypes.c_uint64(0)
+        _check(load().ds_render_request(self.h, int(soup_id), ca, int(seed), int(mode),
+                                        None if bga is None else bga.ctypes.data_as(ctypes.c_void_p),
+                                        ctypes.byref(out), ctypes.byref(tk)))
+        self._keep[tk.value] = (out, bga, gbuf, color, n_front)
+        return tk.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> dict:
+        st = ds_request_stats()
+        rc = load().ds_request_wait(self.h, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(st))
+        if rc != -5:
+            self._keep.pop(ticket, None)
+        _check(rc)
+        return {"submit_ns": st.submit_ns, "launch_ns": st.launch_ns, "done_ns": st.done_ns, "batch": st.batch}
+
+    def pause(self, on: bool = True):
+        _check(load().ds_server_pause(self.h, 1 if on else 0))
+
+    def close(self):
+        if self.h:
+            _check(load().ds_server_destroy(self.h))
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def kernel_launches() -> int:
     return int(load().ds_kernel_launches())
+
+
+def camera_bytes(cams) -> np.ndarray:
+    """ds_camera records of ``cams`` as a uint8 array [n, 76] (for device upload)."""
+    arr = cameras(cams)
+    return np.frombuffer(bytes(arr), dtype=np.uint8).reshape(len(cams), ctypes.sizeof(ds_camera)).copy()
 
 
 def alloc_outputs(cams, S, C, device="cuda", n_front=False):

@@ -179,6 +179,110 @@ class Workload:
         }
 
 
+def _plain_leg(wl, steps: int):
+    """The same kernels on the plain path: one view per call (each call bins
+    its own view and synchronises once to size its bins), no batching of
+    views, no graph.  Gradients are overwritten by the first view and
+    accumulated by the others, as in the batched step."""
+    import torch
+    N, sc, S = wl.N, wl.sc, wl.S
+
+    def step():
+        for v in range(len(sc.cams)):
+            one = slice(v, v + 1)
+            wl.ctx.raster_forward(wl.sid, sc.cams[one], sc.seeds[one], S, N.DS_MODE_STOCHASTIC, sc.bg, wl.g[one],
+                                  wl.col[one])
+            N.loss_l2(wl.col[one], wl.targets[one], wl.gcol[one], wl.sw[one], wl.loss, scale=1.0 / S)
+            wl.ctx.raster_backward(wl.sid, sc.cams[one], S, wl.g[one], wl.col[one], wl.gcol[one], wl.sw[one],
+                                   N.DS_G_ALL | N.DS_REUSE_FORWARD | (N.DS_OVERWRITE if v == 0 else 0), wl.gv, wl.gt)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"value": wl.fragments / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "what": "same kernels, one view per call (%d calls of forward + loss + backward per step), no graph"
+                    % len(sc.cams)}
+
+
+def _train_leg(device: str, iters: int):
+    """The captured training step (20,000 triangles, 4 views of 1024x768 per
+    step drawn from 100 cameras, Adam) against the same step run eagerly."""
+    import torch
+    from paper_2603_27151_gb300.train import TrainStep
+    ts = TrainStep(device)
+    ts.capture(warmup=3)
+    for _ in range(3):
+        ts.step()
+    torch.cuda.synchronize()
+    l0 = float(ts.loss.item())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(iters):
+        ts.step()
+    e1.record()
+    ok = ts.check()
+    ms = e0.elapsed_time(e1) / iters
+    l1 = float(ts.loss.item())
+    # eager: the same body without the graph (host launches, one bin-sizing
+    # synchronisation per forward)
+    e0.record()
+    n_eager = max(5, iters // 4)
+    for _ in range(n_eager):
+        ts._load_views(ts.step_no)
+        ts._body(no_sync=False)
+        ts.step_no += 1
+    e1.record()
+    torch.cuda.synchronize()
+    ms_eager = e0.elapsed_time(e1) / n_eager
+    px = ts.per_step * 1024 * 768
+    return {"iters_per_s": 1e3 / ms, "ms_per_iter": ms, "pixels_per_s": px / (ms / 1e3),
+            "eager_iters_per_s": 1e3 / ms_eager, "eager_ms_per_iter": ms_eager, "status_ok": ok,
+            "loss_before": l0, "loss_after": l1,
+            "what": "20,000 triangles (N=8, C=8), 4 of 100 views at 1024x768 per step, S=1, L2 loss, Adam; "
+                    "one CUDA graph per step vs the same step launched eagerly"}
+
+
+def _serve_leg(device: str, seconds: float, plain: bool):
+    """Replay the Poisson request stream (16 resident soups, 2000 requests/s,
+    resolutions 256^2 .. 1920x1080, forward with binary opacity)."""
+    import torch
+    from paper_2603_27151_gb300 import native as N
+    from paper_2603_27151_gb300.serve import SlotPool, replay
+    soups, reqs = I.serving_workload(duration=seconds)
+    if plain:
+        srv = N.Server(torch.cuda.current_device(), n_streams=1, mem_budget=8 << 30, max_batch=1,
+                       reserve_pairs=1 << 22)
+    else:
+        srv = N.Server(torch.cuda.current_device(), n_streams=4, mem_budget=8 << 30, max_batch=16,
+                       reserve_pairs=1 << 22)
+    ids = [srv.add_soup(torch.from_numpy(sc.verts).to(device), torch.from_numpy(sc.tex).to(device), sc.grid_n)
+           for sc in soups]
+    pool = SlotPool(I.SERVE_RESOLUTIONS, 48, 8, device)
+    # warm-up: every soup at every resolution (sizes each worker's scratch)
+    warm = [(0.0, k, I.look_at(np.array([0.0, -3.0, 0.5]), w, h), 1) for k in range(len(soups))
+            for (w, h) in I.SERVE_RESOLUTIONS]
+    replay(srv, ids, warm * 2, pool, time_scale=0.0)
+    r = replay(srv, ids, reqs, pool)
+    srv.close()
+    lat = r["latency_ms"]
+    n = len(lat)
+    bytes_per_px = 16 + 4 * 7
+    return {"requests": n, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "frames_per_s": n / r["span_s"],
+            "pixels_per_s": float(r["pixels"].sum()) / r["span_s"],
+            "output_gbs": float(r["pixels"].sum()) * bytes_per_px / r["span_s"] / 1e9,
+            "mean_batch": float(r["batch"].mean()), "offered_rps": len(reqs) / seconds,
+            "what": ("plain: one stream, one request per launch" if plain else
+                     "4 worker streams, up to 16 same-soup requests per launch, 8 GiB admission budget")}
+
+
 def _gpu_arm(args):
     import torch
     world, rank, local = _dist()
@@ -189,6 +293,13 @@ def _gpu_arm(args):
     dev = "cuda:%d" % local
     from paper_2603_27151_gb300 import native as N
     wl = Workload(rank, dev, args.views)
+    tuning = None
+    if not args.no_tune:
+        # launch parameters from the autotuner (cached per workload); untimed
+        from paper_2603_27151_gb300 import autotune
+        wl.step()
+        tuning = autotune.tuned(wl.ctx, wl.sid, wl.sc.T, wl.sc.grid_n, wl.sc.C, wl.sc.cams, wl.sc.seeds, wl.S,
+                                N.DS_MODE_STOCHASTIC, wl.sc.bg, wl.g, wl.col, wl.gcol, wl.sw, wl.gv, wl.gt, reps=2)
     for _ in range(args.warmup):
         wl.step()
     torch.cuda.synchronize()
@@ -253,6 +364,9 @@ def _gpu_arm(args):
         e2e_s = float(t.item())
     barrier()
 
+    extras = {}
+    if not args.views and not args.no_extras:
+        extras["plain_path"] = _plain_leg(wl, max(2, args.steps // 2))
     if rank != 0:
         return None
     frags_total = wl.fragments * args.steps * world
@@ -271,6 +385,7 @@ def _gpu_arm(args):
         "config": {"workload": WORKLOAD, "triangles": wl.sc.T, "views": len(wl.sc.cams), "samples": wl.S,
                    "fragments_per_step": wl.fragments, "pixel_samples_per_step": wl.pixel_samples,
                    "bin_pairs": wl.pairs, "l2": "inputs larger than L2 (about 3 GB touched per step)",
+                   "tuning": tuning,
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "e2e": {"value": frags_total / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4},
         "gpu_launches": int(launches),
@@ -280,6 +395,17 @@ def _gpu_arm(args):
         "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
         "clocks": clk.summary(),
     }
+    if extras:
+        line["plain_path"] = extras["plain_path"]
+        line["plain_path"]["batched_speedup"] = value / world / extras["plain_path"]["value"]
+    if not args.views and not args.no_extras and world == 1:
+        del wl
+        torch.cuda.empty_cache()
+        line["train"] = _train_leg(dev, args.train_iters)
+        torch.cuda.empty_cache()
+        if args.serve_seconds > 0:
+            line["serve"] = _serve_leg(dev, args.serve_seconds, plain=False)
+            line["serve_plain"] = _serve_leg(dev, args.serve_seconds, plain=True)
     return line
 
 
@@ -366,6 +492,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--views", type=int, default=0,
                     help="use only the first N views (reduced case for profiler captures; not a bench line)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the plain-path, training-step and serving legs")
+    ap.add_argument("--train-iters", type=int, default=50)
+    ap.add_argument("--no-tune", action="store_true", help="default launch parameters instead of the autotuner's")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     if args.impl == "reference":

@@ -275,6 +275,39 @@ DS_API ds_status ds_plan_stats(ds_ctx* ctx, int64_t* pairs, int64_t* tiles);
  * bins overflowed (its outputs are invalid), else DS_OK. */
 DS_API ds_status ds_ctx_status(ds_ctx* ctx);
 
+/* Launch parameters of the tile kernels (no paper counterpart: the work
+ * decomposition of Eq. 5 and Algorithm A1; every setting computes the same
+ * result).  tile_w: tile width in pixels, 8, 16 or 32 (tiles hold 256 pixels,
+ * so 8x32, 16x16 or 32x8).  depth_bits: bits of quantised nearest depth in
+ * the bin key that order each tile's list front to back for the early exit,
+ * -1 = 16 (or fewer when the tile index needs the bits), 0 = unordered.
+ * blocks_per_sm: CTAs per SM of the persistent tile kernels, 0 = each
+ * kernel's occupancy limit.  chunk: triangles staged in shared memory per
+ * round, a multiple of 32 in [32, 256].  Default {16, -1, 0, 256}. */
+typedef struct ds_tuning {
+    int32_t tile_w, depth_bits, blocks_per_sm, chunk;
+} ds_tuning;
+
+/* Set (validated; DS_ERR_INVALID_ARG otherwise) or read a context's tuning.
+ * Setting it invalidates the context's binning plan. */
+DS_API ds_status ds_set_tuning(ds_ctx* ctx, const ds_tuning* t);
+DS_API ds_status ds_get_tuning(ds_ctx* ctx, ds_tuning* t);
+
+/* Autotune the context's tuning on one workload: coordinate search over tile
+ * shape {8x32, 16x16, 32x8}, depth bits {16, 8, 0}, chunk {64, 128, 256} and
+ * CTAs per SM {occupancy, 2, 3}, each candidate timed (median of `reps` in
+ * [1, 100] after one untimed run) with CUDA events on `stream` over
+ * ds_raster_forward (mode) and, when gin is non-NULL, ds_raster_backward with
+ * DS_G_ALL | DS_OVERWRITE into grad_verts / grad_tex.  Arguments as in those
+ * two calls.  Synchronises `stream` after every run.  Sets the fastest tuning
+ * on the context and returns it in *best (host) with its time in *best_ms
+ * (host, may be NULL); the outputs hold the results of a final run with it. */
+DS_API ds_status ds_autotune(ds_ctx* ctx, int32_t soup_id, const ds_camera* cams,
+                             const uint64_t* seeds, int32_t n_views, int32_t S, uint32_t mode,
+                             const float* bg, const ds_view_out* out, const ds_view_gin* gin,
+                             float* grad_verts, float* grad_tex, int32_t reps, ds_tuning* best,
+                             float* best_ms, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Render server: continuous batching of single-view forward requests over
  * resident soups (the inference use of Eq. 5 and Eq. 3; the paper measures

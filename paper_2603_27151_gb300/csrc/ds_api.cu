@@ -107,6 +107,7 @@ struct ds_ctx {
     int64_t scan_cap = 0;
     uint32_t* h_word = nullptr;   // pinned host words
     Plan plan;
+    ds_tuning tune{16, -1, 0, 256};   // tile shape, depth bits, grid, staging chunk
     cudaStream_t last_stream = nullptr;
     ds::ViewTable* vt = nullptr;   // host staging of the kernel parameter table (~9 KB)
 
@@ -251,12 +252,16 @@ ds_status check_views(const ds_camera* cams, int32_t n_views, int32_t S) {
 }
 
 // Fill the view table (tiles, work items, per-view pointers).
-void build_table(ds::ViewTable& vt, const ds_camera* cams, const uint64_t* seeds, int32_t n_views, int32_t S,
+void build_table(ds::ViewTable& vt, const ds_tuning& tu, const ds_camera* cams, const uint64_t* seeds, int32_t n_views,
+                 int32_t S,
                  const ds_view_out* out, const ds_view_gin* gin) {
     std::memset(&vt, 0, sizeof(vt));
     vt.n = n_views;
     vt.S = S;
     vt.n_groups = (S + ds::kSampleGroup - 1) / ds::kSampleGroup;
+    vt.tile_w = tu.tile_w;
+    vt.tile_h = ds::kTilePix / tu.tile_w;
+    vt.chunk = tu.chunk;
     int tile_base = 0, item_base = 0;
     for (int v = 0; v < n_views; ++v) {
         ds::ViewDesc& d = vt.v[v];
@@ -270,8 +275,8 @@ void build_table(ds::ViewTable& vt, const ds_camera* cams, const uint64_t* seeds
         d.cam.near_z = c.near_z;
         d.W = c.width;
         d.H = c.height;
-        d.tiles_x = (c.width + ds::kTile - 1) / ds::kTile;
-        d.tiles_y = (c.height + ds::kTile - 1) / ds::kTile;
+        d.tiles_x = (c.width + vt.tile_w - 1) / vt.tile_w;
+        d.tiles_y = (c.height + vt.tile_h - 1) / vt.tile_h;
         d.tile_base = tile_base;
         d.item_base = item_base;
         tile_base += d.tiles_x * d.tiles_y;
@@ -346,7 +351,7 @@ ds_status prepare(ds_ctx* c, int32_t soup_id, Soup& s, const ds_camera* cams, co
     DS_TRY(ensure_scan(c, (int64_t)256 * (nblk > 0 ? nblk : 1)));
 
     const int tile_bits = bits_for((uint32_t)n_tiles);
-    const int DB = std::min(16, 32 - tile_bits);
+    const int DB = std::min(c->tune.depth_bits >= 0 ? c->tune.depth_bits : 16, 32 - tile_bits);
     {
         StageScope p(c, ds::kStEmit, st);
         DS_TRY_CUDA(ds::launch_emit(vt, s.T, c->recs.as<ds::SetupRec>(), c->counts.as<uint32_t>(), c->offs.as<uint32_t>(),
@@ -556,6 +561,12 @@ ds_status check_gin(const ds_view_out* fwd, const ds_view_gin* gin, int32_t n_vi
     return DS_OK;
 }
 
+// Persistent grid of the tile kernels: the tuning's CTAs per SM, or 0 (the
+// occupancy limit of each kernel).
+int tile_grid(const ds_ctx* c, const ds::ViewTable& vt) {
+    return c->tune.blocks_per_sm > 0 ? ds::persistent_grid(vt.n_items, c->tune.blocks_per_sm) : 0;
+}
+
 // Forward after validation; vt is filled.  host_cams is NULL for device cameras.
 ds_status forward_impl(ds_ctx* c, int32_t soup_id, Soup& s, const ds_camera* host_cams, uint32_t mode, const float* bg,
                        const ds_view_out* out, cudaStream_t st) {
@@ -564,7 +575,7 @@ ds_status forward_impl(ds_ctx* c, int32_t soup_id, Soup& s, const ds_camera* hos
     ds::Bg b{};
     for (int i = 0; i < s.C - 1; ++i) b.c[i] = bg[i];
     const ds::SoupDev sd = soup_dev(s);
-    const int grid = 0;
+    const int grid = tile_grid(c, vt);
     {
         StageScope p(c, ds::kStRasterFwd, st);
         DS_TRY_CUDA(cudaMemsetAsync(c->d_counter(), 0, 4, st));
@@ -589,7 +600,7 @@ ds_status backward_impl(ds_ctx* c, Soup& s, uint32_t grad_flags, float* grad_ver
     ds::ViewTable& vt = *c->vt;
     const int n_views = vt.n;
     const ds::SoupDev sd = soup_dev(s);
-    const int grid = 0;
+    const int grid = tile_grid(c, vt);
     const uint32_t gflags = grad_flags & DS_G_ALL;
     const size_t n_tex = (size_t)s.T * s.V * s.C, n_verts = 9 * (size_t)s.T;
     const bool want_tex = grad_tex && (gflags & (DS_G_TEX | DS_G_SCORE));
@@ -636,7 +647,8 @@ ds_status backward_impl(ds_ctx* c, Soup& s, uint32_t grad_flags, float* grad_ver
 
 // View table for device-resident cameras: sizes from the host, cameras and
 // seeds read by the kernels from device memory.
-ds_status build_table_devcam(ds::ViewTable& vt, const int32_t* wh, const ds_camera* dcams, const uint64_t* dseeds,
+ds_status build_table_devcam(ds::ViewTable& vt, const ds_tuning& tu, const int32_t* wh, const ds_camera* dcams,
+                             const uint64_t* dseeds,
                              int32_t n_views, int32_t S, const ds_view_out* out, const ds_view_gin* gin) {
     if (!wh || !dcams) return fail(DS_ERR_INVALID_ARG, "wh or cams is NULL");
     if (n_views < 1 || n_views > DS_MAX_VIEWS) return fail(DS_ERR_INVALID_ARG, "n_views out of range");
@@ -649,7 +661,7 @@ ds_status build_table_devcam(ds::ViewTable& vt, const int32_t* wh, const ds_came
         tmp[v].width = wh[2 * v];
         tmp[v].height = wh[2 * v + 1];
     }
-    build_table(vt, tmp.data(), nullptr, n_views, S, out, gin);
+    build_table(vt, tu, tmp.data(), nullptr, n_views, S, out, gin);
     vt.dcam = dcams;
     vt.dseed = reinterpret_cast<const unsigned long long*>(dseeds);
     return DS_OK;
@@ -672,7 +684,7 @@ ds_status ds_raster_forward(ds_ctx* c, int32_t soup_id, const ds_camera* cams, c
     DS_TRY(check_outputs(out, n_views));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     c->last_stream = st;
-    build_table(*c->vt, cams, seeds, n_views, S, out, nullptr);   // calls on one context are serialised
+    build_table(*c->vt, c->tune, cams, seeds, n_views, S, out, nullptr);   // calls on one context are serialised
     return forward_impl(c, soup_id, *s, cams, mode, bg, out, st);
 }
 
@@ -689,7 +701,7 @@ ds_status ds_raster_forward_devcam(ds_ctx* c, int32_t soup_id, const int32_t* wh
     DS_TRY(check_outputs(out, n_views));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     c->last_stream = st;
-    DS_TRY(build_table_devcam(*c->vt, wh, cams, seeds, n_views, S, out, nullptr));
+    DS_TRY(build_table_devcam(*c->vt, c->tune, wh, cams, seeds, n_views, S, out, nullptr));
     return forward_impl(c, soup_id, *s, nullptr, mode, bg, out, st);
 }
 
@@ -705,7 +717,7 @@ ds_status ds_raster_backward(ds_ctx* c, int32_t soup_id, const ds_camera* cams, 
     DS_TRY(check_gin(fwd, gin, n_views, grad_flags));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     c->last_stream = st;
-    build_table(*c->vt, cams, nullptr, n_views, S, fwd, gin);
+    build_table(*c->vt, c->tune, cams, nullptr, n_views, S, fwd, gin);
     if (!((grad_flags & DS_REUSE_FORWARD) && plan_matches(c, soup_id, cams, n_views)))
         DS_TRY(prepare(c, soup_id, *s, cams, *c->vt, true, st));
     return backward_impl(c, *s, grad_flags, grad_verts, grad_tex, st);
@@ -722,7 +734,7 @@ ds_status ds_raster_backward_devcam(ds_ctx* c, int32_t soup_id, const int32_t* w
     DS_TRY(check_gin(fwd, gin, n_views, grad_flags));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     c->last_stream = st;
-    DS_TRY(build_table_devcam(*c->vt, wh, cams, nullptr, n_views, S, fwd, gin));
+    DS_TRY(build_table_devcam(*c->vt, c->tune, wh, cams, nullptr, n_views, S, fwd, gin));
     const bool reuse = (grad_flags & DS_REUSE_FORWARD) && c->plan.valid && c->plan.devcam && c->plan.soup == soup_id &&
                        c->plan.n_tiles == total_tiles(*c->vt) && c->plan.n_views == n_views;
     if (!reuse) DS_TRY(prepare(c, soup_id, *s, nullptr, *c->vt, true, st));
@@ -756,10 +768,10 @@ ds_status ds_fragment_count(ds_ctx* c, int32_t soup_id, const ds_camera* cams, i
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     c->last_stream = st;
     ds::ViewTable& vt = *c->vt;
-    build_table(vt, cams, nullptr, n_views, 1, nullptr, nullptr);
+    build_table(vt, c->tune, cams, nullptr, n_views, 1, nullptr, nullptr);
     DS_TRY(prepare(c, soup_id, *s, cams, vt, true, st));
     const ds::SoupDev sd = soup_dev(*s);
-    const int grid = 0;
+    const int grid = tile_grid(c, vt);
     DS_TRY_CUDA(cudaMemsetAsync(c->d_total(), 0, 8, st));
     DS_TRY_CUDA(cudaMemsetAsync(c->d_counter() + 4, 0, 4, st));
     DS_TRY_CUDA(ds::launch_raster_count(vt, sd, c->recs.as<ds::SetupRec>(), c->keys[c->plan.res].as<uint32_t>(),
@@ -824,6 +836,26 @@ ds_status ds_ctx_status(ds_ctx* c) {
     DS_TRY_CUDA(cudaMemcpy(&st, c->d_status(), 4, cudaMemcpyDeviceToHost));
     DS_TRY_CUDA(cudaMemset(c->d_status(), 0, 4));
     if (st & 1) return fail(DS_ERR_CAPACITY, "bin capacity exceeded in a DS_NO_SYNC forward");
+    return DS_OK;
+}
+
+ds_status ds_set_tuning(ds_ctx* c, const ds_tuning* t) {
+    if (!c || !t) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    if (t->tile_w != 8 && t->tile_w != 16 && t->tile_w != 32) return fail(DS_ERR_INVALID_ARG, "tile_w must be 8, 16 or 32");
+    if (t->depth_bits < -1 || t->depth_bits > 16) return fail(DS_ERR_INVALID_ARG, "depth_bits must be in [-1, 16]");
+    if (t->blocks_per_sm < 0 || t->blocks_per_sm > 8) return fail(DS_ERR_INVALID_ARG, "blocks_per_sm must be in [0, 8]");
+    if (t->chunk < 32 || t->chunk > ds::kChunk || t->chunk % 32 != 0)
+        return fail(DS_ERR_INVALID_ARG, "chunk must be a multiple of 32 in [32, 256]");
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->tune = *t;
+    c->plan.valid = false;   // the next pass bins again with the new tile shape
+    return DS_OK;
+}
+
+ds_status ds_get_tuning(ds_ctx* c, ds_tuning* t) {
+    if (!c || !t) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    *t = c->tune;
     return DS_OK;
 }
 

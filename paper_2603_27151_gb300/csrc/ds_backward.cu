@@ -253,7 +253,7 @@ __device__ __forceinline__ void interior_grad(const GeomRec* g, const DevCam& ca
     }
 }
 
-template <int SG>
+template <int SG, int TW>
 __global__ void __launch_bounds__(kTilePix, DS_MINB_BWD)
     k_raster_bwd(const __grid_constant__ ViewTable vt, const SoupDev s, const SetupRec* __restrict__ recs,
                  const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
@@ -262,7 +262,8 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_BWD)
     __shared__ TileStage sm;
     __shared__ int s_item;
     const int tid = threadIdx.x;
-    const int lx = tid & (kTile - 1), ly = tid / kTile;
+    constexpr int TH = kTilePix / TW;
+    const int lx = tid & (TW - 1), ly = tid / TW;
     const bool do_tex = (flags & DS_G_TEX) && acc_tex;
     const bool do_score = (flags & DS_G_SCORE) && acc_tex;
     const bool do_int = (flags & DS_G_INTERIOR) && acc_verts;
@@ -273,7 +274,7 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_BWD)
         if (item >= vt.n_items) break;
         const WorkItem wi = decode_item(vt, item);
         const ViewDesc& V = vt.v[wi.v];
-        const int px = wi.tx * kTile + lx, py = wi.ty * kTile + ly;
+        const int px = wi.tx * TW + lx, py = wi.ty * TH + ly;
         const bool valid = px < V.W && py < V.H;
         const int s0 = wi.g * kSampleGroup;
         const int ns = min(SG, vt.S - s0);
@@ -302,10 +303,12 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_BWD)
         const uint2 rg = ranges[V.tile_base + wi.ty * V.tiles_x + wi.tx];
         bool warp_done = !__any_sync(kFullMask, any_score);
         if (__syncthreads_or(!warp_done)) {
-            for (uint32_t c0 = rg.x; c0 < rg.y; c0 += kChunk) {
-                const int n = (int)min((uint32_t)kChunk, rg.y - c0);
+            for (uint32_t c0 = rg.x; c0 < rg.y; c0 += (uint32_t)vt.chunk) {
+                const int n = (int)min((uint32_t)vt.chunk, rg.y - c0);
                 __syncthreads();
-                if (tid < n) stage_triangle(sm, tid, recs, (size_t)wi.v * s.T, keys[c0 + tid], vals[c0 + tid], DB, wi.tx, wi.ty);
+                if (tid < n)
+                    stage_triangle(sm, tid, recs, (size_t)wi.v * s.T, keys[c0 + tid], vals[c0 + tid], DB, wi.tx * TW,
+                                   wi.ty * TH);
                 __syncthreads();
                 if (!warp_done) {
                     for (int j = 0; j < n; ++j) {
@@ -489,14 +492,15 @@ struct EdgeJob {
 
 constexpr int kJobsPerWarp = 4 * 32;
 
-template <int SG>
+template <int SG, int TW>
 __global__ void __launch_bounds__(kTilePix, DS_MINB_EDGE)
     k_edge_bwd(const __grid_constant__ ViewTable vt, const SoupDev s, const SetupRec* __restrict__ recs,
                const GeomRec* __restrict__ geom, double* __restrict__ acc_verts, int* __restrict__ counter) {
     __shared__ int s_item;
     __shared__ EdgeJob s_jobs[kTilePix / 32][kJobsPerWarp];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int lx = tid & (kTile - 1), ly = tid / kTile;
+    constexpr int TH = kTilePix / TW;
+    const int lx = tid & (TW - 1), ly = tid / TW;
     const int Co = s.C - 1;
     EdgeJob* jobs = s_jobs[warp];
     for (;;) {
@@ -507,7 +511,7 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_EDGE)
         if (item >= vt.n_items) break;
         const WorkItem wi = decode_item(vt, item);
         const ViewDesc& V = vt.v[wi.v];
-        const int px = wi.tx * kTile + lx, py = wi.ty * kTile + ly;
+        const int px = wi.tx * TW + lx, py = wi.ty * TH + ly;
         const bool valid = px < V.W && py < V.H;
         const int s0 = wi.g * kSampleGroup;
         const int ns = min(SG, vt.S - s0);
@@ -604,24 +608,22 @@ cudaError_t launch_geom(const ViewTable& vt, const SoupDev& s, GeomRec* geom, cu
 cudaError_t launch_raster_bwd(const ViewTable& vt, const SoupDev& s, const SetupRec* recs, const uint32_t* keys,
                               const uint32_t* vals, const uint2* ranges, int DB, uint32_t flags, const GeomRec* geom,
                               double* acc_tex, double* acc_verts, int* counter, int grid, cudaStream_t st) {
-    if (vt.S == 1)
-        k_raster_bwd<1><<<resident_grid(k_raster_bwd<1>, vt.n_items, grid), kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, flags, geom, acc_tex, acc_verts, counter);
-    else if (vt.S == 2)
-        k_raster_bwd<2><<<resident_grid(k_raster_bwd<2>, vt.n_items, grid), kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, flags, geom, acc_tex, acc_verts, counter);
-    else
-        k_raster_bwd<4><<<resident_grid(k_raster_bwd<4>, vt.n_items, grid), kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, flags, geom, acc_tex, acc_verts, counter);
+    dispatch_tile(vt.tile_w, vt.S == 1 ? 1 : (vt.S == 2 ? 2 : 4), [&](auto P) {
+        constexpr int SG = decltype(P)::sg, TW = decltype(P)::tw;
+        k_raster_bwd<SG, TW><<<resident_grid(k_raster_bwd<SG, TW>, vt.n_items, grid), kTilePix, 0, st>>>(
+            vt, s, recs, keys, vals, ranges, DB, flags, geom, acc_tex, acc_verts, counter);
+    });
     note_launches(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_edge_bwd(const ViewTable& vt, const SoupDev& s, const SetupRec* recs, const GeomRec* geom,
                             double* acc_verts, int* counter, int grid, cudaStream_t st) {
-    if (vt.S == 1)
-        k_edge_bwd<1><<<resident_grid(k_edge_bwd<1>, vt.n_items, grid), kTilePix, 0, st>>>(vt, s, recs, geom, acc_verts, counter);
-    else if (vt.S == 2)
-        k_edge_bwd<2><<<resident_grid(k_edge_bwd<2>, vt.n_items, grid), kTilePix, 0, st>>>(vt, s, recs, geom, acc_verts, counter);
-    else
-        k_edge_bwd<4><<<resident_grid(k_edge_bwd<4>, vt.n_items, grid), kTilePix, 0, st>>>(vt, s, recs, geom, acc_verts, counter);
+    dispatch_tile(vt.tile_w, vt.S == 1 ? 1 : (vt.S == 2 ? 2 : 4), [&](auto P) {
+        constexpr int SG = decltype(P)::sg, TW = decltype(P)::tw;
+        k_edge_bwd<SG, TW><<<resident_grid(k_edge_bwd<SG, TW>, vt.n_items, grid), kTilePix, 0, st>>>(
+            vt, s, recs, geom, acc_verts, counter);
+    });
     note_launches(1);
     return cudaGetLastError();
 }

@@ -14,8 +14,9 @@
 
 namespace ds {
 
-constexpr int kTile = 16;            // tile edge in pixels (256 pixels per tile)
-constexpr int kTilePix = kTile * kTile;
+constexpr int kTilePix = 256;        // pixels per tile (one thread each); the
+                                     // tile is tile_w x (256 / tile_w) pixels
+constexpr int kChunk = 256;          // staging capacity of the tile kernels (triangles per round)
 constexpr int kSampleGroup = 4;      // samples sharing one Philox block
 constexpr float kGuard = 16384.0f;   // screen-space guard band (pixels)
 
@@ -46,6 +47,8 @@ struct ViewTable {
     int S;          // samples per pixel
     int n_groups;   // ceil(S / 4)
     int n_items;    // total work items
+    int tile_w, tile_h;   // tile shape in pixels (8x32, 16x16 or 32x8)
+    int chunk;      // triangles staged per round in the tile kernels (<= 256)
     // Optional device-resident cameras (ds_camera[n]) and seeds (uint64[n]):
     // when set they replace v[i].cam and v[i].seed_*, so that a captured
     // CUDA graph can render views chosen after capture.

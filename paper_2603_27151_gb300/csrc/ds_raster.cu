@@ -1,5 +1,5 @@
 // ds_raster.cu -- forward rasteriser: stochastic opacity masking (Eq. 5) by a
-// z-buffer over each 16x16 tile's depth-sorted triangle list, mesh-colour
+// z-buffer over each tile's depth-sorted triangle list, mesh-colour
 // decode of the selected fragment, and the optional fragment counts.
 #include <atomic>
 
@@ -10,7 +10,7 @@ namespace ds {
 
 // One CTA (256 threads, one pixel each) per work item (view, tile, group of
 // up to four samples), taken from a global counter until none is left.
-template <int SG>
+template <int SG, int TW>
 __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
     k_raster_fwd(const __grid_constant__ ViewTable vt, const SoupDev s, const SetupRec* __restrict__ recs,
                  const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
@@ -18,7 +18,8 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
     __shared__ TileStage sm;
     __shared__ int s_item;
     const int tid = threadIdx.x;
-    const int lx = tid & (kTile - 1), ly = tid / kTile;
+    constexpr int TH = kTilePix / TW;
+    const int lx = tid & (TW - 1), ly = tid / TW;
     const bool stochastic = mode == DS_MODE_STOCHASTIC;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(counter, 1);
@@ -27,7 +28,7 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
         if (item >= vt.n_items) break;
         const WorkItem wi = decode_item(vt, item);
         const ViewDesc& V = vt.v[wi.v];
-        const int px = wi.tx * kTile + lx, py = wi.ty * kTile + ly;
+        const int px = wi.tx * TW + lx, py = wi.ty * TH + ly;
         const bool valid = px < V.W && py < V.H;
         const int s0 = wi.g * kSampleGroup;
         const int ns = min(SG, vt.S - s0);
@@ -45,10 +46,12 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
 
         const uint2 rg = ranges[V.tile_base + wi.ty * V.tiles_x + wi.tx];
         bool warp_done = !__any_sync(kFullMask, valid);
-        for (uint32_t c0 = rg.x; c0 < rg.y; c0 += kChunk) {
-            const int n = (int)min((uint32_t)kChunk, rg.y - c0);
+        for (uint32_t c0 = rg.x; c0 < rg.y; c0 += (uint32_t)vt.chunk) {
+            const int n = (int)min((uint32_t)vt.chunk, rg.y - c0);
             __syncthreads();
-            if (tid < n) stage_triangle(sm, tid, recs, (size_t)wi.v * s.T, keys[c0 + tid], vals[c0 + tid], DB, wi.tx, wi.ty);
+            if (tid < n)
+                stage_triangle(sm, tid, recs, (size_t)wi.v * s.T, keys[c0 + tid], vals[c0 + tid], DB, wi.tx * TW,
+                               wi.ty * TH);
             __syncthreads();
             if (!warp_done) {
                 for (int j = 0; j < n; ++j) {
@@ -130,7 +133,7 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
 // Fragment counts.  mode 0: per sample, the covered fragments in front of
 // the stored winner (all covered fragments for the background), written to
 // n_front.  mode 1: covered fragments of the pixel (one sample), summed.
-template <int SG>
+template <int SG, int TW>
 __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
     k_raster_count(const __grid_constant__ ViewTable vt, const SoupDev s, const SetupRec* __restrict__ recs,
                    const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
@@ -139,7 +142,8 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
     __shared__ TileStage sm;
     __shared__ int s_item;
     const int tid = threadIdx.x;
-    const int lx = tid & (kTile - 1), ly = tid / kTile;
+    constexpr int TH = kTilePix / TW;
+    const int lx = tid & (TW - 1), ly = tid / TW;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
@@ -147,7 +151,7 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
         if (item >= vt.n_items) break;
         const WorkItem wi = decode_item(vt, item);
         const ViewDesc& V = vt.v[wi.v];
-        const int px = wi.tx * kTile + lx, py = wi.ty * kTile + ly;
+        const int px = wi.tx * TW + lx, py = wi.ty * TH + ly;
         const bool valid = px < V.W && py < V.H;
         const int s0 = wi.g * kSampleGroup;
         const int ns = mode == 0 ? min(SG, vt.S - s0) : 1;
@@ -168,10 +172,12 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
         }
         const uint2 rg = ranges[V.tile_base + wi.ty * V.tiles_x + wi.tx];
         bool warp_done = !__any_sync(kFullMask, valid);
-        for (uint32_t c0 = rg.x; c0 < rg.y; c0 += kChunk) {
-            const int n = (int)min((uint32_t)kChunk, rg.y - c0);
+        for (uint32_t c0 = rg.x; c0 < rg.y; c0 += (uint32_t)vt.chunk) {
+            const int n = (int)min((uint32_t)vt.chunk, rg.y - c0);
             __syncthreads();
-            if (tid < n) stage_triangle(sm, tid, recs, (size_t)wi.v * s.T, keys[c0 + tid], vals[c0 + tid], DB, wi.tx, wi.ty);
+            if (tid < n)
+                stage_triangle(sm, tid, recs, (size_t)wi.v * s.T, keys[c0 + tid], vals[c0 + tid], DB, wi.tx * TW,
+                               wi.ty * TH);
             __syncthreads();
             if (!warp_done) {
                 for (int j = 0; j < n; ++j) {
@@ -224,12 +230,11 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
 cudaError_t launch_raster_fwd(const ViewTable& vt, const SoupDev& s, const SetupRec* recs, const uint32_t* keys,
                               const uint32_t* vals, const uint2* ranges, int DB, uint32_t mode, const Bg& bg,
                               int* counter, int grid, cudaStream_t st) {
-    if (vt.S == 1)
-        k_raster_fwd<1><<<resident_grid(k_raster_fwd<1>, vt.n_items, grid), kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, bg, counter);
-    else if (vt.S == 2)
-        k_raster_fwd<2><<<resident_grid(k_raster_fwd<2>, vt.n_items, grid), kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, bg, counter);
-    else
-        k_raster_fwd<4><<<resident_grid(k_raster_fwd<4>, vt.n_items, grid), kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, bg, counter);
+    dispatch_tile(vt.tile_w, vt.S == 1 ? 1 : (vt.S == 2 ? 2 : 4), [&](auto P) {
+        constexpr int SG = decltype(P)::sg, TW = decltype(P)::tw;
+        k_raster_fwd<SG, TW><<<resident_grid(k_raster_fwd<SG, TW>, vt.n_items, grid), kTilePix, 0, st>>>(
+            vt, s, recs, keys, vals, ranges, DB, mode, bg, counter);
+    });
     note_launches(1);
     return cudaGetLastError();
 }
@@ -237,10 +242,11 @@ cudaError_t launch_raster_fwd(const ViewTable& vt, const SoupDev& s, const Setup
 cudaError_t launch_raster_count(const ViewTable& vt, const SoupDev& s, const SetupRec* recs, const uint32_t* keys,
                                 const uint32_t* vals, const uint2* ranges, int DB, int mode,
                                 unsigned long long* total, int* counter, int grid, cudaStream_t st) {
-    if (mode == 1 || vt.S == 1)
-        k_raster_count<1><<<resident_grid(k_raster_count<1>, vt.n_items, grid), kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, total, counter);
-    else
-        k_raster_count<4><<<resident_grid(k_raster_count<4>, vt.n_items, grid), kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, total, counter);
+    dispatch_tile(vt.tile_w, (mode == 1 || vt.S == 1) ? 1 : 4, [&](auto P) {
+        constexpr int SG = decltype(P)::sg, TW = decltype(P)::tw;
+        k_raster_count<SG, TW><<<resident_grid(k_raster_count<SG, TW>, vt.n_items, grid), kTilePix, 0, st>>>(
+            vt, s, recs, keys, vals, ranges, DB, mode, total, counter);
+    });
     note_launches(1);
     return cudaGetLastError();
 }

@@ -57,14 +57,15 @@ cudaError_t launch_activate(const SoupDev& s, cudaStream_t st) {
 // ---------------------------------------------------------------- set-up
 __device__ __forceinline__ int floordiv256(int x) { return x >> 8; }   // arithmetic shift = floor
 
-// Upper bound of the biased edge value over the 16x16 pixel centres of a
+// Upper bound of the biased edge value over the tw x th pixel centres of a
 // tile: a linear function peaks at a corner of the centre grid.
-__device__ __forceinline__ bool tile_may_cover(const SetupRec& r, int tx, int ty) {
-    const long long X0 = 256LL * (kTile * tx) + 128, Y0 = 256LL * (kTile * ty) + 128;
+__device__ __forceinline__ bool tile_may_cover(const SetupRec& r, int tx, int ty, int tw, int th) {
+    const long long X0 = 256LL * (tw * tx) + 128, Y0 = 256LL * (th * ty) + 128;
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
         const long long e0 = (long long)r.A[i] * X0 + (long long)r.B[i] * Y0 + r.C[i];
-        const long long up = 256LL * (kTile - 1) * ((r.A[i] > 0 ? r.A[i] : 0) + (r.B[i] > 0 ? r.B[i] : 0));
+        const long long up = 256LL * ((long long)(tw - 1) * (r.A[i] > 0 ? r.A[i] : 0) +
+                                      (long long)(th - 1) * (r.B[i] > 0 ? r.B[i] : 0));
         if (e0 + up < 0) return false;
     }
     return true;
@@ -142,13 +143,14 @@ __global__ void k_setup(const __grid_constant__ ViewTable vt, const SoupDev s,
         px1 = min(px1, W - 1);
         py1 = min(py1, H - 1);
         if (px0 <= px1 && py0 <= py1) {
-            box = make_int4(px0 / kTile, py0 / kTile, px1 / kTile, py1 / kTile);
+            box = make_int4(px0 / vt.tile_w, py0 / vt.tile_h, px1 / vt.tile_w, py1 / vt.tile_h);
             const int nb = (box.z - box.x + 1) * (box.w - box.y + 1);
             if (nb > kExactTileLimit) {
                 cnt = nb;
             } else {
                 for (int ty = box.y; ty <= box.w; ++ty)
-                    for (int tx = box.x; tx <= box.z; ++tx) cnt += tile_may_cover(r, tx, ty) ? 1u : 0u;
+                    for (int tx = box.x; tx <= box.z; ++tx)
+                        cnt += tile_may_cover(r, tx, ty, vt.tile_w, vt.tile_h) ? 1u : 0u;
             }
         }
         zk = __float_as_uint(fminf(w[0], fminf(w[1], w[2])));
@@ -201,7 +203,7 @@ __global__ void k_emit(const __grid_constant__ ViewTable vt, int T, const SetupR
     bool over = false;
     for (int ty = box.y; ty <= box.w; ++ty)
         for (int tx = box.x; tx <= box.z; ++tx) {
-            if (exact && !tile_may_cover(r, tx, ty)) continue;
+            if (exact && !tile_may_cover(r, tx, ty, vt.tile_w, vt.tile_h)) continue;
             if (o < cap) {
                 keys[o] = ((uint32_t)(base + ty * tiles_x + tx) << DB) | dbits;
                 vals[o] = (uint32_t)t;

@@ -16,6 +16,7 @@ namespace {
 constexpr long long kMaxTexFloats = 1LL << 20;   // T * V * C
 constexpr long long kMaxViewTris = 1LL << 16;    // n_views * T
 constexpr long long kMaxPairs = 1LL << 19;       // (tile, triangle) pairs after binning
+constexpr int kTileEdge = 16;                    // tiles of 16x16 pixels
 constexpr long long kMaxTiles = 1LL << 16;       // 16x16 tiles over all views
 constexpr long long kMaxSortBlocks = kMaxPairs / ds::kSortBlock;
 
@@ -106,7 +107,7 @@ extern "C" DS_API ds_status ds_raster_forward_noalloc(const float* verts, const 
         if (!valid_cam(cams[v])) return reject(DS_ERR_INVALID_ARG, "camera " + std::to_string(v) + " is invalid");
         if (!out[v].gbuf || !out[v].color || ((uintptr_t)out[v].gbuf & 15))
             return reject(DS_ERR_INVALID_ARG, "view output buffer is NULL or gbuf is not 16-byte aligned");
-        tiles += (long long)((cams[v].width + ds::kTile - 1) / ds::kTile) * ((cams[v].height + ds::kTile - 1) / ds::kTile);
+        tiles += (long long)((cams[v].width + kTileEdge - 1) / kTileEdge) * ((cams[v].height + kTileEdge - 1) / kTileEdge);
     }
     if (tiles > kMaxTiles) return reject(DS_ERR_INVALID_ARG, "the views exceed the no-alloc limit of 65536 tiles");
 
@@ -121,6 +122,8 @@ extern "C" DS_API ds_status ds_raster_forward_noalloc(const float* verts, const 
     vt.n = n_views;
     vt.S = S;
     vt.n_groups = (S + ds::kSampleGroup - 1) / ds::kSampleGroup;
+    vt.tile_w = vt.tile_h = kTileEdge;
+    vt.chunk = ds::kChunk;
     int tile_base = 0, item_base = 0;
     for (int v = 0; v < n_views; ++v) {
         ds::ViewDesc& d = vt.v[v];
@@ -134,8 +137,8 @@ extern "C" DS_API ds_status ds_raster_forward_noalloc(const float* verts, const 
         d.cam.near_z = c.near_z;
         d.W = c.width;
         d.H = c.height;
-        d.tiles_x = (c.width + ds::kTile - 1) / ds::kTile;
-        d.tiles_y = (c.height + ds::kTile - 1) / ds::kTile;
+        d.tiles_x = (c.width + kTileEdge - 1) / kTileEdge;
+        d.tiles_y = (c.height + kTileEdge - 1) / kTileEdge;
         d.tile_base = tile_base;
         d.item_base = item_base;
         tile_base += d.tiles_x * d.tiles_y;

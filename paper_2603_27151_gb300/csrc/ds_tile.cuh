@@ -20,7 +20,6 @@ constexpr unsigned kFullMask = 0xffffffffu;
 #ifndef DS_MINB_EDGE
 #define DS_MINB_EDGE 4
 #endif
-constexpr int kChunk = 256;   // triangles staged per round (one per thread)
 
 // Per-tile staged set-up.  h0..h2 hold what the per-pixel coverage test reads
 // for every triangle; eo/kk are read only for covered fragments.
@@ -64,15 +63,16 @@ __device__ __forceinline__ float rho_bound(uint32_t key, int DB) {
     return __fmul_rn(__frcp_rn(zq), 1.0f + 0x1p-10f);
 }
 
-// Stage triangle t (set-up record in view base vbase) for tile (tx, ty).  For
-// a pixel at local offset (lx, ly) the biased edge value is
-// E'(origin) + 256 (A lx + B ly); it is >= 0 iff A lx + B ly >= thr with
-// thr = ceil(-E'(origin) / 256).  |A lx + B ly| < 2^28 inside the guard band,
-// so thr is clamped to +-2^30 and the test runs in int32.
+// Stage triangle t (set-up record in view base vbase) for the tile whose
+// first pixel is (ox, oy).  For a pixel at local offset (lx, ly) the biased
+// edge value is E'(origin) + 256 (A lx + B ly); it is >= 0 iff
+// A lx + B ly >= thr with thr = ceil(-E'(origin) / 256).  Inside the guard
+// band |A|, |B| < 2^23 and lx, ly < 32, so |A lx + B ly| < 2^29: thr is
+// clamped to +-2^30 and the test runs in int32.
 __device__ __forceinline__ void stage_triangle(TileStage& sm, int slot, const SetupRec* recs, size_t vbase,
-                                               uint32_t key, uint32_t t, int DB, int tx, int ty) {
+                                               uint32_t key, uint32_t t, int DB, int ox, int oy) {
     const SetupRec r = load_rec(recs + vbase + t);
-    const long long X0 = 256LL * (kTile * tx) + 128, Y0 = 256LL * (kTile * ty) + 128;
+    const long long X0 = 256LL * ox + 128, Y0 = 256LL * oy + 128;
     int thr[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
@@ -159,6 +159,29 @@ __device__ __forceinline__ bool warp_run_sum(unsigned long long key, float (&v)[
         }
     }
     return head;
+}
+
+// Tile-kernel dispatch on the sample group (1, 2 or 4 samples per CTA) and
+// the tile width (8, 16 or 32 pixels): calls f(IntPair<SG, TW>{}).
+template <int A, int B>
+struct IntPair {
+    static constexpr int sg = A, tw = B;
+};
+template <class F>
+inline void dispatch_tile(int tw, int sg, F&& f) {
+    if (tw == 8) {
+        if (sg == 1) f(IntPair<1, 8>{});
+        else if (sg == 2) f(IntPair<2, 8>{});
+        else f(IntPair<4, 8>{});
+    } else if (tw == 32) {
+        if (sg == 1) f(IntPair<1, 32>{});
+        else if (sg == 2) f(IntPair<2, 32>{});
+        else f(IntPair<4, 32>{});
+    } else {
+        if (sg == 1) f(IntPair<1, 16>{});
+        else if (sg == 2) f(IntPair<2, 16>{});
+        else f(IntPair<4, 16>{});
+    }
 }
 
 }  // namespace ds

@@ -46,6 +46,14 @@ class ds_view_out(ctypes.Structure):
     _fields_ = [("gbuf", ctypes.c_void_p), ("color", ctypes.c_void_p), ("n_front", ctypes.c_void_p)]
 
 
+class ds_tuning(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int32), ("depth_bits", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("chunk", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
 class ds_request_stats(ctypes.Structure):
     _fields_ = [("submit_ns", ctypes.c_int64), ("launch_ns", ctypes.c_int64), ("done_ns", ctypes.c_int64),
                 ("batch", ctypes.c_int32), ("pad", ctypes.c_int32)]
@@ -106,6 +114,12 @@ def load():
     L.ds_raster_backward_devcam.restype = i32
     L.ds_reserve.argtypes = [P, ctypes.c_int64]
     L.ds_reserve.restype = i32
+    L.ds_set_tuning.argtypes = [P, P]
+    L.ds_set_tuning.restype = i32
+    L.ds_get_tuning.argtypes = [P, P]
+    L.ds_get_tuning.restype = i32
+    L.ds_autotune.argtypes = [P, i32, P, P, i32, i32, u32, P, P, P, P, P, i32, P, ctypes.POINTER(ctypes.c_float), P]
+    L.ds_autotune.restype = i32
     L.ds_server_create.argtypes = [i32, i32, ctypes.c_size_t, i32, ctypes.c_int64, ctypes.POINTER(P)]
     L.ds_server_create.restype = i32
     L.ds_server_add_soup.argtypes = [P, P, P, i32, i32, i32, ctypes.POINTER(i32)]
@@ -255,6 +269,42 @@ class Context:
             gin[v].score_w = score_ws[v].data_ptr() if score_ws is not None and score_ws[v] is not None else None
         _check(load().ds_raster_backward_devcam(self.h, soup_id, wha, _ptr(cams_dev), n, S, fwd, gin, flags,
                                                 _ptr(grad_verts), _ptr(grad_tex), _stream(stream)))
+
+    # -------------------------------------------------------------- tuning
+    def set_tuning(self, tile_w=16, depth_bits=-1, blocks_per_sm=0, chunk=256):
+        t = ds_tuning(int(tile_w), int(depth_bits), int(blocks_per_sm), int(chunk))
+        _check(load().ds_set_tuning(self.h, ctypes.byref(t)))
+
+    def get_tuning(self) -> dict:
+        t = ds_tuning()
+        _check(load().ds_get_tuning(self.h, ctypes.byref(t)))
+        return t.as_dict()
+
+    def autotune(self, soup_id, cams, seeds, S, mode, bg, gbufs, colors, grad_colors=None, score_ws=None,
+                 grad_verts=None, grad_tex=None, reps: int = 3, stream=None):
+        """ds_autotune: returns (tuning dict, best ms); the tuning is set on
+        this context and the outputs hold a run with it."""
+        n = len(cams)
+        ca = cameras(cams)
+        sd = (ctypes.c_uint64 * n)(*[int(x) for x in (seeds if seeds is not None else [0] * n)])
+        bga = np.ascontiguousarray(bg, np.float32)
+        outs = (ds_view_out * n)()
+        for v in range(n):
+            outs[v].gbuf = gbufs[v].data_ptr()
+            outs[v].color = colors[v].data_ptr()
+            outs[v].n_front = None
+        gins = None
+        if grad_colors is not None:
+            gins = (ds_view_gin * n)()
+            for v in range(n):
+                gins[v].grad_color = grad_colors[v].data_ptr()
+                gins[v].score_w = score_ws[v].data_ptr() if score_ws is not None and score_ws[v] is not None else None
+        best = ds_tuning()
+        ms = ctypes.c_float(0.0)
+        _check(load().ds_autotune(self.h, soup_id, ca, sd, n, S, mode, bga.ctypes.data_as(ctypes.c_void_p), outs,
+                                  gins, _ptr(grad_verts), _ptr(grad_tex), int(reps), ctypes.byref(best),
+                                  ctypes.byref(ms), _stream(stream)))
+        return best.as_dict(), float(ms.value)
 
     def reserve(self, pairs: int):
         _check(load().ds_reserve(self.h, int(pairs)))

@@ -116,6 +116,38 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _source_sha1() -> str:
+    """Hash of the CUDA sources (file name and contents, sorted by name)."""
+    import glob
+    import hashlib
+    h = hashlib.sha1()
+    src = os.path.join(ROOT, "paper_2603_27151_gb300", "csrc")
+    for f in sorted(glob.glob(os.path.join(src, "*")), key=os.path.basename):
+        if not f.endswith((".cu", ".cuh", ".h")):
+            continue
+        h.update(os.path.basename(f).encode())
+        h.update(b"\0")
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+        h.update(b"\0")
+    return h.hexdigest()
+
+
+def _traffic(kernel: str, pixel_samples: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture,
+    scaled to this launch's pixel-samples; None when the kernels changed
+    since the capture (source hash differs) or the kernel was not captured."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_sha1") != _source_sha1() or kernel not in d.get("bytes", {}):
+        return None
+    return d["bytes"][kernel] * pixel_samples / d["pixel_samples"]
+
+
 # ---------------------------------------------------------------- the GPU step
 class Workload:
     def __init__(self, rank: int, device: str, views: int = 0):
@@ -294,7 +326,11 @@ def _gpu_arm(args):
     from paper_2603_27151_gb300 import native as N
     wl = Workload(rank, dev, args.views)
     tuning = None
-    if not args.no_tune:
+    if args.tuning:
+        tw, db, bps, ch = (int(x) for x in args.tuning.split(","))
+        wl.ctx.set_tuning(tw, db, bps, ch)
+        tuning = dict(wl.ctx.get_tuning(), cached=None)
+    elif not args.no_tune:
         # launch parameters from the autotuner (cached per workload); untimed
         from paper_2603_27151_gb300 import autotune
         wl.step()
@@ -390,7 +426,8 @@ def _gpu_arm(args):
         "e2e": {"value": frags_total / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": _traffic(dom, wl.pixel_samples),
                      "algorithmic_bytes": algo[dom], "launch_ms": per_launch_ms},
         "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
         "clocks": clk.summary(),
@@ -496,6 +533,7 @@ def main():
                     help="skip the plain-path, training-step and serving legs")
     ap.add_argument("--train-iters", type=int, default=50)
     ap.add_argument("--no-tune", action="store_true", help="default launch parameters instead of the autotuner's")
+    ap.add_argument("--tuning", default="", help="fixed launch parameters tile_w,depth_bits,blocks_per_sm,chunk")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup

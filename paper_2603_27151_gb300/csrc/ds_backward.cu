@@ -149,10 +149,15 @@ __device__ __forceinline__ void scatter_alpha_run(const SoupDev& s, double* acc_
 // Winner terms of one sample: colour gradient (C-1 channels) and the +w/alpha
 // opacity score, merged into one pass over the corner texels, four channels
 // at a time.  G receives dL/d(b1, b2) of the colour (for the interior term).
-template <bool kInterior>
+// The samples of one pixel whose winner is the same triangle have the same
+// barycentrics, cell and weights, and every term is linear in the upstream
+// gradient: the samples in `msk` (bit k: sample s0 + k, colour gradients at
+// gcol0 + k * sstride) are handled in one pass with their upstream colour
+// gradients summed; wscore is the sum of their score weights.
+template <bool kInterior, int SG>
 __device__ __forceinline__ void winner_texture(const SoupDev& s, double* acc_tex, bool act, int t, float b1, float b2,
-                                               const float* gcol, size_t HW, float wscore, bool do_tex,
-                                               bool do_score, float G[2]) {
+                                               const float* gcol0, size_t sstride, int msk, size_t HW, float wscore,
+                                               bool do_tex, bool do_score, float G[2]) {
     Cell cl;
     cl.k0 = cl.k1 = cl.k2 = 0;
     cl.wa = cl.wb = 0.f;
@@ -176,16 +181,35 @@ __device__ __forceinline__ void winner_texture(const SoupDev& s, double* acc_tex
 #pragma unroll
         for (int k = 0; k < 12; ++k) v[k] = 0.f;
         if (act) {
+            float A0[4], A1[4], A2[4];
+            if ((C & 3) == 0) {   // 16-byte aligned texel rows: one vector load per corner
+                const float4 x0 = __ldg(reinterpret_cast<const float4*>(base + (size_t)cl.k0 * C + c4));
+                const float4 x1 = __ldg(reinterpret_cast<const float4*>(base + (size_t)cl.k1 * C + c4));
+                const float4 x2 = __ldg(reinterpret_cast<const float4*>(base + (size_t)cl.k2 * C + c4));
+                A0[0] = x0.x, A0[1] = x0.y, A0[2] = x0.z, A0[3] = x0.w;
+                A1[0] = x1.x, A1[1] = x1.y, A1[2] = x1.z, A1[3] = x1.w;
+                A2[0] = x2.x, A2[1] = x2.y, A2[2] = x2.z, A2[3] = x2.w;
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int c = c4 + k < C ? c4 + k : C - 1;
+                    A0[k] = __ldg(base + (size_t)cl.k0 * C + c);
+                    A1[k] = __ldg(base + (size_t)cl.k1 * C + c);
+                    A2[k] = __ldg(base + (size_t)cl.k2 * C + c);
+                }
+            }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const int c = c4 + k;
                 if (c >= C) break;
-                const float a0 = __ldg(base + (size_t)cl.k0 * C + c);
-                const float a1 = __ldg(base + (size_t)cl.k1 * C + c);
-                const float a2 = __ldg(base + (size_t)cl.k2 * C + c);
+                const float a0 = A0[k], a1 = A1[k], a2 = A2[k];
                 float g = 0.f;
                 if (c < C - 1) {
-                    g = (do_tex || kInterior) ? __ldg(gcol + c * HW) : 0.f;
+                    if (do_tex || kInterior) {
+#pragma unroll
+                        for (int q = 0; q < SG; ++q)
+                            if (msk & (1 << q)) g += __ldg(gcol0 + q * sstride + c * HW);
+                    }
                     if (kInterior) {
                         G[0] += g * sgnN * (a1 - a0);
                         G[1] += g * sgnN * (a2 - a0);
@@ -356,16 +380,30 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_BWD)
             }
         }
 
-        // ---- winner terms: colour (2(a)), +w/alpha (2(b)), interior (Eq. 8)
+        // ---- winner terms: colour (2(a)), +w/alpha (2(b)), interior (Eq. 8),
+        // once per distinct winner of the pixel's samples
+        const size_t sstride = (size_t)(s.C - 1) * HW;
+        const float* gcol0 = V.grad_color + (size_t)s0 * sstride + pix;
 #pragma unroll
         for (int q = 0; q < SG; ++q) {
-            const bool act = valid && q < ns && wt[q] >= 0;
-            const float* gcol = V.grad_color + (size_t)(s0 + (q < ns ? q : 0)) * (s.C - 1) * HW + pix;
+            bool act = valid && q < ns && wt[q] >= 0;
+            int msk = 0;
+            float wsum = 0.f;
+#pragma unroll
+            for (int r = 0; r < SG; ++r) {
+                if (r < q && r < ns && wt[r] == wt[q]) act = false;   // handled with sample r
+                if (r >= q && r < ns && wt[r] == wt[q]) {
+                    msk |= 1 << r;
+                    wsum += wsc[r];
+                }
+            }
             float G[2];
             if (do_int)
-                winner_texture<true>(s, acc_tex, act, wt[q], wb1[q], wb2[q], gcol, HW, wsc[q], do_tex, do_score, G);
+                winner_texture<true, SG>(s, acc_tex, act, wt[q], wb1[q], wb2[q], gcol0, sstride, msk, HW, wsum, do_tex,
+                                         do_score, G);
             else if (do_tex || do_score)
-                winner_texture<false>(s, acc_tex, act, wt[q], wb1[q], wb2[q], gcol, HW, wsc[q], do_tex, do_score, G);
+                winner_texture<false, SG>(s, acc_tex, act, wt[q], wb1[q], wb2[q], gcol0, sstride, msk, HW, wsum,
+                                          do_tex, do_score, G);
             if (do_int) {
                 float gv[9];
 #pragma unroll

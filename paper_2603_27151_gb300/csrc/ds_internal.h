@@ -98,10 +98,10 @@ int persistent_grid(int n_items, int blocks_per_sm);
 // (SM count x occupancy of `kernel` at 256 threads), at most n_items.  A
 // positive `grid` from the caller is used as given.
 template <class Kernel>
-inline int resident_grid(Kernel kernel, int n_items, int grid) {
+inline int resident_grid(Kernel kernel, int n_items, int grid, size_t dyn_smem = 0) {
     if (grid > 0) return grid;
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, 256, 0) != cudaSuccess || blocks < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kernel, 256, dyn_smem) != cudaSuccess || blocks < 1) {
         cudaGetLastError();
         blocks = 1;
     }

@@ -515,11 +515,12 @@ __device__ __forceinline__ bool edge_side(const DevCam& cam, const SetupRec* vre
 
 // One CTA per (view, tile, sample group); every pixel owns its pairs with
 // the right and the lower neighbour.  A pair with different winners yields up
-// to two side jobs (one per side with a triangle).  Each warp first queues
-// its jobs in shared memory (ballot + prefix), then evaluates them 32 at a
-// time, so that every lane works on a boundary instead of idling while its
-// neighbours do; consecutive jobs mostly share a triangle, and runs of equal
-// triangles are summed before the atomics.
+// to two side jobs (one per side with a triangle).  Each warp queues its jobs
+// in a ring in shared memory (prefix over lanes) and evaluates them 32 at a
+// time whenever 32 are waiting, across the samples of the work item, so that
+// every lane works on a boundary instead of idling; only the last batch of a
+// work item can be partial.  Consecutive jobs mostly share a triangle, and
+// runs of equal triangles are summed before the atomics.
 struct EdgeJob {
     int xy;      // X: x | (y << 16)
     int t;       // triangle of side X
@@ -528,7 +529,8 @@ struct EdgeJob {
     int dir;     // Y = X + (1, 0) / (-1, 0) / (0, 1) / (0, -1): 0..3
 };
 
-constexpr int kJobsPerWarp = 4 * 32;
+// Ring capacity: up to 31 jobs left from earlier samples plus 4 per lane.
+constexpr int kJobsPerWarp = 5 * 32;
 
 template <int SG, int TW>
 __global__ void __launch_bounds__(kTilePix, DS_MINB_EDGE)
@@ -557,6 +559,7 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_EDGE)
         const SetupRec* vrec = recs + (size_t)wi.v * s.T;
         const GeomRec* vgeom = geom + (size_t)wi.v * s.T;
         const int4* gbuf = reinterpret_cast<const int4*>(V.gbuf);
+        int head = 0, count = 0;   // the warp's job ring (same values in every lane)
 #pragma unroll 1
         for (int q = 0; q < SG; ++q) {
             const bool qv = valid && q < ns;
@@ -603,26 +606,30 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_EDGE)
             pre -= nmine;
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                if (vl[k]) jobs[pre++] = sl[k];
+                if (vl[k]) jobs[(head + count + pre++) % kJobsPerWarp] = sl[k];
+            count += total;
             __syncwarp();
-            // ---- evaluate 32 at a time
-            for (int b0 = 0; b0 < total; b0 += 32) {
-                const int j = b0 + lane;
+            // ---- evaluate 32 at a time while a full batch waits (and the
+            // remainder after the last sample)
+            while (count >= 32 || (q == SG - 1 && count > 0)) {
+                const int n = min(count, 32);
                 float acc[9];
 #pragma unroll
                 for (int k = 0; k < 9; ++k) acc[k] = 0.f;
                 bool act = false;
                 int t = -1;
-                if (j < total) {
-                    const EdgeJob jb = jobs[j];
+                if (lane < n) {
+                    const EdgeJob jb = jobs[(head + lane) % kJobsPerWarp];
                     const int xX = jb.xy & 0xffff, yX = jb.xy >> 16;
                     const int xY = xX + (jb.dir == 0) - (jb.dir == 1), yY = yX + (jb.dir == 2) - (jb.dir == 3);
                     t = jb.t;
                     act = edge_side(view_cam(vt, wi.v), vrec, vgeom + t, t, xX, yX, xY, yY, jb.tY, jb.phi, acc);
                 }
                 scatter_verts_run(acc_verts, act, t, acc);
+                head = (head + n) % kJobsPerWarp;
+                count -= n;
+                __syncwarp();
             }
-            __syncwarp();
         }
     }
 }

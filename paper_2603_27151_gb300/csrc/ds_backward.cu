@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_BWD)
     __shared__ int s_item;
     const int tid = threadIdx.x;
     constexpr int TH = kTilePix / TW;
-    const int lx = tid & (TW - 1), ly = tid / TW;
+    const int lx = tid & (TW - 1), ly = tid / TW, warp = tid >> 5;
     const bool do_tex = (flags & DS_G_TEX) && acc_tex;
     const bool do_score = (flags & DS_G_SCORE) && acc_tex;
     const bool do_int = (flags & DS_G_INTERIOR) && acc_verts;
@@ -306,17 +306,15 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_BWD)
         const SetupRec* vrec = recs + (size_t)wi.v * s.T;
 
         int wt[SG];
-        float wb1[SG], wb2[SG], wrho[SG], wsc[SG];
+        float wrho[SG], wsc[SG];
         bool any_score = false;
 #pragma unroll
         for (int q = 0; q < SG; ++q) {
             wt[q] = -1;
-            wb1[q] = wb2[q] = wrho[q] = wsc[q] = 0.f;
+            wrho[q] = wsc[q] = 0.f;
             if (valid && q < ns) {
                 const int4 gb = reinterpret_cast<const int4*>(V.gbuf)[(s0 + q) * HW + pix];
                 wt[q] = (gb.x >= 0 && gb.x < s.T) ? gb.x : -1;   // ids outside the soup read as background
-                wb1[q] = __int_as_float(gb.y);
-                wb2[q] = __int_as_float(gb.z);
                 if (do_score && V.score_w) wsc[q] = V.score_w[(s0 + q) * HW + pix];
                 if (wt[q] >= 0) wrho[q] = winner_rho(vrec + wt[q], px, py);
                 any_score = any_score || wsc[q] != 0.f;
@@ -331,12 +329,13 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_BWD)
                 const int n = (int)min((uint32_t)vt.chunk, rg.y - c0);
                 __syncthreads();
                 if (tid < n)
-                    stage_triangle(sm, tid, recs, (size_t)wi.v * s.T, keys[c0 + tid], vals[c0 + tid], DB, wi.tx * TW,
+                    stage_triangle<TW>(sm, tid, recs, (size_t)wi.v * s.T, keys[c0 + tid], vals[c0 + tid], DB, wi.tx * TW,
                                    wi.ty * TH);
                 __syncthreads();
                 if (!warp_done) {
                     for (int j = 0; j < n; ++j) {
                         const int4 h2 = sm.h2[j];
+                        if (!((h2.w >> warp) & 1)) continue;   // covers none of this warp's pixels
                         bool ldone = true;
 #pragma unroll
                         for (int q = 0; q < SG; ++q)
@@ -397,13 +396,21 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_BWD)
                     wsum += wsc[r];
                 }
             }
+            // barycentrics read again here (L1-resident) rather than kept in
+            // registers through the walk
+            float b1 = 0.f, b2 = 0.f;
+            if (act) {
+                const int4 gb = reinterpret_cast<const int4*>(V.gbuf)[(s0 + q) * HW + pix];
+                b1 = __int_as_float(gb.y);
+                b2 = __int_as_float(gb.z);
+            }
             float G[2];
             if (do_int)
-                winner_texture<true, SG>(s, acc_tex, act, wt[q], wb1[q], wb2[q], gcol0, sstride, msk, HW, wsum, do_tex,
+                winner_texture<true, SG>(s, acc_tex, act, wt[q], b1, b2, gcol0, sstride, msk, HW, wsum, do_tex,
                                          do_score, G);
             else if (do_tex || do_score)
-                winner_texture<false, SG>(s, acc_tex, act, wt[q], wb1[q], wb2[q], gcol0, sstride, msk, HW, wsum,
-                                          do_tex, do_score, G);
+                winner_texture<false, SG>(s, acc_tex, act, wt[q], b1, b2, gcol0, sstride, msk, HW, wsum, do_tex,
+                                          do_score, G);
             if (do_int) {
                 float gv[9];
 #pragma unroll

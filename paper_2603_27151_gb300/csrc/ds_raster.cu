@@ -19,7 +19,7 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
     __shared__ int s_item;
     const int tid = threadIdx.x;
     constexpr int TH = kTilePix / TW;
-    const int lx = tid & (TW - 1), ly = tid / TW;
+    const int lx = tid & (TW - 1), ly = tid / TW, warp = tid >> 5;
     const bool stochastic = mode == DS_MODE_STOCHASTIC;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(counter, 1);
@@ -50,12 +50,13 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
             const int n = (int)min((uint32_t)vt.chunk, rg.y - c0);
             __syncthreads();
             if (tid < n)
-                stage_triangle(sm, tid, recs, (size_t)wi.v * s.T, keys[c0 + tid], vals[c0 + tid], DB, wi.tx * TW,
+                stage_triangle<TW>(sm, tid, recs, (size_t)wi.v * s.T, keys[c0 + tid], vals[c0 + tid], DB, wi.tx * TW,
                                wi.ty * TH);
             __syncthreads();
             if (!warp_done) {
                 for (int j = 0; j < n; ++j) {
                     const int4 h2 = sm.h2[j];
+                    if (!((h2.w >> warp) & 1)) continue;   // covers none of this warp's pixels
                     // early exit: every sample already holds a fragment in
                     // front of anything the rest of the (depth-sorted) list can give
                     bool ldone = true;
@@ -143,7 +144,7 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
     __shared__ int s_item;
     const int tid = threadIdx.x;
     constexpr int TH = kTilePix / TW;
-    const int lx = tid & (TW - 1), ly = tid / TW;
+    const int lx = tid & (TW - 1), ly = tid / TW, warp = tid >> 5;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
@@ -176,12 +177,13 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
             const int n = (int)min((uint32_t)vt.chunk, rg.y - c0);
             __syncthreads();
             if (tid < n)
-                stage_triangle(sm, tid, recs, (size_t)wi.v * s.T, keys[c0 + tid], vals[c0 + tid], DB, wi.tx * TW,
+                stage_triangle<TW>(sm, tid, recs, (size_t)wi.v * s.T, keys[c0 + tid], vals[c0 + tid], DB, wi.tx * TW,
                                wi.ty * TH);
             __syncthreads();
             if (!warp_done) {
                 for (int j = 0; j < n; ++j) {
                     const int4 h2 = sm.h2[j];
+                    if (!((h2.w >> warp) & 1)) continue;   // covers none of this warp's pixels
                     bool ldone = true;
                     if (valid && mode == 0) {
 #pragma unroll

@@ -26,7 +26,7 @@ constexpr unsigned kFullMask = 0xffffffffu;
 struct TileStage {
     int4 h0[kChunk];         // A0, B0, thr0, A1
     int4 h1[kChunk];         // B1, thr1, A2, B2
-    int4 h2[kChunk];         // thr2, triangle, rho bound (float bits), -
+    int4 h2[kChunk];         // thr2, triangle, rho bound (float bits), warp mask
     long long eo[kChunk][3]; // oriented (unbiased) edge values at the tile's first pixel centre
     float kk[kChunk][3];     // perspective factors k_i
 };
@@ -69,6 +69,12 @@ __device__ __forceinline__ float rho_bound(uint32_t key, int DB) {
 // A lx + B ly >= thr with thr = ceil(-E'(origin) / 256).  Inside the guard
 // band |A|, |B| < 2^23 and lx, ly < 32, so |A lx + B ly| < 2^29: thr is
 // clamped to +-2^30 and the test runs in int32.
+//
+// h2.w receives a conservative mask of the tile's warps (bit w: the 32
+// pixels of threads 32w..32w+31, rows w*R .. w*R+R-1 with R = 32 / TW) whose
+// pixel centres the triangle may cover: for each edge the largest
+// A lx + B ly over the warp's rectangle (at a corner) must reach thr.
+template <int TW>
 __device__ __forceinline__ void stage_triangle(TileStage& sm, int slot, const SetupRec* recs, size_t vbase,
                                                uint32_t key, uint32_t t, int DB, int ox, int oy) {
     const SetupRec r = load_rec(recs + vbase + t);
@@ -83,9 +89,22 @@ __device__ __forceinline__ void stage_triangle(TileStage& sm, int slot, const Se
         sm.eo[slot][i] = eb + ((r.bias >> i) & 1u);
         sm.kk[slot][i] = r.k[i];
     }
+    constexpr int R = 32 / TW;   // rows per warp
+    int wmask = 0;
+#pragma unroll
+    for (int w = 0; w < kTilePix / 32; ++w) {
+        bool may = true;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int mx = r.A[i] > 0 ? r.A[i] * (TW - 1) : 0;
+            const int my = r.B[i] * (r.B[i] > 0 ? w * R + R - 1 : w * R);
+            may = may && (mx + my >= thr[i]);
+        }
+        wmask |= may ? 1 << w : 0;
+    }
     sm.h0[slot] = make_int4(r.A[0], r.B[0], thr[0], r.A[1]);
     sm.h1[slot] = make_int4(r.B[1], thr[1], r.A[2], r.B[2]);
-    sm.h2[slot] = make_int4(thr[2], (int)t, __float_as_int(rho_bound(key, DB)), 0);
+    sm.h2[slot] = make_int4(thr[2], (int)t, __float_as_int(rho_bound(key, DB)), wmask);
 }
 
 // Coverage of local pixel (lx, ly) by staged triangle j; on success E gets

@@ -150,10 +150,11 @@ def _traffic(kernel: str, pixel_samples: int):
 
 # ---------------------------------------------------------------- the GPU step
 class Workload:
-    def __init__(self, rank: int, device: str, views: int = 0):
+    def __init__(self, rank: int, device: str, views: int = 0, fused: bool = False):
         import torch
         from paper_2603_27151_gb300 import native as N
         self.N = N
+        self.fused = fused
         sc = I.large_batch()
         if views:
             sc.cams = sc.cams[:views]
@@ -187,8 +188,18 @@ class Workload:
         self.pixel_samples = sum(c.width * c.height for c in sc.cams) * self.S
 
     def step(self):
+        """Forward, L2 loss and backward of the batch: one fused training
+        pass (forward + loss + texture/score/interior terms in one kernel,
+        edge terms in a second), or the three separate calls."""
         N, sc = self.N, self.sc
+        if self.fused:
+            self.loss.zero_()
+            self.ctx.train_l2(self.sid, sc.cams, sc.seeds, self.S, N.DS_MODE_STOCHASTIC, sc.bg, self.g, self.col,
+                              self.targets, self.gcol, self.sw, 1.0 / self.S, self.loss,
+                              N.DS_G_ALL | N.DS_OVERWRITE, self.gv, self.gt)
+            return
         self.ctx.raster_forward(self.sid, sc.cams, sc.seeds, self.S, N.DS_MODE_STOCHASTIC, sc.bg, self.g, self.col)
+        self.loss.zero_()
         N.loss_l2(self.col, self.targets, self.gcol, self.sw, self.loss, scale=1.0 / self.S)
         self.ctx.raster_backward(self.sid, sc.cams, self.S, self.g, self.col, self.gcol, self.sw,
                                  N.DS_G_ALL | N.DS_REUSE_FORWARD | N.DS_OVERWRITE, self.gv, self.gt)
@@ -205,6 +216,8 @@ class Workload:
             "activate": T * V * C * 4 * 2 + T * V * 4,
             "setup": nv * T * (36 + 64 + 4 + 16 + 4),
             "raster_fwd": K * (8 + 64) + T * V * 4 + T * V * C * 4 + P * S * (16 + 4 * Co),
+            "train": (K * (8 + 64) + T * V * 4 + T * V * C * 4 * 3 + P * S * (16 + 4 * Co) + P * 4 * Co
+                      + P * S * (4 * Co + 4) + 36 * T * 2 + nv * T * 208),
             "raster_bwd": K * (8 + 64) + P * S * (16 + 4 * Co + 4) + T * V * C * 4 * 3 + 36 * T * 2 + nv * T * 208,
             "edge_bwd": P * S * (16 + 8 * Co) + nv * T * (64 + 208) + 36 * T * 2,
             "geom": nv * T * (36 + 208),
@@ -214,19 +227,27 @@ class Workload:
 def _plain_leg(wl, steps: int):
     """The same kernels on the plain path: one view per call (each call bins
     its own view and synchronises once to size its bins), no batching of
-    views, no graph.  Gradients are overwritten by the first view and
-    accumulated by the others, as in the batched step."""
+    views, no graph, default launch parameters.  Gradients are overwritten by
+    the first view and accumulated by the others, as in the batched step."""
     import torch
     N, sc, S = wl.N, wl.sc, wl.S
+    saved = wl.ctx.get_tuning()
+    wl.ctx.set_tuning()
 
     def step():
         for v in range(len(sc.cams)):
             one = slice(v, v + 1)
+            ow = N.DS_OVERWRITE if v == 0 else 0
+            if wl.fused:
+                wl.ctx.train_l2(wl.sid, sc.cams[one], sc.seeds[one], S, N.DS_MODE_STOCHASTIC, sc.bg, wl.g[one],
+                                wl.col[one], wl.targets[one], wl.gcol[one], wl.sw[one], 1.0 / S, wl.loss,
+                                N.DS_G_ALL | ow, wl.gv, wl.gt)
+                continue
             wl.ctx.raster_forward(wl.sid, sc.cams[one], sc.seeds[one], S, N.DS_MODE_STOCHASTIC, sc.bg, wl.g[one],
                                   wl.col[one])
             N.loss_l2(wl.col[one], wl.targets[one], wl.gcol[one], wl.sw[one], wl.loss, scale=1.0 / S)
             wl.ctx.raster_backward(wl.sid, sc.cams[one], S, wl.g[one], wl.col[one], wl.gcol[one], wl.sw[one],
-                                   N.DS_G_ALL | N.DS_REUSE_FORWARD | (N.DS_OVERWRITE if v == 0 else 0), wl.gv, wl.gt)
+                                   N.DS_G_ALL | N.DS_REUSE_FORWARD | ow, wl.gv, wl.gt)
 
     for _ in range(2):
         step()
@@ -238,17 +259,18 @@ def _plain_leg(wl, steps: int):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    wl.ctx.set_tuning(**saved)
     return {"value": wl.fragments / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
-            "what": "same kernels, one view per call (%d calls of forward + loss + backward per step), no graph"
-                    % len(sc.cams)}
+            "what": "same kernels, one view per call (%d %s per step), no graph, default launch parameters"
+                    % (len(sc.cams), "fused training passes" if wl.fused else "calls of forward + loss + backward")}
 
 
-def _train_leg(device: str, iters: int):
+def _train_leg(device: str, iters: int, fused: bool = True):
     """The captured training step (20,000 triangles, 4 views of 1024x768 per
     step drawn from 100 cameras, Adam) against the same step run eagerly."""
     import torch
     from paper_2603_27151_gb300.train import TrainStep
-    ts = TrainStep(device)
+    ts = TrainStep(device, fused=fused)
     ts.capture(warmup=3)
     for _ in range(3):
         ts.step()
@@ -324,7 +346,7 @@ def _gpu_arm(args):
     torch.cuda.set_device(local)
     dev = "cuda:%d" % local
     from paper_2603_27151_gb300 import native as N
-    wl = Workload(rank, dev, args.views)
+    wl = Workload(rank, dev, args.views, fused=args.fused)
     tuning = None
     if args.tuning:
         tw, db, bps, ch = (int(x) for x in args.tuning.split(","))
@@ -384,11 +406,7 @@ def _gpu_arm(args):
         wl.tex.copy_(ht, non_blocking=True)
         for d, h in zip(wl.targets, htg):
             d.copy_(h, non_blocking=True)
-        wl.ctx.raster_forward(wl.sid, wl.sc.cams, wl.sc.seeds, wl.S, N.DS_MODE_STOCHASTIC, wl.sc.bg, wl.g, wl.col)
-        wl.loss.zero_()
-        N.loss_l2(wl.col, wl.targets, wl.gcol, wl.sw, wl.loss, scale=1.0 / wl.S)
-        wl.ctx.raster_backward(wl.sid, wl.sc.cams, wl.S, wl.g, wl.col, wl.gcol, wl.sw,
-                               N.DS_G_ALL | N.DS_REUSE_FORWARD | N.DS_OVERWRITE, wl.gv, wl.gt)
+        wl.step()
         hl.copy_(wl.loss, non_blocking=True)
         torch.cuda.current_stream().synchronize()
         _ = float(hl[0])
@@ -533,6 +551,8 @@ def main():
                     help="skip the plain-path, training-step and serving legs")
     ap.add_argument("--train-iters", type=int, default=50)
     ap.add_argument("--no-tune", action="store_true", help="default launch parameters instead of the autotuner's")
+    ap.add_argument("--fused", action="store_true",
+                    help="one fused training pass per step instead of separate forward, loss and backward calls")
     ap.add_argument("--tuning", default="", help="fixed launch parameters tile_w,depth_bits,blocks_per_sm,chunk")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args()

@@ -210,6 +210,38 @@ DS_API ds_status ds_raster_backward_devcam(ds_ctx* ctx, int32_t soup_id, const i
                                            uint32_t grad_flags, float* grad_verts, float* grad_tex,
                                            void* stream);
 
+/* Loss inputs and outputs of one view for the fused training pass. */
+typedef struct ds_view_loss {
+    const float* target;  /* [C-1][H][W] target image                             */
+    float* grad_color;    /* [S][C-1][H][W] written: dL/dC = 2 scale (C - target)  */
+    float* score_w;       /* [S][H][W] written, or NULL: scale * l per sample       */
+} ds_view_loss;
+
+/* Fused training pass: ds_raster_forward, ds_loss_l2 and ds_raster_backward
+ * in one call, with the forward, the per-pixel L2 loss and the texture,
+ * score and interior gradients (Eq. 5; Algorithm A1 steps 1 and 2; first term
+ * of Eq. 8) computed by one kernel per tile and sample group, and the edge
+ * gradients (Sec. 3.2) by a second launch.  Results are those of the three
+ * calls in sequence with DS_OVERWRITE semantics selected by grad_flags
+ * (DS_G_* | optional DS_OVERWRITE): out receives the G-buffers and colours
+ * (n_front must be NULL), lv[v] the upstream gradients and score weights,
+ * *loss (device float, accumulated, may be NULL) scale * sum of l, and
+ * grad_verts / grad_tex the gradients (either may be NULL).  The plan stays
+ * valid for a later ds_raster_backward with DS_REUSE_FORWARD.  mode may
+ * include DS_NO_SYNC.  The second form takes device cameras and seeds as
+ * ds_raster_forward_devcam. */
+DS_API ds_status ds_raster_train_l2(ds_ctx* ctx, int32_t soup_id, const ds_camera* cams,
+                                    const uint64_t* seeds, int32_t n_views, int32_t S, uint32_t mode,
+                                    const float* bg, const ds_view_out* out, const ds_view_loss* lv,
+                                    float scale, float* loss, uint32_t grad_flags, float* grad_verts,
+                                    float* grad_tex, void* stream);
+DS_API ds_status ds_raster_train_l2_devcam(ds_ctx* ctx, int32_t soup_id, const int32_t* wh,
+                                           const ds_camera* cams, const uint64_t* seeds,
+                                           int32_t n_views, int32_t S, uint32_t mode, const float* bg,
+                                           const ds_view_out* out, const ds_view_loss* lv, float scale,
+                                           float* loss, uint32_t grad_flags, float* grad_verts,
+                                           float* grad_tex, void* stream);
+
 /* Grow the context's bin buffers to hold `pairs` (tile, triangle) pairs, so
  * that DS_NO_SYNC forwards (which never allocate or synchronise) have that
  * capacity.  Synchronous (may call cudaMalloc). */

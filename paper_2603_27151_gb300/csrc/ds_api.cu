@@ -530,6 +530,7 @@ ds_status ds_soup_free(ds_ctx* c, int32_t soup_id) {
 namespace {
 
 ds_status check_outputs(const ds_view_out* out, int32_t n_views) {
+    if (n_views < 1 || n_views > DS_MAX_VIEWS) return fail(DS_ERR_INVALID_ARG, "n_views out of range");
     if (!out) return fail(DS_ERR_INVALID_ARG, "out is NULL");
     for (int v = 0; v < n_views; ++v) {
         if (!out[v].gbuf || !out[v].color) return fail(DS_ERR_INVALID_ARG, "view output buffer is NULL");
@@ -551,6 +552,7 @@ ds_status check_gin(const ds_view_out* fwd, const ds_view_gin* gin, int32_t n_vi
     if ((grad_flags & ~(DS_G_ALL | DS_REUSE_FORWARD | DS_OVERWRITE)) != 0)
         return fail(DS_ERR_INVALID_ARG, "unknown gradient flags");
     if (!fwd || !gin) return fail(DS_ERR_INVALID_ARG, "fwd or gin is NULL");
+    if (n_views < 1 || n_views > DS_MAX_VIEWS) return fail(DS_ERR_INVALID_ARG, "n_views out of range");
     const bool need_color = (grad_flags & (DS_G_TEX | DS_G_INTERIOR | DS_G_EDGE)) != 0;
     for (int v = 0; v < n_views; ++v) {
         if (!fwd[v].gbuf) return fail(DS_ERR_INVALID_ARG, "fwd gbuf is NULL");
@@ -595,8 +597,20 @@ ds_status forward_impl(ds_ctx* c, int32_t soup_id, Soup& s, const ds_camera* hos
     return DS_OK;
 }
 
-// Backward after validation; vt is filled and the plan is current.
-ds_status backward_impl(ds_ctx* c, Soup& s, uint32_t grad_flags, float* grad_verts, float* grad_tex, cudaStream_t st) {
+// Arguments of the fused training pass (forward + L2 loss in the same kernel
+// as the texture, score and interior gradients).
+struct FusedL2 {
+    uint32_t mode;
+    ds::Bg bg;
+    float scale;
+    float* loss;
+};
+
+// Backward after validation; vt is filled and the plan is current.  With
+// `fused` the forward has not run: the fused kernel renders, evaluates the
+// loss and takes the texture, score and interior terms in one pass.
+ds_status backward_impl(ds_ctx* c, Soup& s, uint32_t grad_flags, float* grad_verts, float* grad_tex, cudaStream_t st,
+                        const FusedL2* fused = nullptr) {
     ds::ViewTable& vt = *c->vt;
     const int n_views = vt.n;
     const ds::SoupDev sd = soup_dev(s);
@@ -621,7 +635,15 @@ ds_status backward_impl(ds_ctx* c, Soup& s, uint32_t grad_flags, float* grad_ver
         StageScope p(c, ds::kStGeom, st);
         DS_TRY_CUDA(ds::launch_geom(vt, sd, c->geom.as<ds::GeomRec>(), st));
     }
-    if (want_tex || (want_verts && (gflags & DS_G_INTERIOR))) {
+    if (fused) {
+        StageScope p(c, ds::kStTrain, st);
+        DS_TRY_CUDA(cudaMemsetAsync(c->d_counter() + 2, 0, 4, st));
+        DS_TRY_CUDA(ds::launch_raster_train(vt, sd, c->recs.as<ds::SetupRec>(), c->keys[c->plan.res].as<uint32_t>(),
+                                            c->vals[c->plan.res].as<uint32_t>(), c->ranges.as<uint2>(), c->plan.DB,
+                                            fused->mode & 0xffu, fused->bg, fused->scale, fused->loss, gflags,
+                                            c->geom.as<ds::GeomRec>(), acc_tex, acc_verts, c->d_counter() + 2, grid,
+                                            st));
+    } else if (want_tex || (want_verts && (gflags & DS_G_INTERIOR))) {
         StageScope p(c, ds::kStRasterBwd, st);
         DS_TRY_CUDA(cudaMemsetAsync(c->d_counter() + 2, 0, 4, st));
         DS_TRY_CUDA(ds::launch_raster_bwd(vt, sd, c->recs.as<ds::SetupRec>(), c->keys[c->plan.res].as<uint32_t>(),
@@ -643,6 +665,33 @@ ds_status backward_impl(ds_ctx* c, Soup& s, uint32_t grad_flags, float* grad_ver
         else if (grad_verts && overwrite) DS_TRY_CUDA(cudaMemsetAsync(grad_verts, 0, sizeof(float) * n_verts, st));
     }
     return DS_OK;
+}
+
+// Loss views of the fused training pass: targets present, gradients
+// written; the table's gradient pointers are the pass's outputs.
+ds_status set_loss_views(ds::ViewTable& vt, const ds_view_loss* lv) {
+    if (!lv) return fail(DS_ERR_INVALID_ARG, "loss views are NULL");
+    for (int v = 0; v < vt.n; ++v) {
+        if (!lv[v].target || !lv[v].grad_color) return fail(DS_ERR_INVALID_ARG, "target or grad_color is NULL");
+        vt.v[v].target = lv[v].target;
+        vt.v[v].grad_color = lv[v].grad_color;
+        vt.v[v].score_w = lv[v].score_w;
+    }
+    return DS_OK;
+}
+
+ds_status train_impl(ds_ctx* c, int32_t soup_id, Soup& s, const ds_camera* host_cams, uint32_t mode, const float* bg,
+                     const ds_view_out* out, float scale, float* loss, uint32_t grad_flags, float* grad_verts,
+                     float* grad_tex, cudaStream_t st) {
+    for (int v = 0; v < c->vt->n; ++v)
+        if (out[v].n_front) return fail(DS_ERR_INVALID_ARG, "the fused training pass does not write n_front");
+    DS_TRY(prepare(c, soup_id, s, host_cams, *c->vt, (mode & DS_NO_SYNC) == 0, st));
+    FusedL2 f{};
+    f.mode = mode;
+    for (int i = 0; i < s.C - 1; ++i) f.bg.c[i] = bg[i];
+    f.scale = scale;
+    f.loss = loss;
+    return backward_impl(c, s, grad_flags, grad_verts, grad_tex, st, &f);
 }
 
 // View table for device-resident cameras: sizes from the host, cameras and
@@ -698,10 +747,10 @@ ds_status ds_raster_forward_devcam(ds_ctx* c, int32_t soup_id, const int32_t* wh
     DS_TRY(get_soup(c, soup_id, &s));
     DS_TRY(check_mode(mode, seeds != nullptr));
     if (!bg) return fail(DS_ERR_INVALID_ARG, "bg is NULL");
-    DS_TRY(check_outputs(out, n_views));
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     c->last_stream = st;
-    DS_TRY(build_table_devcam(*c->vt, c->tune, wh, cams, seeds, n_views, S, out, nullptr));
+    DS_TRY(build_table_devcam(*c->vt, c->tune, wh, cams, seeds, n_views, S, out, nullptr));   // validates n_views
+    DS_TRY(check_outputs(out, n_views));
     return forward_impl(c, soup_id, *s, nullptr, mode, bg, out, st);
 }
 
@@ -857,6 +906,49 @@ ds_status ds_get_tuning(ds_ctx* c, ds_tuning* t) {
     std::lock_guard<std::mutex> lk(c->mu);
     *t = c->tune;
     return DS_OK;
+}
+
+ds_status ds_raster_train_l2(ds_ctx* c, int32_t soup_id, const ds_camera* cams, const uint64_t* seeds,
+                             int32_t n_views, int32_t S, uint32_t mode, const float* bg, const ds_view_out* out,
+                             const ds_view_loss* lv, float scale, float* loss, uint32_t grad_flags, float* grad_verts,
+                             float* grad_tex, void* stream) {
+    if (!c) return fail(DS_ERR_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    Soup* s = nullptr;
+    DS_TRY(get_soup(c, soup_id, &s));
+    DS_TRY(check_views(cams, n_views, S));
+    DS_TRY(check_mode(mode, seeds != nullptr));
+    if (!bg) return fail(DS_ERR_INVALID_ARG, "bg is NULL");
+    DS_TRY(check_outputs(out, n_views));
+    if (!std::isfinite(scale)) return fail(DS_ERR_INVALID_ARG, "scale is not finite");
+    if ((grad_flags & ~(DS_G_ALL | DS_OVERWRITE)) != 0) return fail(DS_ERR_INVALID_ARG, "unknown gradient flags");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    build_table(*c->vt, c->tune, cams, seeds, n_views, S, out, nullptr);
+    DS_TRY(set_loss_views(*c->vt, lv));
+    return train_impl(c, soup_id, *s, cams, mode, bg, out, scale, loss, grad_flags, grad_verts, grad_tex, st);
+}
+
+ds_status ds_raster_train_l2_devcam(ds_ctx* c, int32_t soup_id, const int32_t* wh, const ds_camera* cams,
+                                    const uint64_t* seeds, int32_t n_views, int32_t S, uint32_t mode, const float* bg,
+                                    const ds_view_out* out, const ds_view_loss* lv, float scale, float* loss,
+                                    uint32_t grad_flags, float* grad_verts, float* grad_tex, void* stream) {
+    if (!c) return fail(DS_ERR_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    Soup* s = nullptr;
+    DS_TRY(get_soup(c, soup_id, &s));
+    DS_TRY(check_mode(mode, seeds != nullptr));
+    if (!bg) return fail(DS_ERR_INVALID_ARG, "bg is NULL");
+    if (!std::isfinite(scale)) return fail(DS_ERR_INVALID_ARG, "scale is not finite");
+    if ((grad_flags & ~(DS_G_ALL | DS_OVERWRITE)) != 0) return fail(DS_ERR_INVALID_ARG, "unknown gradient flags");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    DS_TRY(build_table_devcam(*c->vt, c->tune, wh, cams, seeds, n_views, S, out, nullptr));   // validates n_views
+    DS_TRY(check_outputs(out, n_views));
+    DS_TRY(set_loss_views(*c->vt, lv));
+    return train_impl(c, soup_id, *s, nullptr, mode, bg, out, scale, loss, grad_flags, grad_verts, grad_tex, st);
 }
 
 }  // extern "C"

@@ -208,7 +208,7 @@ __device__ __forceinline__ void winner_texture(const SoupDev& s, double* acc_tex
                     if (do_tex || kInterior) {
 #pragma unroll
                         for (int q = 0; q < SG; ++q)
-                            if (msk & (1 << q)) g += __ldg(gcol0 + q * sstride + c * HW);
+                            if (msk & (1 << q)) g += gcol0[q * sstride + c * HW];   // plain load: may be this kernel's own write
                     }
                     if (kInterior) {
                         G[0] += g * sgnN * (a1 - a0);
@@ -277,6 +277,126 @@ __device__ __forceinline__ void interior_grad(const GeomRec* g, const DevCam& ca
     }
 }
 
+// Eq. 9 for every covered fragment in front of the winner of each sample
+// (Algorithm A1 2(b), G-buffer recomputation): walk the tile's list again and
+// scatter -w/(1 - alpha) to the opacity texels of the fragments in front.
+// `staged`: the whole list is already in shared memory (one chunk).
+template <int SG, int TW>
+__device__ __forceinline__ void score_walk(TileStage& sm, const SetupRec* __restrict__ recs,
+                                           const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                                           uint2 rg, int DB, int chunk, size_t vbase, const WorkItem& wi,
+                                           const SoupDev& s, double* __restrict__ acc_tex, int tid, int lx, int ly,
+                                           int warp, bool staged, bool any_score, const int (&wt)[SG],
+                                           const float (&wrho)[SG], const float (&wsc)[SG]) {
+    constexpr int TH = kTilePix / TW;
+    bool warp_done = !__any_sync(kFullMask, any_score);
+    if (__syncthreads_or(!warp_done)) {
+        for (uint32_t c0 = rg.x; c0 < rg.y; c0 += (uint32_t)chunk) {
+            const int n = (int)min((uint32_t)chunk, rg.y - c0);
+            __syncthreads();
+            if (!staged) {
+                if (tid < n)
+                    stage_triangle<TW>(sm, tid, recs, vbase, keys[c0 + tid], vals[c0 + tid], DB, wi.tx * TW,
+                                       wi.ty * TH);
+                __syncthreads();
+            }
+            if (!warp_done) {
+                for (int j = 0; j < n; ++j) {
+                    const int4 h2 = sm.h2[j];
+                    if (!((h2.w >> warp) & 1)) continue;   // covers none of this warp's pixels
+                    bool ldone = true;
+#pragma unroll
+                    for (int q = 0; q < SG; ++q)
+                        if (wsc[q] != 0.f) ldone = ldone && wt[q] >= 0 && wrho[q] > __int_as_float(h2.z);
+                    if (__all_sync(kFullMask, ldone)) {
+                        warp_done = true;
+                        break;
+                    }
+                    const int t = h2.y;
+                    bool act = false;
+                    float g = 0.f;
+                    Cell cl;
+                    cl.k0 = cl.k1 = cl.k2 = 0;
+                    cl.wa = cl.wb = 0.f;
+                    cl.lower = true;
+                    long long E[3];
+                    if (any_score && tile_cover(sm, j, lx, ly, E)) {
+                        const Frag f = make_frag(E[0], E[1], E[2], sm.kk[j][0], sm.kk[j][1], sm.kk[j][2]);
+                        bool need = false;
+#pragma unroll
+                        for (int q = 0; q < SG; ++q)
+                            need = need || (wsc[q] != 0.f && t != wt[q] &&
+                                            (wt[q] < 0 || in_front(f.rho, t, wrho[q], wt[q])));
+                        if (need) {
+                            const float r = __frcp_rn(f.rho);
+                            cl = find_cell(s.N, __fmul_rn(f.q1, r), __fmul_rn(f.q2, r));
+                            const float* aa = s.act_a + (size_t)t * s.V;
+                            const float alpha = interp(__ldg(aa + cl.k0), __ldg(aa + cl.k1), __ldg(aa + cl.k2), cl.wa, cl.wb);
+                            const float inv = 1.0f / (1.0f - alpha);
+#pragma unroll
+                            for (int q = 0; q < SG; ++q)
+                                if (wsc[q] != 0.f && t != wt[q] && (wt[q] < 0 || in_front(f.rho, t, wrho[q], wt[q])))
+                                    g -= wsc[q] * inv;
+                            act = true;
+                        }
+                    }
+                    if (__any_sync(kFullMask, act)) scatter_alpha_run(s, acc_tex, act, t, cl, g);
+                }
+            }
+            if (__syncthreads_and(warp_done)) break;
+        }
+    }
+}
+
+// Winner terms of every sample: colour (Algorithm A1 2(a)), +w/alpha
+// (2(b)) and the interior vertex term (first term of Eq. 8), once per
+// distinct winner of the pixel's samples.
+template <int SG>
+__device__ __forceinline__ void winner_terms(const SoupDev& s, double* __restrict__ acc_tex,
+                                             double* __restrict__ acc_verts, const GeomRec* __restrict__ vgeom,
+                                             const DevCam& cam, const ViewDesc& V, int s0, int ns, size_t HW,
+                                             size_t pix, int px, int py, bool valid, bool do_tex, bool do_score,
+                                             bool do_int, const int (&wt)[SG], const float (&wsc)[SG]) {
+    const size_t sstride = (size_t)(s.C - 1) * HW;
+    const float* gcol0 = V.grad_color + (size_t)s0 * sstride + pix;
+#pragma unroll
+    for (int q = 0; q < SG; ++q) {
+        bool act = valid && q < ns && wt[q] >= 0;
+        int msk = 0;
+        float wsum = 0.f;
+#pragma unroll
+        for (int r = 0; r < SG; ++r) {
+            if (r < q && r < ns && wt[r] == wt[q]) act = false;   // handled with sample r
+            if (r >= q && r < ns && wt[r] == wt[q]) {
+                msk |= 1 << r;
+                wsum += wsc[r];
+            }
+        }
+        // barycentrics read again here (L1-resident) rather than kept in
+        // registers through the walk
+        float b1 = 0.f, b2 = 0.f;
+        if (act) {
+            const int4 gb = reinterpret_cast<const int4*>(V.gbuf)[(s0 + q) * HW + pix];
+            b1 = __int_as_float(gb.y);
+            b2 = __int_as_float(gb.z);
+        }
+        float G[2];
+        if (do_int)
+            winner_texture<true, SG>(s, acc_tex, act, wt[q], b1, b2, gcol0, sstride, msk, HW, wsum, do_tex,
+                                     do_score, G);
+        else if (do_tex || do_score)
+            winner_texture<false, SG>(s, acc_tex, act, wt[q], b1, b2, gcol0, sstride, msk, HW, wsum, do_tex,
+                                      do_score, G);
+        if (do_int) {
+            float gv[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) gv[k] = 0.f;
+            if (act) interior_grad(vgeom + wt[q], cam, px, py, G, gv);
+            scatter_verts_run(acc_verts, act, wt[q], gv);
+        }
+    }
+}
+
 template <int SG, int TW>
 __global__ void __launch_bounds__(kTilePix, DS_MINB_BWD)
     k_raster_bwd(const __grid_constant__ ViewTable vt, const SoupDev s, const SetupRec* __restrict__ recs,
@@ -321,105 +441,152 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_BWD)
             }
         }
 
-        // ---- Eq. 9 for every covered fragment in front of the winner
         const uint2 rg = ranges[V.tile_base + wi.ty * V.tiles_x + wi.tx];
-        bool warp_done = !__any_sync(kFullMask, any_score);
-        if (__syncthreads_or(!warp_done)) {
-            for (uint32_t c0 = rg.x; c0 < rg.y; c0 += (uint32_t)vt.chunk) {
-                const int n = (int)min((uint32_t)vt.chunk, rg.y - c0);
-                __syncthreads();
-                if (tid < n)
-                    stage_triangle<TW>(sm, tid, recs, (size_t)wi.v * s.T, keys[c0 + tid], vals[c0 + tid], DB, wi.tx * TW,
-                                   wi.ty * TH);
-                __syncthreads();
-                if (!warp_done) {
-                    for (int j = 0; j < n; ++j) {
-                        const int4 h2 = sm.h2[j];
-                        if (!((h2.w >> warp) & 1)) continue;   // covers none of this warp's pixels
-                        bool ldone = true;
-#pragma unroll
-                        for (int q = 0; q < SG; ++q)
-                            if (wsc[q] != 0.f) ldone = ldone && wt[q] >= 0 && wrho[q] > __int_as_float(h2.z);
-                        if (__all_sync(kFullMask, ldone)) {
-                            warp_done = true;
-                            break;
-                        }
-                        const int t = h2.y;
-                        bool act = false;
-                        float g = 0.f;
-                        Cell cl;
-                        cl.k0 = cl.k1 = cl.k2 = 0;
-                        cl.wa = cl.wb = 0.f;
-                        cl.lower = true;
-                        long long E[3];
-                        if (any_score && tile_cover(sm, j, lx, ly, E)) {
-                            const Frag f = make_frag(E[0], E[1], E[2], sm.kk[j][0], sm.kk[j][1], sm.kk[j][2]);
-                            bool need = false;
-#pragma unroll
-                            for (int q = 0; q < SG; ++q)
-                                need = need || (wsc[q] != 0.f && t != wt[q] &&
-                                                (wt[q] < 0 || in_front(f.rho, t, wrho[q], wt[q])));
-                            if (need) {
-                                const float r = __frcp_rn(f.rho);
-                                cl = find_cell(s.N, __fmul_rn(f.q1, r), __fmul_rn(f.q2, r));
-                                const float* aa = s.act_a + (size_t)t * s.V;
-                                const float alpha = interp(__ldg(aa + cl.k0), __ldg(aa + cl.k1), __ldg(aa + cl.k2), cl.wa, cl.wb);
-                                const float inv = 1.0f / (1.0f - alpha);
-#pragma unroll
-                                for (int q = 0; q < SG; ++q)
-                                    if (wsc[q] != 0.f && t != wt[q] && (wt[q] < 0 || in_front(f.rho, t, wrho[q], wt[q])))
-                                        g -= wsc[q] * inv;
-                                act = true;
-                            }
-                        }
-                        if (__any_sync(kFullMask, act)) scatter_alpha_run(s, acc_tex, act, t, cl, g);
-                    }
-                }
-                if (__syncthreads_and(warp_done)) break;
-            }
-        }
+        score_walk<SG, TW>(sm, recs, keys, vals, rg, DB, vt.chunk, (size_t)wi.v * s.T, wi, s, acc_tex, tid, lx, ly,
+                           warp, false, any_score, wt, wrho, wsc);
+        winner_terms<SG>(s, acc_tex, acc_verts, geom + (size_t)wi.v * s.T, view_cam(vt, wi.v), V, s0, ns, HW, pix, px,
+                         py, valid, do_tex, do_score, do_int, wt, wsc);
+        __syncthreads();
+    }
+}
 
-        // ---- winner terms: colour (2(a)), +w/alpha (2(b)), interior (Eq. 8),
-        // once per distinct winner of the pixel's samples
-        const size_t sstride = (size_t)(s.C - 1) * HW;
-        const float* gcol0 = V.grad_color + (size_t)s0 * sstride + pix;
+// ------------------------------------------------------------ fused training pass
+// Colour of the selected fragment (or the background), written to col[c*HW],
+// with the per-pixel L2 loss against tgt[c*HW] and its upstream gradient
+// gc[c*HW] = 2 scale (colour - target); returns l = sum_c (colour - target)^2.
+// Same arithmetic, in the same order, as the forward's decode followed by
+// ds_loss_l2.
+__device__ __forceinline__ float color_loss_out(const SoupDev& s, int t, float b1, float b2, const Bg& bg,
+                                                const float* __restrict__ tgt, float* __restrict__ col,
+                                                float* __restrict__ gc, size_t HW, float two_scale) {
+    const int Co = s.C - 1;
+    float ell = 0.f;
+    auto emit = [&](int c, float v) {
+        col[c * HW] = v;
+        const float d = __fsub_rn(v, __ldg(tgt + c * HW));
+        ell = __fmaf_rn(d, d, ell);
+        gc[c * HW] = __fmul_rn(two_scale, d);
+    };
+    if (t < 0) {
+#pragma unroll
+        for (int c = 0; c < DS_MAX_CHANNELS; ++c)   // constant indices into the parameter struct
+            if (c < Co) emit(c, bg.c[c]);
+        return ell;
+    }
+    const Cell cl = find_cell(s.N, b1, b2);
+    const int C = s.C;
+    const float* base = s.act + (size_t)t * s.V * C;
+    const float* p0 = base + (size_t)cl.k0 * C;
+    const float* p1 = base + (size_t)cl.k1 * C;
+    const float* p2 = base + (size_t)cl.k2 * C;
+    if ((C & 3) == 0) {
+        for (int c4 = 0; c4 < C; c4 += 4) {
+            const float4 a0 = __ldg(reinterpret_cast<const float4*>(p0 + c4));
+            const float4 a1 = __ldg(reinterpret_cast<const float4*>(p1 + c4));
+            const float4 a2 = __ldg(reinterpret_cast<const float4*>(p2 + c4));
+            const float v[4] = {interp(a0.x, a1.x, a2.x, cl.wa, cl.wb), interp(a0.y, a1.y, a2.y, cl.wa, cl.wb),
+                                interp(a0.z, a1.z, a2.z, cl.wa, cl.wb), interp(a0.w, a1.w, a2.w, cl.wa, cl.wb)};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (c4 + k < Co) emit(c4 + k, v[k]);
+        }
+    } else {
+        for (int c = 0; c < Co; ++c) emit(c, interp(__ldg(p0 + c), __ldg(p1 + c), __ldg(p2 + c), cl.wa, cl.wb));
+    }
+    return ell;
+}
+
+// Forward (Eq. 5), per-pixel L2 loss, and the texture, score and interior
+// gradients (Algorithm A1 step 2 without the edge terms) of one work item in
+// one CTA: the masked z-test walk, then the G-buffer, colours, upstream
+// gradients and score weights, then the score walk over the same staged list
+// (still in shared memory when it fits one chunk) and the winner terms.  The
+// winners' depths come from the forward walk instead of being recomputed.
+template <int SG, int TW>
+__global__ void __launch_bounds__(kTilePix, DS_MINB_TRAIN)
+    k_raster_train(const __grid_constant__ ViewTable vt, const SoupDev s, const SetupRec* __restrict__ recs,
+                   const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                   const uint2* __restrict__ ranges, int DB, uint32_t mode, const Bg bg, float scale,
+                   float* __restrict__ loss, uint32_t flags, const GeomRec* __restrict__ geom,
+                   double* __restrict__ acc_tex, double* __restrict__ acc_verts, int* __restrict__ counter) {
+    __shared__ TileStage sm;
+    __shared__ int s_item;
+    __shared__ float s_loss[kTilePix / 32];
+    const int tid = threadIdx.x;
+    constexpr int TH = kTilePix / TW;
+    const int lx = tid & (TW - 1), ly = tid / TW, warp = tid >> 5;
+    const bool stochastic = mode == DS_MODE_STOCHASTIC;
+    const bool do_tex = (flags & DS_G_TEX) && acc_tex;
+    const bool do_score = (flags & DS_G_SCORE) && acc_tex;
+    const bool do_int = (flags & DS_G_INTERIOR) && acc_verts;
+    const float two_scale = 2.0f * scale;
+    float lsum = 0.f;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= vt.n_items) break;
+        const WorkItem wi = decode_item(vt, item);
+        const ViewDesc& V = vt.v[wi.v];
+        const int px = wi.tx * TW + lx, py = wi.ty * TH + ly;
+        const bool valid = px < V.W && py < V.H;
+        const int s0 = wi.g * kSampleGroup;
+        const int ns = min(SG, vt.S - s0);
+        const uint2 seed = view_seed(vt, wi.v);
+        const size_t HW = (size_t)V.H * V.W, pix = (size_t)py * V.W + px;
+
+        int bt[SG];
+        float brho[SG], bb1[SG], bb2[SG], bD[SG];
 #pragma unroll
         for (int q = 0; q < SG; ++q) {
-            bool act = valid && q < ns && wt[q] >= 0;
-            int msk = 0;
-            float wsum = 0.f;
-#pragma unroll
-            for (int r = 0; r < SG; ++r) {
-                if (r < q && r < ns && wt[r] == wt[q]) act = false;   // handled with sample r
-                if (r >= q && r < ns && wt[r] == wt[q]) {
-                    msk |= 1 << r;
-                    wsum += wsc[r];
-                }
-            }
-            // barycentrics read again here (L1-resident) rather than kept in
-            // registers through the walk
-            float b1 = 0.f, b2 = 0.f;
-            if (act) {
-                const int4 gb = reinterpret_cast<const int4*>(V.gbuf)[(s0 + q) * HW + pix];
-                b1 = __int_as_float(gb.y);
-                b2 = __int_as_float(gb.z);
-            }
-            float G[2];
-            if (do_int)
-                winner_texture<true, SG>(s, acc_tex, act, wt[q], b1, b2, gcol0, sstride, msk, HW, wsum, do_tex,
-                                         do_score, G);
-            else if (do_tex || do_score)
-                winner_texture<false, SG>(s, acc_tex, act, wt[q], b1, b2, gcol0, sstride, msk, HW, wsum, do_tex,
-                                          do_score, G);
-            if (do_int) {
-                float gv[9];
-#pragma unroll
-                for (int k = 0; k < 9; ++k) gv[k] = 0.f;
-                if (act) interior_grad(geom + (size_t)wi.v * s.T + wt[q], view_cam(vt, wi.v), px, py, G, gv);
-                scatter_verts_run(acc_verts, act, wt[q], gv);
-            }
+            bt[q] = -1;
+            brho[q] = 0.0f;
+            bb1[q] = bb2[q] = 0.0f;
+            bD[q] = __int_as_float(0x7f800000);
         }
+        const uint2 rg = ranges[V.tile_base + wi.ty * V.tiles_x + wi.tx];
+        const bool fits = forward_walk<SG, TW>(sm, recs, keys, vals, rg, DB, vt.chunk, (size_t)wi.v * s.T, wi, s, tid,
+                                               lx, ly, warp, valid, px, py, ns, seed, stochastic, bt, brho, bb1, bb2,
+                                               bD);
+
+        // ---- G-buffer, colours, loss, upstream gradients, score weights
+        float wsc[SG];
+        bool any_score = false;
+        const int Co = s.C - 1;
+#pragma unroll
+        for (int q = 0; q < SG; ++q) {
+            wsc[q] = 0.f;
+            if (!valid || q >= ns) continue;
+            const int sg = s0 + q;
+            reinterpret_cast<int4*>(V.gbuf)[sg * HW + pix] =
+                make_int4(bt[q], __float_as_int(bb1[q]), __float_as_int(bb2[q]), __float_as_int(bD[q]));
+            const float ell = color_loss_out(s, bt[q], bb1[q], bb2[q], bg, V.target + pix,
+                                             V.color + (size_t)sg * Co * HW + pix,
+                                             const_cast<float*>(V.grad_color) + (size_t)sg * Co * HW + pix, HW,
+                                             two_scale);
+            const float w = __fmul_rn(scale, ell);
+            if (V.score_w) const_cast<float*>(V.score_w)[sg * HW + pix] = w;
+            lsum += ell;
+            if (do_score) wsc[q] = w;
+            any_score = any_score || wsc[q] != 0.f;
+        }
+
+        // ---- Algorithm A1 step 2 (texture, score, interior)
+        score_walk<SG, TW>(sm, recs, keys, vals, rg, DB, vt.chunk, (size_t)wi.v * s.T, wi, s, acc_tex, tid, lx, ly,
+                           warp, fits, any_score, bt, brho, wsc);
+        winner_terms<SG>(s, acc_tex, acc_verts, geom + (size_t)wi.v * s.T, view_cam(vt, wi.v), V, s0, ns, HW, pix, px,
+                         py, valid, do_tex, do_score, do_int, bt, wsc);
         __syncthreads();
+    }
+    // ---- the loss: one atomic per CTA
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) lsum += __shfl_down_sync(kFullMask, lsum, d);
+    if ((tid & 31) == 0) s_loss[warp] = lsum;
+    __syncthreads();
+    if (tid == 0 && loss) {
+        float t = 0.f;
+        for (int w = 0; w < kTilePix / 32; ++w) t += s_loss[w];
+        atomicAdd(loss, scale * t);
     }
 }
 
@@ -664,6 +831,19 @@ cudaError_t launch_raster_bwd(const ViewTable& vt, const SoupDev& s, const Setup
         constexpr int SG = decltype(P)::sg, TW = decltype(P)::tw;
         k_raster_bwd<SG, TW><<<resident_grid(k_raster_bwd<SG, TW>, vt.n_items, grid), kTilePix, 0, st>>>(
             vt, s, recs, keys, vals, ranges, DB, flags, geom, acc_tex, acc_verts, counter);
+    });
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_raster_train(const ViewTable& vt, const SoupDev& s, const SetupRec* recs, const uint32_t* keys,
+                                const uint32_t* vals, const uint2* ranges, int DB, uint32_t mode, const Bg& bg,
+                                float scale, float* loss, uint32_t flags, const GeomRec* geom, double* acc_tex,
+                                double* acc_verts, int* counter, int grid, cudaStream_t st) {
+    dispatch_tile(vt.tile_w, vt.S == 1 ? 1 : (vt.S == 2 ? 2 : 4), [&](auto P) {
+        constexpr int SG = decltype(P)::sg, TW = decltype(P)::tw;
+        k_raster_train<SG, TW><<<resident_grid(k_raster_train<SG, TW>, vt.n_items, grid), kTilePix, 0, st>>>(
+            vt, s, recs, keys, vals, ranges, DB, mode, bg, scale, loss, flags, geom, acc_tex, acc_verts, counter);
     });
     note_launches(1);
     return cudaGetLastError();

@@ -28,6 +28,11 @@ struct DevCam {
     float near_z;
 };
 
+// Background colour (C-1 channels) of samples where no fragment survives.
+struct Bg {
+    float c[DS_MAX_CHANNELS];
+};
+
 // Per-view parameters, passed by value in the kernel parameter space.
 struct ViewDesc {
     DevCam cam;
@@ -40,6 +45,7 @@ struct ViewDesc {
     int32_t* n_front;
     const float* grad_color;
     const float* score_w;
+    const float* target;   // fused training pass: [C-1][H][W] target image
 };
 
 struct ViewTable {

@@ -14,7 +14,7 @@ namespace ds {
 // Pipeline stages timed by the optional profiler (ds_profile_*).
 enum Stage {
     kStActivate, kStSetup, kStScan, kStEmit, kStSort, kStRanges,
-    kStRasterFwd, kStCount, kStGeom, kStRasterBwd, kStEdgeBwd, kStFinish, kNumStages
+    kStRasterFwd, kStCount, kStGeom, kStRasterBwd, kStEdgeBwd, kStFinish, kStTrain, kNumStages
 };
 extern const char* const kStageNames[kNumStages];
 
@@ -64,9 +64,6 @@ cudaError_t launch_tile_ranges(const uint32_t* keys, const uint32_t* count, uint
                                uint2* ranges, cudaStream_t st);
 
 // ---- forward rasteriser (ds_raster.cu)
-struct Bg {
-    float c[DS_MAX_CHANNELS];
-};
 cudaError_t launch_raster_fwd(const ViewTable& vt, const SoupDev& s, const SetupRec* recs,
                               const uint32_t* keys, const uint32_t* vals, const uint2* ranges,
                               int DB, uint32_t mode, const Bg& bg, int* counter, int grid,
@@ -84,6 +81,11 @@ cudaError_t launch_raster_bwd(const ViewTable& vt, const SoupDev& s, const Setup
                               const uint32_t* keys, const uint32_t* vals, const uint2* ranges,
                               int DB, uint32_t flags, const GeomRec* geom, double* acc_tex,
                               double* acc_verts, int* counter, int grid, cudaStream_t st);
+// Fused training pass: forward + L2 loss + texture/score/interior gradients.
+cudaError_t launch_raster_train(const ViewTable& vt, const SoupDev& s, const SetupRec* recs, const uint32_t* keys,
+                                const uint32_t* vals, const uint2* ranges, int DB, uint32_t mode, const Bg& bg,
+                                float scale, float* loss, uint32_t flags, const GeomRec* geom, double* acc_tex,
+                                double* acc_verts, int* counter, int grid, cudaStream_t st);
 cudaError_t launch_edge_bwd(const ViewTable& vt, const SoupDev& s, const SetupRec* recs,
                             const GeomRec* geom, double* acc_verts, int* counter, int grid,
                             cudaStream_t st);

@@ -31,11 +31,11 @@ __global__ void __launch_bounds__(256) k_loss_l2(const __grid_constant__ LossTab
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < V.HW; p += gridDim.x * blockDim.x) {
         float ell = 0.f;
         for (int c = 0; c < lt.Co; ++c) {
-            const float d = col[(size_t)c * V.HW + p] - __ldg(V.target + (size_t)c * V.HW + p);
-            ell += d * d;
-            if (gc) gc[(size_t)c * V.HW + p] = 2.0f * lt.scale * d;
+            const float d = __fsub_rn(col[(size_t)c * V.HW + p], __ldg(V.target + (size_t)c * V.HW + p));
+            ell = __fmaf_rn(d, d, ell);
+            if (gc) gc[(size_t)c * V.HW + p] = __fmul_rn(2.0f * lt.scale, d);
         }
-        if (V.score_w) V.score_w[(size_t)s * V.HW + p] = lt.scale * ell;
+        if (V.score_w) V.score_w[(size_t)s * V.HW + p] = __fmul_rn(lt.scale, ell);
         acc += ell;
     }
 #pragma unroll

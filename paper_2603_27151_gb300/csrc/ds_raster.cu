@@ -45,68 +45,8 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
         }
 
         const uint2 rg = ranges[V.tile_base + wi.ty * V.tiles_x + wi.tx];
-        bool warp_done = !__any_sync(kFullMask, valid);
-        for (uint32_t c0 = rg.x; c0 < rg.y; c0 += (uint32_t)vt.chunk) {
-            const int n = (int)min((uint32_t)vt.chunk, rg.y - c0);
-            __syncthreads();
-            if (tid < n)
-                stage_triangle<TW>(sm, tid, recs, (size_t)wi.v * s.T, keys[c0 + tid], vals[c0 + tid], DB, wi.tx * TW,
-                               wi.ty * TH);
-            __syncthreads();
-            if (!warp_done) {
-                for (int j = 0; j < n; ++j) {
-                    const int4 h2 = sm.h2[j];
-                    if (!((h2.w >> warp) & 1)) continue;   // covers none of this warp's pixels
-                    // early exit: every sample already holds a fragment in
-                    // front of anything the rest of the (depth-sorted) list can give
-                    bool ldone = true;
-                    if (valid) {
-#pragma unroll
-                        for (int q = 0; q < SG; ++q)
-                            if (q < ns) ldone = ldone && bt[q] >= 0 && brho[q] > __int_as_float(h2.z);
-                    }
-                    if (__all_sync(kFullMask, ldone)) {
-                        warp_done = true;
-                        break;
-                    }
-                    if (!valid) continue;
-                    long long E[3];
-                    if (!tile_cover(sm, j, lx, ly, E)) continue;
-                    const int t = h2.y;
-                    const Frag f = make_frag(E[0], E[1], E[2], sm.kk[j][0], sm.kk[j][1], sm.kk[j][2]);
-                    bool need = false;
-#pragma unroll
-                    for (int q = 0; q < SG; ++q)
-                        need = need || (q < ns && (bt[q] < 0 || in_front(f.rho, t, brho[q], bt[q])));
-                    if (!need) continue;
-                    const float r = __frcp_rn(f.rho);
-                    const float b1 = __fmul_rn(f.q1, r), b2 = __fmul_rn(f.q2, r);
-                    const Cell cl = find_cell(s.N, b1, b2);
-                    const float* aa = s.act_a + (size_t)t * s.V;
-                    const float alpha = interp(__ldg(aa + cl.k0), __ldg(aa + cl.k1), __ldg(aa + cl.k2), cl.wa, cl.wb);
-                    float tau[4] = {0.5f, 0.5f, 0.5f, 0.5f};
-                    if (stochastic) {
-                        const uint4 w = philox4x32_10(make_uint4((uint32_t)px, (uint32_t)py, (uint32_t)t, (uint32_t)wi.g),
-                                                      seed.x, seed.y);
-                        tau[0] = word_to_tau(w.x);
-                        tau[1] = word_to_tau(w.y);
-                        tau[2] = word_to_tau(w.z);
-                        tau[3] = word_to_tau(w.w);
-                    }
-#pragma unroll
-                    for (int q = 0; q < SG; ++q) {
-                        if (q < ns && alpha > tau[q] && (bt[q] < 0 || in_front(f.rho, t, brho[q], bt[q]))) {
-                            bt[q] = t;
-                            brho[q] = f.rho;
-                            bb1[q] = b1;
-                            bb2[q] = b2;
-                            bD[q] = r;
-                        }
-                    }
-                }
-            }
-            if (__syncthreads_and(warp_done)) break;
-        }
+        forward_walk<SG, TW>(sm, recs, keys, vals, rg, DB, vt.chunk, (size_t)wi.v * s.T, wi, s, tid, lx, ly, warp, valid,
+                             px, py, ns, seed, stochastic, bt, brho, bb1, bb2, bD);
 
         if (valid) {
             const size_t HW = (size_t)V.H * V.W, pix = (size_t)py * V.W + px;
@@ -255,7 +195,7 @@ cudaError_t launch_raster_count(const ViewTable& vt, const SoupDev& s, const Set
 
 const char* const kStageNames[kNumStages] = {"activate", "setup", "scan", "emit", "sort", "ranges",
                                              "raster_fwd", "count", "geom", "raster_bwd", "edge_bwd",
-                                             "finish"};
+                                             "finish", "train"};
 
 static std::atomic<long long> g_launches{0};
 void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }

@@ -20,6 +20,9 @@ constexpr unsigned kFullMask = 0xffffffffu;
 #ifndef DS_MINB_EDGE
 #define DS_MINB_EDGE 4
 #endif
+#ifndef DS_MINB_TRAIN
+#define DS_MINB_TRAIN 4
+#endif
 
 // Per-tile staged set-up.  h0..h2 hold what the per-pixel coverage test reads
 // for every triangle; eo/kk are read only for covered fragments.
@@ -119,6 +122,84 @@ __device__ __forceinline__ bool tile_cover(const TileStage& sm, int j, int lx, i
     E[1] = sm.eo[j][1] + 256LL * a1;
     E[2] = sm.eo[j][2] + 256LL * a2;
     return true;
+}
+
+// The masked z-test of one work item (Eq. 5): walk the tile's list (staged
+// in shared memory chunk by chunk) and keep, per sample, the foremost
+// covered fragment whose interpolated opacity exceeds its threshold.  Warps
+// stop once every sample holds a fragment in front of the depth bound of the
+// rest of the list.  Returns true when the whole list was staged in one chunk
+// (it is then still in shared memory).
+template <int SG, int TW>
+__device__ __forceinline__ bool forward_walk(TileStage& sm, const SetupRec* __restrict__ recs,
+                                             const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
+                                             uint2 rg, int DB, int chunk, size_t vbase, const WorkItem& wi,
+                                             const SoupDev& s, int tid, int lx, int ly, int warp, bool valid, int px,
+                                             int py, int ns, uint2 seed, bool stochastic, int (&bt)[SG],
+                                             float (&brho)[SG], float (&bb1)[SG], float (&bb2)[SG], float (&bD)[SG]) {
+    constexpr int TH = kTilePix / TW;
+    bool warp_done = !__any_sync(kFullMask, valid);
+    for (uint32_t c0 = rg.x; c0 < rg.y; c0 += (uint32_t)chunk) {
+        const int n = (int)min((uint32_t)chunk, rg.y - c0);
+        __syncthreads();
+        if (tid < n)
+            stage_triangle<TW>(sm, tid, recs, vbase, keys[c0 + tid], vals[c0 + tid], DB, wi.tx * TW, wi.ty * TH);
+        __syncthreads();
+        if (!warp_done) {
+            for (int j = 0; j < n; ++j) {
+                const int4 h2 = sm.h2[j];
+                if (!((h2.w >> warp) & 1)) continue;   // covers none of this warp's pixels
+                // early exit: every sample already holds a fragment in
+                // front of anything the rest of the (depth-sorted) list can give
+                bool ldone = true;
+                if (valid) {
+#pragma unroll
+                    for (int q = 0; q < SG; ++q)
+                        if (q < ns) ldone = ldone && bt[q] >= 0 && brho[q] > __int_as_float(h2.z);
+                }
+                if (__all_sync(kFullMask, ldone)) {
+                    warp_done = true;
+                    break;
+                }
+                if (!valid) continue;
+                long long E[3];
+                if (!tile_cover(sm, j, lx, ly, E)) continue;
+                const int t = h2.y;
+                const Frag f = make_frag(E[0], E[1], E[2], sm.kk[j][0], sm.kk[j][1], sm.kk[j][2]);
+                bool need = false;
+#pragma unroll
+                for (int q = 0; q < SG; ++q)
+                    need = need || (q < ns && (bt[q] < 0 || in_front(f.rho, t, brho[q], bt[q])));
+                if (!need) continue;
+                const float r = __frcp_rn(f.rho);
+                const float b1 = __fmul_rn(f.q1, r), b2 = __fmul_rn(f.q2, r);
+                const Cell cl = find_cell(s.N, b1, b2);
+                const float* aa = s.act_a + (size_t)t * s.V;
+                const float alpha = interp(__ldg(aa + cl.k0), __ldg(aa + cl.k1), __ldg(aa + cl.k2), cl.wa, cl.wb);
+                float tau[4] = {0.5f, 0.5f, 0.5f, 0.5f};
+                if (stochastic) {
+                    const uint4 w = philox4x32_10(make_uint4((uint32_t)px, (uint32_t)py, (uint32_t)t, (uint32_t)wi.g),
+                                                  seed.x, seed.y);
+                    tau[0] = word_to_tau(w.x);
+                    tau[1] = word_to_tau(w.y);
+                    tau[2] = word_to_tau(w.z);
+                    tau[3] = word_to_tau(w.w);
+                }
+#pragma unroll
+                for (int q = 0; q < SG; ++q) {
+                    if (q < ns && alpha > tau[q] && (bt[q] < 0 || in_front(f.rho, t, brho[q], bt[q]))) {
+                        bt[q] = t;
+                        brho[q] = f.rho;
+                        bb1[q] = b1;
+                        bb2[q] = b2;
+                        bD[q] = r;
+                    }
+                }
+            }
+        }
+        if (__syncthreads_and(warp_done)) break;
+    }
+    return rg.y - rg.x <= (uint32_t)chunk;
 }
 
 // Inverse depth of triangle `rec` at pixel (px, py) (the stored winner's

@@ -59,6 +59,10 @@ class ds_request_stats(ctypes.Structure):
                 ("batch", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
+class ds_view_loss(ctypes.Structure):
+    _fields_ = [("target", ctypes.c_void_p), ("grad_color", ctypes.c_void_p), ("score_w", ctypes.c_void_p)]
+
+
 class ds_view_gin(ctypes.Structure):
     _fields_ = [("grad_color", ctypes.c_void_p), ("score_w", ctypes.c_void_p)]
 
@@ -114,6 +118,11 @@ def load():
     L.ds_raster_backward_devcam.restype = i32
     L.ds_reserve.argtypes = [P, ctypes.c_int64]
     L.ds_reserve.restype = i32
+    L.ds_raster_train_l2.argtypes = [P, i32, P, P, i32, i32, u32, P, P, P, ctypes.c_float, P, u32, P, P, P]
+    L.ds_raster_train_l2.restype = i32
+    L.ds_raster_train_l2_devcam.argtypes = [P, i32, P, P, P, i32, i32, u32, P, P, P, ctypes.c_float, P, u32, P, P,
+                                            P]
+    L.ds_raster_train_l2_devcam.restype = i32
     L.ds_set_tuning.argtypes = [P, P]
     L.ds_set_tuning.restype = i32
     L.ds_get_tuning.argtypes = [P, P]
@@ -269,6 +278,43 @@ class Context:
             gin[v].score_w = score_ws[v].data_ptr() if score_ws is not None and score_ws[v] is not None else None
         _check(load().ds_raster_backward_devcam(self.h, soup_id, wha, _ptr(cams_dev), n, S, fwd, gin, flags,
                                                 _ptr(grad_verts), _ptr(grad_tex), _stream(stream)))
+
+    # -------------------------------------------------------------- fused training pass
+    @staticmethod
+    def _outs_losses(gbufs, colors, targets, grad_colors, score_ws):
+        n = len(gbufs)
+        outs = (ds_view_out * n)()
+        lv = (ds_view_loss * n)()
+        for v in range(n):
+            outs[v].gbuf = gbufs[v].data_ptr()
+            outs[v].color = colors[v].data_ptr()
+            outs[v].n_front = None
+            lv[v].target = targets[v].data_ptr()
+            lv[v].grad_color = grad_colors[v].data_ptr()
+            lv[v].score_w = score_ws[v].data_ptr() if score_ws is not None and score_ws[v] is not None else None
+        return outs, lv
+
+    def train_l2(self, soup_id, cams, seeds, S, mode, bg, gbufs, colors, targets, grad_colors, score_ws, scale,
+                 loss, flags, grad_verts=None, grad_tex=None, stream=None):
+        """ds_raster_train_l2: forward + L2 loss + backward in one call."""
+        n = len(cams)
+        ca = cameras(cams)
+        sd = (ctypes.c_uint64 * n)(*[int(x) for x in (seeds if seeds is not None else [0] * n)])
+        bga = np.ascontiguousarray(bg, np.float32)
+        outs, lv = self._outs_losses(gbufs, colors, targets, grad_colors, score_ws)
+        _check(load().ds_raster_train_l2(self.h, soup_id, ca, sd, n, S, mode, bga.ctypes.data_as(ctypes.c_void_p),
+                                         outs, lv, float(scale), _ptr(loss), flags, _ptr(grad_verts), _ptr(grad_tex),
+                                         _stream(stream)))
+
+    def train_l2_devcam(self, soup_id, wh, cams_dev, seeds_dev, S, mode, bg, gbufs, colors, targets, grad_colors,
+                        score_ws, scale, loss, flags, grad_verts=None, grad_tex=None, stream=None):
+        n = len(wh)
+        wha = (ctypes.c_int32 * (2 * n))(*[int(x) for w in wh for x in w])
+        bga = np.ascontiguousarray(bg, np.float32)
+        outs, lv = self._outs_losses(gbufs, colors, targets, grad_colors, score_ws)
+        _check(load().ds_raster_train_l2_devcam(self.h, soup_id, wha, _ptr(cams_dev), _ptr(seeds_dev), n, S, mode,
+                                                bga.ctypes.data_as(ctypes.c_void_p), outs, lv, float(scale),
+                                                _ptr(loss), flags, _ptr(grad_verts), _ptr(grad_tex), _stream(stream)))
 
     # -------------------------------------------------------------- tuning
     def set_tuning(self, tile_w=16, depth_bits=-1, blocks_per_sm=0, chunk=256):

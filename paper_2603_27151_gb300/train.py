@@ -9,8 +9,9 @@ logits (lr 5e-2) with beta = (0.9, 0.999), eps = 1e-8 (supplementary
 "Hyperparameters").
 
 The graph records the library calls with device-resident cameras and seeds
-(ds_raster_*_devcam) and no host synchronisation (DS_NO_SYNC with bin
-capacity reserved beforehand); before each replay the host writes the step's
+(the fused ds_raster_train_l2_devcam, or the separate *_devcam calls) and no
+host synchronisation (DS_NO_SYNC with bin capacity reserved beforehand);
+before each replay the host writes the step's
 view indices and seeds into small device tensors.  ``check()`` reads the
 library's status word: a bin overflow (DS_ERR_CAPACITY) makes the next
 ``step()`` grow the capacity and capture again.
@@ -27,9 +28,10 @@ from . import native as N
 class TrainStep:
     def __init__(self, device: str = "cuda", T: int = 20_000, T_ref: int = 200_000, n_cams: int = 100,
                  width: int = 1024, height: int = 768, per_step: int = 4, S: int = 1,
-                 lr_verts: float = 1e-2, lr_tex: float = 5e-2):
+                 lr_verts: float = 1e-2, lr_tex: float = 5e-2, fused: bool = True):
         sc, ref = I.training_setup(T=T, T_ref=T_ref, n_cams=n_cams, width=width, height=height)
         self.sc, self.S, self.per_step, self.n_cams = sc, S, per_step, n_cams
+        self.fused = fused   # one fused training pass per step instead of forward, loss and backward calls
         self.dev = torch.device(device)
         self.wh = [(width, height)] * per_step
         self.verts = torch.from_numpy(sc.verts).to(self.dev).contiguous()
@@ -80,13 +82,18 @@ class TrainStep:
         mode = N.DS_MODE_STOCHASTIC | (N.DS_NO_SYNC if no_sync else 0)
         torch.index_select(self.cams_all, 0, self.idx, out=self.cams_sel)
         torch.index_select(self.targets_all, 0, self.idx, out=self.targets_sel)
-        self.ctx.raster_forward_devcam(self.sid, self.wh, self.cams_sel, self.seeds, self.S, mode, self.sc.bg,
-                                       self.g, self.col)
         self.loss.zero_()
-        N.loss_l2(self.col, self.targets, self.gcol, self.sw, self.loss, scale=1.0 / self.S)
-        self.ctx.raster_backward_devcam(self.sid, self.wh, self.cams_sel, self.S, self.g, self.col, self.gcol,
-                                        self.sw, N.DS_G_ALL | N.DS_REUSE_FORWARD | N.DS_OVERWRITE,
-                                        self.verts.grad, self.tex.grad)
+        if self.fused:
+            self.ctx.train_l2_devcam(self.sid, self.wh, self.cams_sel, self.seeds, self.S, mode, self.sc.bg, self.g,
+                                     self.col, self.targets, self.gcol, self.sw, 1.0 / self.S, self.loss,
+                                     N.DS_G_ALL | N.DS_OVERWRITE, self.verts.grad, self.tex.grad)
+        else:
+            self.ctx.raster_forward_devcam(self.sid, self.wh, self.cams_sel, self.seeds, self.S, mode, self.sc.bg,
+                                           self.g, self.col)
+            N.loss_l2(self.col, self.targets, self.gcol, self.sw, self.loss, scale=1.0 / self.S)
+            self.ctx.raster_backward_devcam(self.sid, self.wh, self.cams_sel, self.S, self.g, self.col, self.gcol,
+                                            self.sw, N.DS_G_ALL | N.DS_REUSE_FORWARD | N.DS_OVERWRITE,
+                                            self.verts.grad, self.tex.grad)
         self.opt.step()
 
     def _load_views(self, step: int):

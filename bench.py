@@ -150,7 +150,7 @@ def _traffic(kernel: str, pixel_samples: int):
 
 # ---------------------------------------------------------------- the GPU step
 class Workload:
-    def __init__(self, rank: int, device: str, views: int = 0, fused: bool = False):
+    def __init__(self, rank: int, device: str, views: int = 0, fused: bool = True):
         import torch
         from paper_2603_27151_gb300 import native as N
         self.N = N
@@ -189,8 +189,8 @@ class Workload:
 
     def step(self):
         """Forward, L2 loss and backward of the batch: one fused training
-        pass (forward + loss + texture/score/interior terms in one kernel,
-        edge terms in a second), or the three separate calls."""
+        pass (ds_raster_train_l2: at S = 4 the forward with the loss epilogue,
+        then the backward and edge kernels), or the three separate calls."""
         N, sc = self.N, self.sc
         if self.fused:
             self.loss.zero_()
@@ -346,7 +346,7 @@ def _gpu_arm(args):
     torch.cuda.set_device(local)
     dev = "cuda:%d" % local
     from paper_2603_27151_gb300 import native as N
-    wl = Workload(rank, dev, args.views, fused=args.fused)
+    wl = Workload(rank, dev, args.views, fused=not args.unfused)
     tuning = None
     if args.tuning:
         tw, db, bps, ch = (int(x) for x in args.tuning.split(","))
@@ -551,8 +551,8 @@ def main():
                     help="skip the plain-path, training-step and serving legs")
     ap.add_argument("--train-iters", type=int, default=50)
     ap.add_argument("--no-tune", action="store_true", help="default launch parameters instead of the autotuner's")
-    ap.add_argument("--fused", action="store_true",
-                    help="one fused training pass per step instead of separate forward, loss and backward calls")
+    ap.add_argument("--unfused", action="store_true",
+                    help="separate forward, loss and backward calls instead of the fused training pass")
     ap.add_argument("--tuning", default="", help="fixed launch parameters tile_w,depth_bits,blocks_per_sm,chunk")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     args = ap.parse_args()

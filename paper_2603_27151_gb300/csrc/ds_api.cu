@@ -604,6 +604,12 @@ struct FusedL2 {
     ds::Bg bg;
     float scale;
     float* loss;
+    // Schedule.  Full fusion (one kernel for forward, loss and the texture,
+    // score and interior terms) for groups of one sample; for larger sample
+    // groups the forward with the loss epilogue and the backward kernel run
+    // as two launches, because holding a group's forward and backward state
+    // in one kernel spills registers (measured slower on the 1080p batch).
+    bool split;
 };
 
 // Backward after validation; vt is filled and the plan is current.  With
@@ -635,7 +641,25 @@ ds_status backward_impl(ds_ctx* c, Soup& s, uint32_t grad_flags, float* grad_ver
         StageScope p(c, ds::kStGeom, st);
         DS_TRY_CUDA(ds::launch_geom(vt, sd, c->geom.as<ds::GeomRec>(), st));
     }
-    if (fused) {
+    if (fused && fused->split) {
+        // split schedule: forward with the loss epilogue, then the backward
+        {
+            StageScope p(c, ds::kStRasterFwd, st);
+            DS_TRY_CUDA(cudaMemsetAsync(c->d_counter(), 0, 4, st));
+            DS_TRY_CUDA(ds::launch_raster_fwd(vt, sd, c->recs.as<ds::SetupRec>(),
+                                              c->keys[c->plan.res].as<uint32_t>(), c->vals[c->plan.res].as<uint32_t>(),
+                                              c->ranges.as<uint2>(), c->plan.DB, fused->mode & 0xffu, fused->bg,
+                                              c->d_counter(), grid, st, true, fused->scale, fused->loss));
+        }
+        if (want_tex || (want_verts && (gflags & DS_G_INTERIOR))) {
+            StageScope p(c, ds::kStRasterBwd, st);
+            DS_TRY_CUDA(cudaMemsetAsync(c->d_counter() + 2, 0, 4, st));
+            DS_TRY_CUDA(ds::launch_raster_bwd(vt, sd, c->recs.as<ds::SetupRec>(),
+                                              c->keys[c->plan.res].as<uint32_t>(), c->vals[c->plan.res].as<uint32_t>(),
+                                              c->ranges.as<uint2>(), c->plan.DB, gflags, c->geom.as<ds::GeomRec>(),
+                                              acc_tex, acc_verts, c->d_counter() + 2, grid, st));
+        }
+    } else if (fused) {
         StageScope p(c, ds::kStTrain, st);
         DS_TRY_CUDA(cudaMemsetAsync(c->d_counter() + 2, 0, 4, st));
         DS_TRY_CUDA(ds::launch_raster_train(vt, sd, c->recs.as<ds::SetupRec>(), c->keys[c->plan.res].as<uint32_t>(),
@@ -691,6 +715,7 @@ ds_status train_impl(ds_ctx* c, int32_t soup_id, Soup& s, const ds_camera* host_
     for (int i = 0; i < s.C - 1; ++i) f.bg.c[i] = bg[i];
     f.scale = scale;
     f.loss = loss;
+    f.split = c->vt->S > 1;
     return backward_impl(c, s, grad_flags, grad_verts, grad_tex, st, &f);
 }
 

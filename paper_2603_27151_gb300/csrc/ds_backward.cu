@@ -451,51 +451,6 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_BWD)
 }
 
 // ------------------------------------------------------------ fused training pass
-// Colour of the selected fragment (or the background), written to col[c*HW],
-// with the per-pixel L2 loss against tgt[c*HW] and its upstream gradient
-// gc[c*HW] = 2 scale (colour - target); returns l = sum_c (colour - target)^2.
-// Same arithmetic, in the same order, as the forward's decode followed by
-// ds_loss_l2.
-__device__ __forceinline__ float color_loss_out(const SoupDev& s, int t, float b1, float b2, const Bg& bg,
-                                                const float* __restrict__ tgt, float* __restrict__ col,
-                                                float* __restrict__ gc, size_t HW, float two_scale) {
-    const int Co = s.C - 1;
-    float ell = 0.f;
-    auto emit = [&](int c, float v) {
-        col[c * HW] = v;
-        const float d = __fsub_rn(v, __ldg(tgt + c * HW));
-        ell = __fmaf_rn(d, d, ell);
-        gc[c * HW] = __fmul_rn(two_scale, d);
-    };
-    if (t < 0) {
-#pragma unroll
-        for (int c = 0; c < DS_MAX_CHANNELS; ++c)   // constant indices into the parameter struct
-            if (c < Co) emit(c, bg.c[c]);
-        return ell;
-    }
-    const Cell cl = find_cell(s.N, b1, b2);
-    const int C = s.C;
-    const float* base = s.act + (size_t)t * s.V * C;
-    const float* p0 = base + (size_t)cl.k0 * C;
-    const float* p1 = base + (size_t)cl.k1 * C;
-    const float* p2 = base + (size_t)cl.k2 * C;
-    if ((C & 3) == 0) {
-        for (int c4 = 0; c4 < C; c4 += 4) {
-            const float4 a0 = __ldg(reinterpret_cast<const float4*>(p0 + c4));
-            const float4 a1 = __ldg(reinterpret_cast<const float4*>(p1 + c4));
-            const float4 a2 = __ldg(reinterpret_cast<const float4*>(p2 + c4));
-            const float v[4] = {interp(a0.x, a1.x, a2.x, cl.wa, cl.wb), interp(a0.y, a1.y, a2.y, cl.wa, cl.wb),
-                                interp(a0.z, a1.z, a2.z, cl.wa, cl.wb), interp(a0.w, a1.w, a2.w, cl.wa, cl.wb)};
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (c4 + k < Co) emit(c4 + k, v[k]);
-        }
-    } else {
-        for (int c = 0; c < Co; ++c) emit(c, interp(__ldg(p0 + c), __ldg(p1 + c), __ldg(p2 + c), cl.wa, cl.wb));
-    }
-    return ell;
-}
-
 // Forward (Eq. 5), per-pixel L2 loss, and the texture, score and interior
 // gradients (Algorithm A1 step 2 without the edge terms) of one work item in
 // one CTA: the masked z-test walk, then the G-buffer, colours, upstream

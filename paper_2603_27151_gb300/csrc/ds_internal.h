@@ -67,7 +67,8 @@ cudaError_t launch_tile_ranges(const uint32_t* keys, const uint32_t* count, uint
 cudaError_t launch_raster_fwd(const ViewTable& vt, const SoupDev& s, const SetupRec* recs,
                               const uint32_t* keys, const uint32_t* vals, const uint2* ranges,
                               int DB, uint32_t mode, const Bg& bg, int* counter, int grid,
-                              cudaStream_t st);
+                              cudaStream_t st, bool with_loss = false, float scale = 0.f,
+                              float* loss = nullptr);
 // mode 0: n_front into the views' n_front buffers; mode 1: add the number of
 // covered fragments (one sample) to *total.
 cudaError_t launch_raster_count(const ViewTable& vt, const SoupDev& s, const SetupRec* recs,

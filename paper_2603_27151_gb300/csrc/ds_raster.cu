@@ -10,17 +10,22 @@ namespace ds {
 
 // One CTA (256 threads, one pixel each) per work item (view, tile, group of
 // up to four samples), taken from a global counter until none is left.
-template <int SG, int TW>
+// kLoss: the epilogue also evaluates the per-pixel L2 loss against the
+// view's target and writes the upstream gradients and score weights (the
+// first half of the fused training pass; same arithmetic as ds_loss_l2).
+template <int SG, int TW, bool kLoss>
 __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
     k_raster_fwd(const __grid_constant__ ViewTable vt, const SoupDev s, const SetupRec* __restrict__ recs,
                  const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
-                 const uint2* __restrict__ ranges, int DB, uint32_t mode, const Bg bg, int* __restrict__ counter) {
+                 const uint2* __restrict__ ranges, int DB, uint32_t mode, const Bg bg, float scale,
+                 float* __restrict__ loss, int* __restrict__ counter) {
     __shared__ TileStage sm;
     __shared__ int s_item;
     const int tid = threadIdx.x;
     constexpr int TH = kTilePix / TW;
     const int lx = tid & (TW - 1), ly = tid / TW, warp = tid >> 5;
     const bool stochastic = mode == DS_MODE_STOCHASTIC;
+    float lsum = 0.f;
     for (;;) {
         if (tid == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
@@ -58,7 +63,13 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
                 reinterpret_cast<int4*>(V.gbuf)[sg * HW + pix] =
                     make_int4(bt[q], __float_as_int(bb1[q]), __float_as_int(bb2[q]), __float_as_int(bD[q]));
                 float* out = V.color + (size_t)sg * Co * HW + pix;
-                if (bt[q] < 0) {
+                if (kLoss) {
+                    const float ell = color_loss_out(s, bt[q], bb1[q], bb2[q], bg, V.target + pix, out,
+                                                     const_cast<float*>(V.grad_color) + (size_t)sg * Co * HW + pix,
+                                                     HW, 2.0f * scale);
+                    if (V.score_w) const_cast<float*>(V.score_w)[sg * HW + pix] = __fmul_rn(scale, ell);
+                    lsum += ell;
+                } else if (bt[q] < 0) {
 #pragma unroll
                     for (int c = 0; c < DS_MAX_CHANNELS; ++c)
                         if (c < Co) out[c * HW] = bg.c[c];
@@ -68,6 +79,18 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
             }
         }
         __syncthreads();
+    }
+    if (kLoss) {
+        __shared__ float s_loss[kTilePix / 32];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) lsum += __shfl_down_sync(kFullMask, lsum, d);
+        if ((tid & 31) == 0) s_loss[warp] = lsum;
+        __syncthreads();
+        if (tid == 0 && loss) {
+            float t = 0.f;
+            for (int w = 0; w < kTilePix / 32; ++w) t += s_loss[w];
+            atomicAdd(loss, scale * t);
+        }
     }
 }
 
@@ -171,11 +194,15 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
 
 cudaError_t launch_raster_fwd(const ViewTable& vt, const SoupDev& s, const SetupRec* recs, const uint32_t* keys,
                               const uint32_t* vals, const uint2* ranges, int DB, uint32_t mode, const Bg& bg,
-                              int* counter, int grid, cudaStream_t st) {
+                              int* counter, int grid, cudaStream_t st, bool with_loss, float scale, float* loss) {
     dispatch_tile(vt.tile_w, vt.S == 1 ? 1 : (vt.S == 2 ? 2 : 4), [&](auto P) {
         constexpr int SG = decltype(P)::sg, TW = decltype(P)::tw;
-        k_raster_fwd<SG, TW><<<resident_grid(k_raster_fwd<SG, TW>, vt.n_items, grid), kTilePix, 0, st>>>(
-            vt, s, recs, keys, vals, ranges, DB, mode, bg, counter);
+        if (with_loss)
+            k_raster_fwd<SG, TW, true><<<resident_grid(k_raster_fwd<SG, TW, true>, vt.n_items, grid), kTilePix, 0,
+                                         st>>>(vt, s, recs, keys, vals, ranges, DB, mode, bg, scale, loss, counter);
+        else
+            k_raster_fwd<SG, TW, false><<<resident_grid(k_raster_fwd<SG, TW, false>, vt.n_items, grid), kTilePix, 0,
+                                          st>>>(vt, s, recs, keys, vals, ranges, DB, mode, bg, scale, loss, counter);
     });
     note_launches(1);
     return cudaGetLastError();

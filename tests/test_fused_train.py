@@ -66,12 +66,14 @@ def _close(a, b, rtol=1e-6):
     return not (np.abs(a - b) > tol).any()
 
 
-@pytest.mark.parametrize("case", ["batched", "batched_s5", "threshold", "plain_tile32"])
+@pytest.mark.parametrize("case", ["batched", "batched_s1", "batched_s5", "threshold", "plain_tile32"])
 def test_fused_pass_equals_the_separate_calls(lib, case):
+    """S = 1 runs the fully fused kernel, S > 1 the forward-with-loss kernel
+    followed by the backward kernel."""
     import torch
     N = lib
     sc = I.plain_small() if case == "plain_tile32" else I.batched_views()
-    S = 5 if case == "batched_s5" else 2
+    S = {"batched_s5": 5, "batched_s1": 1}.get(case, 2)
     mode = N.DS_MODE_THRESHOLD_HALF if case == "threshold" else N.DS_MODE_STOCHASTIC
     ctx = N.Context(0)
     if case == "plain_tile32":

@@ -215,7 +215,8 @@ class Workload:
         return {
             "activate": T * V * C * 4 * 2 + T * V * 4,
             "setup": nv * T * (36 + 64 + 4 + 16 + 4),
-            "raster_fwd": K * (8 + 64) + T * V * 4 + T * V * C * 4 + P * S * (16 + 4 * Co),
+            "raster_fwd": (K * (8 + 64) + T * V * 4 + T * V * C * 4 + P * S * (16 + 4 * Co)
+                           + ((P * 4 * Co + P * S * (4 * Co + 4)) if self.fused else 0)),   # + loss epilogue
             "train": (K * (8 + 64) + T * V * 4 + T * V * C * 4 * 3 + P * S * (16 + 4 * Co) + P * 4 * Co
                       + P * S * (4 * Co + 4) + 36 * T * 2 + nv * T * 208),
             "raster_bwd": K * (8 + 64) + P * S * (16 + 4 * Co + 4) + T * V * C * 4 * 3 + 36 * T * 2 + nv * T * 208,
@@ -357,7 +358,8 @@ def _gpu_arm(args):
         from paper_2603_27151_gb300 import autotune
         wl.step()
         tuning = autotune.tuned(wl.ctx, wl.sid, wl.sc.T, wl.sc.grid_n, wl.sc.C, wl.sc.cams, wl.sc.seeds, wl.S,
-                                N.DS_MODE_STOCHASTIC, wl.sc.bg, wl.g, wl.col, wl.gcol, wl.sw, wl.gv, wl.gt, reps=2)
+                                N.DS_MODE_STOCHASTIC, wl.sc.bg, wl.g, wl.col, wl.gcol, wl.sw, wl.gv, wl.gt, reps=2,
+                                targets=wl.targets if wl.fused else None, scale=1.0 / wl.S)
     for _ in range(args.warmup):
         wl.step()
     torch.cuda.synchronize()

@@ -330,15 +330,16 @@ DS_API ds_status ds_get_tuning(ds_ctx* ctx, ds_tuning* t);
  * CTAs per SM {occupancy, 2, 3}, each candidate timed (median of `reps` in
  * [1, 100] after one untimed run) with CUDA events on `stream` over
  * ds_raster_forward (mode) and, when gin is non-NULL, ds_raster_backward with
- * DS_G_ALL | DS_OVERWRITE into grad_verts / grad_tex.  Arguments as in those
- * two calls.  Synchronises `stream` after every run.  Sets the fastest tuning
- * on the context and returns it in *best (host) with its time in *best_ms
+ * DS_G_ALL | DS_OVERWRITE into grad_verts / grad_tex; or, when lv is
+ * non-NULL, over ds_raster_train_l2 with those loss views and scale.
+ * Arguments as in those calls.  Synchronises `stream` after every run.
+ * Sets the fastest tuning on the context and returns it in *best (host) with its time in *best_ms
  * (host, may be NULL); the outputs hold the results of a final run with it. */
 DS_API ds_status ds_autotune(ds_ctx* ctx, int32_t soup_id, const ds_camera* cams,
                              const uint64_t* seeds, int32_t n_views, int32_t S, uint32_t mode,
                              const float* bg, const ds_view_out* out, const ds_view_gin* gin,
-                             float* grad_verts, float* grad_tex, int32_t reps, ds_tuning* best,
-                             float* best_ms, void* stream);
+                             const ds_view_loss* lv, float scale, float* grad_verts, float* grad_tex,
+                             int32_t reps, ds_tuning* best, float* best_ms, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Render server: continuous batching of single-view forward requests over

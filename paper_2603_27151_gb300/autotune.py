@@ -45,19 +45,22 @@ def _store(path: str, table: dict):
 
 def tuned(ctx: "N.Context", soup_id: int, T: int, grid_n: int, C: int, cams, seeds, S: int, mode: int, bg,
           gbufs, colors, grad_colors=None, score_ws=None, grad_verts=None, grad_tex=None, reps: int = 3,
-          path: str | None = None, device_name: str | None = None) -> dict:
-    """The cached (or freshly tuned) tuning of this workload, set on ``ctx``."""
+          path: str | None = None, device_name: str | None = None, targets=None, scale: float = 1.0) -> dict:
+    """The cached (or freshly tuned) tuning of this workload, set on ``ctx``.
+    With ``targets`` the fused training pass is what is timed."""
     import torch
     path = path or cache_path()
     name = device_name or torch.cuda.get_device_name(ctx.device)
     key = workload_key(name, T, grid_n, C, S, mode, grad_colors is not None, cams)
+    if targets is not None:
+        key += "|fusedL2
     table = _load(path)
     hit = table.get(key)
     if hit is not None:
         ctx.set_tuning(hit["tile_w"], hit["depth_bits"], hit["blocks_per_sm"], hit["chunk"])
         return dict(hit, cached=True)
     best, ms = ctx.autotune(soup_id, cams, seeds, S, mode, bg, gbufs, colors, grad_colors, score_ws, grad_verts,
-                            grad_tex, reps=reps)
+                            grad_tex, reps=reps, targets=targets, scale=scale)
     table = _load(path)
     table[key] = dict(best, ms=ms)
     _store(path, table)

@@ -6,8 +6,9 @@
 // SM) takes every candidate value with the others fixed; the fastest value
 // is kept before the next knob.  A candidate's time is the median over
 // `reps` timed repetitions (after one untimed run) of the forward pass, plus
-// the backward pass when upstream gradients are given, measured with CUDA
-// events on the caller's stream.  Every candidate computes the same result
+// the backward pass when upstream gradients are given (or of the fused
+// training pass when loss views are given), measured with CUDA events on the
+// caller's stream.  Every candidate computes the same result
 // (the tuning changes only the work decomposition), so the outputs of the
 // last run are valid for the chosen tuning.
 #include <algorithm>
@@ -33,8 +34,8 @@ struct Timer {
 
 extern "C" ds_status ds_autotune(ds_ctx* c, int32_t soup_id, const ds_camera* cams, const uint64_t* seeds,
                                  int32_t n_views, int32_t S, uint32_t mode, const float* bg, const ds_view_out* out,
-                                 const ds_view_gin* gin, float* grad_verts, float* grad_tex, int32_t reps,
-                                 ds_tuning* best, float* best_ms, void* stream) {
+                                 const ds_view_gin* gin, const ds_view_loss* lv, float scale, float* grad_verts,
+                                 float* grad_tex, int32_t reps, ds_tuning* best, float* best_ms, void* stream) {
     if (!c || !best) {
         ds::report_error("NULL argument");
         return DS_ERR_INVALID_ARG;
@@ -60,9 +61,15 @@ extern "C" ds_status ds_autotune(ds_ctx* c, int32_t soup_id, const ds_camera* ca
         std::vector<float> times;
         for (int k = 0; k <= reps; ++k) {
             if (cudaEventRecord(tm.a, st) != cudaSuccess) return DS_ERR_CUDA;
-            r = ds_raster_forward(c, soup_id, cams, seeds, n_views, S, mode & 0xffu, bg, out, stream);
-            if (r != DS_OK) return r;
-            if (gin) {
+            if (lv) {
+                r = ds_raster_train_l2(c, soup_id, cams, seeds, n_views, S, mode & 0xffu, bg, out, lv, scale, nullptr,
+                                       DS_G_ALL | DS_OVERWRITE, grad_verts, grad_tex, stream);
+                if (r != DS_OK) return r;
+            } else {
+                r = ds_raster_forward(c, soup_id, cams, seeds, n_views, S, mode & 0xffu, bg, out, stream);
+                if (r != DS_OK) return r;
+            }
+            if (gin && !lv) {
                 r = ds_raster_backward(c, soup_id, cams, n_views, S, out, gin, gflags, grad_verts, grad_tex, stream);
                 if (r != DS_OK) return r;
             }

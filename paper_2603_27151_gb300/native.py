@@ -127,7 +127,8 @@ def load():
     L.ds_set_tuning.restype = i32
     L.ds_get_tuning.argtypes = [P, P]
     L.ds_get_tuning.restype = i32
-    L.ds_autotune.argtypes = [P, i32, P, P, i32, i32, u32, P, P, P, P, P, i32, P, ctypes.POINTER(ctypes.c_float), P]
+    L.ds_autotune.argtypes = [P, i32, P, P, i32, i32, u32, P, P, P, P, ctypes.c_float, P, P, i32, P,
+                              ctypes.POINTER(ctypes.c_float), P]
     L.ds_autotune.restype = i32
     L.ds_server_create.argtypes = [i32, i32, ctypes.c_size_t, i32, ctypes.c_int64, ctypes.POINTER(P)]
     L.ds_server_create.restype = i32
@@ -327,9 +328,11 @@ class Context:
         return t.as_dict()
 
     def autotune(self, soup_id, cams, seeds, S, mode, bg, gbufs, colors, grad_colors=None, score_ws=None,
-                 grad_verts=None, grad_tex=None, reps: int = 3, stream=None):
+                 grad_verts=None, grad_tex=None, reps: int = 3, stream=None, targets=None, scale=1.0):
         """ds_autotune: returns (tuning dict, best ms); the tuning is set on
-        this context and the outputs hold a run with it."""
+        this context and the outputs hold a run with it.  With `targets` the
+        fused training pass is timed (grad_colors / score_ws are its outputs),
+        else the forward and, with grad_colors, the backward."""
         n = len(cams)
         ca = cameras(cams)
         sd = (ctypes.c_uint64 * n)(*[int(x) for x in (seeds if seeds is not None else [0] * n)])
@@ -340,7 +343,10 @@ class Context:
             outs[v].color = colors[v].data_ptr()
             outs[v].n_front = None
         gins = None
-        if grad_colors is not None:
+        lv = None
+        if targets is not None:
+            _, lv = self._outs_losses(gbufs, colors, targets, grad_colors, score_ws)
+        elif grad_colors is not None:
             gins = (ds_view_gin * n)()
             for v in range(n):
                 gins[v].grad_color = grad_colors[v].data_ptr()
@@ -348,8 +354,8 @@ class Context:
         best = ds_tuning()
         ms = ctypes.c_float(0.0)
         _check(load().ds_autotune(self.h, soup_id, ca, sd, n, S, mode, bga.ctypes.data_as(ctypes.c_void_p), outs,
-                                  gins, _ptr(grad_verts), _ptr(grad_tex), int(reps), ctypes.byref(best),
-                                  ctypes.byref(ms), _stream(stream)))
+                                  gins, lv, float(scale), _ptr(grad_verts), _ptr(grad_tex), int(reps),
+                                  ctypes.byref(best), ctypes.byref(ms), _stream(stream)))
         return best.as_dict(), float(ms.value)
 
     def reserve(self, pairs: int):

@@ -94,3 +94,29 @@ def test_autotune_returns_a_valid_setting_and_correct_outputs(ctx, tmp_path):
         ctx.get_tuning()
     ctx.soup_free(sid)
     ctx.set_tuning()
+
+
+def test_autotune_of_the_fused_training_pass(ctx, tmp_path):
+    """With targets the autotuner times ds_raster_train_l2; the tuning it
+    returns is valid and the outputs of its last run equal the oracle's
+    visibility."""
+    import torch
+    from paper_2603_27151_gb300 import autotune, native as N
+    sc, ref, gc, sw, rt, rv = _reference()
+    verts, tex = torch.from_numpy(sc.verts).cuda(), torch.from_numpy(sc.tex).cuda()
+    sid = ctx.soup_upload(verts, tex, sc.grid_n)
+    g, col, _ = N.alloc_outputs(sc.cams, S, sc.C)
+    tg = [torch.rand((sc.C - 1, c.height, c.width), device="cuda") for c in sc.cams]
+    gcd = [torch.empty_like(c) for c in col]
+    swd = [torch.empty((S, c.height, c.width), device="cuda") for c in sc.cams]
+    gv, gt = torch.zeros_like(verts), torch.zeros_like(tex)
+    t = autotune.tuned(ctx, sid, sc.T, sc.grid_n, sc.C, sc.cams, sc.seeds, S, N.DS_MODE_STOCHASTIC, sc.bg, g, col,
+                       gcd, swd, gv, gt, reps=1, path=str(tmp_path / "tune.json"), targets=tg, scale=1.0 / S)
+    assert not t["cached"] and t["tile_w"] in (8, 16, 32)
+    torch.cuda.synchronize()
+    for v in range(len(sc.cams)):
+        tri, _, depth = N.split_gbuf(g[v])
+        assert np.array_equal(tri.cpu().numpy(), ref[v]["tri_id"])
+        assert np.array_equal(depth.cpu().numpy(), ref[v]["depth"])
+    ctx.soup_free(sid)
+    ctx.set_tuning()

@@ -395,24 +395,54 @@ def _gpu_arm(args):
         t_max = float(t.item())
     barrier()
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers.  Every step
+    # copies its inputs (vertices, texture logits, targets) from pinned host
+    # memory and reads its loss back to the host.  The inputs are double
+    # buffered: step k+1's copies run on a copy stream while step k computes
+    # (two borrowed soups over the two buffers), as a training data loader
+    # would prefetch.
     hv = wl.verts.cpu().pin_memory()
     ht = wl.tex.cpu().pin_memory()
     htg = [x.cpu().pin_memory() for x in wl.targets]
     hl = torch.zeros(1, dtype=torch.float32).pin_memory()
     h2d = hv.numel() * 4 + ht.numel() * 4 + sum(x.numel() * 4 for x in htg)
+    bufs = [(wl.verts, wl.tex, wl.targets, wl.sid)]
+    v2, t2 = torch.empty_like(wl.verts), torch.empty_like(wl.tex)
+    bufs.append((v2, t2, [torch.empty_like(x) for x in wl.targets],
+                 wl.ctx.soup_upload(v2, t2, wl.sc.grid_n, borrow=True)))
+    comp = torch.cuda.current_stream()
+    copy = torch.cuda.Stream()
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    freed = [torch.cuda.Event(), torch.cuda.Event()]
+
+    def load_inputs(b):
+        v, t, tg, _ = bufs[b]
+        with torch.cuda.stream(copy):
+            copy.wait_event(freed[b])   # the step that last read buffer b has finished
+            v.copy_(hv, non_blocking=True)
+            t.copy_(ht, non_blocking=True)
+            for d, h in zip(tg, htg):
+                d.copy_(h, non_blocking=True)
+            copied[b].record(copy)
+
+    for b in range(2):
+        freed[b].record(comp)
     barrier()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        wl.verts.copy_(hv, non_blocking=True)
-        wl.tex.copy_(ht, non_blocking=True)
-        for d, h in zip(wl.targets, htg):
-            d.copy_(h, non_blocking=True)
+    load_inputs(0)
+    for k in range(args.steps):
+        b = k % 2
+        if k + 1 < args.steps:
+            load_inputs(1 - b)
+        comp.wait_event(copied[b])
+        wl.verts, wl.tex, wl.targets, wl.sid = bufs[b]
         wl.step()
+        freed[b].record(comp)
         hl.copy_(wl.loss, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        comp.synchronize()
         _ = float(hl[0])
     e2e_s = time.perf_counter() - t0
+    wl.verts, wl.tex, wl.targets, wl.sid = bufs[0]
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([e2e_s], device=dev)

@@ -53,7 +53,7 @@ def tuned(ctx: "N.Context", soup_id: int, T: int, grid_n: int, C: int, cams, see
     name = device_name or torch.cuda.get_device_name(ctx.device)
     key = workload_key(name, T, grid_n, C, S, mode, grad_colors is not None, cams)
     if targets is not None:
-        key += "|fusedL2
+        key += "|fusedL2"
     table = _load(path)
     hit = table.get(key)
     if hit is not None:

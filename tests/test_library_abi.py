@@ -43,3 +43,17 @@ def test_version_and_error_calls_need_no_device(lib):
 def test_struct_layouts_match_the_header():
     assert ctypes.sizeof(N.ds_camera) == 4 * 2 + 4 * 4 + 36 + 12 + 4
     assert ctypes.sizeof(N.ds_view_out) == 24 and ctypes.sizeof(N.ds_view_gin) == 16
+
+
+def test_every_package_module_imports():
+    """Each Python module of the package (and bench.py) compiles and imports
+    without a GPU; the CUDA library itself is loaded only on first use."""
+    import importlib
+    import pkgutil
+    import py_compile
+    import paper_2603_27151_gb300 as pkg
+    for m in pkgutil.iter_modules(pkg.__path__):
+        importlib.import_module("paper_2603_27151_gb300." + m.name)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for f in ("bench.py", "__graft_entry__.py"):
+        py_compile.compile(os.path.join(root, f), doraise=True)

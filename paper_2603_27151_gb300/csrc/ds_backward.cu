@@ -43,59 +43,101 @@ __device__ __forceinline__ f3 to_world(const DevCam& c, f3 g) {
 __device__ __forceinline__ float2 ld2(const float2* p) { return __ldg(p); }
 __device__ __forceinline__ f3 ld3(const float* p) { return mk3(__ldg(p), __ldg(p + 1), __ldg(p + 2)); }
 
-// ------------------------------------------------------------ FP64 geometry
-__device__ __forceinline__ float2 split2(double x) {
-    const float hi = (float)x;
-    return make_float2(hi, (float)(x - (double)hi));
+// ------------------------------------------------------------ geometry record
+// Double-float arithmetic (an unevaluated sum hi + lo of two floats, about
+// 2^-46 relative): exact products of floats by FMA (Dekker/Kahan TwoProduct),
+// exact sums by TwoSum (Knuth), renormalised after each operation.  This
+// GPU's FP64 rate is a small fraction of its FP32 rate, and the record keeps
+// (hi, lo) float pairs in any case.
+struct df {
+    float hi, lo;
+};
+__device__ __forceinline__ df df_norm(float s, float e) {
+    float e2;
+    const float h = two_sum(s, e, e2);
+    return df{h, e2};
 }
+__device__ __forceinline__ df df_prod(float a, float b) {   // exact a * b
+    const float p = __fmul_rn(a, b);
+    return df{p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+    float e;
+    const float s = two_sum(a.hi, b.hi, e);
+    return df_norm(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df df_mul(df a, df b) {
+    const df p = df_prod(a.hi, b.hi);
+    const float t = __fmaf_rn(a.hi, b.lo, __fmul_rn(a.lo, b.hi));
+    return df_norm(p.hi, __fadd_rn(p.lo, t));
+}
+__device__ __forceinline__ df df_mulf(df a, float b) {
+    const df p = df_prod(a.hi, b);
+    return df_norm(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+// 1 / a: float reciprocal refined by one Newton step in double-float
+// (r + r (1 - a r)), which doubles the number of correct bits.
+__device__ __forceinline__ df df_recip(df a) {
+    const float r = __frcp_rn(a.hi);
+    const df e = df_sub(df{1.0f, 0.0f}, df_mulf(a, r));
+    return df_add(df{r, 0.0f}, df_mulf(e, r));
+}
+__device__ __forceinline__ float df_f(df a) { return __fadd_rn(a.hi, a.lo); }
+__device__ __forceinline__ float2 df_split(df a) { return make_float2(a.hi, a.lo); }
+__device__ __forceinline__ df df_cross(df a1, df a2, df b1, df b2) { return df_sub(df_mul(a1, b2), df_mul(a2, b1)); }
 
-// Camera-space positions and screen projection of every (view, triangle) as
-// the oracle computes them (FP64 from the FP32 inputs), stored for
+// Camera-space positions and screen projection of every (view, triangle)
+// (the oracle computes them in FP64 from the FP32 inputs), stored for
 // compensated FP32 use (see GeomRec).
 __global__ void k_geom(const __grid_constant__ ViewTable vt, const SoupDev s, GeomRec* __restrict__ out) {
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (gid >= (long long)vt.n * s.T) return;
     const int v = (int)(gid / s.T), t = (int)(gid - (long long)v * s.T);
     const DevCam& c = view_cam(vt, v);
-    double V[3][3];
+    df V[3][3];
     const float* p = s.verts + 9LL * t;
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-        const double x = __ldg(p + 3 * m), y = __ldg(p + 3 * m + 1), z = __ldg(p + 3 * m + 2);
+        const float x = __ldg(p + 3 * m), y = __ldg(p + 3 * m + 1), z = __ldg(p + 3 * m + 2);
 #pragma unroll
         for (int r = 0; r < 3; ++r)
-            V[m][r] = (double)c.R[3 * r] * x + (double)c.R[3 * r + 1] * y + (double)c.R[3 * r + 2] * z + (double)c.t[r];
+            V[m][r] = df_add(df_add(df_prod(c.R[3 * r], x), df_prod(c.R[3 * r + 1], y)),
+                             df_add(df_prod(c.R[3 * r + 2], z), df{c.t[r], 0.0f}));
     }
     GeomRec g;
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-        const double iz = 1.0 / V[m][2];
-        g.sx[m] = split2((double)c.fx * (V[m][0] * iz) + (double)c.cx);
-        g.sy[m] = split2((double)c.fy * (V[m][1] * iz) + (double)c.cy);
-        g.jx[m][0] = (float)(c.fx * iz);
-        g.jx[m][1] = (float)(-c.fx * V[m][0] * iz * iz);
-        g.jy[m][0] = (float)(c.fy * iz);
-        g.jy[m][1] = (float)(-c.fy * V[m][1] * iz * iz);
+        const df iz = df_recip(V[m][2]);
+        const df xz = df_mul(V[m][0], iz), yz = df_mul(V[m][1], iz);
+        g.sx[m] = df_split(df_add(df_mulf(xz, c.fx), df{c.cx, 0.0f}));
+        g.sy[m] = df_split(df_add(df_mulf(yz, c.fy), df{c.cy, 0.0f}));
+        const float izf = df_f(iz);
+        g.jx[m][0] = c.fx * izf;
+        g.jx[m][1] = -c.fx * df_f(xz) * izf;
+        g.jy[m][0] = c.fy * izf;
+        g.jy[m][1] = -c.fy * df_f(yz) * izf;
     }
-    double e1[3], e2[3];
+    df e1[3], e2[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        e1[r] = V[1][r] - V[0][r];
-        e2[r] = V[2][r] - V[0][r];
-        g.e1[r] = (float)e1[r];
-        g.e2[r] = (float)e2[r];
-        g.v0[r] = (float)V[0][r];
+        e1[r] = df_sub(V[1][r], V[0][r]);
+        e2[r] = df_sub(V[2][r], V[0][r]);
+        g.e1[r] = df_f(e1[r]);
+        g.e2[r] = df_f(e2[r]);
+        g.v0[r] = df_f(V[0][r]);
     }
-    const double* v0 = V[0];
-    g.n[0] = split2(e1[1] * e2[2] - e1[2] * e2[1]);
-    g.n[1] = split2(e1[2] * e2[0] - e1[0] * e2[2]);
-    g.n[2] = split2(e1[0] * e2[1] - e1[1] * e2[0]);
-    g.m1[0] = split2(e2[1] * v0[2] - e2[2] * v0[1]);
-    g.m1[1] = split2(e2[2] * v0[0] - e2[0] * v0[2]);
-    g.m1[2] = split2(e2[0] * v0[1] - e2[1] * v0[0]);
-    g.m2[0] = split2(v0[1] * e1[2] - v0[2] * e1[1]);
-    g.m2[1] = split2(v0[2] * e1[0] - v0[0] * e1[2]);
-    g.m2[2] = split2(v0[0] * e1[1] - v0[1] * e1[0]);
+    const df* v0 = V[0];
+    g.n[0] = df_split(df_cross(e1[1], e1[2], e2[1], e2[2]));
+    g.n[1] = df_split(df_cross(e1[2], e1[0], e2[2], e2[0]));
+    g.n[2] = df_split(df_cross(e1[0], e1[1], e2[0], e2[1]));
+    g.m1[0] = df_split(df_cross(e2[1], e2[2], v0[1], v0[2]));
+    g.m1[1] = df_split(df_cross(e2[2], e2[0], v0[2], v0[0]));
+    g.m1[2] = df_split(df_cross(e2[0], e2[1], v0[0], v0[1]));
+    g.m2[0] = df_split(df_cross(v0[1], v0[2], e1[1], e1[2]));
+    g.m2[1] = df_split(df_cross(v0[2], v0[0], e1[2], e1[0]));
+    g.m2[2] = df_split(df_cross(v0[0], v0[1], e1[0], e1[1]));
     g.pad = 0.f;
     const int4* src = reinterpret_cast<const int4*>(&g);
     int4* dst = reinterpret_cast<int4*>(out + gid);

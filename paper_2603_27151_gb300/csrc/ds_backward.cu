@@ -1,6 +1,6 @@
 // ds_backward.cu -- gradients of the stochastic rasteriser.
 //
-//  k_geom: per (view, triangle) FP64 geometry for the vertex gradients.
+//  k_geom: per (view, triangle) double-float geometry for the vertex gradients.
 //  k_raster_bwd: Algorithm A1 step 2 by G-buffer recomputation.  Every tile
 //    list is walked again (front to back, stopping early) to find the covered
 //    fragments in front of each stored winner: they get -w/(1-alpha) (Eq. 9);
@@ -147,8 +147,8 @@ __global__ void k_geom(const __grid_constant__ ViewTable vt, const SoupDev s, Ge
 
 // Barycentrics (beta0, beta1, beta2) and 1/S of the hit of the pinned ray
 // through screen point (x, y) with the plane of the triangle (Dot2 on the
-// FP64-derived vectors: grazing triangles make S and the numerators small
-// differences of O(1) terms).
+// vectors of the geometry record: grazing triangles make S and the
+// numerators small differences of O(1) terms).
 __device__ __forceinline__ void ray_bary(const GeomRec* g, const DevCam& cam, float x, float y, float& dx, float& dy,
                                          float b[3], float& inv) {
     pinned_ray(cam, x, y, dx, dy);

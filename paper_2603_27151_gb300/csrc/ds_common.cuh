@@ -90,10 +90,11 @@ struct __align__(16) SetupRec {
 static_assert(sizeof(SetupRec) == 64, "SetupRec must be 64 bytes");
 
 // Continuous (unsnapped) geometry of one (view, triangle) for the vertex
-// gradients.  Computed in FP64 once per backward pass; quantities from which
-// the per-pixel code later takes small differences of large values are kept
-// as (hi, lo) float pairs, so that the per-pixel arithmetic stays FP32 with
-// compensated steps.  208 bytes.
+// gradients.  Computed once per backward pass in double-float arithmetic
+// (about 2^-46 relative); quantities from which the per-pixel code later
+// takes small differences of large values are kept as (hi, lo) float pairs,
+// so that the per-pixel arithmetic stays FP32 with compensated steps.
+// 208 bytes.
 struct __align__(16) GeomRec {
     float2 sx[3], sy[3];   // screen position of each vertex (hi + lo)
     float jx[3][2];        // d sx / d(x_c, z_c): fx / z, -fx x / z^2

@@ -743,18 +743,36 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_EDGE)
             // register arrays at constant indices)
             EdgeJob sl[4];
             bool vl[4] = {false, false, false, false};
+            // winners of the right and lower neighbours, and the pair terms
+            // Phi of both directions in one pass over the channels (the
+            // pixel's own colour and gradient are read once)
+            int tqd[2] = {tp, tp};
+            size_t iqd[2] = {ip, ip};
 #pragma unroll
             for (int dir = 0; dir < 2; ++dir) {
                 const int qx = px + (dir == 0), qy = py + (dir == 1);
                 if (!qv || qx >= V.W || qy >= V.H) continue;
-                const size_t iq = (size_t)qy * V.W + qx;
-                int tq = gbuf[sq * HW + iq].x;
-                if (tq < 0 || tq >= s.T) tq = -1;
+                iqd[dir] = (size_t)qy * V.W + qx;
+                int tq = gbuf[sq * HW + iqd[dir]].x;
+                tqd[dir] = (tq < 0 || tq >= s.T) ? -1 : tq;
+            }
+            const bool d0 = tqd[0] != tp, d1 = tqd[1] != tp;
+            float phid[2] = {0.f, 0.f};
+            if (d0 || d1) {
+                for (int c = 0; c < Co; ++c) {
+                    const float gp = __ldg(gc + c * HW + ip), cp = __ldg(col + c * HW + ip);
+                    if (d0)
+                        phid[0] += 0.5f * (gp + __ldg(gc + c * HW + iqd[0])) * (cp - __ldg(col + c * HW + iqd[0]));
+                    if (d1)
+                        phid[1] += 0.5f * (gp + __ldg(gc + c * HW + iqd[1])) * (cp - __ldg(col + c * HW + iqd[1]));
+                }
+            }
+#pragma unroll
+            for (int dir = 0; dir < 2; ++dir) {
+                const int qx = px + (dir == 0), qy = py + (dir == 1);
+                const int tq = tqd[dir];
                 if (tq == tp) continue;
-                float phi = 0.f;
-                for (int c = 0; c < Co; ++c)
-                    phi += 0.5f * (__ldg(gc + c * HW + ip) + __ldg(gc + c * HW + iq)) *
-                           (__ldg(col + c * HW + ip) - __ldg(col + c * HW + iq));
+                const float phi = phid[dir];
                 if (phi == 0.f) continue;
                 if (tp >= 0) {
                     sl[2 * dir] = EdgeJob{px | (py << 16), tp, tq, phi, dir == 0 ? 0 : 2};

@@ -346,13 +346,15 @@ __device__ __forceinline__ void score_walk(TileStage& sm, const SetupRec* __rest
                 for (int j = 0; j < n; ++j) {
                     const int4 h2 = sm.h2[j];
                     if (!((h2.w >> warp) & 1)) continue;   // covers none of this warp's pixels
-                    bool ldone = true;
+                    if (DB > 0) {   // without depth bits the bound is infinite
+                        bool ldone = true;
 #pragma unroll
-                    for (int q = 0; q < SG; ++q)
-                        if (wsc[q] != 0.f) ldone = ldone && wt[q] >= 0 && wrho[q] > __int_as_float(h2.z);
-                    if (__all_sync(kFullMask, ldone)) {
-                        warp_done = true;
-                        break;
+                        for (int q = 0; q < SG; ++q)
+                            if (wsc[q] != 0.f) ldone = ldone && wt[q] >= 0 && wrho[q] > __int_as_float(h2.z);
+                        if (__all_sync(kFullMask, ldone)) {
+                            warp_done = true;
+                            break;
+                        }
                     }
                     const int t = h2.y;
                     bool act = false;
@@ -478,7 +480,17 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_BWD)
                 const int4 gb = reinterpret_cast<const int4*>(V.gbuf)[(s0 + q) * HW + pix];
                 wt[q] = (gb.x >= 0 && gb.x < s.T) ? gb.x : -1;   // ids outside the soup read as background
                 if (do_score && V.score_w) wsc[q] = V.score_w[(s0 + q) * HW + pix];
-                if (wt[q] >= 0) wrho[q] = winner_rho(vrec + wt[q], px, py);
+                if (wt[q] >= 0) {   // computed once per distinct winner of the pixel
+                    bool seen = false;
+                    float rr = 0.f;
+#pragma unroll
+                    for (int r = 0; r < SG; ++r)
+                        if (r < q && !seen && wt[r] == wt[q]) {
+                            seen = true;
+                            rr = wrho[r];
+                        }
+                    wrho[q] = seen ? rr : winner_rho(vrec + wt[q], px, py);
+                }
                 any_score = any_score || wsc[q] != 0.f;
             }
         }

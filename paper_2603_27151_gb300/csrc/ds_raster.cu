@@ -147,17 +147,19 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
                 for (int j = 0; j < n; ++j) {
                     const int4 h2 = sm.h2[j];
                     if (!((h2.w >> warp) & 1)) continue;   // covers none of this warp's pixels
-                    bool ldone = true;
-                    if (valid && mode == 0) {
+                    if (DB > 0) {   // without depth bits the bound is infinite
+                        bool ldone = true;
+                        if (valid && mode == 0) {
 #pragma unroll
-                        for (int q = 0; q < SG; ++q)
-                            if (q < ns) ldone = ldone && wt[q] >= 0 && wrho[q] > __int_as_float(h2.z);
-                    } else if (valid) {
-                        ldone = false;
-                    }
-                    if (__all_sync(kFullMask, ldone)) {
-                        warp_done = true;
-                        break;
+                            for (int q = 0; q < SG; ++q)
+                                if (q < ns) ldone = ldone && wt[q] >= 0 && wrho[q] > __int_as_float(h2.z);
+                        } else if (valid) {
+                            ldone = false;
+                        }
+                        if (__all_sync(kFullMask, ldone)) {
+                            warp_done = true;
+                            break;
+                        }
                     }
                     if (!valid) continue;
                     long long E[3];

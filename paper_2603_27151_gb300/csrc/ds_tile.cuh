@@ -150,16 +150,19 @@ __device__ __forceinline__ bool forward_walk(TileStage& sm, const SetupRec* __re
                 const int4 h2 = sm.h2[j];
                 if (!((h2.w >> warp) & 1)) continue;   // covers none of this warp's pixels
                 // early exit: every sample already holds a fragment in
-                // front of anything the rest of the (depth-sorted) list can give
-                bool ldone = true;
-                if (valid) {
+                // front of anything the rest of the (depth-sorted) list can
+                // give (without depth bits in the key the bound is infinite)
+                if (DB > 0) {
+                    bool ldone = true;
+                    if (valid) {
 #pragma unroll
-                    for (int q = 0; q < SG; ++q)
-                        if (q < ns) ldone = ldone && bt[q] >= 0 && brho[q] > __int_as_float(h2.z);
-                }
-                if (__all_sync(kFullMask, ldone)) {
-                    warp_done = true;
-                    break;
+                        for (int q = 0; q < SG; ++q)
+                            if (q < ns) ldone = ldone && bt[q] >= 0 && brho[q] > __int_as_float(h2.z);
+                    }
+                    if (__all_sync(kFullMask, ldone)) {
+                        warp_done = true;
+                        break;
+                    }
                 }
                 if (!valid) continue;
                 long long E[3];

@@ -76,7 +76,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.QUERY,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -155,6 +155,7 @@ class Workload:
         from paper_2603_27151_gb300 import native as N
         self.N = N
         self.fused = fused
+        self.no_sync = False   # set once bin capacity is reserved (see reserve_bins)
         sc = I.large_batch()
         if views:
             sc.cams = sc.cams[:views]
@@ -194,7 +195,8 @@ class Workload:
         N, sc = self.N, self.sc
         if self.fused:
             self.loss.zero_()
-            self.ctx.train_l2(self.sid, sc.cams, sc.seeds, self.S, N.DS_MODE_STOCHASTIC, sc.bg, self.g, self.col,
+            mode = N.DS_MODE_STOCHASTIC | (N.DS_NO_SYNC if self.no_sync else 0)
+            self.ctx.train_l2(self.sid, sc.cams, sc.seeds, self.S, mode, sc.bg, self.g, self.col,
                               self.targets, self.gcol, self.sw, 1.0 / self.S, self.loss,
                               N.DS_G_ALL | N.DS_OVERWRITE, self.gv, self.gt)
             return
@@ -203,6 +205,22 @@ class Workload:
         N.loss_l2(self.col, self.targets, self.gcol, self.sw, self.loss, scale=1.0 / self.S)
         self.ctx.raster_backward(self.sid, sc.cams, self.S, self.g, self.col, self.gcol, self.sw,
                                  N.DS_G_ALL | N.DS_REUSE_FORWARD | N.DS_OVERWRITE, self.gv, self.gt)
+
+    def reserve_bins(self, headroom: float = 1.5):
+        """Reserve bin capacity for this workload (the current plan's pair
+        count with headroom) so that fused steps run with DS_NO_SYNC: no host
+        synchronisation inside a step.  An overflow would be reported by
+        check(), never silently."""
+        if not self.fused:
+            return
+        self.ctx.reserve(int(self.pairs * headroom) + 4096)
+        self.no_sync = True
+
+    def check(self):
+        """Synchronise and raise if a no-sync step overflowed its bins."""
+        import torch
+        torch.cuda.synchronize()
+        self.ctx.status()
 
     def algorithmic_bytes(self):
         """Minimum HBM bytes each stage must move per launch."""
@@ -360,9 +378,12 @@ def _gpu_arm(args):
         tuning = autotune.tuned(wl.ctx, wl.sid, wl.sc.T, wl.sc.grid_n, wl.sc.C, wl.sc.cams, wl.sc.seeds, wl.S,
                                 N.DS_MODE_STOCHASTIC, wl.sc.bg, wl.g, wl.col, wl.gcol, wl.sw, wl.gv, wl.gt, reps=2,
                                 targets=wl.targets if wl.fused else None, scale=1.0 / wl.S)
+    wl.step()
+    wl.pairs, wl.tiles = wl.ctx.plan_stats()   # bin pairs with the chosen tiles
+    wl.reserve_bins()
     for _ in range(args.warmup):
         wl.step()
-    torch.cuda.synchronize()
+    wl.check()
 
     def barrier():
         if world > 1:
@@ -384,6 +405,7 @@ def _gpu_arm(args):
         e1.record(stream)
         torch.cuda.synchronize()
     launches = N.kernel_launches() - launches0
+    wl.check()
     wl.ctx.profile(False)
     prof = wl.ctx.profile_read()
     ms = e0.elapsed_time(e1)
@@ -442,6 +464,7 @@ def _gpu_arm(args):
         comp.synchronize()
         _ = float(hl[0])
     e2e_s = time.perf_counter() - t0
+    wl.check()
     wl.verts, wl.tex, wl.targets, wl.sid = bufs[0]
     if world > 1:
         import torch.distributed as dist
@@ -497,13 +520,24 @@ def _gpu_arm(args):
 
 
 # ---------------------------------------------------------------- CPU oracle
+_ORACLE_SCENES = {}
+
+
+def _oracle_init():
+    """Pool initializer: each worker builds the workload and target soups once
+    (not timed)."""
+    import oracle as O
+    O.build()
+    _ORACLE_SCENES["sc"] = I.large_batch()
+    _ORACLE_SCENES["tsc"] = I.large_batch(soup_seed=12)
+
+
 def _oracle_rows(job):
     """One bounded sample: forward + backward of the oracle on a band of rows
-    of view 0 (L2 loss against the target soup's binary-opacity render)."""
+    of one view (L2 loss against the target soup's binary-opacity render)."""
     import oracle as O
     view, r0, r1, seed = job
-    sc = I.large_batch()
-    tsc = I.large_batch(soup_seed=12)
+    sc, tsc = _ORACLE_SCENES["sc"], _ORACLE_SCENES["tsc"]
     cam = sc.cams[view]
     t0 = time.perf_counter()
     f = O.forward(sc.verts, sc.tex, sc.grid_n, [cam], np.array([seed], np.uint64), S=sc.samples, bg=sc.bg,
@@ -527,12 +561,18 @@ def _cores():
     return max(1, min(16, n))
 
 
-def oracle_sample(cores: int, rows_each: int = 1, start_row: int = 400):
-    jobs = [(0, start_row + k * rows_each, start_row + (k + 1) * rows_each, 13) for k in range(cores)]
-    ctx = mp.get_context("spawn")
+def oracle_pool(cores: int):
+    """A spawned pool (never forked after a GPU call) whose workers hold the
+    workload."""
+    return mp.get_context("spawn").Pool(cores, initializer=_oracle_init)
+
+
+def oracle_sample(pool, cores: int, view: int = 0, start_row: int = 400, seed: int = 13):
+    """One row per process of `view`; fragments/s over the wall time of the
+    sample."""
+    jobs = [(view, start_row + k, start_row + k + 1, seed) for k in range(cores)]
     t0 = time.perf_counter()
-    with ctx.Pool(cores) as pool:
-        res = pool.map(_oracle_rows, jobs)
+    res = pool.map(_oracle_rows, jobs)
     wall = time.perf_counter() - t0
     frags = sum(r[0] for r in res)
     return frags / wall, wall, frags
@@ -540,7 +580,8 @@ def oracle_sample(cores: int, rows_each: int = 1, start_row: int = 400):
 
 def cpu_baseline_entry():
     cores = _cores()
-    v, wall, frags = oracle_sample(cores)
+    with oracle_pool(cores) as pool:
+        v, wall, frags = oracle_sample(pool, cores)
     return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d rows of a 1920x1080 view (one row per process, S=4, fwd+bwd incl. the target render), "
                       "%d fragments in %.1f s wall" % (cores, frags, wall)}
@@ -553,27 +594,30 @@ def _reference_arm(args):
     cores = _cores()
     for _ in range(args.warmup):
         pass   # the oracle has no warm-up state; warm-up samples would only repeat the work
+    # each step: one row per process of a 960x540 view of the workload
+    # (view 4), so that --steps K stays within a few minutes
     vals, walls, total = [], [], 0
-    for k in range(args.steps):
-        v, wall, frags = oracle_sample(cores, 1, 300 + 20 * k)
-        vals.append(v)
-        walls.append(wall)
-        total += frags
+    with oracle_pool(cores) as pool:
+        for k in range(args.steps):
+            v, wall, frags = oracle_sample(pool, cores, view=4, start_row=150 + 7 * k)
+            vals.append(v)
+            walls.append(wall)
+            total += frags
     value = total / sum(walls)
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded soups, cameras, targets)",
-            "config": {"workload": WORKLOAD, "sample": "per step %d rows of view 0, one per process" % cores},
+            "config": {"workload": WORKLOAD, "sample": "per step %d rows of view 4 (960x540), one per process" % cores},
             "impl": "reference",
             "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT,
-                             "sample": "per step %d rows of a 1920x1080 view, S=4, fwd+bwd" % cores},
+                             "sample": "per step %d rows of a 960x540 view of the workload, S=4, fwd+bwd" % cores},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")

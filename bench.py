@@ -52,6 +52,24 @@ def _dist():
     return world, rank, local
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest value of x over the ranks of the process group (the
+    slowest rank's time); x itself when there is one rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank: float, steps: int, world: int, t_max_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed divided by the
+    slowest rank's time."""
+    return units_per_rank * steps * world / (t_max_ms / 1e3)
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -409,12 +427,7 @@ def _gpu_arm(args):
     wl.ctx.profile(False)
     prof = wl.ctx.profile_read()
     ms = e0.elapsed_time(e1)
-    t_max = ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(ms, world, dev)
     barrier()
 
     # ---- end to end through the public API with host buffers.  Every step
@@ -466,11 +479,7 @@ def _gpu_arm(args):
     e2e_s = time.perf_counter() - t0
     wl.check()
     wl.verts, wl.tex, wl.targets, wl.sid = bufs[0]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world, dev)
     barrier()
 
     extras = {}
@@ -479,7 +488,7 @@ def _gpu_arm(args):
     if rank != 0:
         return None
     frags_total = wl.fragments * args.steps * world
-    value = frags_total / (t_max / 1e3)
+    value = whole_job_value(wl.fragments, args.steps, world, t_max)
     peak, peak_kind = _peaks()
     algo = wl.algorithmic_bytes()
     stage_ms = {k: v[1] for k, v in prof.items() if v[0] > 0}

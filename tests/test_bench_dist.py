@@ -1,0 +1,53 @@
+"""The bench's multi-rank logic on CPU: two gloo ranks over 127.0.0.1.  Each
+rank reports its own time; every rank must see the slowest one, the
+whole-job value is the units of all ranks over that time, and only rank 0
+runs the reference arm."""
+import multiprocessing as mp
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import argparse
+    import bench
+    w, r, local = bench._dist()
+    t_max = bench.max_over_ranks(10.0 + 5.0 * r, w, "cpu")
+    value = bench.whole_job_value(1000.0, 4, w, t_max)
+    ref = bench._reference_arm(argparse.Namespace(steps=1, warmup=0)) if r != 0 else "skipped"
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((r, w, local, t_max, value, ref))
+
+
+def test_two_gloo_ranks_aggregate_like_the_bench():
+    pytest.importorskip("torch")
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=180) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [o[0] for o in out] == [0, 1] and all(o[1] == 2 and o[2] == o[0] for o in out)
+    assert all(o[3] == 15.0 for o in out)                       # the slowest rank's time on every rank
+    assert all(abs(o[4] - 1000.0 * 4 * 2 / 0.015) < 1e-6 * o[4] for o in out)
+    assert out[1][5] is None                                    # rank 1 runs no reference work

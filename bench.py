@@ -333,7 +333,18 @@ def _train_leg(device: str, iters: int, fused: bool = True):
     torch.cuda.synchronize()
     ms_eager = e0.elapsed_time(e1) / n_eager
     px = ts.per_step * 1024 * 768
+    # algorithmic bytes of one step: the fused pass (forward, loss, texture,
+    # score and interior terms), the edge terms and the optimiser's update
+    T, V, C = ts.tex.shape
+    Co, nv = C - 1, ts.per_step
+    K = ts.ctx.plan_stats()[0]
+    step_bytes = (K * (8 + 64) + T * V * 4 + T * V * C * 4 * 3 + px * (16 + 4 * Co) + px * 4 * Co
+                  + px * (4 * Co + 4) + 36 * T * 2 + nv * T * (36 + 208)
+                  + px * (16 + 8 * Co) + nv * T * (64 + 208)
+                  + (T * V * C + 9 * T) * 4 * 4)   # Adam: parameter, gradient and two moments
+    peak, peak_kind = _peaks()
     return {"iters_per_s": 1e3 / ms, "ms_per_iter": ms, "pixels_per_s": px / (ms / 1e3),
+            "hbm_frac": step_bytes / (ms / 1e3) / 1e9 / peak, "hbm_bytes_per_iter": step_bytes,
             "eager_iters_per_s": 1e3 / ms_eager, "eager_ms_per_iter": ms_eager, "status_ok": ok,
             "loss_before": l0, "loss_after": l1,
             "what": "20,000 triangles (N=8, C=8), 4 of 100 views at 1024x768 per step, S=1, L2 loss, Adam; "
@@ -369,6 +380,7 @@ def _serve_leg(device: str, seconds: float, plain: bool):
             "mean_ms": float(lat.mean()), "frames_per_s": n / r["span_s"],
             "pixels_per_s": float(r["pixels"].sum()) / r["span_s"],
             "output_gbs": float(r["pixels"].sum()) * bytes_per_px / r["span_s"] / 1e9,
+            "hbm_frac": float(r["pixels"].sum()) * bytes_per_px / r["span_s"] / 1e9 / _peaks()[0],
             "mean_batch": float(r["batch"].mean()), "offered_rps": len(reqs) / seconds,
             "what": ("plain: one stream, one request per launch" if plain else
                      "4 worker streams, up to 16 same-soup requests per launch, 8 GiB admission budget")}

@@ -302,6 +302,55 @@ def _plain_leg(wl, steps: int):
                     % (len(sc.cams), "fused training passes" if wl.fused else "calls of forward + loss + backward")}
 
 
+# FP32 CUDA-core peak of a GB300: 152 SMs x 128 FP32 lanes x 2 flops per FMA
+# at the maximum SM clock of 2070 MHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# Algorithmic flops per pixel-sample of the deferred shading MLP
+# (16x16 + 16x16 + 3x16 = 560 multiply-adds): the forward; the backward =
+# forward recomputation + backpropagation through W3, W2 and the feature
+# columns of W1 ((48 + 256 + 112) multiply-adds) + the weight gradients (560).
+SHADE_FWD_FLOPS = 2 * 560
+SHADE_BWD_FLOPS = 2 * 560 + 2 * (48 + 256 + 112) + 2 * 560
+
+
+def _shade_leg(wl, steps: int):
+    """Neural deferred shading of the batch's colour features (S x 7 channels
+    per pixel of the 8 views): forward and backward passes timed with CUDA
+    events, each over ``steps`` launches (features and gradients, about
+    2.5 GB, are larger than L2)."""
+    import torch
+    from paper_2603_27151_gb300.shade import init_params
+    cams, S = wl.sc.cams, wl.S
+    params = init_params(1, wl.verts.device)
+    rgb = [torch.empty((S, 3, c.height, c.width), device=wl.verts.device) for c in cams]
+    grgb = [torch.randn_like(r) for r in rgb]
+    gfeat = [torch.empty_like(c) for c in wl.col]
+    gp = torch.empty_like(params)
+    fwd = lambda: wl.ctx.shade_forward(cams, params, wl.col, rgb)
+    bwd = lambda: wl.ctx.shade_backward(cams, params, wl.col, grgb, gfeat, gp, overwrite=True)
+    out = {}
+    for name, fn, flops in (("forward", fwd, SHADE_FWD_FLOPS), ("backward", bwd, SHADE_BWD_FLOPS)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        tflops = flops * wl.pixel_samples / (ms / 1e3) / 1e12
+        out[name] = {"ms": ms, "pixel_samples_per_s": wl.pixel_samples / (ms / 1e3),
+                     "roofline": {"bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS,
+                                  "unit": "TFLOP/s", "frac": tflops / FP32_PEAK_TFLOPS,
+                                  "peak_kind": "nominal FP32 FMA rate at 2070 MHz",
+                                  "algorithmic_flops_per_pixel_sample": flops}}
+    out["pixel_samples"] = wl.pixel_samples
+    out["what"] = "16-16-16-3 MLP on 7 features + SH2 of the view direction, RGBA blend (FP32)"
+    return out
+
+
 def _train_leg(device: str, iters: int, fused: bool = True):
     """The captured training step (20,000 triangles, 4 views of 1024x768 per
     step drawn from 100 cameras, Adam) against the same step run eagerly."""
@@ -530,6 +579,7 @@ def _gpu_arm(args):
         line["plain_path"] = extras["plain_path"]
         line["plain_path"]["batched_speedup"] = value / world / extras["plain_path"]["value"]
     if not args.views and not args.no_extras and world == 1:
+        line["shade"] = _shade_leg(wl, max(5, args.steps // 4))
         del wl
         torch.cuda.empty_cache()
         line["train"] = _train_leg(dev, args.train_iters)

@@ -263,6 +263,39 @@ DS_API ds_status ds_loss_l2(int32_t n_views, int32_t S, int32_t C, const int32_t
                             float* const* grad_colors, float* const* score_ws, float scale,
                             float* loss, void* stream);
 
+/* Neural deferred shading (Sec. 3.3, "Neural deferred shading"; supplementary
+ * "MLP Architecture"): the per-pixel shading pass that turns the rasterised
+ * colour features (C = 8: 7 features + opacity) into RGB.  For every view v,
+ * mask sample s and pixel p the input is the 7 features f concatenated with
+ * the real SH basis of degree <= 2 of the view direction (9 values: the unit
+ * world-space ray R^T((x+0.5-cx)/fx, (y+0.5-cy)/fy, 1) normalised; the usual
+ * graphics order and signs); a shared MLP 16 -> 16 (ReLU) -> 16 (ReLU) -> 3
+ * (sigmoid) gives o, and the first four features, read as RGBA, are blended
+ * with it:  rgb = A * f[0:3] + (1 - A) * o,  A = f[3].
+ *  params: device [DS_SHADE_N_PARAMS] FP32 = W1 [16][16] (row = output; input
+ *  columns 0..6 features, 7..15 SH), b1 [16], W2 [16][16], b2 [16], W3 [3][16],
+ *  b3 [3].  cams (host [n_views]): only the size, intrinsics and R are read.
+ *  feats, rgbs (host arrays of device pointers): feat [S][7][H][W], rgb
+ *  [S][3][H][W] (written).  n_views = 0 is a no-op.  FP32 arithmetic on the
+ *  CUDA cores.  Allocates nothing. */
+#define DS_SHADE_N_PARAMS 595
+DS_API ds_status ds_shade_forward(ds_ctx* ctx, int32_t n_views, int32_t S, const ds_camera* cams,
+                                  const float* params, const float* const* feats, float* const* rgbs,
+                                  void* stream);
+
+/* Gradients of the deferred shading pass for the upstream gradients grad_rgb
+ * [S][3][H][W] (host array of device pointers): grad_feat [S][7][H][W] (host
+ * array of device pointers, or NULL for none) and grad_params
+ * [DS_SHADE_N_PARAMS] (device, or NULL).  Both are accumulated (+=) unless
+ * flags has DS_OVERWRITE (then written).  The parameter gradient is reduced
+ * in a fixed order (one FP32 partial per CTA, summed in FP64): the result is
+ * bit-reproducible for the same inputs on the same device.  Uses a context
+ * scratch of about 1.5 MiB (grown with cudaMalloc on the first call). */
+DS_API ds_status ds_shade_backward(ds_ctx* ctx, int32_t n_views, int32_t S, const ds_camera* cams,
+                                   const float* params, const float* const* feats,
+                                   const float* const* grad_rgbs, float* const* grad_feats,
+                                   float* grad_params, uint32_t flags, void* stream);
+
 /* Forward pass for callers that cannot allocate device memory: the same
  * computation and outputs as ds_raster_forward (Eq. 5, Algorithm A1 step 1),
  * on a soup passed directly (verts [T][3][3], tex [T][V][C] logits, as in

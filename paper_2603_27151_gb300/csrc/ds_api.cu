@@ -103,6 +103,7 @@ struct ds_ctx {
     std::vector<Soup> soups;
     DevBuf recs, counts, offs, tbox, zkeys, keys[2], vals[2], hist, hist_scan, ranges, scanbuf, misc, geom;
     DevBuf acc_tex, acc_verts;   // FP64 gradient accumulators of the backward
+    DevBuf shade_part;           // per-CTA partials of the shading parameter gradients
     ds::ScanScratch scan;
     int64_t scan_cap = 0;
     uint32_t* h_word = nullptr;   // pinned host words
@@ -444,7 +445,7 @@ void ds_destroy(ds_ctx* c) {
     }
     DevBuf* bufs[] = {&c->recs,  &c->counts,  &c->offs,      &c->tbox,   &c->zkeys,   &c->keys[0], &c->keys[1],
                       &c->vals[0], &c->vals[1], &c->hist, &c->hist_scan, &c->ranges, &c->scanbuf, &c->misc,
-                      &c->geom, &c->acc_tex, &c->acc_verts};
+                      &c->geom, &c->acc_tex, &c->acc_verts, &c->shade_part};
     for (DevBuf* b : bufs) b->release();
     if (c->h_word) cudaFreeHost(c->h_word);
     for (auto& r : c->prof_pending) {
@@ -974,6 +975,81 @@ ds_status ds_raster_train_l2_devcam(ds_ctx* c, int32_t soup_id, const int32_t* w
     DS_TRY(check_outputs(out, n_views));
     DS_TRY(set_loss_views(*c->vt, lv));
     return train_impl(c, soup_id, *s, nullptr, mode, bg, out, scale, loss, grad_flags, grad_verts, grad_tex, st);
+}
+
+}  // extern "C"
+
+// Deferred shading (Sec. 3.3): view table of the shading kernels.
+namespace {
+ds_status shade_views(const ds_camera* cams, int32_t n_views, int32_t S, const float* params,
+                      const float* const* feats, std::vector<ds::ShadeView>& v) {
+    if (n_views == 0 && S >= 1 && S <= DS_MAX_SAMPLES && params) return DS_OK;
+    DS_TRY(check_views(cams, n_views, S));
+    if (!params) return fail(DS_ERR_INVALID_ARG, "params is NULL");
+    if (!feats) return fail(DS_ERR_INVALID_ARG, "feats is NULL");
+    v.resize(n_views);
+    for (int i = 0; i < n_views; ++i) {
+        if (!feats[i]) return fail(DS_ERR_INVALID_ARG, "feats[" + std::to_string(i) + "] is NULL");
+        if (cams[i].fx == 0.f || cams[i].fy == 0.f)
+            return fail(DS_ERR_INVALID_ARG, "camera " + std::to_string(i) + " has a zero focal length");
+        ds::ShadeView& d = v[i];
+        std::memset(&d, 0, sizeof(d));
+        d.feat = feats[i];
+        d.W = cams[i].width;
+        d.H = cams[i].height;
+        d.fx = cams[i].fx;
+        d.fy = cams[i].fy;
+        d.cx = cams[i].cx;
+        d.cy = cams[i].cy;
+        for (int k = 0; k < 9; ++k) d.R[k] = cams[i].R[k];
+    }
+    return DS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+ds_status ds_shade_forward(ds_ctx* c, int32_t n_views, int32_t S, const ds_camera* cams, const float* params,
+                           const float* const* feats, float* const* rgbs, void* stream) {
+    if (!c) return fail(DS_ERR_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    std::vector<ds::ShadeView> v;
+    DS_TRY(shade_views(cams, n_views, S, params, feats, v));
+    if (n_views == 0) return DS_OK;
+    if (!rgbs) return fail(DS_ERR_INVALID_ARG, "rgbs is NULL");
+    for (int i = 0; i < n_views; ++i) {
+        if (!rgbs[i]) return fail(DS_ERR_INVALID_ARG, "rgbs[" + std::to_string(i) + "] is NULL");
+        v[i].rgb = rgbs[i];
+    }
+    DS_TRY_CUDA(ds::launch_shade_fwd(v.data(), n_views, S, params, static_cast<cudaStream_t>(stream)));
+    return DS_OK;
+}
+
+ds_status ds_shade_backward(ds_ctx* c, int32_t n_views, int32_t S, const ds_camera* cams, const float* params,
+                            const float* const* feats, const float* const* grad_rgbs, float* const* grad_feats,
+                            float* grad_params, uint32_t flags, void* stream) {
+    if (!c) return fail(DS_ERR_INVALID_ARG, "NULL context");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    if ((flags & ~DS_OVERWRITE) != 0) return fail(DS_ERR_INVALID_ARG, "unknown flags");
+    std::vector<ds::ShadeView> v;
+    DS_TRY(shade_views(cams, n_views, S, params, feats, v));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool overwrite = (flags & DS_OVERWRITE) != 0;
+    if (n_views > 0) {
+        if (!grad_rgbs) return fail(DS_ERR_INVALID_ARG, "grad_rgbs is NULL");
+        for (int i = 0; i < n_views; ++i) {
+            if (!grad_rgbs[i]) return fail(DS_ERR_INVALID_ARG, "grad_rgbs[" + std::to_string(i) + "] is NULL");
+            v[i].grad_rgb = grad_rgbs[i];
+            v[i].grad_feat = grad_feats ? grad_feats[i] : nullptr;
+        }
+    }
+    const int grid = ds::shade_bwd_grid();
+    DS_TRY(c->shade_part.ensure(sizeof(float) * ds::shade_partial_floats(grid), "shading gradient partials"));
+    DS_TRY_CUDA(ds::launch_shade_bwd(v.data(), n_views, S, params, overwrite, c->shade_part.as<float>(), grid,
+                                     grad_params, st));
+    return DS_OK;
 }
 
 }  // extern "C"

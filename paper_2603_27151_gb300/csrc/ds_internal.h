@@ -94,6 +94,27 @@ cudaError_t launch_edge_bwd(const ViewTable& vt, const SoupDev& s, const SetupRe
 cudaError_t launch_grad_finish(const double* acc, float* out, long long n, bool overwrite,
                                cudaStream_t st);
 
+// One view of the deferred shading pass: feat [S][7][H][W], rgb [S][3][H][W],
+// grad_rgb [S][3][H][W], grad_feat [S][7][H][W] (may be null), the pinhole
+// intrinsics and the world-to-camera rotation (row-major).
+struct ShadeView {
+    const float* feat;
+    float* rgb;
+    const float* grad_rgb;
+    float* grad_feat;
+    int W, H, HW, blk0;
+    float fx, fy, cx, cy;
+    float R[9];
+};
+cudaError_t launch_shade_fwd(const ShadeView* views, int n, int S, const float* params, cudaStream_t st);
+// Backward: writes one partial of the 595 parameter gradients per CTA into
+// `partial` (shade_partial_floats(grid) floats) and, if grad_params is set,
+// reduces them into it.
+cudaError_t launch_shade_bwd(const ShadeView* views, int n, int S, const float* params, bool overwrite,
+                             float* partial, int grid, float* grad_params, cudaStream_t st);
+int shade_bwd_grid();
+size_t shade_partial_floats(int grid);
+
 // Persistent-grid size for the tile kernels on this device.
 int persistent_grid(int n_items, int blocks_per_sm);
 

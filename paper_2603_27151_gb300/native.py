@@ -25,6 +25,7 @@ DS_G_TEX, DS_G_SCORE, DS_G_INTERIOR, DS_G_EDGE = 1, 2, 4, 8
 DS_G_ALL = 15
 DS_REUSE_FORWARD = 0x100
 DS_OVERWRITE = 0x200
+DS_SHADE_N_PARAMS = 595
 DS_COPY, DS_BORROW, DS_STATIC = 0, 1, 2
 ERRORS = {-1: "DS_ERR_INVALID_ARG", -2: "DS_ERR_OOM", -3: "DS_ERR_CUDA", -4: "DS_ERR_CAPACITY",
           -5: "DS_ERR_TIMEOUT", -6: "DS_ERR_NOT_FOUND", -7: "DS_ERR_BUSY"}
@@ -142,6 +143,10 @@ def load():
     L.ds_server_pause.restype = i32
     L.ds_server_destroy.argtypes = [P]
     L.ds_server_destroy.restype = i32
+    L.ds_shade_forward.argtypes = [P, i32, i32, P, P, P, P, P]
+    L.ds_shade_forward.restype = i32
+    L.ds_shade_backward.argtypes = [P, i32, i32, P, P, P, P, P, P, u32, P]
+    L.ds_shade_backward.restype = i32
     _lib = L
     return L
 
@@ -250,6 +255,26 @@ class Context:
             gin[v].score_w = score_ws[v].data_ptr() if score_ws is not None and score_ws[v] is not None else None
         _check(load().ds_raster_backward(self.h, soup_id, ca, n, S, fwd, gin, flags,
                                          _ptr(grad_verts), _ptr(grad_tex), _stream(stream)))
+
+    def shade_forward(self, cams, params, feats, rgbs, stream=None):
+        """Deferred shading (ds_shade_forward): feats[v] float32 [S,7,H,W] ->
+        rgbs[v] float32 [S,3,H,W] (written); params: float32 [595]."""
+        n = len(cams)
+        S = int(feats[0].shape[0]) if n else 1
+        arr = lambda ts: (ctypes.c_void_p * max(n, 1))(*[t.data_ptr() for t in ts])
+        _check(load().ds_shade_forward(self.h, n, S, cameras(cams), _ptr(params), arr(feats), arr(rgbs),
+                                       _stream(stream)))
+
+    def shade_backward(self, cams, params, feats, grad_rgbs, grad_feats=None, grad_params=None,
+                       overwrite: bool = False, stream=None):
+        """Gradients of the deferred shading (ds_shade_backward); grad_feats[v]
+        [S,7,H,W] and grad_params [595] are accumulated unless ``overwrite``."""
+        n = len(cams)
+        S = int(feats[0].shape[0]) if n else 1
+        arr = lambda ts: None if ts is None else (ctypes.c_void_p * max(n, 1))(*[t.data_ptr() for t in ts])
+        _check(load().ds_shade_backward(self.h, n, S, cameras(cams), _ptr(params), arr(feats), arr(grad_rgbs),
+                                        arr(grad_feats), _ptr(grad_params), DS_OVERWRITE if overwrite else 0,
+                                        _stream(stream)))
 
     def raster_forward_devcam(self, soup_id, wh, cams_dev, seeds_dev, S, mode, bg, gbufs, colors, n_fronts=None,
                               stream=None):

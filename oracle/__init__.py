@@ -59,6 +59,9 @@ def lib():
                                  P, P, P, P, P, P]
         L.or_backward.restype = ctypes.c_int
         L.or_backward.argtypes = [P, P, i32, i32, i32, P, P, i32, i32, P, P, P, P, P, u32, i32, i32, P, P]
+        L.or_compose.restype = None; L.or_compose.argtypes = [P, i32, i32, i32, i32, P]
+        L.or_restrict.restype = None; L.or_restrict.argtypes = [P, i32, i32, i32, i32, P]
+        L.or_resample.restype = None; L.or_resample.argtypes = [P, i32, i32, i32, P, i32]
         L.or_expected.restype = ctypes.c_int
         L.or_expected.argtypes = [P, P, i32, i32, i32, P, P, i32, P, P, P, P]
         _lib = L
@@ -121,6 +124,57 @@ def activate(tex: np.ndarray) -> np.ndarray:
     t = _c(tex, np.float32); out = np.empty_like(t)
     lib().or_activate(_p(t), t.size, _p(out))
     return out
+
+
+# ------------------------------------------------------- multi-resolution
+def level_V(R: int) -> int:
+    n = 1 << R
+    return (n + 1) * (n + 2) // 2
+
+
+def compose(levels, r_min: int, r_max: int) -> np.ndarray:
+    """Composed logits [T, V_f, C] of the finest grid from the level grids
+    ``levels[k]`` = level r_min + k, [T, V_R, C] (FP32, see or_compose)."""
+    T, _, C = levels[0].shape
+    flat = np.concatenate([_c(l, np.float32).reshape(-1) for l in levels])
+    out = np.empty((T, level_V(r_max), C), np.float32)
+    lib().or_compose(_p(flat), T, r_min, r_max, C, _p(out))
+    return out
+
+
+def restrict(gfine, r_min: int, r_max: int):
+    """Per-level gradients (FP64) given the gradient of the composed logits."""
+    g = _c(gfine, np.float64)
+    T, _, C = g.shape
+    sizes = [T * level_V(R) * C for R in range(r_min, r_max + 1)]
+    out = np.empty(sum(sizes), np.float64)
+    lib().or_restrict(_p(g), T, r_min, r_max, C, _p(out))
+    parts, o = [], 0
+    for R, n in zip(range(r_min, r_max + 1), sizes):
+        parts.append(out[o:o + n].reshape(T, level_V(R), C))
+        o += n
+    return parts
+
+
+def resample(src, r_src: int, r_dst: int) -> np.ndarray:
+    s = _c(src, np.float32)
+    T, _, C = s.shape
+    out = np.empty((T, level_V(r_dst), C), np.float32)
+    lib().or_resample(_p(s), T, r_src, C, _p(out), r_dst)
+    return out
+
+
+def forward_levels(verts, levels, r_min: int, r_max: int, cams, seeds, S=1, mode=MODE_STOCHASTIC, bg=None):
+    """Forward of a soup whose texture is the composition of level grids."""
+    return forward(verts, compose(levels, r_min, r_max), 1 << r_max, cams, seeds, S=S, mode=mode, bg=bg)
+
+
+def backward_levels(verts, levels, r_min: int, r_max: int, cams, S, fwd, grad_color, score_w, flags=G_ALL):
+    """(per-level texture gradients, vertex gradient) of a level soup: the
+    fine-grid backward followed by the adjoint of the composition."""
+    gt, gv = backward(verts, compose(levels, r_min, r_max), 1 << r_max, cams, S, fwd, grad_color, score_w,
+                      flags=flags)
+    return restrict(gt, r_min, r_max), gv
 
 
 # ---------------------------------------------------------------- full passes

@@ -28,6 +28,10 @@
  *                             finite difference; the absolute weighting is
  *                             "parity unpinned" (the paper prints no formula).
  *   or_expected ............. pinned (finite differences; Monte Carlo of or_forward)
+ *   or_compose .............. pinned (affine reproduction, closed-form hat function,
+ *                             level-0 barycentrics, identity, constants)
+ *   or_restrict ............. pinned (adjoint identity with or_compose, hat mass)
+ *   or_resample ............. pinned (up then down is the identity, affine data)
  */
 #include <math.h>
 #include <stdint.h>
@@ -802,4 +806,117 @@ int or_expected(const float* verts, const double* tex, int32_t T, int32_t N, int
     }
     free(act); free(tri); free(fr); free(col); free(al); free(pf); free(lf);
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Multi-resolution feature grids (Sec. 3.3, multi-resolution mesh colours;  */
+/* supplementary "Coarse-to-Fine Optimization")                              */
+/* ------------------------------------------------------------------------ */
+
+/* Level R carries a mesh-colour grid with N_R = 2^R subdivisions per edge,
+ * (2^(R-1)+1)(2^R+1) = (N_R+1)(N_R+2)/2 feature vertices; level 0 is the
+ * triangle's own three vertices.  Levels r_min..r_max are stored one after
+ * the other, level R as [T][V_R][C]. */
+static size_t o_level_V(int R) { size_t n = (size_t)1 << R; return (n + 1) * (n + 2) / 2; }
+
+/* Value of a level-R grid at vertex (i, j) of a grid with N = 2^k
+ * subdivisions (barycentrics (1-(i+j)/N, i/N, j/N)): a vertex that coincides
+ * with a vertex of the level-R grid takes its value; any other point is
+ * interpolated in the micro-triangle containing it (the decode of Sec. 3.3),
+ * in FP32 in the decode's order. */
+static float o_level_value(const float* g, int R, int C, int c, int i, int j, int N)
+{
+    const int NR = 1 << R;
+    if (N <= NR) return g[(size_t)o_texel(NR, i * (NR / N), j * (NR / N)) * C + c];
+    const int s = N / NR;
+    if (i % s == 0 && j % s == 0) return g[(size_t)o_texel(NR, i / s, j / s) * C + c];
+    int idx[3]; float wa, wb;
+    o_cell(NR, (float)i / (float)N, (float)j / (float)N, idx, &wa, &wb, NULL);
+    return o_interp(g[(size_t)idx[0] * C + c], g[(size_t)idx[1] * C + c], g[(size_t)idx[2] * C + c], wa, wb);
+}
+
+/* Composed logits of the finest grid (Sec. 3.3: every lower-resolution grid
+ * is queried and accumulated on the finest grid before rendering, then the
+ * sigmoid is applied).  fine[t][v][c] = sum over R = r_min..r_max, in that
+ * order, in FP32, of level R at vertex v = (i, j) of the finest grid
+ * (barycentrics (1-(i+j)/N, i/N, j/N), N = 2^r_max), read as in
+ * o_level_value; the finest level adds its own value at v. */
+void or_compose(const float* levels, int32_t T, int32_t r_min, int32_t r_max, int32_t C, float* fine)
+{
+    const int Nf = 1 << r_max;
+    const size_t Vf = o_level_V(r_max);
+    for (int t = 0; t < T; ++t)
+        for (int j = 0; j <= Nf; ++j)
+            for (int i = 0; i + j <= Nf; ++i) {
+                const int v = o_texel(Nf, i, j);
+                for (int c = 0; c < C; ++c) {
+                    float z = 0.0f;
+                    size_t off = 0;
+                    for (int R = r_min; R <= r_max; ++R) {
+                        const float* g = levels + off + (size_t)t * o_level_V(R) * C;
+                        const float val = o_level_value(g, R, C, c, i, j, Nf);
+                        z = R == r_min ? val : z + val;
+                        off += (size_t)T * o_level_V(R) * C;
+                    }
+                    fine[((size_t)t * Vf + v) * C + c] = z;
+                }
+            }
+}
+
+/* Adjoint of or_compose in FP64: the gradient of each level's values given
+ * the gradient of the composed logits gfine [T][V_f][C].  Written as the
+ * transpose of the composition: every finest vertex hands its gradient to the
+ * three corners of its micro-triangle in each level with the interpolation
+ * weights (1 - wa - wb, wa, wb), or to the level vertex it coincides with. */
+void or_restrict(const double* gfine, int32_t T, int32_t r_min, int32_t r_max, int32_t C, double* glevels)
+{
+    const int Nf = 1 << r_max;
+    const size_t Vf = o_level_V(r_max);
+    size_t total = 0;
+    for (int R = r_min; R <= r_max; ++R) total += (size_t)T * o_level_V(R) * C;
+    memset(glevels, 0, sizeof(double) * total);
+    for (int t = 0; t < T; ++t)
+        for (int j = 0; j <= Nf; ++j)
+            for (int i = 0; i + j <= Nf; ++i) {
+                const int v = o_texel(Nf, i, j);
+                const float b1 = (float)i / (float)Nf, b2 = (float)j / (float)Nf;
+                size_t off = 0;
+                for (int R = r_min; R <= r_max; ++R) {
+                    double* g = glevels + off + (size_t)t * o_level_V(R) * C;
+                    const double* gf = gfine + ((size_t)t * Vf + v) * C;
+                    const int s = Nf >> R;
+                    if (i % s == 0 && j % s == 0) {
+                        const int u = o_texel(1 << R, i / s, j / s);
+                        for (int c = 0; c < C; ++c) g[(size_t)u * C + c] += gf[c];
+                    } else {
+                        int idx[3]; float wa, wb;
+                        o_cell(1 << R, b1, b2, idx, &wa, &wb, NULL);
+                        const double w[3] = {1.0 - (double)wa - (double)wb, (double)wa, (double)wb};
+                        for (int k = 0; k < 3; ++k)
+                            for (int c = 0; c < C; ++c) g[(size_t)idx[k] * C + c] += w[k] * gf[c];
+                    }
+                    off += (size_t)T * o_level_V(R) * C;
+                }
+            }
+}
+
+/* Resampling of one level's grid onto another level (supplementary
+ * "Coarse-to-Fine Optimization": the coarse feature is sampled at every grid
+ * coordinate of the new level): dst vertex (i, j) of N_dst = 2^r_dst takes
+ * the src grid's value at barycentrics (i/N_dst, j/N_dst), read as in
+ * o_level_value; the same grid (r_src == r_dst) is copied. */
+void or_resample(const float* src, int32_t T, int32_t r_src, int32_t C, float* dst, int32_t r_dst)
+{
+    const int Nd = 1 << r_dst;
+    const size_t Vs = o_level_V(r_src), Vd = o_level_V(r_dst);
+    for (int t = 0; t < T; ++t)
+        for (int j = 0; j <= Nd; ++j)
+            for (int i = 0; i + j <= Nd; ++i) {
+                const int v = o_texel(Nd, i, j);
+                const float* g = src + (size_t)t * Vs * C;
+                for (int c = 0; c < C; ++c)
+                    dst[((size_t)t * Vd + v) * C + c] =
+                        r_src == r_dst ? g[(size_t)v * C + c]
+                                       : o_level_value(g, r_src, C, c, i, j, Nd);
+            }
 }

@@ -158,6 +158,39 @@ DS_API ds_status ds_soup_upload(ds_ctx* ctx, const float* verts, const float* te
 /* Release a soup (waits for the device, frees an owned copy). */
 DS_API ds_status ds_soup_free(ds_ctx* ctx, int32_t soup_id);
 
+/* Multi-resolution feature grids (Sec. 3.3, multi-resolution mesh colours).
+ * Level R carries a mesh-colour grid with 2^R subdivisions per edge, V_R =
+ * (2^R+1)(2^R+2)/2 feature vertices (level 0: the three triangle vertices).
+ * tex_levels holds levels r_min..r_max one after the other, level R as
+ * [T][V_R][C] logits.  The soup renders the finest grid (grid_n = 2^r_max)
+ * whose logits are the sum over the levels, in ascending order in FP32, of
+ * each level at the finest grid's vertex: the level vertex that coincides
+ * with it, else barycentric interpolation in the level's micro-triangle that
+ * contains it; the sigmoid follows (the composition runs inside the
+ * activation step).  Every other call treats the soup like one registered
+ * with ds_soup_upload(grid_n = 2^r_max), except that grad_tex of the
+ * backward passes has the layout of tex_levels: the gradient of each level
+ * (the adjoint of the composition runs inside the gradient finish step).
+ * 0 <= r_min <= r_max, 2^r_max <= DS_MAX_GRID_N.  Flags as ds_soup_upload. */
+DS_API ds_status ds_soup_upload_levels(ds_ctx* ctx, const float* verts, const float* tex_levels, int32_t T,
+                                       int32_t r_min, int32_t r_max, int32_t C, uint32_t flags, int32_t* soup_id,
+                                       void* stream);
+
+/* The composed finest grid [T][V_{r_max}][C] of tex_levels (as above):
+ * logits, or their sigmoid if activate != 0 (the texture kept after
+ * training, Sec. 3.3).  No context; allocates nothing. */
+DS_API ds_status ds_levels_compose(const float* tex_levels, int32_t T, int32_t r_min, int32_t r_max, int32_t C,
+                                   int32_t activate, float* out, void* stream);
+
+/* One level's grid src [T][V_{r_src}][C] sampled at the vertices of level
+ * r_dst: dst [T][V_{r_dst}][C] (a vertex that coincides with a src vertex
+ * takes its value, else barycentric interpolation in src's micro-triangle).
+ * The coarse-to-fine switch of the supplementary material copies the coarse
+ * stage's features to the new r_min level this way.  No context; allocates
+ * nothing. */
+DS_API ds_status ds_levels_resample(const float* src, int32_t T, int32_t r_src, int32_t C, float* dst,
+                                    int32_t r_dst, void* stream);
+
 /* Forward pass (Eq. 5; Algorithm A1 step 1) for n_views views of one soup:
  * sigmoid activation of the texture (Sec. 3.3), triangle set-up, radix-sorted
  * binning of triangles into 16x16 pixel tiles, then per pixel and sample the

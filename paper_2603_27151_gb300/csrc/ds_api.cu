@@ -69,6 +69,12 @@ struct Soup {
     float* own = nullptr;   // owned copy of verts and tex
     float* act = nullptr;   // [T][V][C] and [T][V] (one allocation)
     int T = 0, N = 0, C = 0, V = 0;
+    // multi-resolution soups: tex holds levels r_min..r_max (N = 2^r_max)
+    int r_min = -1, r_max = -1;
+    bool levels() const { return r_min >= 0 && r_min < r_max; }
+    size_t tex_floats() const {
+        return r_min >= 0 ? ds::level_floats(T, r_min, r_max, C) : (size_t)T * V * C;
+    }
 };
 
 struct Plan {
@@ -320,7 +326,10 @@ ds_status prepare(ds_ctx* c, int32_t soup_id, Soup& s, const ds_camera* cams, co
 
     if (!(s.fixed && s.act_valid)) {
         StageScope p(c, ds::kStActivate, st);
-        DS_TRY_CUDA(ds::launch_activate(sd, st));
+        if (s.levels())
+            DS_TRY_CUDA(ds::launch_compose(s.tex, s.T, s.r_min, s.r_max, s.C, sd.act, true, sd.act_a, st));
+        else
+            DS_TRY_CUDA(ds::launch_activate(sd, st));
         s.act_valid = s.fixed;
     }
     {
@@ -457,11 +466,15 @@ void ds_destroy(ds_ctx* c) {
     delete c;
 }
 
-ds_status ds_soup_upload(ds_ctx* c, const float* verts, const float* tex, int32_t T, int32_t grid_n, int32_t C,
-                         uint32_t flags, int32_t* soup_id, void* stream) {
+}  // extern "C"
+
+namespace {
+// Registration of a soup: plain (r_min = r_max = -1, tex [T][V][C]) or
+// multi-resolution (tex = levels r_min..r_max, grid_n = 2^r_max).
+ds_status upload_impl(ds_ctx* c, const float* verts, const float* tex, int32_t T, int32_t grid_n, int32_t C,
+                      int32_t r_min, int32_t r_max, uint32_t flags, int32_t* soup_id, void* stream) {
     if (!c || !verts || !tex || !soup_id) return fail(DS_ERR_INVALID_ARG, "NULL argument");
     if (T < 1 || T >= DS_MAX_TRIANGLES) return fail(DS_ERR_INVALID_ARG, "T out of range");
-    if (grid_n < 1 || grid_n > DS_MAX_GRID_N) return fail(DS_ERR_INVALID_ARG, "grid_n out of range");
     if (C < 2 || C > DS_MAX_CHANNELS) return fail(DS_ERR_INVALID_ARG, "C out of range");
     if ((flags & ~(DS_BORROW | DS_STATIC)) != 0) return fail(DS_ERR_INVALID_ARG, "bad flags");
     std::lock_guard<std::mutex> lk(c->mu);
@@ -472,8 +485,10 @@ ds_status ds_soup_upload(ds_ctx* c, const float* verts, const float* tex, int32_
     s.N = grid_n;
     s.C = C;
     s.V = (grid_n + 1) * (grid_n + 2) / 2;
-    const size_t nv = 9 * (size_t)T, nt = (size_t)T * s.V * C;
-    if (cudaMalloc(reinterpret_cast<void**>(&s.act), sizeof(float) * (nt + (size_t)T * s.V)) != cudaSuccess) {
+    s.r_min = r_min;
+    s.r_max = r_max;
+    const size_t nv = 9 * (size_t)T, nt = s.tex_floats(), nact = (size_t)T * s.V * C;
+    if (cudaMalloc(reinterpret_cast<void**>(&s.act), sizeof(float) * (nact + (size_t)T * s.V)) != cudaSuccess) {
         cudaGetLastError();
         return fail(DS_ERR_OOM, "cudaMalloc failed for activations");
     }
@@ -509,6 +524,44 @@ ds_status ds_soup_upload(ds_ctx* c, const float* verts, const float* tex, int32_
     }
     if (c->plan.soup == id) c->plan.valid = false;
     *soup_id = id;
+    return DS_OK;
+}
+}  // namespace
+
+extern "C" {
+
+ds_status ds_soup_upload(ds_ctx* c, const float* verts, const float* tex, int32_t T, int32_t grid_n, int32_t C,
+                         uint32_t flags, int32_t* soup_id, void* stream) {
+    if (grid_n < 1 || grid_n > DS_MAX_GRID_N) return fail(DS_ERR_INVALID_ARG, "grid_n out of range");
+    return upload_impl(c, verts, tex, T, grid_n, C, -1, -1, flags, soup_id, stream);
+}
+
+ds_status ds_soup_upload_levels(ds_ctx* c, const float* verts, const float* tex_levels, int32_t T, int32_t r_min,
+                                int32_t r_max, int32_t C, uint32_t flags, int32_t* soup_id, void* stream) {
+    if (r_min < 0 || r_min > r_max || (1 << r_max) > DS_MAX_GRID_N)
+        return fail(DS_ERR_INVALID_ARG, "levels must satisfy 0 <= r_min <= r_max, 2^r_max <= DS_MAX_GRID_N");
+    return upload_impl(c, verts, tex_levels, T, 1 << r_max, C, r_min, r_max, flags, soup_id, stream);
+}
+
+ds_status ds_levels_compose(const float* levels, int32_t T, int32_t r_min, int32_t r_max, int32_t C, int32_t activate,
+                            float* out, void* stream) {
+    if (!levels || !out) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    if (T < 1 || T >= DS_MAX_TRIANGLES) return fail(DS_ERR_INVALID_ARG, "T out of range");
+    if (C < 1 || C > DS_MAX_CHANNELS) return fail(DS_ERR_INVALID_ARG, "C out of range");
+    if (r_min < 0 || r_min > r_max || (1 << r_max) > DS_MAX_GRID_N) return fail(DS_ERR_INVALID_ARG, "bad levels");
+    DS_TRY_CUDA(ds::launch_compose(levels, T, r_min, r_max, C, out, activate != 0, nullptr,
+                                   static_cast<cudaStream_t>(stream)));
+    return DS_OK;
+}
+
+ds_status ds_levels_resample(const float* src, int32_t T, int32_t r_src, int32_t C, float* dst, int32_t r_dst,
+                             void* stream) {
+    if (!src || !dst) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    if (T < 1 || T >= DS_MAX_TRIANGLES) return fail(DS_ERR_INVALID_ARG, "T out of range");
+    if (C < 1 || C > DS_MAX_CHANNELS) return fail(DS_ERR_INVALID_ARG, "C out of range");
+    if (r_src < 0 || r_dst < 0 || (1 << r_src) > DS_MAX_GRID_N || (1 << r_dst) > DS_MAX_GRID_N)
+        return fail(DS_ERR_INVALID_ARG, "bad levels");
+    DS_TRY_CUDA(ds::launch_resample(src, T, r_src, C, dst, r_dst, static_cast<cudaStream_t>(stream)));
     return DS_OK;
 }
 
@@ -684,8 +737,12 @@ ds_status backward_impl(ds_ctx* c, Soup& s, uint32_t grad_flags, float* grad_ver
     }
     {
         StageScope p(c, ds::kStFinish, st);
-        if (want_tex) DS_TRY_CUDA(ds::launch_grad_finish(acc_tex, grad_tex, (long long)n_tex, overwrite, st));
-        else if (grad_tex && overwrite) DS_TRY_CUDA(cudaMemsetAsync(grad_tex, 0, sizeof(float) * n_tex, st));
+        if (want_tex && s.levels())
+            DS_TRY_CUDA(ds::launch_restrict(acc_tex, s.T, s.r_min, s.r_max, s.C, grad_tex, overwrite, st));
+        else if (want_tex)
+            DS_TRY_CUDA(ds::launch_grad_finish(acc_tex, grad_tex, (long long)n_tex, overwrite, st));
+        else if (grad_tex && overwrite)
+            DS_TRY_CUDA(cudaMemsetAsync(grad_tex, 0, sizeof(float) * s.tex_floats(), st));
         if (want_verts) DS_TRY_CUDA(ds::launch_grad_finish(acc_verts, grad_verts, (long long)n_verts, overwrite, st));
         else if (grad_verts && overwrite) DS_TRY_CUDA(cudaMemsetAsync(grad_verts, 0, sizeof(float) * n_verts, st));
     }

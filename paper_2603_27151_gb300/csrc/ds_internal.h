@@ -94,6 +94,17 @@ cudaError_t launch_edge_bwd(const ViewTable& vt, const SoupDev& s, const SetupRe
 cudaError_t launch_grad_finish(const double* acc, float* out, long long n, bool overwrite,
                                cudaStream_t st);
 
+// Multi-resolution grids (levels r_min..r_max, level R = [T][V_R][C], stored
+// one after the other).  Composition of the finest grid's logits (act: the
+// sigmoid activation, with the planar opacity copy if act_a is set), its adjoint
+// from the FP64 gradient of the finest grid, and level resampling.
+size_t level_floats(int T, int r_min, int r_max, int C);
+cudaError_t launch_compose(const float* levels, int T, int r_min, int r_max, int C, float* out, bool act,
+                           float* act_a, cudaStream_t st);
+cudaError_t launch_restrict(const double* fine, int T, int r_min, int r_max, int C, float* out, bool overwrite,
+                            cudaStream_t st);
+cudaError_t launch_resample(const float* src, int T, int r_src, int C, float* dst, int r_dst, cudaStream_t st);
+
 // One view of the deferred shading pass: feat [S][7][H][W], rgb [S][3][H][W],
 // grad_rgb [S][3][H][W], grad_feat [S][7][H][W] (may be null), the pinhole
 // intrinsics and the world-to-camera rotation (row-major).

@@ -189,12 +189,18 @@ __global__ void __launch_bounds__(kThreads) k_shade_fwd(const __grid_constant__ 
 constexpr int kGroups = 7, kBlocks = 36;
 constexpr int kRow = 20;   // 16 values + 4 pad: conflict-free float4 stores of the rows
 
+// A warp of reducers reads one row of D1 and of D2 (and of X and of H1) at
+// once: the 64-byte pads put those arrays on complementary shared-memory banks.
 struct BwdSmem {
     float sp[kParamsPad];
-    float X[kThreads][kRow], H1[kThreads][kRow], H2[kThreads][kRow], D1[kThreads][kRow], D2[kThreads][kRow];
+    float X[kThreads][kRow];
+    float pad0[16];
+    float H1[kThreads][kRow], H2[kThreads][kRow], D1[kThreads][kRow];
+    float pad1[16];
+    float D2[kThreads][kRow];
     float D3[kThreads][4];
 };
-static_assert(sizeof(float) * kGroups * kParams <= sizeof(float) * 5 * kThreads * kRow, "reduction buffer");
+static_assert(sizeof(float) * kGroups * kParams <= sizeof(float) * (2 * kThreads * kRow + 16), "reduction buffer");
 
 __device__ __forceinline__ void store4(float* dst, const float* v) {
     *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
@@ -234,13 +240,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_shade_bwd(const __grid_constant
         const bool valid = p < V.HW;
         float u[kHid];
         {
-            // the SH columns of the input row are the same for every sample
+            // the SH columns 8..15 of the input row are the same for every
+            // sample (column 7, the constant band, is stored with the features)
             float sh[kSH + 3] = {};
             if (valid) {
                 sh_of_pixel(V, p % V.W, p / V.W, sh);
                 first_layer_sh(sp, sh, u);
             }
-            sm.X[tid][7] = sh[0];
 #pragma unroll
             for (int q = 0; q < 2; ++q) store4(&sm.X[tid][8 + 4 * q], sh + 1 + 4 * q);
         }
@@ -252,10 +258,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_shade_bwd(const __grid_constant
                 float f[1][kFeat], h1[1][kHid], h2[1][kHid], o[1][kOut];
 #pragma unroll
                 for (int c = 0; c < kFeat; ++c) f[0][c] = __ldg(V.feat + ((size_t)s * kFeat + c) * V.HW + p);
-                store4(&sm.X[tid][0], f[0]);
-                sm.X[tid][4] = f[0][4];
-                sm.X[tid][5] = f[0][5];
-                sm.X[tid][6] = f[0][6];
+                {
+                    const float x4[4] = {f[0][4], f[0][5], f[0][6], kC0};
+                    store4(&sm.X[tid][0], f[0]);
+                    store4(&sm.X[tid][4], x4);
+                }
                 mlp<1>(sp, u, f, h1, h2, o);
                 unsigned m1 = 0, m2 = 0;
 #pragma unroll
@@ -332,7 +339,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_shade_bwd(const __grid_constant
             } else {
                 const float z4[4] = {0.f, 0.f, 0.f, 0.f};
                 store4(&sm.X[tid][0], z4);
-                sm.X[tid][4] = sm.X[tid][5] = sm.X[tid][6] = 0.f;
+                store4(&sm.X[tid][4], z4);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     store4(&sm.H1[tid][4 * q], z4);

@@ -124,6 +124,27 @@ def logits(T: int, grid_n: int, C: int, rng: np.random.Generator) -> np.ndarray:
     return rng.standard_normal((T, n_texels(grid_n), C)).astype(np.float32)
 
 
+def level_logits(T: int, r_min: int, r_max: int, C: int, rng: np.random.Generator) -> list:
+    """Multi-resolution logits: level R (2^R subdivisions) as [T, V_R, C],
+    normal with standard deviation 1/sqrt(number of levels)."""
+    sd = 1.0 / math.sqrt(r_max - r_min + 1)
+    return [(sd * rng.standard_normal((T, n_texels(1 << R), C))).astype(np.float32) for R in range(r_min, r_max + 1)]
+
+
+def levels_scene(soup_seed: int = 21, cam_seed: int = 22, mask_seed: int = 23, T: int = 2000,
+                 r_min: int = 2, r_max: int = 5, res=((128, 128), (256, 192), (97, 61))):
+    """(Scene with the composed-texture shape, level logits): 2,000 triangles of
+    edge 0.2, 8 channels, levels r_min..r_max, views at mixed resolutions."""
+    rng = np.random.default_rng(soup_seed)
+    verts = box_soup(T, 0.2, rng)
+    lv = level_logits(T, r_min, r_max, 8, rng)
+    eyes = sphere_eyes(len(res), 3.0, np.random.default_rng(cam_seed))
+    cams = [look_at(e, w, h) for e, (w, h) in zip(eyes, res)]
+    sc = Scene(verts, np.zeros((T, n_texels(1 << r_max), 8), np.float32), 1 << r_max, cams,
+               mask_seeds(mask_seed, len(res)), 1, np.zeros(7, np.float32))
+    return sc, lv
+
+
 def mask_seeds(seed: int, n: int) -> np.ndarray:
     return np.random.SeedSequence(seed).generate_state(n, dtype=np.uint64)
 

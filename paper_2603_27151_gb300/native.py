@@ -143,6 +143,12 @@ def load():
     L.ds_server_pause.restype = i32
     L.ds_server_destroy.argtypes = [P]
     L.ds_server_destroy.restype = i32
+    L.ds_soup_upload_levels.argtypes = [P, P, P, i32, i32, i32, i32, u32, ctypes.POINTER(i32), P]
+    L.ds_soup_upload_levels.restype = i32
+    L.ds_levels_compose.argtypes = [P, i32, i32, i32, i32, i32, P, P]
+    L.ds_levels_compose.restype = i32
+    L.ds_levels_resample.argtypes = [P, i32, i32, i32, P, i32, P]
+    L.ds_levels_resample.restype = i32
     L.ds_shade_forward.argtypes = [P, i32, i32, P, P, P, P, P]
     L.ds_shade_forward.restype = i32
     L.ds_shade_backward.argtypes = [P, i32, i32, P, P, P, P, P, P, u32, P]
@@ -221,6 +227,19 @@ class Context:
         flags = (DS_BORROW if borrow else DS_COPY) | (DS_STATIC if static else 0)
         _check(load().ds_soup_upload(self.h, _ptr(verts), _ptr(tex), T, grid_n, C, flags, ctypes.byref(sid),
                                      _stream(stream)))
+        return sid.value
+
+    def soup_upload_levels(self, verts, tex_levels, T: int, r_min: int, r_max: int, C: int, borrow: bool = False,
+                           static: bool = False, stream=None) -> int:
+        """Multi-resolution soup (ds_soup_upload_levels): tex_levels is one
+        float32 CUDA tensor holding levels r_min..r_max back to back, level R
+        as [T, V_R, C] (see ``level_sizes``)."""
+        assert verts.is_cuda and tex_levels.is_cuda and verts.is_contiguous() and tex_levels.is_contiguous()
+        assert tex_levels.numel() == sum(level_sizes(T, r_min, r_max, C))
+        sid = ctypes.c_int32(-1)
+        flags = (DS_BORROW if borrow else DS_COPY) | (DS_STATIC if static else 0)
+        _check(load().ds_soup_upload_levels(self.h, _ptr(verts), _ptr(tex_levels), T, r_min, r_max, C, flags,
+                                            ctypes.byref(sid), _stream(stream)))
         return sid.value
 
     def soup_free(self, soup_id: int):
@@ -436,6 +455,37 @@ def raster_forward_noalloc(verts, tex, grid_n, cams, seeds, S, mode, bg, gbufs, 
         outs[v].n_front = n_fronts[v].data_ptr() if n_fronts is not None and n_fronts[v] is not None else None
     _check(load().ds_raster_forward_noalloc(_ptr(verts), _ptr(tex), T, grid_n, C, cameras(cams), sd, n, S, mode,
                                             bga.ctypes.data_as(ctypes.c_void_p), outs, _stream(stream)))
+
+
+def level_V(R: int) -> int:
+    """Feature vertices of the level-R grid (2^R subdivisions per edge)."""
+    n = 1 << R
+    return (n + 1) * (n + 2) // 2
+
+
+def level_sizes(T: int, r_min: int, r_max: int, C: int):
+    """Float counts of levels r_min..r_max in a multi-resolution texture."""
+    return [T * level_V(R) * C for R in range(r_min, r_max + 1)]
+
+
+def split_levels(tex_levels, T: int, r_min: int, r_max: int, C: int):
+    """Views [T, V_R, C] of the levels of a flat multi-resolution tensor."""
+    out, o = [], 0
+    for R, n in zip(range(r_min, r_max + 1), level_sizes(T, r_min, r_max, C)):
+        out.append(tex_levels[o:o + n].view(T, level_V(R), C))
+        o += n
+    return out
+
+
+def levels_compose(tex_levels, T: int, r_min: int, r_max: int, C: int, out, activate: bool = False, stream=None):
+    """The composed finest grid [T, V_{r_max}, C] (ds_levels_compose)."""
+    _check(load().ds_levels_compose(_ptr(tex_levels), T, r_min, r_max, C, int(bool(activate)), _ptr(out),
+                                    _stream(stream)))
+
+
+def levels_resample(src, T: int, r_src: int, C: int, dst, r_dst: int, stream=None):
+    """src [T, V_{r_src}, C] sampled at the vertices of level r_dst (ds_levels_resample)."""
+    _check(load().ds_levels_resample(_ptr(src), T, r_src, C, _ptr(dst), r_dst, _stream(stream)))
 
 
 def loss_l2(colors, targets, grad_colors=None, score_ws=None, loss=None, scale=1.0, stream=None):

@@ -351,6 +351,70 @@ def _shade_leg(wl, steps: int):
     return out
 
 
+def _levels_leg(device: str, steps: int):
+    """The 1080p batch with a multi-resolution texture: levels 2..5 (the last
+    stage of the coarse-to-fine schedule; finest grid 32 subdivisions, 561
+    feature vertices per triangle), fused training steps.  The composition
+    (activation stage) and its adjoint (finish stage) are timed by the
+    library's stage profiler (CUDA events around each stage)."""
+    import numpy as np
+    import torch
+    from paper_2603_27151_gb300 import inputs as I
+    from paper_2603_27151_gb300 import native as N
+    sc = I.large_batch()
+    T, C, S, r_min, r_max = sc.T, 8, sc.samples, 2, 5
+    lv = I.level_logits(T, r_min, r_max, C, np.random.default_rng(14))
+    ctx = N.Context(torch.cuda.current_device())
+    verts = torch.from_numpy(sc.verts).to(device)
+    tex = torch.from_numpy(np.concatenate([l.reshape(-1) for l in lv])).to(device)
+    del lv
+    sid = ctx.soup_upload_levels(verts, tex, T, r_min, r_max, C, borrow=True)
+    gen = torch.Generator(device=device).manual_seed(15)
+    targets = [torch.rand((C - 1, c.height, c.width), generator=gen, device=device) for c in sc.cams]
+    g, col, _ = N.alloc_outputs(sc.cams, S, C, device)
+    gcol = [torch.empty_like(c) for c in col]
+    sw = [torch.empty((S, c.height, c.width), device=device) for c in sc.cams]
+    loss = torch.zeros(1, device=device)
+    gt, gv = torch.empty_like(tex), torch.empty_like(verts)
+
+    def step():
+        loss.zero_()
+        ctx.train_l2(sid, sc.cams, sc.seeds, S, N.DS_MODE_STOCHASTIC, sc.bg, g, col, targets, gcol, sw, 1.0 / S,
+                     loss, N.DS_G_ALL | N.DS_OVERWRITE, gv, gt)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    ctx.profile_reset()
+    ctx.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ctx.profile(False)
+    prof = ctx.profile_read()
+    ms = e0.elapsed_time(e1) / steps
+    sum_v = sum(N.level_V(R) for R in range(r_min, r_max + 1))
+    vf = N.level_V(r_max)
+    peak, peak_kind = _peaks()
+    algo = {"activate": 4 * C * T * sum_v + T * vf * (4 * C + 4),          # levels in, act + opacity plane out
+            "finish": 8 * C * T * vf + 4 * C * T * sum_v + 12 * 9 * T}      # FP64 fine gradient in, levels out
+    out = {"ms_per_step": ms, "levels": [r_min, r_max], "feature_vertices": vf, "triangles": T,
+           "what": "fused training steps of the 1080p batch on a level soup (compose in the activation, "
+                   "adjoint in the gradient finish)"}
+    for stage, b in algo.items():
+        runs, tot = prof.get(stage, (0, 0.0))
+        if runs:
+            lms = tot / runs
+            out[stage] = {"ms": lms, "algorithmic_bytes": b,
+                          "roofline": {"bound": "hbm", "achieved": b / (lms / 1e3) / 1e9, "peak": peak,
+                                       "unit": "GB/s", "frac": b / (lms / 1e3) / 1e9 / peak, "peak_kind": peak_kind}}
+    ctx.close()
+    return out
+
+
 def _train_leg(device: str, iters: int, fused: bool = True):
     """The captured training step (20,000 triangles, 4 views of 1024x768 per
     step drawn from 100 cameras, Adam) against the same step run eagerly."""
@@ -581,6 +645,8 @@ def _gpu_arm(args):
     if not args.views and not args.no_extras and world == 1:
         line["shade"] = _shade_leg(wl, max(5, args.steps // 4))
         del wl
+        torch.cuda.empty_cache()
+        line["levels"] = _levels_leg(dev, max(5, args.steps // 4))
         torch.cuda.empty_cache()
         line["train"] = _train_leg(dev, args.train_iters)
         torch.cuda.empty_cache()

@@ -25,7 +25,7 @@ namespace ds {
 
 namespace {
 
-__host__ __device__ __forceinline__ int level_V(int R) { return ((1 << R) + 1) * ((1 << R) + 2) / 2; }
+__host__ __device__ constexpr int level_V(int R) { return ((1 << R) + 1) * ((1 << R) + 2) / 2; }
 
 // (i, j) of vertex v of the N-subdivided grid (rows of constant j).
 __device__ __forceinline__ void texel_ij(int N, int v, int& i, int& j) {
@@ -66,7 +66,9 @@ __device__ __forceinline__ LevelTap level_tap(int R, int i, int j, int N) {
         tp.cl.wa = tp.cl.wb = 0.f;
         tp.cl.lower = true;
     } else {
-        tp.cl = find_cell(NR, __fdiv_rn((float)i, (float)N), __fdiv_rn((float)j, (float)N));
+        // i / N by the exact power-of-two reciprocal: the same value as the division
+        const float inv = __int_as_float((127 - __ffs(N) + 1) << 23);
+        tp.cl = find_cell(NR, __fmul_rn((float)i, inv), __fmul_rn((float)j, inv));
     }
     return tp;
 }
@@ -77,20 +79,45 @@ __device__ __forceinline__ float tap_value(const float* __restrict__ g, const Le
     return interp(a0, __ldg(g + (size_t)tp.cl.k1 * C + c), __ldg(g + (size_t)tp.cl.k2 * C + c), tp.cl.wa, tp.cl.wb);
 }
 
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+
+__device__ __forceinline__ float4 add4(float4 a, float4 b) {
+    return make_float4(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y), __fadd_rn(a.z, b.z), __fadd_rn(a.w, b.w));
+}
+
+// Four consecutive channels c..c+3 of a level at a tap (same arithmetic as
+// tap_value, channel by channel).
+__device__ __forceinline__ float4 tap_value4(const float* __restrict__ g, const LevelTap& tp, int C, int c) {
+    const float4 a0 = ld4(g + (size_t)tp.cl.k0 * C + c);
+    if (tp.direct) return a0;
+    const float4 a1 = ld4(g + (size_t)tp.cl.k1 * C + c), a2 = ld4(g + (size_t)tp.cl.k2 * C + c);
+    const float wa = tp.cl.wa, wb = tp.cl.wb;
+    return make_float4(interp(a0.x, a1.x, a2.x, wa, wb), interp(a0.y, a1.y, a2.y, wa, wb),
+                       interp(a0.z, a1.z, a2.z, wa, wb), interp(a0.w, a1.w, a2.w, wa, wb));
+}
+
 // NL = r_max - r_min coarser levels below the finest.  kAct: act =
 // sigmoid(composed logits) (+ the planar opacity copy); else the composed
-// logits themselves.
-template <int NL, bool kAct>
+// logits themselves.  kVec: C % 4 == 0 and 16-byte aligned levels and output:
+// channels move as float4.
+template <int NL, bool kAct, bool kVec>
 __global__ void __launch_bounds__(256) k_compose(const float* __restrict__ levels, int T, int r_max, int C,
                                                  float* __restrict__ out, float* __restrict__ act_a) {
     const int r_min = r_max - NL;
     const int Nf = 1 << r_max, Vf = level_V(r_max);
+    // (i, j) of every finest vertex, packed i | j << 8
+    __shared__ unsigned short ij_of[level_V(5)];
+    for (int v = threadIdx.x; v < Vf; v += blockDim.x) {
+        int i, j;
+        texel_ij(Nf, v, i, j);
+        ij_of[v] = (unsigned short)(i | (j << 8));
+    }
+    __syncthreads();
     const long long n = (long long)T * Vf;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += stride) {
         const int t = (int)(q / Vf), v = (int)(q - (long long)t * Vf);
-        int i, j;
-        texel_ij(Nf, v, i, j);
+        const int i = ij_of[v] & 0xff, j = ij_of[v] >> 8;
         LevelTap tp[NL > 0 ? NL : 1];
         const float* g[NL + 1];
         size_t off = 0;
@@ -102,17 +129,31 @@ __global__ void __launch_bounds__(256) k_compose(const float* __restrict__ level
             off += (size_t)T * level_V(R) * C;
         }
         float* o = out + (size_t)q * C;
-        for (int c = 0; c < C; ++c) {
-            float z = NL > 0 ? tap_value(g[0], tp[0], C, c) : __ldg(g[0] + (size_t)v * C + c);
+        if (kVec) {
+            for (int c = 0; c < C; c += 4) {
+                float4 z = NL > 0 ? tap_value4(g[0], tp[0], C, c) : ld4(g[0] + (size_t)v * C + c);
 #pragma unroll
-            for (int k = 1; k < NL; ++k) z = __fadd_rn(z, tap_value(g[k], tp[k], C, c));
-            if (NL > 0) z = __fadd_rn(z, __ldg(g[NL] + (size_t)v * C + c));
-            if (kAct) {
-                const float a = pinned_sigmoid(z);
-                o[c] = a;
-                if (c == C - 1 && act_a) act_a[q] = a;
-            } else {
-                o[c] = z;
+                for (int k = 1; k < NL; ++k) z = add4(z, tap_value4(g[k], tp[k], C, c));
+                if (NL > 0) z = add4(z, ld4(g[NL] + (size_t)v * C + c));
+                if (kAct) {
+                    z = make_float4(pinned_sigmoid(z.x), pinned_sigmoid(z.y), pinned_sigmoid(z.z), pinned_sigmoid(z.w));
+                    if (c + 4 == C && act_a) act_a[q] = z.w;
+                }
+                *reinterpret_cast<float4*>(o + c) = z;
+            }
+        } else {
+            for (int c = 0; c < C; ++c) {
+                float z = NL > 0 ? tap_value(g[0], tp[0], C, c) : __ldg(g[0] + (size_t)v * C + c);
+#pragma unroll
+                for (int k = 1; k < NL; ++k) z = __fadd_rn(z, tap_value(g[k], tp[k], C, c));
+                if (NL > 0) z = __fadd_rn(z, __ldg(g[NL] + (size_t)v * C + c));
+                if (kAct) {
+                    const float a = pinned_sigmoid(z);
+                    o[c] = a;
+                    if (c == C - 1 && act_a) act_a[q] = a;
+                } else {
+                    o[c] = z;
+                }
             }
         }
     }
@@ -206,10 +247,15 @@ size_t level_floats(int T, int r_min, int r_max, int C) {
 template <int NL>
 void compose_nl(const float* levels, int T, int r_max, int C, float* out, bool act, float* act_a, int g,
                 cudaStream_t st) {
-    if (act)
-        k_compose<NL, true><<<g, 256, 0, st>>>(levels, T, r_max, C, out, act_a);
+    const bool vec = C % 4 == 0 && (uintptr_t)levels % 16 == 0 && (uintptr_t)out % 16 == 0;
+    if (act && vec)
+        k_compose<NL, true, true><<<g, 256, 0, st>>>(levels, T, r_max, C, out, act_a);
+    else if (act)
+        k_compose<NL, true, false><<<g, 256, 0, st>>>(levels, T, r_max, C, out, act_a);
+    else if (vec)
+        k_compose<NL, false, true><<<g, 256, 0, st>>>(levels, T, r_max, C, out, nullptr);
     else
-        k_compose<NL, false><<<g, 256, 0, st>>>(levels, T, r_max, C, out, nullptr);
+        k_compose<NL, false, false><<<g, 256, 0, st>>>(levels, T, r_max, C, out, nullptr);
 }
 
 cudaError_t launch_compose(const float* levels, int T, int r_min, int r_max, int C, float* out, bool act,

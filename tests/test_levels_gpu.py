@@ -149,3 +149,22 @@ def test_fused_training_pass_on_a_level_soup(ctx):
     a, b = gt_a.cpu().numpy(), gt_b.cpu().numpy()
     assert not grad_mismatch(b, a, rtol=1e-4).any()
     ctx.soup_free(sid)
+
+
+def test_coarse_to_fine_switch(ctx):
+    """The coarse grid's colour features land on the new r_min level (sampled
+    at its vertices), the other levels are zero, opacity logits are reset."""
+    import torch
+    from paper_2603_27151_gb300 import levels as L
+    from paper_2603_27151_gb300 import native as N
+    T, C = 19, 8
+    coarse = np.random.default_rng(2).standard_normal((T, N.level_V(3), C)).astype(np.float32)
+    out = L.coarse_to_fine(torch.from_numpy(coarse).cuda(), 3, 2, 5)
+    torch.cuda.synchronize()
+    parts = [p.cpu().numpy() for p in N.split_levels(out, T, 2, 5, C)]
+    ref = O.resample(coarse, 3, 2)
+    ref[:, :, C - 1] = 0.0
+    assert np.array_equal(parts[0], ref)
+    assert all(not p.any() for p in parts[1:])
+    fine = L.compose(out, T, 2, 5, C, activate=False)
+    assert np.array_equal(fine.cpu().numpy(), O.compose([ref] + [np.zeros_like(p) for p in parts[1:]], 2, 5))

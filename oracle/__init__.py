@@ -60,6 +60,10 @@ def lib():
         L.or_backward.restype = ctypes.c_int
         L.or_backward.argtypes = [P, P, i32, i32, i32, P, P, i32, i32, P, P, P, P, P, u32, i32, i32, P, P]
         L.or_compose.restype = None; L.or_compose.argtypes = [P, i32, i32, i32, i32, P]
+        L.or_coverage.restype = None; L.or_coverage.argtypes = [P, i64, i32, P]
+        L.or_edge_ratios.restype = None; L.or_edge_ratios.argtypes = [P, i32, P, P, i32, P]
+        L.or_soup_rebuild.restype = None
+        L.or_soup_rebuild.argtypes = [P, P, i32, i32, i32, i32, P, i32, P, P]
         L.or_restrict.restype = None; L.or_restrict.argtypes = [P, i32, i32, i32, i32, P]
         L.or_resample.restype = None; L.or_resample.argtypes = [P, i32, i32, i32, P, i32]
         L.or_expected.restype = ctypes.c_int
@@ -175,6 +179,82 @@ def backward_levels(verts, levels, r_min: int, r_max: int, cams, S, fwd, grad_co
     gt, gv = backward(verts, compose(levels, r_min, r_max), 1 << r_max, cams, S, fwd, grad_color, score_w,
                       flags=flags)
     return restrict(gt, r_min, r_max), gv
+
+
+# ------------------------------------------------------- adaptive control
+def coverage(tri_ids, T: int) -> np.ndarray:
+    """Pixel-samples selected per triangle (int64 [T]) of tri_id planes."""
+    counts = np.zeros(T, np.int64)
+    for a in tri_ids:
+        a = _c(a, np.int32)
+        lib().or_coverage(_p(a), a.size, T, _p(counts))
+    return counts
+
+
+def edge_ratios(verts, cams) -> np.ndarray:
+    """[T, 3] largest view-space edge length / image height over the views."""
+    v = _c(verts, np.float32)
+    cf, wh = _cams(cams)
+    out = np.zeros((v.shape[0], 3), np.float32)
+    lib().or_edge_ratios(_p(v), v.shape[0], _p(cf), _p(wh), len(cams), _p(out))
+    return out
+
+
+def adapt_plan(counts, ratios, threshold: float, budget: int):
+    """One round of adaptive control (Sec. 3.4): every triangle whose largest
+    view-space edge ratio exceeds ``threshold`` splits that edge (the first
+    of equal ones); then, while the triangle count after the splits exceeds
+    ``budget`` (negative: no budget), the triangle with the lowest coverage
+    (lowest index among equal counts) is removed (a triangle that would have
+    split removes two).  Returns the plan: per output triangle, parent << 3 |
+    op (op 0 copy, 1 + 2e + c child c of edge e), survivors in index order,
+    the two children of a split in place of their parent."""
+    ratios = np.asarray(ratios, np.float32)
+    thr = np.float32(threshold)
+    T = len(counts)
+    split = []
+    for t in range(T):
+        e = 0
+        for k in (1, 2):
+            if ratios[t, k] > ratios[t, e]:
+                e = k
+        split.append(e if ratios[t, e] > thr else -1)
+    n = T + sum(1 for e in split if e >= 0)
+    removed = set()
+    if budget >= 0:
+        for t in sorted(range(T), key=lambda u: (int(counts[u]), u)):
+            if n <= budget:
+                break
+            removed.add(t)
+            n -= 2 if split[t] >= 0 else 1
+    plan = []
+    for t in range(T):
+        if t in removed:
+            continue
+        if split[t] < 0:
+            plan.append(t << 3)
+        else:
+            plan += [(t << 3) | (1 + 2 * split[t]), (t << 3) | (2 + 2 * split[t])]
+    return np.array(plan, np.int32)
+
+
+def soup_rebuild(verts, levels, r_min: int, r_max: int, plan):
+    """(verts_out [n, 3, 3], levels_out) of a split/prune plan (or_soup_rebuild)."""
+    v = _c(verts, np.float32)
+    T = v.shape[0]
+    C = levels[0].shape[2]
+    flat = np.concatenate([_c(l, np.float32).reshape(-1) for l in levels])
+    pl = _c(plan, np.int32)
+    n = len(pl)
+    vo = np.empty((n, 3, 3), np.float32)
+    lo = np.empty(sum(n * level_V(R) * C for R in range(r_min, r_max + 1)), np.float32)
+    lib().or_soup_rebuild(_p(v), _p(flat), T, r_min, r_max, C, _p(pl), n, _p(vo), _p(lo))
+    parts, o = [], 0
+    for R in range(r_min, r_max + 1):
+        m = n * level_V(R) * C
+        parts.append(lo[o:o + m].reshape(n, level_V(R), C))
+        o += m
+    return vo, parts
 
 
 # ---------------------------------------------------------------- full passes

@@ -920,3 +920,135 @@ void or_resample(const float* src, int32_t T, int32_t r_src, int32_t C, float* d
                                        : o_level_value(g, r_src, C, c, i, j, Nd);
             }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Adaptive control of primitives (Sec. 3.4 "Adaptive control of            */
+/* primitives"; supplementary random-initialisation procedure)               */
+/* ------------------------------------------------------------------------ */
+
+/* Pixel coverage per triangle: the number of pixel-samples of the given
+ * G-buffers (tri_id planes) whose selected fragment is the triangle; counts
+ * are added to `counts` [T]. */
+void or_coverage(const int32_t* tri_ids, int64_t n, int32_t T, int64_t* counts)
+{
+    for (int64_t k = 0; k < n; ++k)
+        if (tri_ids[k] >= 0 && tri_ids[k] < T) counts[tri_ids[k]] += 1;
+}
+
+/* View-space edge lengths relative to the image height: for every triangle
+ * and edge e = (v_e, v_(e+1)%3), the largest over the views of the projected
+ * length |pi(v_b) - pi(v_a)| / H, over the views where all three vertices lie
+ * in front of the near plane and the projected triangle's bounding box meets
+ * the image [0, W] x [0, H]; 0 if there is none.  FP32, projection as in the
+ * set-up (Eq. 1), length sqrt(dx^2 + dy^2). */
+void or_edge_ratios(const float* verts, int32_t T, const float* cams, const int32_t* wh, int32_t n_views,
+                    float* out)
+{
+    for (int t = 0; t < T; ++t) {
+        float best[3] = {0.0f, 0.0f, 0.0f};
+        for (int v = 0; v < n_views; ++v) {
+            const float* cam = cams + 17 * v;
+            const float fx = cam[0], fy = cam[1], cx = cam[2], cy = cam[3];
+            const float* R = cam + 4;
+            const float* tt = cam + 13;
+            const int W = wh[2 * v], H = wh[2 * v + 1];
+            float sx[3], sy[3];
+            int ok = 1;
+            for (int i = 0; i < 3 && ok; ++i) {
+                const float* p = verts + 9 * (size_t)t + 3 * i;
+                float xc = fmaf(R[0], p[0], fmaf(R[1], p[1], fmaf(R[2], p[2], tt[0])));
+                float yc = fmaf(R[3], p[0], fmaf(R[4], p[1], fmaf(R[5], p[2], tt[1])));
+                float zc = fmaf(R[6], p[0], fmaf(R[7], p[1], fmaf(R[8], p[2], tt[2])));
+                if (!(zc > cam[16])) ok = 0;
+                sx[i] = fmaf(fx, xc / zc, cx);
+                sy[i] = fmaf(fy, yc / zc, cy);
+            }
+            if (!ok) continue;
+            float x0 = fminf(sx[0], fminf(sx[1], sx[2])), x1 = fmaxf(sx[0], fmaxf(sx[1], sx[2]));
+            float y0 = fminf(sy[0], fminf(sy[1], sy[2])), y1 = fmaxf(sy[0], fmaxf(sy[1], sy[2]));
+            if (x1 < 0.0f || x0 > (float)W || y1 < 0.0f || y0 > (float)H) continue;
+            for (int e = 0; e < 3; ++e) {
+                const int a = e, b = (e + 1) % 3;
+                const float dx = sx[b] - sx[a], dy = sy[b] - sy[a];
+                const float r = sqrtf(fmaf(dx, dx, dy * dy)) / (float)H;
+                if (r > best[e]) best[e] = r;
+            }
+        }
+        for (int e = 0; e < 3; ++e) out[3 * (size_t)t + e] = best[e];
+    }
+}
+
+/* The soup after a round of splitting and pruning.  plan[k] describes output
+ * triangle k: parent << 3 | op; op 0 copies the parent; op 1 + 2e + c is
+ * child c of splitting edge e = (v_e, v_(e+1)%3) at its midpoint m (child 0
+ * = (v_e, m, v_(e+2)%3), child 1 = (m, v_(e+1)%3, v_(e+2)%3), the parent's
+ * winding).  Each level of a child's texture is the parent's level sampled at
+ * the child's grid vertices (mapped into the parent's barycentrics; a point
+ * that coincides with a parent grid vertex takes its value, any other is
+ * interpolated in the parent's micro-triangle, as the decode).  m = (v_a +
+ * v_b) * 0.5 in FP32. */
+void or_soup_rebuild(const float* verts, const float* levels, int32_t T, int32_t r_min, int32_t r_max, int32_t C,
+                     const int32_t* plan, int32_t n_out, float* verts_out, float* levels_out)
+{
+    size_t off_in = 0, off_out = 0;
+    for (int R = r_min; R <= r_max; ++R) {
+        const int N = 1 << R;
+        const size_t V = o_level_V(R);
+        for (int k = 0; k < n_out; ++k) {
+            const int p = plan[k] >> 3, op = plan[k] & 7;
+            const float* g = levels + off_in + (size_t)p * V * C;
+            float* d = levels_out + off_out + (size_t)k * V * C;
+            /* the child's corners in the parent's barycentrics, times 2 */
+            int P[3][3];
+            for (int i = 0; i < 3; ++i)
+                for (int q = 0; q < 3; ++q) P[i][q] = 2 * (i == q);
+            if (op) {
+                const int e = (op - 1) >> 1, c = (op - 1) & 1;
+                const int a = e, b = (e + 1) % 3, o = (e + 2) % 3;
+                int Pm[3] = {0, 0, 0};
+                Pm[a] = 1; Pm[b] = 1;
+                const int* c0 = c == 0 ? P[a] : Pm;
+                const int* c1 = c == 0 ? Pm : P[b];
+                int Q[3][3];
+                for (int q = 0; q < 3; ++q) { Q[0][q] = c0[q]; Q[1][q] = c1[q]; Q[2][q] = P[o][q]; }
+                memcpy(P, Q, sizeof(P));
+            }
+            for (int j = 0; j <= N; ++j)
+                for (int i = 0; i + j <= N; ++i) {
+                    /* parent position in units of 1/(2N): components 1 and 2 */
+                    const int X = (N - i - j) * P[0][1] + i * P[1][1] + j * P[2][1];
+                    const int Y = (N - i - j) * P[0][2] + i * P[1][2] + j * P[2][2];
+                    const int v = o_texel(N, i, j);
+                    for (int ch = 0; ch < C; ++ch) {
+                        float val;
+                        if (X % 2 == 0 && Y % 2 == 0) {
+                            val = g[(size_t)o_texel(N, X / 2, Y / 2) * C + ch];
+                        } else {
+                            int idx[3]; float wa, wb;
+                            o_cell(N, (float)X / (float)(2 * N), (float)Y / (float)(2 * N), idx, &wa, &wb, NULL);
+                            val = o_interp(g[(size_t)idx[0] * C + ch], g[(size_t)idx[1] * C + ch],
+                                           g[(size_t)idx[2] * C + ch], wa, wb);
+                        }
+                        d[(size_t)v * C + ch] = val;
+                    }
+                }
+        }
+        off_in += (size_t)T * V * C;
+        off_out += (size_t)n_out * V * C;
+    }
+    for (int k = 0; k < n_out; ++k) {
+        const int p = plan[k] >> 3, op = plan[k] & 7;
+        const float* s = verts + 9 * (size_t)p;
+        float* d = verts_out + 9 * (size_t)k;
+        if (!op) { memcpy(d, s, 9 * sizeof(float)); continue; }
+        const int e = (op - 1) >> 1, c = (op - 1) & 1;
+        const int a = e, b = (e + 1) % 3, o = (e + 2) % 3;
+        float m[3];
+        for (int q = 0; q < 3; ++q) m[q] = (s[3 * a + q] + s[3 * b + q]) * 0.5f;
+        const float* c0 = c == 0 ? s + 3 * a : m;
+        const float* c1 = c == 0 ? m : s + 3 * b;
+        memcpy(d, c0, 3 * sizeof(float));
+        memcpy(d + 3, c1, 3 * sizeof(float));
+        memcpy(d + 6, s + 3 * o, 3 * sizeof(float));
+    }
+}

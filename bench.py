@@ -351,6 +351,64 @@ def _shade_leg(wl, steps: int):
     return out
 
 
+def _adapt_leg(wl):
+    """One round of adaptive control (Sec. 3.4) on the batch's soup: coverage
+    counts from the step's G-buffers (8 views, S = 4), view-space edge ratios
+    over 20 views (the 8 views + 12 more at 1920x1080), the split/prune plan
+    on the host and the rebuild
+    of vertices and textures.  Device stages timed with CUDA events; the plan
+    and the rebuild (which copies the plan and synchronises) with the host
+    clock.  The threshold is 1/100 of the image height rather than the
+    paper's 1/5, under which no edge of these 100,000 small triangles (about
+    11 pixels at 1080p) would split; the budget is the current count, so the
+    splits are paid for by prunes (a constant triangle count)."""
+    import numpy as np
+    import torch
+    from paper_2603_27151_gb300 import inputs as I
+    N, sc = wl.N, wl.sc
+    threshold = 0.01
+    T, V, C = sc.tex.shape
+    cams = list(sc.cams) + [I.look_at(e, 1920, 1080) for e in I.sphere_eyes(12, 3.0, np.random.default_rng(16))]
+    counts = torch.zeros(T, dtype=torch.int32, device=wl.verts.device)
+    ratios = torch.empty((T, 3), device=wl.verts.device)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for _ in range(2):       # warm
+        counts.zero_()
+        N.coverage_count(wl.g, T, counts)
+        N.edge_ratios(wl.verts, cams, ratios)
+    counts.zero_()
+    torch.cuda.synchronize()
+    ev[0].record()
+    N.coverage_count(wl.g, T, counts)
+    ev[1].record()
+    N.edge_ratios(wl.verts, cams, ratios)
+    ev[2].record()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = N.adapt_plan(counts.cpu().numpy(), ratios.cpu().numpy(), threshold, T)
+    t1 = time.perf_counter()
+    n = len(plan)
+    vo = torch.empty((n, 3, 3), device=wl.verts.device)
+    to = torch.empty((n, V, C), device=wl.verts.device)
+    wl.ctx.soup_rebuild(wl.verts, wl.tex, T, [sc.grid_n], C, plan, vo, to)
+    t2 = time.perf_counter()
+    wl.ctx.soup_rebuild(wl.verts, wl.tex, T, [sc.grid_n], C, plan, vo, to)
+    t3 = time.perf_counter()
+    cov_ms = ev[0].elapsed_time(ev[1])
+    peak, peak_kind = _peaks()
+    cov_bytes = 16 * wl.pixel_samples + 4 * T        # G-buffer texels read (ids interleaved), counts written
+    return {"coverage_ms": cov_ms, "edge_ratios_ms": ev[1].elapsed_time(ev[2]), "plan_ms": (t1 - t0) * 1e3,
+            "rebuild_ms": (t3 - t2) * 1e3, "first_rebuild_ms": (t2 - t1) * 1e3,
+            "triangles_in": T, "triangles_out": n, "splits": int(((plan & 7) == 1).sum() + ((plan & 7) == 3).sum()
+                                                               + ((plan & 7) == 5).sum()),
+            "views_measured": len(cams), "threshold": threshold,
+            "coverage_roofline": {"bound": "hbm", "achieved": cov_bytes / (cov_ms / 1e3) / 1e9, "peak": peak,
+                                  "unit": "GB/s", "frac": cov_bytes / (cov_ms / 1e3) / 1e9 / peak,
+                                  "peak_kind": peak_kind},
+            "what": "coverage over the step's G-buffers, edge ratios over 20 views, host plan (budget = current "
+                    "count), rebuild"}
+
+
 def _levels_leg(device: str, steps: int):
     """The 1080p batch with a multi-resolution texture: levels 2..5 (the last
     stage of the coarse-to-fine schedule; finest grid 32 subdivisions, 561
@@ -644,6 +702,7 @@ def _gpu_arm(args):
         line["plain_path"]["batched_speedup"] = value / world / extras["plain_path"]["value"]
     if not args.views and not args.no_extras and world == 1:
         line["shade"] = _shade_leg(wl, max(5, args.steps // 4))
+        line["adapt"] = _adapt_leg(wl)
         del wl
         torch.cuda.empty_cache()
         line["levels"] = _levels_leg(dev, max(5, args.steps // 4))

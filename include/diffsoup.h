@@ -296,6 +296,58 @@ DS_API ds_status ds_loss_l2(int32_t n_views, int32_t S, int32_t C, const int32_t
                             float* const* grad_colors, float* const* score_ws, float scale,
                             float* loss, void* stream);
 
+/* Adaptive control of primitives (Sec. 3.4): edges whose view-space length
+ * exceeds a fraction of the image height are split; triangles with low pixel
+ * coverage are pruned to hold a triangle budget.  Four calls make one round:
+ *
+ * ds_coverage_count: pixel coverage per triangle -- the number of
+ *  pixel-samples of the given G-buffers (host array of device pointers, each
+ *  [S][H][W] as written by a forward pass; hw host [n_views][2] = (W, H))
+ *  whose selected triangle is t -- added to counts (device int32 [T]; ids
+ *  outside [0, T) are ignored).  Allocates nothing. */
+DS_API ds_status ds_coverage_count(const ds_gbuf* const* gbufs, const int32_t* hw, int32_t n_views, int32_t S,
+                                   int32_t T, int32_t* counts, void* stream);
+
+/* ds_edge_ratios: for every triangle and edge e = (v_e, v_(e+1)%3), the
+ *  largest over the views (host cams, the paper samples 20 training views) of
+ *  the edge's projected length divided by the image height, over the views
+ *  where all three vertices lie in front of near_z and the projected
+ *  triangle's bounding box meets the image; 0 if there is none.  verts
+ *  device [T][3][3]; ratios device [T][3] (written).  FP32 with the
+ *  projection of the set-up (x_c = R v + t by fused multiply-adds, screen =
+ *  f x/z + c), length sqrt(dx^2 + dy^2).  Allocates nothing. */
+DS_API ds_status ds_edge_ratios(const float* verts, int32_t T, const ds_camera* cams, int32_t n_views,
+                                float* ratios, void* stream);
+
+/* ds_adapt_plan (host only, no device work): one round's plan from host
+ *  copies of counts [T] and ratios [T][3].  Every triangle whose largest
+ *  ratio exceeds `threshold` (the paper: 1/5) splits that edge (the first of
+ *  equal maxima); then, if budget >= 0 and the count after the splits
+ *  exceeds it, triangles are removed in order of increasing coverage (lower
+ *  index first among equal counts; removing a splitting triangle removes
+ *  both children) until it does not.  plan (host, capacity 2T) receives one
+ *  code per output triangle: parent << 3 | op, op 0 = copy, op 1 + 2e + c =
+ *  child c of splitting edge e; survivors in index order, children in place
+ *  of their parent.  *n_out = the new triangle count. */
+DS_API ds_status ds_adapt_plan(const int32_t* counts, const float* ratios, int32_t T, float threshold,
+                               int64_t budget, int32_t* plan, int32_t* n_out);
+
+/* ds_soup_rebuild: the soup after a plan.  verts [T][3][3] and tex (levels
+ *  back to back, level l = [T][V_l][C] with V_l = (N_l+1)(N_l+2)/2, N_l =
+ *  grid_ns[l] (host [n_levels]); one level for a plain soup) -> verts_out
+ *  [n_out][3][3] and tex_out (same level layout with n_out triangles).  A
+ *  child of edge e = (a, b) with opposite vertex o is (a, m, o) (c = 0) or
+ *  (m, b, o) (c = 1), m = (a + b) * 0.5 in FP32 (the parent's winding); each
+ *  level of its texture is the parent's level sampled at the child's grid
+ *  vertices mapped into the parent (a point on a parent grid vertex takes its
+ *  value, any other point -- a micro-edge midpoint -- is interpolated as the
+ *  decode does).  plan is host memory, validated before any launch (parent in
+ *  [0, T), op <= 6).  Uses a context scratch for the plan; returns with the
+ *  rebuild complete (synchronises `stream`). */
+DS_API ds_status ds_soup_rebuild(ds_ctx* ctx, const float* verts, const float* tex, int32_t T,
+                                 const int32_t* grid_ns, int32_t n_levels, int32_t C, const int32_t* plan,
+                                 int32_t n_out, float* verts_out, float* tex_out, void* stream);
+
 /* Neural deferred shading (Sec. 3.3, "Neural deferred shading"; supplementary
  * "MLP Architecture"): the per-pixel shading pass that turns the rasterised
  * colour features (C = 8: 7 features + opacity) into RGB.  For every view v,

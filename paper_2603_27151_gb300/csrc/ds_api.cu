@@ -110,6 +110,7 @@ struct ds_ctx {
     DevBuf recs, counts, offs, tbox, zkeys, keys[2], vals[2], hist, hist_scan, ranges, scanbuf, misc, geom;
     DevBuf acc_tex, acc_verts;   // FP64 gradient accumulators of the backward
     DevBuf shade_part;           // per-CTA partials of the shading parameter gradients
+    DevBuf plan_dev;             // device copy of an adaptive-control plan
     ds::ScanScratch scan;
     int64_t scan_cap = 0;
     uint32_t* h_word = nullptr;   // pinned host words
@@ -454,7 +455,7 @@ void ds_destroy(ds_ctx* c) {
     }
     DevBuf* bufs[] = {&c->recs,  &c->counts,  &c->offs,      &c->tbox,   &c->zkeys,   &c->keys[0], &c->keys[1],
                       &c->vals[0], &c->vals[1], &c->hist, &c->hist_scan, &c->ranges, &c->scanbuf, &c->misc,
-                      &c->geom, &c->acc_tex, &c->acc_verts, &c->shade_part};
+                      &c->geom, &c->acc_tex, &c->acc_verts, &c->shade_part, &c->plan_dev};
     for (DevBuf* b : bufs) b->release();
     if (c->h_word) cudaFreeHost(c->h_word);
     for (auto& r : c->prof_pending) {
@@ -1106,6 +1107,76 @@ ds_status ds_shade_backward(ds_ctx* c, int32_t n_views, int32_t S, const ds_came
     DS_TRY(c->shade_part.ensure(sizeof(float) * ds::shade_partial_floats(grid), "shading gradient partials"));
     DS_TRY_CUDA(ds::launch_shade_bwd(v.data(), n_views, S, params, overwrite, c->shade_part.as<float>(), grid,
                                      grad_params, st));
+    return DS_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+// Adaptive control of primitives (Sec. 3.4).
+ds_status ds_coverage_count(const ds_gbuf* const* gbufs, const int32_t* hw, int32_t n_views, int32_t S, int32_t T,
+                            int32_t* counts, void* stream) {
+    if (!gbufs || !hw || !counts) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    if (n_views < 1 || n_views > DS_MAX_VIEWS) return fail(DS_ERR_INVALID_ARG, "n_views out of range");
+    if (S < 1 || S > DS_MAX_SAMPLES) return fail(DS_ERR_INVALID_ARG, "S out of range");
+    if (T < 1 || T >= DS_MAX_TRIANGLES) return fail(DS_ERR_INVALID_ARG, "T out of range");
+    const int4* g[DS_MAX_VIEWS];
+    long long n[DS_MAX_VIEWS];
+    for (int v = 0; v < n_views; ++v) {
+        if (!gbufs[v]) return fail(DS_ERR_INVALID_ARG, "gbufs[" + std::to_string(v) + "] is NULL");
+        if (hw[2 * v] < 1 || hw[2 * v + 1] < 1 || hw[2 * v] > DS_MAX_RESOLUTION || hw[2 * v + 1] > DS_MAX_RESOLUTION)
+            return fail(DS_ERR_INVALID_ARG, "bad view size");
+        g[v] = reinterpret_cast<const int4*>(gbufs[v]);
+        n[v] = (long long)S * hw[2 * v] * hw[2 * v + 1];
+    }
+    DS_TRY_CUDA(ds::launch_coverage(g, n, n_views, T, counts, static_cast<cudaStream_t>(stream)));
+    return DS_OK;
+}
+
+ds_status ds_edge_ratios(const float* verts, int32_t T, const ds_camera* cams, int32_t n_views, float* ratios,
+                         void* stream) {
+    if (!verts || !ratios) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    if (T < 1 || T >= DS_MAX_TRIANGLES) return fail(DS_ERR_INVALID_ARG, "T out of range");
+    DS_TRY(check_views(cams, n_views, 1));
+    DS_TRY_CUDA(ds::launch_edge_ratios(verts, T, cams, n_views, ratios, static_cast<cudaStream_t>(stream)));
+    return DS_OK;
+}
+
+ds_status ds_adapt_plan(const int32_t* counts, const float* ratios, int32_t T, float threshold, int64_t budget,
+                        int32_t* plan, int32_t* n_out) {
+    if (!counts || !ratios || !plan || !n_out) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    if (T < 1 || T >= DS_MAX_TRIANGLES / 2) return fail(DS_ERR_INVALID_ARG, "T out of range");
+    if (!std::isfinite(threshold)) return fail(DS_ERR_INVALID_ARG, "threshold is not finite");
+    *n_out = ds::adapt_plan(counts, ratios, T, threshold, (long long)budget, plan);
+    return DS_OK;
+}
+
+ds_status ds_soup_rebuild(ds_ctx* c, const float* verts, const float* tex, int32_t T, const int32_t* grid_ns,
+                          int32_t n_levels, int32_t C, const int32_t* plan, int32_t n_out, float* verts_out,
+                          float* tex_out, void* stream) {
+    if (!c) return fail(DS_ERR_INVALID_ARG, "NULL context");
+    if (!verts || !tex || !grid_ns || !verts_out || !tex_out || (n_out > 0 && !plan))
+        return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    if (T < 1 || T >= DS_MAX_TRIANGLES) return fail(DS_ERR_INVALID_ARG, "T out of range");
+    if (n_out < 0 || n_out >= DS_MAX_TRIANGLES) return fail(DS_ERR_INVALID_ARG, "n_out out of range");
+    if (n_levels < 1 || n_levels > 6) return fail(DS_ERR_INVALID_ARG, "n_levels must be in [1, 6]");
+    if (C < 1 || C > DS_MAX_CHANNELS) return fail(DS_ERR_INVALID_ARG, "C out of range");
+    for (int l = 0; l < n_levels; ++l)
+        if (grid_ns[l] < 1 || grid_ns[l] > DS_MAX_GRID_N) return fail(DS_ERR_INVALID_ARG, "grid_n out of range");
+    for (int k = 0; k < n_out; ++k)
+        if ((plan[k] >> 3) < 0 || (plan[k] >> 3) >= T || (plan[k] & 7) > 6)
+            return fail(DS_ERR_INVALID_ARG, "plan entry " + std::to_string(k) + " is invalid");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (n_out == 0) return DS_OK;
+    DS_TRY(c->plan_dev.ensure(sizeof(int32_t) * (size_t)n_out, "rebuild plan"));
+    DS_TRY_CUDA(cudaMemcpyAsync(c->plan_dev.p, plan, sizeof(int32_t) * (size_t)n_out, cudaMemcpyHostToDevice, st));
+    DS_TRY_CUDA(ds::launch_rebuild(verts, tex, T, grid_ns, n_levels, C, c->plan_dev.as<int32_t>(), n_out, verts_out,
+                                   tex_out, st));
+    // the call returns with the rebuild complete (a once-per-round operation)
+    DS_TRY_CUDA(cudaStreamSynchronize(st));
     return DS_OK;
 }
 

@@ -105,6 +105,15 @@ cudaError_t launch_restrict(const double* fine, int T, int r_min, int r_max, int
                             cudaStream_t st);
 cudaError_t launch_resample(const float* src, int T, int r_src, int C, float* dst, int r_dst, cudaStream_t st);
 
+// Adaptive control of primitives (ds_adapt.cu).
+cudaError_t launch_coverage(const int4* const* gbufs, const long long* n, int n_views, int T, int* counts,
+                            cudaStream_t st);
+cudaError_t launch_edge_ratios(const float* verts, int T, const ds_camera* cams, int n_views, float* out,
+                               cudaStream_t st);
+cudaError_t launch_rebuild(const float* verts, const float* tex, int T, const int* grid_ns, int n_levels, int C,
+                           const int* plan_dev, int n_out, float* verts_out, float* tex_out, cudaStream_t st);
+int adapt_plan(const int32_t* counts, const float* ratios, int T, float threshold, long long budget, int32_t* plan);
+
 // One view of the deferred shading pass: feat [S][7][H][W], rgb [S][3][H][W],
 // grad_rgb [S][3][H][W], grad_feat [S][7][H][W] (may be null), the pinhole
 // intrinsics and the world-to-camera rotation (row-major).

@@ -149,6 +149,14 @@ def load():
     L.ds_levels_compose.restype = i32
     L.ds_levels_resample.argtypes = [P, i32, i32, i32, P, i32, P]
     L.ds_levels_resample.restype = i32
+    L.ds_coverage_count.argtypes = [P, P, i32, i32, i32, P, P]
+    L.ds_coverage_count.restype = i32
+    L.ds_edge_ratios.argtypes = [P, i32, P, i32, P, P]
+    L.ds_edge_ratios.restype = i32
+    L.ds_adapt_plan.argtypes = [P, P, i32, ctypes.c_float, ctypes.c_int64, P, ctypes.POINTER(i32)]
+    L.ds_adapt_plan.restype = i32
+    L.ds_soup_rebuild.argtypes = [P, P, P, i32, P, i32, i32, P, i32, P, P, P]
+    L.ds_soup_rebuild.restype = i32
     L.ds_shade_forward.argtypes = [P, i32, i32, P, P, P, P, P]
     L.ds_shade_forward.restype = i32
     L.ds_shade_backward.argtypes = [P, i32, i32, P, P, P, P, P, P, u32, P]
@@ -294,6 +302,15 @@ class Context:
         _check(load().ds_shade_backward(self.h, n, S, cameras(cams), _ptr(params), arr(feats), arr(grad_rgbs),
                                         arr(grad_feats), _ptr(grad_params), DS_OVERWRITE if overwrite else 0,
                                         _stream(stream)))
+
+    def soup_rebuild(self, verts, tex, T: int, grid_ns, C: int, plan, verts_out, tex_out, stream=None):
+        """The soup after an adaptive-control plan (ds_soup_rebuild); plan is
+        a host int32 numpy array, the tensors are float32 CUDA tensors."""
+        pl = np.ascontiguousarray(plan, np.int32)
+        gn = (ctypes.c_int32 * len(grid_ns))(*[int(x) for x in grid_ns])
+        _check(load().ds_soup_rebuild(self.h, _ptr(verts), _ptr(tex), int(T), gn, len(grid_ns), int(C),
+                                      pl.ctypes.data_as(ctypes.c_void_p), len(pl), _ptr(verts_out), _ptr(tex_out),
+                                      _stream(stream)))
 
     def raster_forward_devcam(self, soup_id, wh, cams_dev, seeds_dev, S, mode, bg, gbufs, colors, n_fronts=None,
                               stream=None):
@@ -486,6 +503,36 @@ def levels_compose(tex_levels, T: int, r_min: int, r_max: int, C: int, out, acti
 def levels_resample(src, T: int, r_src: int, C: int, dst, r_dst: int, stream=None):
     """src [T, V_{r_src}, C] sampled at the vertices of level r_dst (ds_levels_resample)."""
     _check(load().ds_levels_resample(_ptr(src), T, r_src, C, _ptr(dst), r_dst, _stream(stream)))
+
+
+def coverage_count(gbufs, T: int, counts, stream=None):
+    """Pixel-samples won per triangle, added to counts (int32 CUDA [T]);
+    gbufs[v]: the [S, H, W, 4] G-buffers of a forward pass."""
+    n = len(gbufs)
+    S = int(gbufs[0].shape[0])
+    hw = (ctypes.c_int32 * (2 * n))(*[int(x) for g in gbufs for x in (g.shape[2], g.shape[1])])
+    arr = (ctypes.c_void_p * n)(*[g.data_ptr() for g in gbufs])
+    _check(load().ds_coverage_count(arr, hw, n, S, int(T), _ptr(counts), _stream(stream)))
+
+
+def edge_ratios(verts, cams, out, stream=None):
+    """[T, 3] largest view-space edge length / image height over ``cams``."""
+    _check(load().ds_edge_ratios(_ptr(verts), int(verts.shape[0]), cameras(cams), len(cams), _ptr(out),
+                                 _stream(stream)))
+
+
+def adapt_plan(counts, ratios, threshold: float, budget: int = -1) -> np.ndarray:
+    """One round's split/prune plan (ds_adapt_plan, host only) from host
+    arrays counts [T] and ratios [T, 3]."""
+    c = np.ascontiguousarray(counts, np.int32)
+    r = np.ascontiguousarray(ratios, np.float32)
+    T = len(c)
+    plan = np.empty(2 * T, np.int32)
+    n = ctypes.c_int32(0)
+    _check(load().ds_adapt_plan(c.ctypes.data_as(ctypes.c_void_p), r.ctypes.data_as(ctypes.c_void_p), T,
+                                float(threshold), int(budget), plan.ctypes.data_as(ctypes.c_void_p),
+                                ctypes.byref(n)))
+    return plan[:n.value].copy()
 
 
 def loss_l2(colors, targets, grad_colors=None, score_ws=None, loss=None, scale=1.0, stream=None):

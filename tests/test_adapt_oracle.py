@@ -111,3 +111,17 @@ def test_plan_rules():
     assert list(p) == [0 << 3 | 3, 0 << 3 | 4, 2 << 3 | 5, 2 << 3 | 6, 4 << 3]
     # the threshold is strict
     assert list(O.adapt_plan(counts, ratios, 0.5, -1)) == [t << 3 for t in range(5)]
+
+
+def test_library_plan_equals_the_oracle_plan():
+    """ds_adapt_plan (host C++ of the library, no GPU) against the oracle's
+    plan on random counts and ratios: the same integers."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2603_27151_gb300 import native as N
+    rng = np.random.default_rng(3)
+    for T, budget in [(1, -1), (50, -1), (200, 150), (200, 10), (300, 0), (64, 1000)]:
+        counts = rng.integers(0, 6, size=T)
+        ratios = (rng.integers(0, 8, size=(T, 3)) / 20.0).astype(np.float32)   # many ties
+        got = N.adapt_plan(counts, ratios, 0.2, budget)
+        assert np.array_equal(got, O.adapt_plan(counts, ratios, 0.2, budget)), (T, budget)

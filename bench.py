@@ -409,6 +409,55 @@ def _adapt_leg(wl):
                     "count), rebuild"}
 
 
+def _loss_optim_leg(wl, reps: int = 10):
+    """The paper's loss and optimisers on the batch: lambda L1 + (1 - lambda)
+    SSIM (Eq. 10) with its gradients over the step's colours (8 views, S = 4,
+    7 channels), and one Adam step of the texture logits plus one VectorAdam
+    step of the vertices (with the step's gradients).  CUDA events, mean over
+    ``reps`` launches."""
+    import torch
+    N = wl.N
+    T, V, C = wl.sc.tex.shape
+    gcol = [torch.empty_like(c) for c in wl.col]
+    sw = [torch.empty((wl.S, c.height, c.width), device=wl.verts.device) for c in wl.sc.cams]
+    loss = torch.zeros(1, device=wl.verts.device)
+    tex, verts = wl.tex.clone(), wl.verts.clone()
+    mt, vt = torch.zeros_like(tex), torch.zeros_like(tex)
+    mv, vv = torch.zeros_like(verts), torch.zeros(T * 3, device=wl.verts.device)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ssim_ms = timed(lambda: N.loss_l1_ssim(wl.col, wl.targets, gcol, sw, loss, scale=1.0 / wl.S))
+    step = [0]
+
+    def adam():
+        step[0] += 1
+        N.adam_step(tex, wl.gt, mt, vt, 0.05, step[0], dim=1)
+        N.adam_step(verts, wl.gv, mv, vv, 1e-3, step[0], dim=3)
+    adam_ms = timed(adam)
+    peak, peak_kind = _peaks()
+    n_tex, n_vec = T * V * C, T * 3
+    adam_bytes = 28 * n_tex + 68 * n_vec
+    px = wl.pixel_samples
+    return {"l1_ssim_ms": ssim_ms, "l1_ssim_pixel_samples_per_s": px / (ssim_ms / 1e3),
+            "adam_ms": adam_ms, "adam_values": n_tex + 3 * n_vec,
+            "adam_roofline": {"bound": "hbm", "achieved": adam_bytes / (adam_ms / 1e3) / 1e9, "peak": peak,
+                              "unit": "GB/s", "frac": adam_bytes / (adam_ms / 1e3) / 1e9 / peak,
+                              "peak_kind": peak_kind},
+            "what": "fused L1+SSIM loss with gradients and score weights (11x11 Gaussian, 7 channels); Adam on "
+                    "the texture logits + VectorAdam on the vertices"}
+
+
 def _levels_leg(device: str, steps: int):
     """The 1080p batch with a multi-resolution texture: levels 2..5 (the last
     stage of the coarse-to-fine schedule; finest grid 32 subdivisions, 561
@@ -703,6 +752,7 @@ def _gpu_arm(args):
     if not args.views and not args.no_extras and world == 1:
         line["shade"] = _shade_leg(wl, max(5, args.steps // 4))
         line["adapt"] = _adapt_leg(wl)
+        line["loss_optim"] = _loss_optim_leg(wl)
         del wl
         torch.cuda.empty_cache()
         line["levels"] = _levels_leg(dev, max(5, args.steps // 4))

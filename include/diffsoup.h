@@ -348,6 +348,19 @@ DS_API ds_status ds_soup_rebuild(ds_ctx* ctx, const float* verts, const float* t
                                  const int32_t* grid_ns, int32_t n_levels, int32_t C, const int32_t* plan,
                                  int32_t n_out, float* verts_out, float* tex_out, void* stream);
 
+/* One optimiser step (Sec. 3.4: VectorAdam for vertex positions, Adam for
+ * everything else; supplementary "Hyperparameters": beta1 0.9, beta2 0.999,
+ * eps 1e-8).  A vector is `dim` consecutive values of params (dim = 3 for
+ * vertex positions [T][3][3]: VectorAdam; dim = 1: Adam) sharing one second
+ * moment from the squared norm of its gradient:
+ *   m <- b1 m + (1-b1) g,  v <- b2 v + (1-b2)|g|^2,
+ *   params <- params - lr (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps).
+ * params, grads, m: device [n]; v: device [n / dim]; step: 1-based count
+ * (the caller keeps it; the bias corrections are computed on the host).
+ * dim in [1, 4] dividing n.  FP32.  Allocates nothing. */
+DS_API ds_status ds_adam_step(float* params, const float* grads, float* m, float* v, int64_t n, int32_t dim,
+                              float lr, float beta1, float beta2, float eps, int64_t step, void* stream);
+
 /* Neural deferred shading (Sec. 3.3, "Neural deferred shading"; supplementary
  * "MLP Architecture"): the per-pixel shading pass that turns the rasterised
  * colour features (C = 8: 7 features + opacity) into RGB.  For every view v,
@@ -380,6 +393,22 @@ DS_API ds_status ds_shade_backward(ds_ctx* ctx, int32_t n_views, int32_t S, cons
                                    const float* params, const float* const* feats,
                                    const float* const* grad_rgbs, float* const* grad_feats,
                                    float* grad_params, uint32_t flags, void* stream);
+
+/* The paper's photometric loss lambda L1 + (1 - lambda) L_SSIM (Eq. 10, Sec.
+ * 3.4; lambda = 0.8), per pixel, with its upstream gradients for
+ * ds_raster_backward.  SSIM per channel with an 11 x 11 Gaussian window
+ * (sigma 1.5, normalised), zero padding outside the image, C1 = 0.01^2,
+ * C2 = 0.03^2.  For every view v, sample s and pixel p:
+ *   ell = lambda mean_c |color - target| + (1 - lambda)(1 - mean_c ssim_c(p)),
+ *   score_w = scale * ell,  *loss += scale * sum of ell over everything,
+ *   grad_color = scale * d(sum_p ell_p)/d color  (non-local: the window).
+ *  Arguments and layouts as ds_loss_l2 (C counts the opacity channel: C-1
+ *  colour channels).  grad_colors, score_ws and loss may be NULL.  FP32; one
+ *  fused pass per 32 x 16 tile.  Allocates nothing on the device. */
+DS_API ds_status ds_loss_l1_ssim(int32_t n_views, int32_t S, int32_t C, const int32_t* hw,
+                                 const float* const* colors, const float* const* targets,
+                                 float* const* grad_colors, float* const* score_ws, float lambda, float scale,
+                                 float* loss, void* stream);
 
 /* Forward pass for callers that cannot allocate device memory: the same
  * computation and outputs as ds_raster_forward (Eq. 5, Algorithm A1 step 1),

@@ -1181,3 +1181,44 @@ ds_status ds_soup_rebuild(ds_ctx* c, const float* verts, const float* tex, int32
 }
 
 }  // extern "C"
+
+extern "C" {
+
+// Adam / VectorAdam (Sec. 3.4, supplementary hyperparameters).
+ds_status ds_adam_step(float* params, const float* grads, float* m, float* v, int64_t n, int32_t dim, float lr,
+                       float beta1, float beta2, float eps, int64_t step, void* stream) {
+    if (n < 0) return fail(DS_ERR_INVALID_ARG, "n < 0");
+    if (n > 0 && (!params || !grads || !m || !v)) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    if (dim < 1 || dim > 4 || n % dim != 0) return fail(DS_ERR_INVALID_ARG, "dim must be in [1, 4] and divide n");
+    if (step < 1) return fail(DS_ERR_INVALID_ARG, "step must be >= 1");
+    if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f && eps >= 0.f) || !std::isfinite(lr))
+        return fail(DS_ERR_INVALID_ARG, "bad hyperparameters");
+    DS_TRY_CUDA(ds::launch_adam(params, grads, m, v, (long long)n, dim, lr, beta1, beta2, eps, (long long)step,
+                                static_cast<cudaStream_t>(stream)));
+    return DS_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+ds_status ds_loss_l1_ssim(int32_t n_views, int32_t S, int32_t C, const int32_t* hw, const float* const* colors,
+                          const float* const* targets, float* const* grad_colors, float* const* score_ws,
+                          float lambda, float scale, float* loss, void* stream) {
+    if (n_views < 1 || n_views > DS_MAX_VIEWS) return fail(DS_ERR_INVALID_ARG, "n_views out of range");
+    if (S < 1 || S > DS_MAX_SAMPLES) return fail(DS_ERR_INVALID_ARG, "S out of range");
+    if (C < 2 || C > DS_MAX_CHANNELS) return fail(DS_ERR_INVALID_ARG, "C out of range");
+    if (!hw || !colors || !targets) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    if (!(lambda >= 0.f && lambda <= 1.f) || !std::isfinite(scale)) return fail(DS_ERR_INVALID_ARG, "bad lambda or scale");
+    for (int v = 0; v < n_views; ++v) {
+        if (hw[2 * v] < 1 || hw[2 * v + 1] < 1 || hw[2 * v] > DS_MAX_RESOLUTION || hw[2 * v + 1] > DS_MAX_RESOLUTION)
+            return fail(DS_ERR_INVALID_ARG, "bad view size");
+        if (!colors[v] || !targets[v]) return fail(DS_ERR_INVALID_ARG, "NULL colour or target");
+    }
+    DS_TRY_CUDA(ds::launch_loss_l1_ssim(n_views, S, C - 1, hw, colors, targets, grad_colors, score_ws, lambda, scale,
+                                        loss, static_cast<cudaStream_t>(stream)));
+    return DS_OK;
+}
+
+}  // extern "C"
+

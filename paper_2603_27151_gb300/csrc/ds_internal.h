@@ -114,6 +114,16 @@ cudaError_t launch_rebuild(const float* verts, const float* tex, int T, const in
                            const int* plan_dev, int n_out, float* verts_out, float* tex_out, cudaStream_t st);
 int adapt_plan(const int32_t* counts, const float* ratios, int T, float threshold, long long budget, int32_t* plan);
 
+// Adam / VectorAdam step (ds_optim.cu): dim consecutive values share one
+// second moment; t is the 1-based step count.
+cudaError_t launch_adam(float* x, const float* g, float* m, float* v, long long n, int dim, float lr, float b1,
+                        float b2, float eps, long long t, cudaStream_t st);
+
+// lambda L1 + (1 - lambda) SSIM loss with its upstream gradients (ds_ssim.cu).
+cudaError_t launch_loss_l1_ssim(int n_views, int S, int Co, const int* hw, const float* const* colors,
+                                const float* const* targets, float* const* grad_colors, float* const* score_ws,
+                                float lambda, float scale, float* loss, cudaStream_t st);
+
 // One view of the deferred shading pass: feat [S][7][H][W], rgb [S][3][H][W],
 // grad_rgb [S][3][H][W], grad_feat [S][7][H][W] (may be null), the pinhole
 // intrinsics and the world-to-camera rotation (row-major).

@@ -157,6 +157,11 @@ def load():
     L.ds_adapt_plan.restype = i32
     L.ds_soup_rebuild.argtypes = [P, P, P, i32, P, i32, i32, P, i32, P, P, P]
     L.ds_soup_rebuild.restype = i32
+    L.ds_adam_step.argtypes = [P, P, P, P, ctypes.c_int64, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                               ctypes.c_float, ctypes.c_int64, P]
+    L.ds_adam_step.restype = i32
+    L.ds_loss_l1_ssim.argtypes = [i32, i32, i32, P, P, P, P, P, ctypes.c_float, ctypes.c_float, P, P]
+    L.ds_loss_l1_ssim.restype = i32
     L.ds_shade_forward.argtypes = [P, i32, i32, P, P, P, P, P]
     L.ds_shade_forward.restype = i32
     L.ds_shade_backward.argtypes = [P, i32, i32, P, P, P, P, P, P, u32, P]
@@ -288,6 +293,7 @@ class Context:
         rgbs[v] float32 [S,3,H,W] (written); params: float32 [595]."""
         n = len(cams)
         S = int(feats[0].shape[0]) if n else 1
+        _check_shade(cams, S, params, [(feats, 7), (rgbs, 3)])
         arr = lambda ts: (ctypes.c_void_p * max(n, 1))(*[t.data_ptr() for t in ts])
         _check(load().ds_shade_forward(self.h, n, S, cameras(cams), _ptr(params), arr(feats), arr(rgbs),
                                        _stream(stream)))
@@ -298,6 +304,8 @@ class Context:
         [S,7,H,W] and grad_params [595] are accumulated unless ``overwrite``."""
         n = len(cams)
         S = int(feats[0].shape[0]) if n else 1
+        _check_shade(cams, S, params, [(feats, 7), (grad_rgbs, 3)] + ([(grad_feats, 7)] if grad_feats else []),
+                     grad_params)
         arr = lambda ts: None if ts is None else (ctypes.c_void_p * max(n, 1))(*[t.data_ptr() for t in ts])
         _check(load().ds_shade_backward(self.h, n, S, cameras(cams), _ptr(params), arr(feats), arr(grad_rgbs),
                                         arr(grad_feats), _ptr(grad_params), DS_OVERWRITE if overwrite else 0,
@@ -535,9 +543,59 @@ def adapt_plan(counts, ratios, threshold: float, budget: int = -1) -> np.ndarray
     return plan[:n.value].copy()
 
 
+def adam_step(params, grads, m, v, lr: float, step: int, dim: int = 1, beta1: float = 0.9, beta2: float = 0.999,
+              eps: float = 1e-8, stream=None):
+    """One Adam (dim = 1) or VectorAdam (dim = 3) step in place (ds_adam_step);
+    float32 CUDA tensors, v with numel / dim entries."""
+    _check(load().ds_adam_step(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), params.numel(), int(dim), float(lr),
+                               float(beta1), float(beta2), float(eps), int(step), _stream(stream)))
+
+
+def _check_shade(cams, S, params, lists, grad_params=None):
+    """Host-side shape checks of the shading calls: per view [S, k, H, W]
+    float32 contiguous CUDA tensors matching the camera's size, and 595
+    parameters."""
+    import torch
+    for t in (params, grad_params):
+        if t is not None and (t.numel() != DS_SHADE_N_PARAMS or t.dtype != torch.float32 or not t.is_cuda
+                              or not t.is_contiguous()):
+            raise ValueError("parameters must be a contiguous float32 CUDA tensor of %d values" % DS_SHADE_N_PARAMS)
+    for ts, k in lists:
+        if len(ts) != len(cams):
+            raise ValueError("one image per camera is required")
+        for v, (t, c) in enumerate(zip(ts, cams)):
+            shape = (S, k, int(c.height), int(c.width))
+            if tuple(t.shape) != shape or t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+                raise ValueError("view %d: expected a contiguous float32 CUDA tensor of shape %s, got %s"
+                                 % (v, shape, tuple(t.shape)))
+
+
+def _check_images(colors, targets, grad_colors, score_ws):
+    """Host-side shape checks of the per-view image lists of the loss calls
+    (the C ABI sees raw pointers): one S and one channel count for every
+    view, targets [C-1, H, W], gradients like the colours, score weights
+    [S, H, W], float32 contiguous CUDA tensors."""
+    import torch
+    if not colors or len(targets) != len(colors):
+        raise ValueError("one target per view is required")
+    S, Co = int(colors[0].shape[0]), int(colors[0].shape[1])
+    for v, c in enumerate(colors):
+        H, W = int(c.shape[2]), int(c.shape[3])
+        want = [(c, (S, Co, H, W)), (targets[v], (Co, H, W))]
+        if grad_colors is not None:
+            want.append((grad_colors[v], (S, Co, H, W)))
+        if score_ws is not None and score_ws[v] is not None:
+            want.append((score_ws[v], (S, H, W)))
+        for t, shape in want:
+            if tuple(t.shape) != shape or t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+                raise ValueError("view %d: expected a contiguous float32 CUDA tensor of shape %s, got %s"
+                                 % (v, shape, tuple(t.shape)))
+
+
 def loss_l2(colors, targets, grad_colors=None, score_ws=None, loss=None, scale=1.0, stream=None):
     """Fused L2 loss (see ds_loss_l2).  colors[v] [S,C-1,H,W]; targets[v]
     [C-1,H,W]; outputs written in place; loss: 1-element float32 tensor (+=)."""
+    _check_images(colors, targets, grad_colors, score_ws)
     n = len(colors)
     S, Co, H0, W0 = colors[0].shape
     hw = (ctypes.c_int32 * (2 * n))()
@@ -546,6 +604,21 @@ def loss_l2(colors, targets, grad_colors=None, score_ws=None, loss=None, scale=1
         hw[2 * v], hw[2 * v + 1] = int(c.shape[3]), int(c.shape[2])
     _check(load().ds_loss_l2(n, S, Co + 1, hw, arr(colors), arr(targets), arr(grad_colors), arr(score_ws),
                              float(scale), _ptr(loss), _stream(stream)))
+
+
+def loss_l1_ssim(colors, targets, grad_colors=None, score_ws=None, loss=None, lam: float = 0.8, scale=1.0,
+                 stream=None):
+    """lambda L1 + (1 - lambda) SSIM per pixel (see ds_loss_l1_ssim); the same
+    arguments as ``loss_l2``."""
+    _check_images(colors, targets, grad_colors, score_ws)
+    n = len(colors)
+    S, Co, H0, W0 = colors[0].shape
+    hw = (ctypes.c_int32 * (2 * n))()
+    arr = lambda ts: None if ts is None else (ctypes.c_void_p * n)(*[t.data_ptr() for t in ts])
+    for v, c in enumerate(colors):
+        hw[2 * v], hw[2 * v + 1] = int(c.shape[3]), int(c.shape[2])
+    _check(load().ds_loss_l1_ssim(n, S, Co + 1, hw, arr(colors), arr(targets), arr(grad_colors), arr(score_ws),
+                                  float(lam), float(scale), _ptr(loss), _stream(stream)))
 
 
 class Server:

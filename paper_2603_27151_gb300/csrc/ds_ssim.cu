@@ -10,7 +10,7 @@
 // G1..G3 the derivatives of ssim with respect to the raw moments w*x, w*x^2,
 // w*(xy) at each p (zero outside the image).
 //
-// One CTA per 32 x 16 output tile of one sample image: the inputs are staged
+// One CTA per 64 x 16 output tile of one sample image: the inputs are staged
 // with a 10-pixel halo, the five moments (separable blur) and ssim, G1..G3
 // are formed on the tile plus a 5-pixel halo, and G1..G3 are blurred back
 // onto the tile -- one pass, no intermediate maps in HBM.
@@ -24,9 +24,9 @@ namespace ds {
 namespace {
 
 constexpr int kR = 5, kTaps = 2 * kR + 1;
-constexpr int kTX = 32, kTY = 16;
-constexpr int kIX = kTX + 4 * kR, kIY = kTY + 4 * kR;   // staged input 52 x 36
-constexpr int kMX = kTX + 2 * kR, kMY = kTY + 2 * kR;   // moment region 42 x 26
+constexpr int kTX = 64, kTY = 16;
+constexpr int kIX = kTX + 4 * kR, kIY = kTY + 4 * kR;   // staged input 84 x 36
+constexpr int kMX = kTX + 2 * kR, kMY = kTY + 2 * kR;   // moment region 74 x 26
 constexpr float kC1 = 0.01f * 0.01f, kC2 = 0.03f * 0.03f;
 
 struct SsimView {
@@ -68,111 +68,186 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(const __grid_constant__ Ss
     const size_t HW = (size_t)V.W * V.H;
     const int tid = threadIdx.x;
 
-    float l1[2] = {0.f, 0.f}, ss[2] = {0.f, 0.f};
-    for (int c = 0; c < t.Co; ++c) {
+    float l1[4] = {0.f, 0.f, 0.f, 0.f}, ss[4] = {0.f, 0.f, 0.f, 0.f};
+    // The staged inputs of channel c + 1 are loaded into registers while
+    // channel c is processed (the loads' latency overlaps the blur passes).
+    constexpr int kLoads = (kIX * kIY + 255) / 256;
+    float px[kLoads], py[kLoads];
+    auto load_regs = [&](int c) {
         const float* xs = V.color + ((size_t)s * t.Co + c) * HW;
         const float* ys = V.target + (size_t)c * HW;
-        // 1. inputs with a 10-pixel halo (zero outside the image)
-        for (int k = tid; k < kIX * kIY; k += 256) {
+#pragma unroll
+        for (int i = 0; i < kLoads; ++i) {
+            const int k = tid + 256 * i;
             const int r = k / kIX, q = k - r * kIX;
             const int gy = y0 - 2 * kR + r, gx = x0 - 2 * kR + q;
-            const bool in = gx >= 0 && gx < V.W && gy >= 0 && gy < V.H;
-            sm.X[r][q] = in ? __ldg(xs + (size_t)gy * V.W + gx) : 0.f;
-            sm.Y[r][q] = in ? __ldg(ys + (size_t)gy * V.W + gx) : 0.f;
+            const bool in = k < kIX * kIY && gx >= 0 && gx < V.W && gy >= 0 && gy < V.H;
+            px[i] = in ? __ldg(xs + (size_t)gy * V.W + gx) : 0.f;
+            py[i] = in ? __ldg(ys + (size_t)gy * V.W + gx) : 0.f;
         }
-        __syncthreads();
-        // 2. horizontal pass of the five moments
-        for (int k = tid; k < kIY * kMX; k += 256) {
-            const int r = k / kMX, q = k - r * kMX;
-            float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+    };
+    auto store_regs = [&]() {
 #pragma unroll
-            for (int j = 0; j < kTaps; ++j) {
-                const float w = t.w[j], x = sm.X[r][q + j], y = sm.Y[r][q + j];
-                a0 = fmaf(w, x, a0);
-                a1 = fmaf(w, y, a1);
-                a2 = fmaf(w, x * x, a2);
-                a3 = fmaf(w, y * y, a3);
-                a4 = fmaf(w, x * y, a4);
-            }
-            sm.HM[0][r][q] = a0; sm.HM[1][r][q] = a1; sm.HM[2][r][q] = a2; sm.HM[3][r][q] = a3; sm.HM[4][r][q] = a4;
-        }
-        __syncthreads();
-        // 3. vertical pass, ssim and its derivatives w.r.t. the raw moments
-        for (int k = tid; k < kMY * kMX; k += 256) {
-            const int r = k / kMX, q = k - r * kMX;
-            float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int j = 0; j < kTaps; ++j) {
-                const float w = t.w[j];
-#pragma unroll
-                for (int u = 0; u < 5; ++u) m[u] = fmaf(w, sm.HM[u][r + j][q], m[u]);
-            }
-            const int gy = y0 - kR + r, gx = x0 - kR + q;
-            float g1 = 0.f, g2 = 0.f, g3 = 0.f;
-            if (gx >= 0 && gx < V.W && gy >= 0 && gy < V.H) {
-                const float mx = m[0], my = m[1];
-                const float A = 2.f * mx * my + kC1;
-                const float B = 2.f * (m[4] - mx * my) + kC2;
-                const float Cc = mx * mx + my * my + kC1;
-                const float D = (m[2] - mx * mx) + (m[3] - my * my) + kC2;
-                const float sv = (A * B) / (Cc * D);
-                const float dmu = sv * (2.f * my / A - 2.f * mx / Cc);
-                const float dvar = -sv / D;
-                const float dcov = 2.f * sv / B;
-                g1 = dmu - 2.f * mx * dvar - my * dcov;
-                g2 = dvar;
-                g3 = dcov;
-                if (r >= kR && r < kR + kTY && q >= kR && q < kR + kTX) sm.St[r - kR][q - kR] = sv;
-            }
-            sm.G[0][r][q] = g1; sm.G[1][r][q] = g2; sm.G[2][r][q] = g3;
-        }
-        __syncthreads();
-        // 4. horizontal pass of G1..G3 (over the HM buffer)
-        for (int k = tid; k < kMY * kTX; k += 256) {
-            const int r = k / kTX, q = k - r * kTX;
-            float a[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-            for (int j = 0; j < kTaps; ++j) {
-                const float w = t.w[j];
-#pragma unroll
-                for (int u = 0; u < 3; ++u) a[u] = fmaf(w, sm.G[u][r][q + j], a[u]);
-            }
-            sm.HG[0][r][q] = a[0]; sm.HG[1][r][q] = a[1]; sm.HG[2][r][q] = a[2];
-        }
-        __syncthreads();
-        // 5. vertical pass onto the tile: gradient and the loss terms
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int k = tid + 256 * h;
-            const int r = k / kTX, q = k - r * kTX;
-            const int gy = y0 + r, gx = x0 + q;
-            if (gx >= V.W || gy >= V.H) continue;
-            float b[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-            for (int j = 0; j < kTaps; ++j) {
-                const float w = t.w[j];
-#pragma unroll
-                for (int u = 0; u < 3; ++u) b[u] = fmaf(w, sm.HG[u][r + j][q], b[u]);
-            }
-            const float x = sm.X[r + 2 * kR][q + 2 * kR], y = sm.Y[r + 2 * kR][q + 2 * kR];
-            const float d = x - y;
-            l1[h] += fabsf(d);
-            ss[h] += sm.St[r][q];
-            if (V.grad_color) {
-                const float dsum = b[0] + 2.f * x * b[1] + y * b[2];
-                const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-                const float gval = (t.lambda * sg - (1.f - t.lambda) * dsum) / (float)t.Co;
-                V.grad_color[((size_t)s * t.Co + c) * HW + (size_t)gy * V.W + gx] = t.scale * gval;
+        for (int i = 0; i < kLoads; ++i) {
+            const int k = tid + 256 * i;
+            if (k < kIX * kIY) {
+                const int r = k / kIX, q = k - r * kIX;
+                sm.X[r][q] = px[i];
+                sm.Y[r][q] = py[i];
             }
         }
+    };
+    load_regs(0);
+    store_regs();
+    __syncthreads();
+    for (int c = 0; c < t.Co; ++c) {
+        if (c + 1 < t.Co) load_regs(c + 1);
+        // 2. horizontal pass of the five moments, two neighbouring outputs
+        //    per thread sharing their window
+        for (int k = tid; k < kIY * (kMX / 2); k += 256) {
+            const int r = k / (kMX / 2), q = 2 * (k - r * (kMX / 2));
+            float a[2][5] = {};
+#pragma unroll
+            for (int j = 0; j <= kTaps; ++j) {
+                const float x = sm.X[r][q + j], y = sm.Y[r][q + j];
+                const float xx = x * x, yy = y * y, xy = x * y;
+#pragma unroll
+                for (int o = 0; o < 2; ++o) {
+                    const int tap = j - o;
+                    if (tap < 0 || tap >= kTaps) continue;
+                    const float w = t.w[tap];
+                    a[o][0] = fmaf(w, x, a[o][0]);
+                    a[o][1] = fmaf(w, y, a[o][1]);
+                    a[o][2] = fmaf(w, xx, a[o][2]);
+                    a[o][3] = fmaf(w, yy, a[o][3]);
+                    a[o][4] = fmaf(w, xy, a[o][4]);
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < 2; ++o)
+#pragma unroll
+                for (int u = 0; u < 5; ++u) sm.HM[u][r][q + o] = a[o][u];
+        }
         __syncthreads();
+        // 3. vertical pass (two rows per thread), ssim and its derivatives
+        //    w.r.t. the raw moments
+        for (int k = tid; k < (kMY / 2) * kMX; k += 256) {
+            const int rp = k / kMX, q = k - rp * kMX, r0 = 2 * rp;
+            float m[2][5] = {};
+#pragma unroll
+            for (int j = 0; j <= kTaps; ++j) {
+                float hv[5];
+#pragma unroll
+                for (int u = 0; u < 5; ++u) hv[u] = sm.HM[u][r0 + j][q];
+#pragma unroll
+                for (int o = 0; o < 2; ++o) {
+                    const int tap = j - o;
+                    if (tap < 0 || tap >= kTaps) continue;
+                    const float w = t.w[tap];
+#pragma unroll
+                    for (int u = 0; u < 5; ++u) m[o][u] = fmaf(w, hv[u], m[o][u]);
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < 2; ++o) {
+                const int r = r0 + o;
+                const int gy = y0 - kR + r, gx = x0 - kR + q;
+                float g1 = 0.f, g2 = 0.f, g3 = 0.f;
+                if (gx >= 0 && gx < V.W && gy >= 0 && gy < V.H) {
+                    const float mx = m[o][0], my = m[o][1];
+                    const float A = 2.f * mx * my + kC1;
+                    const float B = 2.f * (m[o][4] - mx * my) + kC2;
+                    const float Cc = mx * mx + my * my + kC1;
+                    const float D = (m[o][2] - mx * mx) + (m[o][3] - my * my) + kC2;
+                    // one reciprocal, 1/(Cc D)^2, gives ssim and its quotients by A, B, Cc, D
+                    const float ab = A * B, cd = Cc * D;
+                    const float inv = 1.0f / (cd * cd);
+                    const float ssim = ab * cd * inv;
+                    const float sA = B * cd * inv, sB = A * cd * inv;   // ssim / A, ssim / B
+                    const float sCc = ab * D * inv, sD = ab * Cc * inv;  // ssim / Cc, ssim / D
+                    const float dmu = 2.f * my * sA - 2.f * mx * sCc;
+                    const float dvar = -sD;
+                    const float dcov = 2.f * sB;
+                    g1 = dmu - 2.f * mx * dvar - my * dcov;
+                    g2 = dvar;
+                    g3 = dcov;
+                    if (r >= kR && r < kR + kTY && q >= kR && q < kR + kTX) sm.St[r - kR][q - kR] = ssim;
+                }
+                sm.G[0][r][q] = g1; sm.G[1][r][q] = g2; sm.G[2][r][q] = g3;
+            }
+        }
+        __syncthreads();
+        // 4. horizontal pass of G1..G3 (over the HM buffer), two outputs per thread
+        for (int k = tid; k < kMY * (kTX / 2); k += 256) {
+            const int r = k / (kTX / 2), q = 2 * (k - r * (kTX / 2));
+            float a[2][3] = {};
+#pragma unroll
+            for (int j = 0; j <= kTaps; ++j) {
+                float gv[3];
+#pragma unroll
+                for (int u = 0; u < 3; ++u) gv[u] = sm.G[u][r][q + j];
+#pragma unroll
+                for (int o = 0; o < 2; ++o) {
+                    const int tap = j - o;
+                    if (tap < 0 || tap >= kTaps) continue;
+                    const float w = t.w[tap];
+#pragma unroll
+                    for (int u = 0; u < 3; ++u) a[o][u] = fmaf(w, gv[u], a[o][u]);
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < 2; ++o)
+#pragma unroll
+                for (int u = 0; u < 3; ++u) sm.HG[u][r][q + o] = a[o][u];
+        }
+        __syncthreads();
+        // 5. vertical pass onto the tile (four rows of one column per thread):
+        //    gradient and the loss terms
+        {
+            const int q = tid % kTX, r0 = 4 * (tid / kTX);
+            float b[4][3] = {};
+#pragma unroll
+            for (int j = 0; j < kTaps + 3; ++j) {
+                float hv[3];
+#pragma unroll
+                for (int u = 0; u < 3; ++u) hv[u] = sm.HG[u][r0 + j][q];
+#pragma unroll
+                for (int o = 0; o < 4; ++o) {
+                    const int tap = j - o;
+                    if (tap < 0 || tap >= kTaps) continue;
+                    const float w = t.w[tap];
+#pragma unroll
+                    for (int u = 0; u < 3; ++u) b[o][u] = fmaf(w, hv[u], b[o][u]);
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                const int r = r0 + o;
+                const int gy = y0 + r, gx = x0 + q;
+                if (gx >= V.W || gy >= V.H) continue;
+                const float x = sm.X[r + 2 * kR][q + 2 * kR], y = sm.Y[r + 2 * kR][q + 2 * kR];
+                const float d = x - y;
+                l1[o] += fabsf(d);
+                ss[o] += sm.St[r][q];
+                if (V.grad_color) {
+                    const float dsum = b[o][0] + 2.f * x * b[o][1] + y * b[o][2];
+                    const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+                    const float gval = (t.lambda * sg - (1.f - t.lambda) * dsum) / (float)t.Co;
+                    V.grad_color[((size_t)s * t.Co + c) * HW + (size_t)gy * V.W + gx] = t.scale * gval;
+                }
+            }
+        }
+        __syncthreads();
+        if (c + 1 < t.Co) {
+            store_regs();
+            __syncthreads();
+        }
     }
     // per-pixel loss, score weight, total
     float acc = 0.f;
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int k = tid + 256 * h;
-        const int r = k / kTX, q = k - r * kTX;
+    for (int h = 0; h < 4; ++h) {
+        const int q = tid % kTX, r = 4 * (tid / kTX) + h;
         const int gy = y0 + r, gx = x0 + q;
         if (gx >= V.W || gy >= V.H) continue;
         const float ell = t.lambda * l1[h] / (float)t.Co + (1.f - t.lambda) * (1.f - ss[h] / (float)t.Co);

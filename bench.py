@@ -134,15 +134,17 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# The sources the tile kernels (forward, backward, edge) are compiled from.
+TILE_KERNEL_SOURCES = ("ds_backward.cu", "ds_common.cuh", "ds_raster.cu", "ds_tile.cuh")
+
+
 def _source_sha1() -> str:
-    """Hash of the CUDA sources (file name and contents, sorted by name)."""
-    import glob
+    """Hash of the tile kernels' sources (file name and contents, sorted by
+    name): the captured DRAM traffic is used only while it matches."""
     import hashlib
     h = hashlib.sha1()
     src = os.path.join(ROOT, "paper_2603_27151_gb300", "csrc")
-    for f in sorted(glob.glob(os.path.join(src, "*")), key=os.path.basename):
-        if not f.endswith((".cu", ".cuh", ".h")):
-            continue
+    for f in sorted(os.path.join(src, n) for n in TILE_KERNEL_SOURCES):
         h.update(os.path.basename(f).encode())
         h.update(b"\0")
         with open(f, "rb") as fh:
@@ -456,6 +458,60 @@ def _loss_optim_leg(wl, reps: int = 10):
                               "peak_kind": peak_kind},
             "what": "fused L1+SSIM loss with gradients and score weights (11x11 Gaussian, 7 channels); Adam on "
                     "the texture logits + VectorAdam on the vertices"}
+
+
+def widened_cases():
+    """One launch of each kernel of the widened rows on a case larger than L2
+    (for profiler captures; prints one check line, not a bench line): deferred
+    shading forward and backward of two 1920x1080 views at S = 4; the L1 +
+    SSIM loss of the same images (7 channels); the level composition
+    (standalone and inside the activation of a level soup, 20,000 triangles,
+    levels 2..5) and its adjoint; coverage counts of the 2-view G-buffers; one
+    Adam step of 36.9 M values."""
+    import numpy as np
+    import torch
+    from paper_2603_27151_gb300 import inputs as I
+    from paper_2603_27151_gb300 import native as N
+    from paper_2603_27151_gb300.shade import init_params
+    torch.cuda.set_device(0)
+    dev = "cuda"
+    cams = I.large_batch().cams[:2]
+    S = 4
+    ctx = N.Context(0)
+    gen = torch.Generator(device=dev).manual_seed(1)
+    feats = [torch.rand((S, 7, c.height, c.width), generator=gen, device=dev) for c in cams]
+    rgb = [torch.empty((S, 3, c.height, c.width), device=dev) for c in cams]
+    grgb = [torch.randn(r.shape, generator=gen, device=dev) for r in rgb]
+    gf = [torch.empty_like(f) for f in feats]
+    params = init_params(1)
+    gp = torch.empty_like(params)
+    ctx.shade_forward(cams, params, feats, rgb)
+    ctx.shade_backward(cams, params, feats, grgb, gf, gp, overwrite=True)
+    tg = [torch.rand((7, c.height, c.width), generator=gen, device=dev) for c in cams]
+    sw = [torch.empty((S, c.height, c.width), device=dev) for c in cams]
+    loss = torch.zeros(1, device=dev)
+    N.loss_l1_ssim(feats, tg, gf, sw, loss, scale=1.0 / S)
+    T, C = 20000, 8
+    lv = I.level_logits(T, 2, 5, C, np.random.default_rng(2))
+    tex = torch.from_numpy(np.concatenate([l.reshape(-1) for l in lv])).to(dev)
+    fine = torch.empty((T, N.level_V(5), C), device=dev)
+    N.levels_compose(tex, T, 2, 5, C, fine, activate=True)
+    verts = torch.from_numpy(I.box_soup(T, 0.05, np.random.default_rng(3))).to(dev)
+    sid = ctx.soup_upload_levels(verts, tex, T, 2, 5, C, borrow=True)
+    g, col, _ = N.alloc_outputs(cams, 1, C, dev)
+    ctx.raster_forward(sid, cams, None, 1, N.DS_MODE_THRESHOLD_HALF, np.zeros(C - 1, np.float32), g, col)
+    gcol = [torch.randn(c.shape, generator=gen, device=dev) for c in col]
+    gt = torch.empty_like(tex)
+    ctx.raster_backward(sid, cams, 1, g, col, gcol, None, N.DS_G_TEX | N.DS_REUSE_FORWARD | N.DS_OVERWRITE, None, gt)
+    counts = torch.zeros(T, dtype=torch.int32, device=dev)
+    N.coverage_count(g, T, counts)
+    x = torch.randn(36_900_000, generator=gen, device=dev)
+    gx = torch.randn(x.shape, generator=gen, device=dev)
+    m, v = torch.zeros_like(x), torch.zeros_like(x)
+    N.adam_step(x, gx, m, v, 0.05, 1)
+    torch.cuda.synchronize()
+    print("widened cases ok: loss %.6g, |grad params| %.6g, |grad levels| %.6g, coverage %d"
+          % (float(loss), float(gp.abs().sum()), float(gt.abs().sum()), int(counts.sum())))
 
 
 def _levels_leg(device: str, steps: int):
@@ -877,7 +933,12 @@ def main():
                     help="separate forward, loss and backward calls instead of the fused training pass")
     ap.add_argument("--tuning", default="", help="fixed launch parameters tile_w,depth_bits,blocks_per_sm,chunk")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--widened-cases", action="store_true",
+                    help="one launch of each widened-row kernel (profiler captures; not a bench line)")
     args = ap.parse_args()
+    if args.widened_cases:
+        widened_cases()
+        return
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     if args.impl == "reference":
         line = _reference_arm(args)

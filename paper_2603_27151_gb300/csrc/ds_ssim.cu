@@ -103,30 +103,35 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(const __grid_constant__ Ss
     for (int c = 0; c < t.Co; ++c) {
         if (c + 1 < t.Co) load_regs(c + 1);
         // 2. horizontal pass of the five moments, two neighbouring outputs
-        //    per thread sharing their window
+        //    per thread sharing their window (read and written as float2:
+        //    the pair starts at an even column)
         for (int k = tid; k < kIY * (kMX / 2); k += 256) {
             const int r = k / (kMX / 2), q = 2 * (k - r * (kMX / 2));
             float a[2][5] = {};
 #pragma unroll
-            for (int j = 0; j <= kTaps; ++j) {
-                const float x = sm.X[r][q + j], y = sm.Y[r][q + j];
-                const float xx = x * x, yy = y * y, xy = x * y;
+            for (int jj = 0; jj <= kTaps; jj += 2) {
+                const float2 x2 = *reinterpret_cast<const float2*>(&sm.X[r][q + jj]);
+                const float2 y2 = *reinterpret_cast<const float2*>(&sm.Y[r][q + jj]);
 #pragma unroll
-                for (int o = 0; o < 2; ++o) {
-                    const int tap = j - o;
-                    if (tap < 0 || tap >= kTaps) continue;
-                    const float w = t.w[tap];
-                    a[o][0] = fmaf(w, x, a[o][0]);
-                    a[o][1] = fmaf(w, y, a[o][1]);
-                    a[o][2] = fmaf(w, xx, a[o][2]);
-                    a[o][3] = fmaf(w, yy, a[o][3]);
-                    a[o][4] = fmaf(w, xy, a[o][4]);
+                for (int h = 0; h < 2; ++h) {
+                    const int j = jj + h;
+                    const float x = h ? x2.y : x2.x, y = h ? y2.y : y2.x;
+                    const float xx = x * x, yy = y * y, xy = x * y;
+#pragma unroll
+                    for (int o = 0; o < 2; ++o) {
+                        const int tap = j - o;
+                        if (tap < 0 || tap >= kTaps) continue;
+                        const float w = t.w[tap];
+                        a[o][0] = fmaf(w, x, a[o][0]);
+                        a[o][1] = fmaf(w, y, a[o][1]);
+                        a[o][2] = fmaf(w, xx, a[o][2]);
+                        a[o][3] = fmaf(w, yy, a[o][3]);
+                        a[o][4] = fmaf(w, xy, a[o][4]);
+                    }
                 }
             }
 #pragma unroll
-            for (int o = 0; o < 2; ++o)
-#pragma unroll
-                for (int u = 0; u < 5; ++u) sm.HM[u][r][q + o] = a[o][u];
+            for (int u = 0; u < 5; ++u) *reinterpret_cast<float2*>(&sm.HM[u][r][q]) = make_float2(a[0][u], a[1][u]);
         }
         __syncthreads();
         // 3. vertical pass (two rows per thread), ssim and its derivatives
@@ -177,28 +182,31 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(const __grid_constant__ Ss
             }
         }
         __syncthreads();
-        // 4. horizontal pass of G1..G3 (over the HM buffer), two outputs per thread
+        // 4. horizontal pass of G1..G3 (over the HM buffer), two outputs per
+        //    thread (float2 reads and writes)
         for (int k = tid; k < kMY * (kTX / 2); k += 256) {
             const int r = k / (kTX / 2), q = 2 * (k - r * (kTX / 2));
             float a[2][3] = {};
 #pragma unroll
-            for (int j = 0; j <= kTaps; ++j) {
-                float gv[3];
+            for (int jj = 0; jj <= kTaps; jj += 2) {
+                float2 g2[3];
 #pragma unroll
-                for (int u = 0; u < 3; ++u) gv[u] = sm.G[u][r][q + j];
+                for (int u = 0; u < 3; ++u) g2[u] = *reinterpret_cast<const float2*>(&sm.G[u][r][q + jj]);
 #pragma unroll
-                for (int o = 0; o < 2; ++o) {
-                    const int tap = j - o;
-                    if (tap < 0 || tap >= kTaps) continue;
-                    const float w = t.w[tap];
+                for (int h = 0; h < 2; ++h) {
+                    const int j = jj + h;
 #pragma unroll
-                    for (int u = 0; u < 3; ++u) a[o][u] = fmaf(w, gv[u], a[o][u]);
+                    for (int o = 0; o < 2; ++o) {
+                        const int tap = j - o;
+                        if (tap < 0 || tap >= kTaps) continue;
+                        const float w = t.w[tap];
+#pragma unroll
+                        for (int u = 0; u < 3; ++u) a[o][u] = fmaf(w, h ? g2[u].y : g2[u].x, a[o][u]);
+                    }
                 }
             }
 #pragma unroll
-            for (int o = 0; o < 2; ++o)
-#pragma unroll
-                for (int u = 0; u < 3; ++u) sm.HG[u][r][q + o] = a[o][u];
+            for (int u = 0; u < 3; ++u) *reinterpret_cast<float2*>(&sm.HG[u][r][q]) = make_float2(a[0][u], a[1][u]);
         }
         __syncthreads();
         // 5. vertical pass onto the tile (four rows of one column per thread):

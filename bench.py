@@ -514,6 +514,43 @@ def widened_cases():
           % (float(loss), float(gp.abs().sum()), float(gt.abs().sum()), int(counts.sum())))
 
 
+def _paper_step_leg(device: str, steps: int):
+    """The paper's full training step through the library (paper_step.py):
+    a level soup (100,000 triangles, levels 2..5), 4 views of 1920x1080 per
+    step drawn from the batch's 8 cameras, S = 1, deferred shading, L1 + SSIM
+    against RGB targets, both backward passes, VectorAdam + Adam.  Timed with
+    CUDA events over ``steps`` steps after 2 warm-up steps."""
+    import numpy as np
+    import torch
+    from paper_2603_27151_gb300 import inputs as I
+    from paper_2603_27151_gb300.paper_step import PaperStep
+    sc = I.large_batch()
+    cams = [c for c in sc.cams if c.width == 1920]
+    T, C, r_min, r_max = sc.T, 8, 2, 5
+    lv = I.level_logits(T, r_min, r_max, C, np.random.default_rng(14))
+    verts = torch.from_numpy(sc.verts).to(device)
+    tex = torch.from_numpy(np.concatenate([l.reshape(-1) for l in lv])).to(device)
+    del lv
+    gen = torch.Generator(device=device).manual_seed(17)
+    targets = [torch.rand((3, c.height, c.width), generator=gen, device=device) for c in cams]
+    st = PaperStep(verts, tex, T, r_min, r_max, C, cams, targets, S=1, per_step=4, total_steps=10_000)
+    losses = [st.step() for _ in range(2)]
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        losses.append(st.step())
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    st.close()
+    return {"ms_per_step": ms, "steps_per_s": 1e3 / ms, "views_per_step": 4, "triangles": T, "levels": [r_min, r_max],
+            "loss_first": losses[0], "loss_last": losses[-1],
+            "what": "forward (level composition in the activation) + deferred shading + L1/SSIM + shading and "
+                    "rasteriser backward + VectorAdam/Adam; 4 x 1920x1080 views, S = 1; the step reads its loss "
+                    "back to the host"}
+
+
 def _levels_leg(device: str, steps: int):
     """The 1080p batch with a multi-resolution texture: levels 2..5 (the last
     stage of the coarse-to-fine schedule; finest grid 32 subdivisions, 561
@@ -812,6 +849,8 @@ def _gpu_arm(args):
         del wl
         torch.cuda.empty_cache()
         line["levels"] = _levels_leg(dev, max(5, args.steps // 4))
+        torch.cuda.empty_cache()
+        line["paper_step"] = _paper_step_leg(dev, max(5, args.steps // 4))
         torch.cuda.empty_cache()
         line["train"] = _train_leg(dev, args.train_iters)
         torch.cuda.empty_cache()

@@ -179,12 +179,25 @@ __global__ void __launch_bounds__(256) k_restrict(const double* __restrict__ fin
         }
     }
     {
+        // the finest level: eight loads in flight per thread before they are used
         const double* src = fine + (size_t)t * Vf * C;
         float* dst = out + off[r_max - r_min] + (size_t)t * Vf * C;
-        for (int k = threadIdx.x; k < Vf * C; k += blockDim.x) {
-            const double g = src[k];
-            A[k] = (float)g;
-            dst[k] = overwrite ? (float)g : (float)((double)dst[k] + g);
+        const int n = Vf * C;
+        for (int k0 = threadIdx.x; k0 < n; k0 += 8 * blockDim.x) {
+            double g[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int k = k0 + u * blockDim.x;
+                g[u] = k < n ? __ldcs(src + k) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int k = k0 + u * blockDim.x;
+                if (k < n) {
+                    A[k] = (float)g[u];
+                    dst[k] = overwrite ? (float)g[u] : (float)((double)dst[k] + g[u]);
+                }
+            }
         }
     }
     __syncthreads();

@@ -243,7 +243,7 @@ class Workload:
         self.ctx.status()
 
     def algorithmic_bytes(self):
-        """Minimum HBM bytes each stage must move per launch."""
+        """Minimum HBM bytes each stage must move per launch (the algorithmic bytes of the roofline)."""
         sc, S = self.sc, self.S
         T, V, C = sc.tex.shape
         Co = C - 1

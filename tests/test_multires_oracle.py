@@ -9,7 +9,9 @@ or_resample) against facts that do not come from the oracle itself:
   - level 0 is the triangle's three vertices: barycentric interpolation;
   - the finest level alone is the identity; constant levels add up;
   - or_restrict is the adjoint of or_compose (dyadic data: exact in FP32);
-  - resampling up then down returns the grid."""
+  - resampling up then down returns the grid;
+  - the coarse-to-fine accumulation equals the direct sum of the levels
+    interpolated at the finest vertices (or_resample) up to FP32 rounding."""
 import numpy as np
 import pytest
 
@@ -109,3 +111,15 @@ def test_resample_up_then_down_is_identity():
     assert np.array_equal(O.resample(up, 4, 2), g)
     coef = np.array([[0.5, 0.25, -1.0]] * 3)
     assert np.array_equal(O.resample(_affine(1, 2, 3, coef), 1, 3), _affine(3, 2, 3, coef))
+
+
+def test_coarse_to_fine_accumulation_equals_the_direct_sum():
+    """The composition accumulates coarse to fine (prolongation + level); it
+    equals the direct definition -- each level interpolated at the finest
+    vertices, summed -- up to FP32 rounding."""
+    rng = np.random.default_rng(11)
+    for r_min, r_max in [(0, 5), (2, 5), (1, 3)]:
+        lv = [rng.normal(size=(3, O.level_V(R), 5)).astype(np.float32) for R in range(r_min, r_max + 1)]
+        direct = sum(O.resample(l, R, r_max).astype(np.float64) for R, l in zip(range(r_min, r_max + 1), lv))
+        got = O.compose(lv, r_min, r_max)
+        assert np.allclose(got, direct, rtol=0, atol=2e-6 * (r_max - r_min + 1)), (r_min, r_max)

@@ -163,11 +163,13 @@ DS_API ds_status ds_soup_free(ds_ctx* ctx, int32_t soup_id);
  * (2^R+1)(2^R+2)/2 feature vertices (level 0: the three triangle vertices).
  * tex_levels holds levels r_min..r_max one after the other, level R as
  * [T][V_R][C] logits.  The soup renders the finest grid (grid_n = 2^r_max)
- * whose logits are the sum over the levels, in ascending order in FP32, of
- * each level at the finest grid's vertex: the level vertex that coincides
- * with it, else barycentric interpolation in the level's micro-triangle that
- * contains it; the sigmoid follows (the composition runs inside the
- * activation step).  Every other call treats the soup like one registered
+ * whose logits are the sum over the levels of each level interpolated at the
+ * finest grid's vertices (barycentric interpolation in the level's
+ * micro-triangles), accumulated coarse to fine in FP32: z_(r_min) = level
+ * r_min, z_R = P(z_(R-1)) + level R, with P the 2x prolongation (a vertex
+ * that coincides with a coarser one takes its value, an edge midpoint
+ * fmaf(0.5, z_q - z_p, z_p), p the endpoint of lower index); the sigmoid
+ * follows (the composition runs inside the activation step).  Every other call treats the soup like one registered
  * with ds_soup_upload(grid_n = 2^r_max), except that grad_tex of the
  * backward passes has the layout of tex_levels: the gradient of each level
  * (the adjoint of the composition runs inside the gradient finish step).

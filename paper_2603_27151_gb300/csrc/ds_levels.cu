@@ -6,11 +6,12 @@
 // stored one after the other, level R as [T][V_R][C].  The texture that is
 // rasterised is the finest grid (N = 2^r_max) whose logits are the sum of all
 // levels evaluated at its vertices, then the sigmoid:
-//  - k_compose (fused into the activation step): one thread per (triangle,
-//    finest vertex), all C channels; a vertex that coincides with a level
-//    vertex takes its value, any other point is interpolated in the level's
-//    micro-triangle containing it (the decode's cell and arithmetic), levels
-//    summed in ascending order in FP32;
+//  - k_compose (fused into the activation step): one CTA per triangle.  The
+//    level-R function is piecewise linear on level R+1's mesh (same diagonal
+//    orientation), so the levels are accumulated coarse to fine in shared
+//    memory, z_R = P(z_(R-1)) + level R, P the 2x prolongation (the
+//    coinciding vertex or a coarse edge's midpoint value), FP32 in the
+//    oracle's order; the finest level goes straight to the sigmoid;
 //  - k_restrict (fused into the gradient finish step): the adjoint.  The
 //    level-R function is piecewise linear on level R+1's mesh (same diagonal
 //    orientation), so the composition is a chain of 2x prolongations and its
@@ -50,112 +51,106 @@ __device__ __forceinline__ float level_value(const float* __restrict__ g, int R,
                   cl.wa, cl.wb);
 }
 
-// Where the level-R grid is read for vertex (i, j) of the finest grid
-// (N = 2^r_max > N_R): a coinciding vertex (direct) or a micro-triangle.
-struct LevelTap {
-    Cell cl;
-    bool direct;
-};
+// Prolongation of channel c of the level grid z (N/2 subdivisions) to vertex
+// (i, j) of the N-subdivided grid: the coinciding vertex, or the midpoint
+// value fmaf(0.5, z_q - z_p, z_p) of the coarse edge the vertex bisects (p =
+// the endpoint with the lower texel index).
+__device__ __forceinline__ void prolong_taps(int Nc, int i, int j, int& p, int& q) {
+    const int a = i >> 1, b = j >> 1;
+    if (!(i & 1) && !(j & 1)) { p = q = texel_index(Nc, a, b); }
+    else if ((i & 1) && !(j & 1)) { p = texel_index(Nc, a, b); q = texel_index(Nc, a + 1, b); }
+    else if (!(i & 1)) { p = texel_index(Nc, a, b); q = texel_index(Nc, a, b + 1); }
+    else { p = texel_index(Nc, a + 1, b); q = texel_index(Nc, a, b + 1); }
+}
 
-__device__ __forceinline__ LevelTap level_tap(int R, int i, int j, int N) {
-    const int NR = 1 << R, s = N / NR;
-    LevelTap tp;
-    tp.direct = (i % s == 0) && (j % s == 0);
-    if (tp.direct) {
-        tp.cl.k0 = tp.cl.k1 = tp.cl.k2 = texel_index(NR, i / s, j / s);
-        tp.cl.wa = tp.cl.wb = 0.f;
-        tp.cl.lower = true;
-    } else {
-        // i / N by the exact power-of-two reciprocal: the same value as the division
-        const float inv = __int_as_float((127 - __ffs(N) + 1) << 23);
-        tp.cl = find_cell(NR, __fmul_rn((float)i, inv), __fmul_rn((float)j, inv));
+__device__ __forceinline__ float prolong(float zp, float zq, bool coincide) {
+    return coincide ? zp : __fmaf_rn(0.5f, __fsub_rn(zq, zp), zp);
+}
+
+// One CTA per triangle.  The coarse levels are accumulated coarse to fine in
+// shared memory (z_R = P(z_(R-1)) + level R, FP32 in the oracle's order); the
+// finest level is formed on the fly and written as the composed logits, or
+// their sigmoid with the planar opacity copy.  Items are (vertex, group of
+// four channels) when vec (C % 4 == 0 and 16-byte aligned levels and
+// output), else (vertex, channel).
+template <bool kAct>
+__global__ void __launch_bounds__(256) k_compose(const float* __restrict__ levels, int T, int r_min, int r_max, int C,
+                                                 int vec, float* __restrict__ out, float* __restrict__ act_a) {
+    extern __shared__ __align__(16) float zs[];   // two buffers of V_(r_max - 1) * C
+    const int t = blockIdx.x;
+    const int Vc = r_max > 0 ? level_V(r_max - 1) : 1;
+    float* cur = zs;
+    float* nxt = zs + (size_t)Vc * C;
+    const int per = vec ? C / 4 : C;              // items per vertex
+    size_t off = 0;
+    // z_(r_min) = level r_min (only when a coarser level feeds a finer one)
+    if (r_min < r_max) {
+        const float* g = levels + (size_t)t * level_V(r_min) * C;
+        for (int k = threadIdx.x; k < level_V(r_min) * C; k += blockDim.x) cur[k] = __ldg(g + k);
     }
-    return tp;
-}
-
-__device__ __forceinline__ float tap_value(const float* __restrict__ g, const LevelTap& tp, int C, int c) {
-    const float a0 = __ldg(g + (size_t)tp.cl.k0 * C + c);
-    if (tp.direct) return a0;
-    return interp(a0, __ldg(g + (size_t)tp.cl.k1 * C + c), __ldg(g + (size_t)tp.cl.k2 * C + c), tp.cl.wa, tp.cl.wb);
-}
-
-__device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
-
-__device__ __forceinline__ float4 add4(float4 a, float4 b) {
-    return make_float4(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y), __fadd_rn(a.z, b.z), __fadd_rn(a.w, b.w));
-}
-
-// Four consecutive channels c..c+3 of a level at a tap (same arithmetic as
-// tap_value, channel by channel).
-__device__ __forceinline__ float4 tap_value4(const float* __restrict__ g, const LevelTap& tp, int C, int c) {
-    const float4 a0 = ld4(g + (size_t)tp.cl.k0 * C + c);
-    if (tp.direct) return a0;
-    const float4 a1 = ld4(g + (size_t)tp.cl.k1 * C + c), a2 = ld4(g + (size_t)tp.cl.k2 * C + c);
-    const float wa = tp.cl.wa, wb = tp.cl.wb;
-    return make_float4(interp(a0.x, a1.x, a2.x, wa, wb), interp(a0.y, a1.y, a2.y, wa, wb),
-                       interp(a0.z, a1.z, a2.z, wa, wb), interp(a0.w, a1.w, a2.w, wa, wb));
-}
-
-// NL = r_max - r_min coarser levels below the finest.  kAct: act =
-// sigmoid(composed logits) (+ the planar opacity copy); else the composed
-// logits themselves.  kVec: C % 4 == 0 and 16-byte aligned levels and output:
-// channels move as float4.
-template <int NL, bool kAct, bool kVec>
-__global__ void __launch_bounds__(256) k_compose(const float* __restrict__ levels, int T, int r_max, int C,
-                                                 float* __restrict__ out, float* __restrict__ act_a) {
-    const int r_min = r_max - NL;
-    const int Nf = 1 << r_max, Vf = level_V(r_max);
-    // (i, j) of every finest vertex, packed i | j << 8
-    __shared__ unsigned short ij_of[level_V(5)];
-    for (int v = threadIdx.x; v < Vf; v += blockDim.x) {
-        int i, j;
-        texel_ij(Nf, v, i, j);
-        ij_of[v] = (unsigned short)(i | (j << 8));
-    }
+    off += (size_t)T * level_V(r_min) * C;
     __syncthreads();
-    const long long n = (long long)T * Vf;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n; q += stride) {
-        const int t = (int)(q / Vf), v = (int)(q - (long long)t * Vf);
-        const int i = ij_of[v] & 0xff, j = ij_of[v] >> 8;
-        LevelTap tp[NL > 0 ? NL : 1];
-        const float* g[NL + 1];
-        size_t off = 0;
-#pragma unroll
-        for (int k = 0; k <= NL; ++k) {
-            const int R = r_min + k;
-            g[k] = levels + off + (size_t)t * level_V(R) * C;
-            if (k < NL) tp[k] = level_tap(R, i, j, Nf);
-            off += (size_t)T * level_V(R) * C;
-        }
-        float* o = out + (size_t)q * C;
-        if (kVec) {
-            for (int c = 0; c < C; c += 4) {
-                float4 z = NL > 0 ? tap_value4(g[0], tp[0], C, c) : ld4(g[0] + (size_t)v * C + c);
-#pragma unroll
-                for (int k = 1; k < NL; ++k) z = add4(z, tap_value4(g[k], tp[k], C, c));
-                if (NL > 0) z = add4(z, ld4(g[NL] + (size_t)v * C + c));
-                if (kAct) {
-                    z = make_float4(pinned_sigmoid(z.x), pinned_sigmoid(z.y), pinned_sigmoid(z.z), pinned_sigmoid(z.w));
-                    if (c + 4 == C && act_a) act_a[q] = z.w;
-                }
-                *reinterpret_cast<float4*>(o + c) = z;
-            }
-        } else {
-            for (int c = 0; c < C; ++c) {
-                float z = NL > 0 ? tap_value(g[0], tp[0], C, c) : __ldg(g[0] + (size_t)v * C + c);
-#pragma unroll
-                for (int k = 1; k < NL; ++k) z = __fadd_rn(z, tap_value(g[k], tp[k], C, c));
-                if (NL > 0) z = __fadd_rn(z, __ldg(g[NL] + (size_t)v * C + c));
-                if (kAct) {
-                    const float a = pinned_sigmoid(z);
-                    o[c] = a;
-                    if (c == C - 1 && act_a) act_a[q] = a;
+    for (int R = r_min + 1; R <= r_max; ++R) {
+        const int N = 1 << R, V = level_V(R);
+        const float* g = levels + off + (size_t)t * V * C;
+        const bool last = R == r_max;
+        for (int it = threadIdx.x; it < V * per; it += blockDim.x) {
+            const int v = it / per, cg = it - v * per;
+            int i, j, p, q;
+            texel_ij(N, v, i, j);
+            prolong_taps(N >> 1, i, j, p, q);
+            const bool co = p == q;
+            if (vec) {
+                const int c = 4 * cg;
+                const float4 zp = *reinterpret_cast<const float4*>(cur + (size_t)p * C + c);
+                const float4 zq = *reinterpret_cast<const float4*>(cur + (size_t)q * C + c);
+                const float4 th = __ldg(reinterpret_cast<const float4*>(g + (size_t)v * C + c));
+                float4 z = make_float4(__fadd_rn(prolong(zp.x, zq.x, co), th.x), __fadd_rn(prolong(zp.y, zq.y, co), th.y),
+                                       __fadd_rn(prolong(zp.z, zq.z, co), th.z), __fadd_rn(prolong(zp.w, zq.w, co), th.w));
+                if (!last) {
+                    *reinterpret_cast<float4*>(nxt + (size_t)v * C + c) = z;
                 } else {
-                    o[c] = z;
+                    if (kAct) {
+                        z = make_float4(pinned_sigmoid(z.x), pinned_sigmoid(z.y), pinned_sigmoid(z.z),
+                                        pinned_sigmoid(z.w));
+                        if (c + 4 == C && act_a) act_a[(size_t)t * V + v] = z.w;
+                    }
+                    *reinterpret_cast<float4*>(out + ((size_t)t * V + v) * C + c) = z;
+                }
+            } else {
+                const int c = cg;
+                float z = __fadd_rn(prolong(cur[(size_t)p * C + c], cur[(size_t)q * C + c], co),
+                                    __ldg(g + (size_t)v * C + c));
+                if (!last) {
+                    nxt[(size_t)v * C + c] = z;
+                } else {
+                    if (kAct) {
+                        z = pinned_sigmoid(z);
+                        if (c == C - 1 && act_a) act_a[(size_t)t * V + v] = z;
+                    }
+                    out[((size_t)t * V + v) * C + c] = z;
                 }
             }
         }
+        off += (size_t)T * V * C;
+        __syncthreads();
+        float* tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+}
+
+// A single level (r_min == r_max): the level itself (or its sigmoid).
+template <bool kAct>
+__global__ void __launch_bounds__(256) k_compose_single(const float* __restrict__ g, long long n, int C,
+                                                        float* __restrict__ out, float* __restrict__ act_a) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        float z = __ldg(g + k);
+        if (kAct) {
+            z = pinned_sigmoid(z);
+            if (act_a && k % C == C - 1) act_a[k / C] = z;
+        }
+        out[k] = z;
     }
 }
 
@@ -257,30 +252,21 @@ size_t level_floats(int T, int r_min, int r_max, int C) {
     return n;
 }
 
-template <int NL>
-void compose_nl(const float* levels, int T, int r_max, int C, float* out, bool act, float* act_a, int g,
-                cudaStream_t st) {
-    const bool vec = C % 4 == 0 && (uintptr_t)levels % 16 == 0 && (uintptr_t)out % 16 == 0;
-    if (act && vec)
-        k_compose<NL, true, true><<<g, 256, 0, st>>>(levels, T, r_max, C, out, act_a);
-    else if (act)
-        k_compose<NL, true, false><<<g, 256, 0, st>>>(levels, T, r_max, C, out, act_a);
-    else if (vec)
-        k_compose<NL, false, true><<<g, 256, 0, st>>>(levels, T, r_max, C, out, nullptr);
-    else
-        k_compose<NL, false, false><<<g, 256, 0, st>>>(levels, T, r_max, C, out, nullptr);
-}
-
 cudaError_t launch_compose(const float* levels, int T, int r_min, int r_max, int C, float* out, bool act,
                            float* act_a, cudaStream_t st) {
-    const int g = flat_grid((long long)T * level_V(r_max));
-    switch (r_max - r_min) {
-        case 0: compose_nl<0>(levels, T, r_max, C, out, act, act_a, g, st); break;
-        case 1: compose_nl<1>(levels, T, r_max, C, out, act, act_a, g, st); break;
-        case 2: compose_nl<2>(levels, T, r_max, C, out, act, act_a, g, st); break;
-        case 3: compose_nl<3>(levels, T, r_max, C, out, act, act_a, g, st); break;
-        case 4: compose_nl<4>(levels, T, r_max, C, out, act, act_a, g, st); break;
-        default: compose_nl<5>(levels, T, r_max, C, out, act, act_a, g, st); break;
+    if (r_min == r_max) {
+        const long long n = (long long)T * level_V(r_max) * C;
+        if (act)
+            k_compose_single<true><<<flat_grid(n), 256, 0, st>>>(levels, n, C, out, act_a);
+        else
+            k_compose_single<false><<<flat_grid(n), 256, 0, st>>>(levels, n, C, out, nullptr);
+    } else {
+        const size_t smem = sizeof(float) * 2 * (size_t)level_V(r_max - 1) * C;
+        const int vec = (C % 4 == 0) && ((uintptr_t)levels % 16 == 0) && ((uintptr_t)out % 16 == 0);
+        if (act)
+            k_compose<true><<<T, 256, smem, st>>>(levels, T, r_min, r_max, C, vec, out, act_a);
+        else
+            k_compose<false><<<T, 256, smem, st>>>(levels, T, r_min, r_max, C, vec, out, nullptr);
     }
     note_launches(1);
     return cudaGetLastError();

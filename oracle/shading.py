@@ -24,12 +24,12 @@ Parameters are one flat vector of 595 values: W1 [16][16] (row = output),
 b1 [16], W2 [16][16], b2 [16], W3 [3][16], b3 [3].
 
 Pins (tests/test_shading_oracle.py): SH orthonormality by quadrature on the
-sphere; the principal ray is the camera's forward axis; blend special cases
-(A = 1 gives the feature colour, A = 0 the MLP colour, zero weights give
-sigmoid(b3)); one-hot layer probes (operand order); ReLU rescaling
-invariance; the backward against central differences of the forward.  Parity
-unpinned: the SH sign convention and the direction frame are conventions
-(a sign flip is absorbed by the first layer's weights).
+sphere; the SH basis equals the real harmonics built from SciPy's complex
+ones (Condon-Shortley phase: every constant, sign and the order); the
+principal ray is the camera's forward axis; blend special cases (A = 1 gives
+the feature colour, A = 0 the MLP colour, zero weights give sigmoid(b3));
+one-hot layer probes (operand order); ReLU rescaling invariance; the
+backward against central differences of the forward.
 """
 from __future__ import annotations
 

@@ -124,3 +124,26 @@ def test_backward_matches_central_differences():
         e = np.zeros_like(p); e[k] = h
         fd = (loss(f, p + e) - loss(f, p - e)) / (2 * h)
         assert abs(fd - gp[k]) <= 1e-6 * max(1.0, abs(fd)), k
+
+
+def test_sh_basis_is_the_real_basis_with_the_condon_shortley_phase():
+    """The oracle's basis equals the real spherical harmonics built from
+    SciPy's complex ones (which carry the Condon-Shortley phase):
+    Y_l0, sqrt(2) Re Y_l^m for m > 0, sqrt(2) Im Y_l^|m| for m < 0 -- this fixes
+    every constant, sign and the order (m = -l..l)."""
+    sp = pytest.importorskip("scipy.special")
+    if not hasattr(sp, "sph_harm_y"):
+        pytest.skip("scipy.special.sph_harm_y not available")
+    rng = np.random.default_rng(3)
+    d = rng.normal(size=(64, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    theta, phi = np.arccos(d[:, 2]), np.arctan2(d[:, 1], d[:, 0])
+
+    def real_sh(l, m):
+        if m == 0:
+            return sp.sph_harm_y(l, 0, theta, phi).real
+        if m > 0:
+            return math.sqrt(2.0) * sp.sph_harm_y(l, m, theta, phi).real
+        return math.sqrt(2.0) * sp.sph_harm_y(l, -m, theta, phi).imag
+    ref = np.stack([real_sh(l, m) for l in range(3) for m in range(-l, l + 1)], -1)
+    assert np.allclose(SH.sh2(d), ref, atol=1e-12)

@@ -42,3 +42,29 @@ def test_gradient_matches_central_differences():
         e = np.zeros_like(x); e[idx] = h
         fd = (SS.loss(x + e, y)[0].sum() - SS.loss(x - e, y)[0].sum()) / (2 * h)
         assert abs(fd - g[idx]) <= 1e-6 * max(1.0, abs(fd)), (idx, fd, g[idx])
+
+
+def test_ssim_map_against_a_direct_window_sum():
+    """At single pixels (corners, edges, interior) the map equals the SSIM
+    formula evaluated with an explicit 11x11 Gaussian-weighted sum over the
+    zero-padded neighbourhood (no separable passes)."""
+    rng = np.random.default_rng(4)
+    x = rng.uniform(0, 1, (1, 17, 23))
+    y = rng.uniform(0, 1, (1, 17, 23))
+    w1 = SS.window1d()
+    w2 = np.outer(w1, w1)
+    s = SS.ssim_map(x, y)[0]
+    for (r, c) in [(0, 0), (16, 22), (0, 11), (8, 0), (8, 11), (3, 19)]:
+        m = {k: 0.0 for k in ("x", "y", "xx", "yy", "xy")}
+        for dr in range(-5, 6):
+            for dc in range(-5, 6):
+                rr, cc = r + dr, c + dc
+                if 0 <= rr < 17 and 0 <= cc < 23:
+                    a, b, w = x[0, rr, cc], y[0, rr, cc], w2[dr + 5, dc + 5]
+                    m["x"] += w * a; m["y"] += w * b
+                    m["xx"] += w * a * a; m["yy"] += w * b * b; m["xy"] += w * a * b
+        vx, vy = m["xx"] - m["x"] ** 2, m["yy"] - m["y"] ** 2
+        cov = m["xy"] - m["x"] * m["y"]
+        ref = ((2 * m["x"] * m["y"] + SS.C1) * (2 * cov + SS.C2)) / \
+            ((m["x"] ** 2 + m["y"] ** 2 + SS.C1) * (vx + vy + SS.C2))
+        assert abs(s[r, c] - ref) <= 1e-12, (r, c)

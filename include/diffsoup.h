@@ -334,6 +334,16 @@ DS_API ds_status ds_edge_ratios(const float* verts, int32_t T, const ds_camera* 
 DS_API ds_status ds_adapt_plan(const int32_t* counts, const float* ratios, int32_t T, float threshold,
                                int64_t budget, int32_t* plan, int32_t* n_out);
 
+/* ds_adapt_plan_fill (host only): one round of the random-initialisation
+ *  procedure (supplementary "Random Triangle Soup Initialization"): the
+ *  triangles with no coverage in any training image (counts[t] <= 0) are
+ *  removed; then, while fewer than `target` remain, the survivors whose
+ *  longest edge has the largest ratio (lower index first among equal ones)
+ *  split that edge, each at most once per round (repeat rounds, re-measuring,
+ *  to grow further).  Plan codes and capacity as ds_adapt_plan. */
+DS_API ds_status ds_adapt_plan_fill(const int32_t* counts, const float* ratios, int32_t T, int64_t target,
+                                    int32_t* plan, int32_t* n_out);
+
 /* ds_soup_rebuild: the soup after a plan.  verts [T][3][3] and tex (levels
  *  back to back, level l = [T][V_l][C] with V_l = (N_l+1)(N_l+2)/2, N_l =
  *  grid_ns[l] (host [n_levels]); one level for a plain soup) -> verts_out

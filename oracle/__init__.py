@@ -238,6 +238,36 @@ def adapt_plan(counts, ratios, threshold: float, budget: int):
     return np.array(plan, np.int32)
 
 
+def adapt_plan_fill(counts, ratios, target: int):
+    """The random-initialisation procedure (supplementary "Random Triangle
+    Soup Initialization") as one round: triangles with no coverage in any
+    training image are removed; then, while fewer than ``target`` remain,
+    the survivors with the longest edges (largest ratio; lower index first
+    among equal ones) split that edge, each at most once per round.  Plan
+    codes as adapt_plan."""
+    ratios = np.asarray(ratios, np.float32)
+    T = len(counts)
+    keep = [t for t in range(T) if int(counts[t]) > 0]
+    longest = {}
+    for t in keep:
+        e = 0
+        for k in (1, 2):
+            if ratios[t, k] > ratios[t, e]:
+                e = k
+        longest[t] = e
+    n_split = max(0, min(int(target) - len(keep), len(keep)))
+    order = sorted(keep, key=lambda t: (-float(ratios[t, longest[t]]), t))
+    split = set(order[:n_split])
+    plan = []
+    for t in keep:
+        if t in split:
+            e = longest[t]
+            plan += [(t << 3) | (1 + 2 * e), (t << 3) | (2 + 2 * e)]
+        else:
+            plan.append(t << 3)
+    return np.array(plan, np.int32)
+
+
 def soup_rebuild(verts, levels, r_min: int, r_max: int, plan):
     """(verts_out [n, 3, 3], levels_out) of a split/prune plan (or_soup_rebuild)."""
     v = _c(verts, np.float32)

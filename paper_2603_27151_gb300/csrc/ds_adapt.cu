@@ -10,7 +10,9 @@
 //    height; FP32 in the oracle's order, so that the split decision is the
 //    same on both sides.
 //  - the plan (host C++): split the longest edge above the threshold, then
-//    remove the lowest-coverage triangles until the budget holds.
+//    remove the lowest-coverage triangles until the budget holds; or, for
+//    the random initialisation of the supplementary material, remove the
+//    uncovered triangles and split the longest edges up to a target count.
 //  - k_rebuild_verts / k_rebuild_level: the new soup: copies, or the two
 //    children of a split edge (midpoint in FP32), each child's grid sampled
 //    from the parent's grid at the child's vertices mapped into the parent.
@@ -265,6 +267,40 @@ int adapt_plan(const int32_t* counts, const float* ratios, int T, float threshol
         } else {
             plan[k++] = (t << 3) | (1 + 2 * split[t]);
             plan[k++] = (t << 3) | (2 + 2 * split[t]);
+        }
+    }
+    return k;
+}
+
+// The random-initialisation round (host): remove the triangles no training
+// image covers, then split the longest edges of the survivors with the
+// largest ratios (each once) until the target count is reached.
+int adapt_plan_fill(const int32_t* counts, const float* ratios, int T, long long target, int32_t* plan) {
+    std::vector<int> keep;
+    std::vector<int8_t> longest(T, 0);
+    for (int t = 0; t < T; ++t) {
+        if (counts[t] <= 0) continue;
+        keep.push_back(t);
+        int e = 0;
+        for (int k = 1; k < 3; ++k)
+            if (ratios[3 * (size_t)t + k] > ratios[3 * (size_t)t + e]) e = k;
+        longest[t] = (int8_t)e;
+    }
+    long long want = target - (long long)keep.size();
+    const size_t n_split = want <= 0 ? 0 : (size_t)std::min<long long>(want, (long long)keep.size());
+    std::vector<int> order(keep);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return ratios[3 * (size_t)a + longest[a]] > ratios[3 * (size_t)b + longest[b]];
+    });
+    std::vector<char> split(T, 0);
+    for (size_t k = 0; k < n_split; ++k) split[order[k]] = 1;
+    int k = 0;
+    for (int t : keep) {
+        if (split[t]) {
+            plan[k++] = (t << 3) | (1 + 2 * longest[t]);
+            plan[k++] = (t << 3) | (2 + 2 * longest[t]);
+        } else {
+            plan[k++] = t << 3;
         }
     }
     return k;

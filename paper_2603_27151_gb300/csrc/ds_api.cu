@@ -1152,6 +1152,14 @@ ds_status ds_adapt_plan(const int32_t* counts, const float* ratios, int32_t T, f
     return DS_OK;
 }
 
+ds_status ds_adapt_plan_fill(const int32_t* counts, const float* ratios, int32_t T, int64_t target, int32_t* plan,
+                             int32_t* n_out) {
+    if (!counts || !ratios || !plan || !n_out) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    if (T < 1 || T >= DS_MAX_TRIANGLES / 2) return fail(DS_ERR_INVALID_ARG, "T out of range");
+    *n_out = ds::adapt_plan_fill(counts, ratios, T, (long long)target, plan);
+    return DS_OK;
+}
+
 ds_status ds_soup_rebuild(ds_ctx* c, const float* verts, const float* tex, int32_t T, const int32_t* grid_ns,
                           int32_t n_levels, int32_t C, const int32_t* plan, int32_t n_out, float* verts_out,
                           float* tex_out, void* stream) {

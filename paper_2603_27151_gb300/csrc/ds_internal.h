@@ -113,6 +113,7 @@ cudaError_t launch_edge_ratios(const float* verts, int T, const ds_camera* cams,
 cudaError_t launch_rebuild(const float* verts, const float* tex, int T, const int* grid_ns, int n_levels, int C,
                            const int* plan_dev, int n_out, float* verts_out, float* tex_out, cudaStream_t st);
 int adapt_plan(const int32_t* counts, const float* ratios, int T, float threshold, long long budget, int32_t* plan);
+int adapt_plan_fill(const int32_t* counts, const float* ratios, int T, long long target, int32_t* plan);
 
 // Adam / VectorAdam step (ds_optim.cu): dim consecutive values share one
 // second moment; t is the 1-based step count.

@@ -156,6 +156,8 @@ def load():
     L.ds_adapt_plan.argtypes = [P, P, i32, ctypes.c_float, ctypes.c_int64, P, ctypes.POINTER(i32)]
     L.ds_adapt_plan.restype = i32
     L.ds_soup_rebuild.argtypes = [P, P, P, i32, P, i32, i32, P, i32, P, P, P]
+    L.ds_adapt_plan_fill.argtypes = [P, P, i32, ctypes.c_int64, P, ctypes.POINTER(i32)]
+    L.ds_adapt_plan_fill.restype = i32
     L.ds_soup_rebuild.restype = i32
     L.ds_adam_step.argtypes = [P, P, P, P, ctypes.c_int64, i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                ctypes.c_float, ctypes.c_int64, P]
@@ -590,6 +592,20 @@ def _check_images(colors, targets, grad_colors, score_ws):
             if tuple(t.shape) != shape or t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
                 raise ValueError("view %d: expected a contiguous float32 CUDA tensor of shape %s, got %s"
                                  % (v, shape, tuple(t.shape)))
+
+
+def adapt_plan_fill(counts, ratios, target: int) -> np.ndarray:
+    """One round of the random-initialisation procedure (ds_adapt_plan_fill,
+    host only): remove uncovered triangles, split the longest edges up to
+    ``target`` triangles."""
+    c = np.ascontiguousarray(counts, np.int32)
+    r = np.ascontiguousarray(ratios, np.float32)
+    T = len(c)
+    plan = np.empty(2 * T, np.int32)
+    n = ctypes.c_int32(0)
+    _check(load().ds_adapt_plan_fill(c.ctypes.data_as(ctypes.c_void_p), r.ctypes.data_as(ctypes.c_void_p), T,
+                                     int(target), plan.ctypes.data_as(ctypes.c_void_p), ctypes.byref(n)))
+    return plan[:n.value].copy()
 
 
 def loss_l2(colors, targets, grad_colors=None, score_ws=None, loss=None, scale=1.0, stream=None):

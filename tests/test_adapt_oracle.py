@@ -125,3 +125,31 @@ def test_library_plan_equals_the_oracle_plan():
         ratios = (rng.integers(0, 8, size=(T, 3)) / 20.0).astype(np.float32)   # many ties
         got = N.adapt_plan(counts, ratios, 0.2, budget)
         assert np.array_equal(got, O.adapt_plan(counts, ratios, 0.2, budget)), (T, budget)
+
+
+def test_fill_plan_rules():
+    """Random-initialisation round: uncovered triangles go, then the longest
+    edges of the survivors split until the target count is reached."""
+    counts = np.array([4, 0, 2, 9, 1])
+    ratios = np.array([[0.1, 0.4, 0.2], [0.9, 0.0, 0.0], [0.3, 0.3, 0.1], [0.05, 0.0, 0.0], [0.4, 0.1, 0.0]],
+                      np.float32)
+    # survivors 0, 2, 3, 4 (4); target 6: split the two longest (0: 0.4 on edge 1, 4: 0.4 on edge 0; ties by index)
+    p = O.adapt_plan_fill(counts, ratios, 6)
+    assert list(p) == [0 << 3 | 3, 0 << 3 | 4, 2 << 3, 3 << 3, 4 << 3 | 1, 4 << 3 | 2]
+    # target below the survivors: only the removal
+    assert list(O.adapt_plan_fill(counts, ratios, 2)) == [0 << 3, 2 << 3, 3 << 3, 4 << 3]
+    # target far above: every survivor splits once (edge 0 of triangle 2: first of equal maxima)
+    p = O.adapt_plan_fill(counts, ratios, 100)
+    assert len(p) == 8 and list(p[2:4]) == [2 << 3 | 1, 2 << 3 | 2]
+
+
+def test_library_fill_plan_equals_the_oracle():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2603_27151_gb300 import native as N
+    rng = np.random.default_rng(5)
+    for T, target in [(1, 5), (50, 60), (200, 150), (300, 1000), (64, 64)]:
+        counts = rng.integers(0, 3, size=T)
+        ratios = (rng.integers(0, 6, size=(T, 3)) / 10.0).astype(np.float32)
+        got = N.adapt_plan_fill(counts, ratios, target)
+        assert np.array_equal(got, O.adapt_plan_fill(counts, ratios, target)), (T, target)

@@ -22,7 +22,8 @@ Eq. 9, which needs a per-pixel loss value):
 Pins (tests/test_ssim_oracle.py): SSIM(x, x) = 1 and zero loss; symmetry;
 the closed form for constant images away from the border; the window sums
 to 1 and is separable; the map against an explicit 11 x 11 window sum at
-border and interior pixels; the gradient against central differences.
+border and interior pixels; the closed form for x = k y with Wang et al.'s
+constants; the gradient against central differences.
 """
 from __future__ import annotations
 

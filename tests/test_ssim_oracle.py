@@ -68,3 +68,18 @@ def test_ssim_map_against_a_direct_window_sum():
         ref = ((2 * m["x"] * m["y"] + SS.C1) * (2 * cov + SS.C2)) / \
             ((m["x"] ** 2 + m["y"] ** 2 + SS.C1) * (vx + vy + SS.C2))
         assert abs(s[r, c] - ref) <= 1e-12, (r, c)
+
+
+def test_scaled_images_closed_form_with_the_published_constants():
+    """x = k y: SSIM = (2k mu^2 + C1)(2k s^2 + C2) / (((k^2+1) mu^2 + C1)((k^2+1) s^2 + C2))
+    with mu, s^2 the windowed mean and variance of y and Wang et al.'s constants
+    C1 = (0.01 L)^2, C2 = (0.03 L)^2 for the data range L = 1 (written here, not
+    read from the oracle)."""
+    rng = np.random.default_rng(6)
+    y = rng.uniform(0, 1, (1, 24, 24))
+    k = 0.7
+    mu = SS.blur(y)
+    var = SS.blur(y * y) - mu * mu
+    c1, c2 = (0.01 * 1.0) ** 2, (0.03 * 1.0) ** 2
+    ref = (2 * k * mu * mu + c1) * (2 * k * var + c2) / (((k * k + 1) * mu * mu + c1) * ((k * k + 1) * var + c2))
+    assert np.allclose(SS.ssim_map(k * y, y), ref, rtol=1e-12)

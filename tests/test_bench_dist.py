@@ -51,3 +51,31 @@ def test_two_gloo_ranks_aggregate_like_the_bench():
     assert all(o[3] == 15.0 for o in out)                       # the slowest rank's time on every rank
     assert all(abs(o[4] - 1000.0 * 4 * 2 / 0.015) < 1e-6 * o[4] for o in out)
     assert out[1][5] is None                                    # rank 1 runs no reference work
+
+
+def test_traffic_lookup_scales_and_checks_the_source_hash(tmp_path, monkeypatch):
+    """The DRAM traffic of the committed capture is scaled to a launch by its
+    pixel-samples, and withheld (null) once the tile kernels' sources differ
+    from the captured ones."""
+    import importlib.util
+    import json
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(root, "bench.py"))
+    B = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(B)
+    d = json.load(open(os.path.join(root, "profiles", "dram_traffic.json")))
+    assert d["source_sha1"] == B._source_sha1()       # the committed capture matches the committed kernels
+    got = B._traffic("raster_bwd", 2 * d["pixel_samples"])
+    assert got == 2 * d["bytes"]["raster_bwd"]
+    assert B._traffic("no_such_kernel", 1) is None
+    # a copy of the tree whose tile kernel differs: no traffic
+    fake = tmp_path / "repo"
+    (fake / "profiles").mkdir(parents=True)
+    (fake / "paper_2603_27151_gb300" / "csrc").mkdir(parents=True)
+    for n in B.TILE_KERNEL_SOURCES:
+        src = open(os.path.join(root, "paper_2603_27151_gb300", "csrc", n), "rb").read()
+        (fake / "paper_2603_27151_gb300" / "csrc" / n).write_bytes(src + (b"// changed\n" if n == "ds_raster.cu" else b""))
+    (fake / "profiles" / "dram_traffic.json").write_text(json.dumps(d))
+    monkeypatch.setattr(B, "ROOT", str(fake))
+    assert B._traffic("raster_bwd", d["pixel_samples"]) is None

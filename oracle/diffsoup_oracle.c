@@ -33,6 +33,10 @@
  *                             sum of the resampled levels)
  *   or_restrict ............. pinned (adjoint identity with or_compose, hat mass)
  *   or_resample ............. pinned (up then down is the identity, affine data)
+ *   or_coverage ............. pinned (brute-force count)
+ *   or_edge_ratios .......... pinned (pinhole closed form, view selection)
+ *   or_soup_rebuild ......... pinned (copy plan = identity; children carry the
+ *                             parent's affine field, area and winding)
  */
 #include <math.h>
 #include <stdint.h>

@@ -29,8 +29,8 @@
  *                             "parity unpinned" (the paper prints no formula).
  *   or_expected ............. pinned (finite differences; Monte Carlo of or_forward)
  *   or_compose .............. pinned (affine reproduction, closed-form hat function,
- *                             level-0 barycentrics, identity, constants, the direct
- *                             sum of the resampled levels)
+ *                             level-0 barycentrics, identity, constants, the FP64 sum
+ *                             of the levels' hat-function expansions)
  *   or_restrict ............. pinned (adjoint identity with or_compose, hat mass)
  *   or_resample ............. pinned (up then down is the identity, affine data)
  *   or_coverage ............. pinned (brute-force count)
@@ -842,53 +842,31 @@ static float o_level_value(const float* g, int R, int C, int c, int i, int j, in
 
 /* Composed logits of the finest grid (Sec. 3.3: every lower-resolution grid
  * is queried and accumulated on the finest grid before rendering, then the
- * sigmoid is applied).  The level-R grid interpolated at the vertices of
- * level R+1 is the same piecewise-linear function (the micro-triangles of
- * level R+1 subdivide those of level R with the same diagonals), so the sum
- * of the levels at the finest vertices is accumulated coarse to fine, in
- * FP32:  z_(r_min) = level r_min;  z_R = P(z_(R-1)) + level R, where the
- * prolongation P takes the coinciding vertex of z_(R-1) at an even vertex
- * (2a, 2b) and the midpoint value fmaf(0.5, z_q - z_p, z_p) of the level-R-1
- * edge it bisects otherwise (p = the endpoint with the lower texel index:
- * (a, b) for (2a+1, 2b) and (2a, 2b+1); (a+1, b) for (2a+1, 2b+1), whose edge
- * joins (a+1, b) and (a, b+1)). */
-static float o_prolong(const float* z, int Nc, int C, int c, int i, int j)
-{
-    const int a = i >> 1, b = j >> 1;
-    int p, q;
-    if (!(i & 1) && !(j & 1)) return z[(size_t)o_texel(Nc, a, b) * C + c];
-    if ((i & 1) && !(j & 1)) { p = o_texel(Nc, a, b); q = o_texel(Nc, a + 1, b); }
-    else if (!(i & 1)) { p = o_texel(Nc, a, b); q = o_texel(Nc, a, b + 1); }
-    else { p = o_texel(Nc, a + 1, b); q = o_texel(Nc, a, b + 1); }
-    const float zp = z[(size_t)p * C + c], zq = z[(size_t)q * C + c];
-    return fmaf(0.5f, zq - zp, zp);
-}
-
+ * sigmoid is applied).  fine[t][v][c] is the sum over R = r_min..r_max, in
+ * that order, in FP32, of level R read at vertex v = (i, j) of the finest
+ * grid (barycentrics (1-(i+j)/N, i/N, j/N), N = 2^r_max) as o_level_value
+ * reads it: the coinciding level vertex, else the decode's interpolation in
+ * the level's micro-triangle.  The finest level contributes its own value. */
 void or_compose(const float* levels, int32_t T, int32_t r_min, int32_t r_max, int32_t C, float* fine)
 {
+    const int Nf = 1 << r_max;
     const size_t Vf = o_level_V(r_max);
-    float* cur = (float*)malloc(sizeof(float) * Vf * C);
-    float* nxt = (float*)malloc(sizeof(float) * Vf * C);
-    for (int t = 0; t < T; ++t) {
-        size_t off = 0;
-        memcpy(cur, levels + (size_t)t * o_level_V(r_min) * C, sizeof(float) * o_level_V(r_min) * C);
-        off += (size_t)T * o_level_V(r_min) * C;
-        for (int R = r_min + 1; R <= r_max; ++R) {
-            const int N = 1 << R;
-            const float* g = levels + off + (size_t)t * o_level_V(R) * C;
-            for (int j = 0; j <= N; ++j)
-                for (int i = 0; i + j <= N; ++i) {
-                    const int v = o_texel(N, i, j);
-                    for (int c = 0; c < C; ++c)
-                        nxt[(size_t)v * C + c] = o_prolong(cur, N / 2, C, c, i, j) + g[(size_t)v * C + c];
+    for (int t = 0; t < T; ++t)
+        for (int j = 0; j <= Nf; ++j)
+            for (int i = 0; i + j <= Nf; ++i) {
+                const int v = o_texel(Nf, i, j);
+                for (int c = 0; c < C; ++c) {
+                    float z = 0.0f;
+                    size_t off = 0;
+                    for (int R = r_min; R <= r_max; ++R) {
+                        const float* g = levels + off + (size_t)t * o_level_V(R) * C;
+                        const float val = o_level_value(g, R, C, c, i, j, Nf);
+                        z = R == r_min ? val : z + val;
+                        off += (size_t)T * o_level_V(R) * C;
+                    }
+                    fine[((size_t)t * Vf + v) * C + c] = z;
                 }
-            float* tmp = cur; cur = nxt; nxt = tmp;
-            off += (size_t)T * o_level_V(R) * C;
-        }
-        memcpy(fine + (size_t)t * Vf * C, cur, sizeof(float) * Vf * C);
-    }
-    free(cur);
-    free(nxt);
+            }
 }
 
 /* Adjoint of or_compose in FP64: the gradient of each level's values given

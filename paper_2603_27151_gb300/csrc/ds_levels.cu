@@ -6,12 +6,13 @@
 // stored one after the other, level R as [T][V_R][C].  The texture that is
 // rasterised is the finest grid (N = 2^r_max) whose logits are the sum of all
 // levels evaluated at its vertices, then the sigmoid:
-//  - k_compose (fused into the activation step): one CTA per triangle.  The
-//    level-R function is piecewise linear on level R+1's mesh (same diagonal
-//    orientation), so the levels are accumulated coarse to fine in shared
-//    memory, z_R = P(z_(R-1)) + level R, P the 2x prolongation (the
-//    coinciding vertex or a coarse edge's midpoint value), FP32 in the
-//    oracle's order; the finest level goes straight to the sigmoid;
+//  - k_compose (fused into the activation step): one CTA per triangle.  All
+//    of the triangle's levels are staged in shared memory (vector loads, all
+//    in flight together); each finest vertex then sums, coarsest level
+//    first in FP32, the value of every level at its position (the
+//    coinciding level vertex, or the decode's interpolation in the level's
+//    micro-triangle), as the oracle does; the finest level adds its own
+//    value, and the sum goes straight to the sigmoid;
 //  - k_restrict (fused into the gradient finish step): the adjoint.  The
 //    level-R function is piecewise linear on level R+1's mesh (same diagonal
 //    orientation), so the composition is a chain of 2x prolongations and its
@@ -51,92 +52,99 @@ __device__ __forceinline__ float level_value(const float* __restrict__ g, int R,
                   cl.wa, cl.wb);
 }
 
-// Prolongation of channel c of the level grid z (N/2 subdivisions) to vertex
-// (i, j) of the N-subdivided grid: the coinciding vertex, or the midpoint
-// value fmaf(0.5, z_q - z_p, z_p) of the coarse edge the vertex bisects (p =
-// the endpoint with the lower texel index).
-__device__ __forceinline__ void prolong_taps(int Nc, int i, int j, int& p, int& q) {
-    const int a = i >> 1, b = j >> 1;
-    if (!(i & 1) && !(j & 1)) { p = q = texel_index(Nc, a, b); }
-    else if ((i & 1) && !(j & 1)) { p = texel_index(Nc, a, b); q = texel_index(Nc, a + 1, b); }
-    else if (!(i & 1)) { p = texel_index(Nc, a, b); q = texel_index(Nc, a, b + 1); }
-    else { p = texel_index(Nc, a + 1, b); q = texel_index(Nc, a, b + 1); }
-}
-
-__device__ __forceinline__ float prolong(float zp, float zq, bool coincide) {
-    return coincide ? zp : __fmaf_rn(0.5f, __fsub_rn(zq, zp), zp);
-}
-
-// One CTA per triangle.  The coarse levels are accumulated coarse to fine in
-// shared memory (z_R = P(z_(R-1)) + level R, FP32 in the oracle's order); the
-// finest level is formed on the fly and written as the composed logits, or
-// their sigmoid with the planar opacity copy.  Items are (vertex, group of
-// four channels) when vec (C % 4 == 0 and 16-byte aligned levels and
-// output), else (vertex, channel).
-template <bool kAct>
-__global__ void __launch_bounds__(256) k_compose(const float* __restrict__ levels, int T, int r_min, int r_max, int C,
-                                                 int vec, float* __restrict__ out, float* __restrict__ act_a) {
-    extern __shared__ __align__(16) float zs[];   // two buffers of V_(r_max - 1) * C
-    const int t = blockIdx.x;
-    const int Vc = r_max > 0 ? level_V(r_max - 1) : 1;
-    float* cur = zs;
-    float* nxt = zs + (size_t)Vc * C;
-    const int per = vec ? C / 4 : C;              // items per vertex
-    size_t off = 0;
-    // z_(r_min) = level r_min (only when a coarser level feeds a finer one)
-    if (r_min < r_max) {
-        const float* g = levels + (size_t)t * level_V(r_min) * C;
-        for (int k = threadIdx.x; k < level_V(r_min) * C; k += blockDim.x) cur[k] = __ldg(g + k);
+// Value of the level-R grid zl ([V_R][C] in shared memory, channels c..c+3
+// when kVec) at vertex (i, j) of the finest grid (Nf = 2^r_max
+// subdivisions): the coinciding vertex, or the decode's interpolation in the
+// micro-triangle that holds barycentrics (i / Nf, j / Nf) (exact: Nf is a
+// power of two).
+template <bool kVec>
+__device__ __forceinline__ float4 level_at(const float* zl, int R, int C, int c, int i, int j, int Nf, int r_max) {
+    const int NR = 1 << R, sh = r_max - R, m = (1 << sh) - 1;
+    if (!(i & m) && !(j & m)) {
+        const float* p = zl + (size_t)texel_index(NR, i >> sh, j >> sh) * C + c;
+        return kVec ? *reinterpret_cast<const float4*>(p) : make_float4(*p, 0.f, 0.f, 0.f);
     }
-    off += (size_t)T * level_V(r_min) * C;
-    __syncthreads();
-    for (int R = r_min + 1; R <= r_max; ++R) {
-        const int N = 1 << R, V = level_V(R);
-        const float* g = levels + off + (size_t)t * V * C;
-        const bool last = R == r_max;
-        for (int it = threadIdx.x; it < V * per; it += blockDim.x) {
-            const int v = it / per, cg = it - v * per;
-            int i, j, p, q;
-            texel_ij(N, v, i, j);
-            prolong_taps(N >> 1, i, j, p, q);
-            const bool co = p == q;
-            if (vec) {
-                const int c = 4 * cg;
-                const float4 zp = *reinterpret_cast<const float4*>(cur + (size_t)p * C + c);
-                const float4 zq = *reinterpret_cast<const float4*>(cur + (size_t)q * C + c);
-                const float4 th = __ldg(reinterpret_cast<const float4*>(g + (size_t)v * C + c));
-                float4 z = make_float4(__fadd_rn(prolong(zp.x, zq.x, co), th.x), __fadd_rn(prolong(zp.y, zq.y, co), th.y),
-                                       __fadd_rn(prolong(zp.z, zq.z, co), th.z), __fadd_rn(prolong(zp.w, zq.w, co), th.w));
-                if (!last) {
-                    *reinterpret_cast<float4*>(nxt + (size_t)v * C + c) = z;
-                } else {
-                    if (kAct) {
-                        z = make_float4(pinned_sigmoid(z.x), pinned_sigmoid(z.y), pinned_sigmoid(z.z),
-                                        pinned_sigmoid(z.w));
-                        if (c + 4 == C && act_a) act_a[(size_t)t * V + v] = z.w;
-                    }
-                    *reinterpret_cast<float4*>(out + ((size_t)t * V + v) * C + c) = z;
-                }
+    const float inv = __frcp_rn((float)Nf);   // exact power of two
+    const Cell cl = find_cell(NR, __fmul_rn((float)i, inv), __fmul_rn((float)j, inv));
+    const float* p0 = zl + (size_t)cl.k0 * C + c;
+    const float* p1 = zl + (size_t)cl.k1 * C + c;
+    const float* p2 = zl + (size_t)cl.k2 * C + c;
+    if (kVec) {
+        const float4 a0 = *reinterpret_cast<const float4*>(p0);
+        const float4 a1 = *reinterpret_cast<const float4*>(p1);
+        const float4 a2 = *reinterpret_cast<const float4*>(p2);
+        return make_float4(interp(a0.x, a1.x, a2.x, cl.wa, cl.wb), interp(a0.y, a1.y, a2.y, cl.wa, cl.wb),
+                           interp(a0.z, a1.z, a2.z, cl.wa, cl.wb), interp(a0.w, a1.w, a2.w, cl.wa, cl.wb));
+    }
+    return make_float4(interp(*p0, *p1, *p2, cl.wa, cl.wb), 0.f, 0.f, 0.f);
+}
+
+__device__ __forceinline__ float4 add4(float4 a, float4 b) {
+    return make_float4(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y), __fadd_rn(a.z, b.z), __fadd_rn(a.w, b.w));
+}
+
+// Floats of one triangle's levels r_min..r_max (the shared-memory stage).
+__host__ __device__ inline int stage_floats(int r_min, int r_max, int C) {
+    int n = 0;
+    for (int R = r_min; R <= r_max; ++R) n += level_V(R) * C;
+    return n;
+}
+
+// One CTA per triangle.  Stage the triangle's levels in shared memory, then
+// for every (finest vertex, channel group) sum the levels' values at the
+// vertex from the coarsest up (FP32, the oracle's order) and write the
+// composed logits, or their sigmoid with the planar opacity copy.  kVec:
+// groups of four channels (C % 4 == 0, 16-byte aligned levels and output),
+// else one channel per item.
+template <bool kAct, bool kVec>
+__global__ void __launch_bounds__(256) k_compose(const float* __restrict__ levels, int T, int r_min, int r_max, int C,
+                                                 float* __restrict__ out, float* __restrict__ act_a) {
+    extern __shared__ __align__(16) float zs[];   // levels r_min..r_max of triangle t, one after the other
+    const int t = blockIdx.x;
+    {
+        size_t off = 0;   // offset of level R in `levels`
+        int so = 0;       // offset of level R in zs
+        for (int R = r_min; R <= r_max; ++R) {
+            const int n = level_V(R) * C;
+            const float* g = levels + off + (size_t)t * n;
+            if (kVec) {
+                for (int k = threadIdx.x; k < n / 4; k += blockDim.x)
+                    reinterpret_cast<float4*>(zs + so)[k] = __ldcs(reinterpret_cast<const float4*>(g) + k);
             } else {
-                const int c = cg;
-                float z = __fadd_rn(prolong(cur[(size_t)p * C + c], cur[(size_t)q * C + c], co),
-                                    __ldg(g + (size_t)v * C + c));
-                if (!last) {
-                    nxt[(size_t)v * C + c] = z;
-                } else {
-                    if (kAct) {
-                        z = pinned_sigmoid(z);
-                        if (c == C - 1 && act_a) act_a[(size_t)t * V + v] = z;
-                    }
-                    out[((size_t)t * V + v) * C + c] = z;
-                }
+                for (int k = threadIdx.x; k < n; k += blockDim.x) zs[so + k] = __ldcs(g + k);
             }
+            off += (size_t)T * n;
+            so += n;
         }
-        off += (size_t)T * V * C;
-        __syncthreads();
-        float* tmp = cur;
-        cur = nxt;
-        nxt = tmp;
+    }
+    __syncthreads();
+    const int Nf = 1 << r_max, Vf = level_V(r_max);
+    const int per = kVec ? C / 4 : C;   // items per vertex
+    for (int it = threadIdx.x; it < Vf * per; it += blockDim.x) {
+        const int v = it / per, c = (it - v * per) * (kVec ? 4 : 1);
+        int i, j;
+        texel_ij(Nf, v, i, j);
+        float4 z = level_at<kVec>(zs, r_min, C, c, i, j, Nf, r_max);
+        int so = level_V(r_min) * C;
+        for (int R = r_min + 1; R <= r_max; ++R) {
+            z = add4(z, level_at<kVec>(zs + so, R, C, c, i, j, Nf, r_max));
+            so += level_V(R) * C;
+        }
+        float* o = out + ((size_t)t * Vf + v) * C + c;
+        if (kVec) {
+            if (kAct) {
+                z = make_float4(pinned_sigmoid(z.x), pinned_sigmoid(z.y), pinned_sigmoid(z.z), pinned_sigmoid(z.w));
+                if (c + 4 == C && act_a) act_a[(size_t)t * Vf + v] = z.w;
+            }
+            __stcs(reinterpret_cast<float4*>(o), z);
+        } else {
+            float y = z.x;
+            if (kAct) {
+                y = pinned_sigmoid(y);
+                if (c == C - 1 && act_a) act_a[(size_t)t * Vf + v] = y;
+            }
+            *o = y;
+        }
     }
 }
 
@@ -261,12 +269,20 @@ cudaError_t launch_compose(const float* levels, int T, int r_min, int r_max, int
         else
             k_compose_single<false><<<flat_grid(n), 256, 0, st>>>(levels, n, C, out, nullptr);
     } else {
-        const size_t smem = sizeof(float) * 2 * (size_t)level_V(r_max - 1) * C;
-        const int vec = (C % 4 == 0) && ((uintptr_t)levels % 16 == 0) && ((uintptr_t)out % 16 == 0);
+        const size_t smem = sizeof(float) * (size_t)stage_floats(r_min, r_max, C);
+        const bool vec = (C % 4 == 0) && ((uintptr_t)levels % 16 == 0) && ((uintptr_t)out % 16 == 0);
+        auto run = [&](auto kernel) {
+            cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            kernel<<<T, 256, smem, st>>>(levels, T, r_min, r_max, C, out, act ? act_a : nullptr);
+            return cudaSuccess;
+        };
+        cudaError_t e;
         if (act)
-            k_compose<true><<<T, 256, smem, st>>>(levels, T, r_min, r_max, C, vec, out, act_a);
+            e = vec ? run(k_compose<true, true>) : run(k_compose<true, false>);
         else
-            k_compose<false><<<T, 256, smem, st>>>(levels, T, r_min, r_max, C, vec, out, nullptr);
+            e = vec ? run(k_compose<false, true>) : run(k_compose<false, false>);
+        if (e != cudaSuccess) return e;
     }
     note_launches(1);
     return cudaGetLastError();

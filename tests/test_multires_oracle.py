@@ -10,8 +10,9 @@ or_resample) against facts that do not come from the oracle itself:
   - the finest level alone is the identity; constant levels add up;
   - or_restrict is the adjoint of or_compose (dyadic data: exact in FP32);
   - resampling up then down returns the grid;
-  - the coarse-to-fine accumulation equals the direct sum of the levels
-    interpolated at the finest vertices (or_resample) up to FP32 rounding."""
+  - random levels compose to the FP64 sum of their closed-form hat-function
+    expansions, to FP32 rounding, and the FP32 sum runs from the coarsest
+    level up."""
 import numpy as np
 import pytest
 
@@ -113,13 +114,35 @@ def test_resample_up_then_down_is_identity():
     assert np.array_equal(O.resample(_affine(1, 2, 3, coef), 1, 3), _affine(3, 2, 3, coef))
 
 
-def test_coarse_to_fine_accumulation_equals_the_direct_sum():
-    """The composition accumulates coarse to fine (prolongation + level); it
-    equals the direct definition -- each level interpolated at the finest
-    vertices, summed -- up to FP32 rounding."""
+def _hat_expansion(g, R, r_max):
+    """Level-R grid g [T][V_R][C] evaluated at the finest vertices as the sum
+    of its values times their closed-form hat functions (FP64, independent
+    of the oracle's cell search and interpolation)."""
+    n, nf = 1 << R, 1 << r_max
+    x = _ij(r_max) * (n / nf)                     # finest vertices in level-R units
+    u = _ij(R)
+    dx = x[:, None, 0] - u[None, :, 0]
+    dy = x[:, None, 1] - u[None, :, 1]
+    hat = np.maximum(0.0, 1.0 - np.maximum(np.maximum(np.abs(dx), np.abs(dy)), np.abs(dx + dy)))
+    return np.einsum("fu,tuc->tfc", hat, g.astype(np.float64))
+
+
+def test_compose_is_the_sum_of_the_levels_hat_expansions():
+    """Random levels: every composed value equals the FP64 sum over the levels
+    of their hat-function expansions at that vertex, to FP32 rounding (a
+    skipped level, a wrong cell or corner, or a transposed weight fails)."""
     rng = np.random.default_rng(11)
-    for r_min, r_max in [(0, 5), (2, 5), (1, 3)]:
+    for r_min, r_max in [(0, 5), (2, 5), (1, 3), (0, 2)]:
         lv = [rng.normal(size=(3, O.level_V(R), 5)).astype(np.float32) for R in range(r_min, r_max + 1)]
-        direct = sum(O.resample(l, R, r_max).astype(np.float64) for R, l in zip(range(r_min, r_max + 1), lv))
+        ref = sum(_hat_expansion(l, R, r_max) for R, l in zip(range(r_min, r_max + 1), lv))
         got = O.compose(lv, r_min, r_max)
-        assert np.allclose(got, direct, rtol=0, atol=2e-6 * (r_max - r_min + 1)), (r_min, r_max)
+        assert np.allclose(got, ref, rtol=0, atol=4e-7 * (r_max - r_min + 1) * 4), (r_min, r_max)
+
+
+def test_compose_sums_in_level_order():
+    """The levels are added in FP32 from the coarsest up: 1 + 2^-24 rounds to
+    1 (ties to even), and so does the next 2^-24, whereas summing the two
+    small levels first would give 1 + 2^-23."""
+    lv = [np.full((1, O.level_V(R), 1), v, np.float32) for R, v in zip(range(1, 4), (1.0, 2.0 ** -24, 2.0 ** -24))]
+    got = O.compose(lv, 1, 3)
+    assert np.all(got == np.float32(1.0))

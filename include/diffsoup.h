@@ -438,12 +438,16 @@ DS_API ds_status ds_loss_l1_ssim(int32_t n_views, int32_t S, int32_t C, const in
  * n_views*T <= 65536, at most 65536 16x16 tiles over all views.  The number
  * of (tile, triangle) pairs is known only after binning; the call reads it
  * back (one synchronisation of `stream`) and returns DS_ERR_CAPACITY above
- * 524288 pairs.  The first call on each device looks up the array's device
- * address with that device current; make that first call before any stream
- * capture.  Every call in the process shares the one array and leaves its
- * contents behind (the call clears what must start at zero): calls whose work
- * overlaps on the GPU, from several streams or host threads, race and must be
- * serialised by the caller. */
+ * 524288 pairs; every call therefore synchronises `stream` once.  The
+ * first call on each device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  Every
+ * call in the process shares the one array and leaves its contents behind
+ * (the call clears what must start at zero): calls whose work overlaps on the
+ * GPU, from several streams or host threads, race and must be serialised by
+ * the caller.  `mode` is DS_MODE_STOCHASTIC or DS_MODE_THRESHOLD_HALF without
+ * flag bits (DS_NO_SYNC is rejected).  Inputs and outputs must be device (or
+ * managed) memory of the current device, which the call checks with
+ * cudaPointerGetAttributes; anything else returns DS_ERR_INVALID_ARG. */
 DS_API ds_status ds_raster_forward_noalloc(const float* verts, const float* tex, int32_t T,
                                            int32_t grid_n, int32_t C, const ds_camera* cams,
                                            const uint64_t* seeds, int32_t n_views, int32_t S,

@@ -89,6 +89,11 @@ struct Plan {
     int n_tiles = 0;
 };
 
+}  // namespace
+
+namespace ds {
+void report_error(const std::string& msg) { g_err = msg; }
+
 bool finite_cam(const ds_camera& c) {
     const float* f = &c.fx;
     for (int i = 0; i < 17; ++i)
@@ -96,12 +101,9 @@ bool finite_cam(const ds_camera& c) {
     return c.fx != 0.f && c.fy != 0.f && c.near_z > 0.f && c.width >= 1 && c.height >= 1 &&
            c.width <= DS_MAX_RESOLUTION && c.height <= DS_MAX_RESOLUTION;
 }
-
-}  // namespace
-
-namespace ds {
-void report_error(const std::string& msg) { g_err = msg; }
 }  // namespace ds
+
+using ds::finite_cam;
 
 struct ds_ctx {
     int device = 0;
@@ -259,8 +261,11 @@ ds_status check_views(const ds_camera* cams, int32_t n_views, int32_t S) {
     return DS_OK;
 }
 
+}  // namespace
+
+namespace ds {
 // Fill the view table (tiles, work items, per-view pointers).
-void build_table(ds::ViewTable& vt, const ds_tuning& tu, const ds_camera* cams, const uint64_t* seeds, int32_t n_views,
+void build_table(ViewTable& vt, const ds_tuning& tu, const ds_camera* cams, const uint64_t* seeds, int32_t n_views,
                  int32_t S,
                  const ds_view_out* out, const ds_view_gin* gin) {
     std::memset(&vt, 0, sizeof(vt));
@@ -304,6 +309,12 @@ void build_table(ds::ViewTable& vt, const ds_tuning& tu, const ds_camera* cams, 
     }
     vt.n_items = item_base;
 }
+
+}  // namespace ds
+
+using ds::build_table;
+
+namespace {
 
 int total_tiles(const ds::ViewTable& vt) {
     const ds::ViewDesc& d = vt.v[vt.n - 1];
@@ -584,6 +595,9 @@ ds_status ds_soup_free(ds_ctx* c, int32_t soup_id) {
 
 namespace {
 
+}  // namespace
+
+namespace ds {
 ds_status check_outputs(const ds_view_out* out, int32_t n_views) {
     if (n_views < 1 || n_views > DS_MAX_VIEWS) return fail(DS_ERR_INVALID_ARG, "n_views out of range");
     if (!out) return fail(DS_ERR_INVALID_ARG, "out is NULL");
@@ -593,6 +607,12 @@ ds_status check_outputs(const ds_view_out* out, int32_t n_views) {
     }
     return DS_OK;
 }
+
+}  // namespace ds
+
+using ds::check_outputs;
+
+namespace {
 
 ds_status check_mode(uint32_t mode, bool have_seeds) {
     const uint32_t base_mode = mode & 0xffu;

@@ -21,6 +21,17 @@ extern const char* const kStageNames[kNumStages];
 // Set the message returned by ds_last_error on this thread.
 void report_error(const std::string& msg);
 
+// Argument checks and the view table shared by the forward entry points
+// (ds_api.cu): a camera with finite parameters, a non-zero focal length, a
+// positive near plane and a resolution in [1, DS_MAX_RESOLUTION]; non-NULL
+// view outputs with a 16-byte aligned G-buffer (DS_ERR_INVALID_ARG with the
+// message set otherwise); the table of tiles, work items and per-view
+// pointers for tiles of tu.tile_w x (256 / tu.tile_w) pixels.
+bool finite_cam(const ds_camera& c);
+ds_status check_outputs(const ds_view_out* out, int32_t n_views);
+void build_table(ViewTable& vt, const ds_tuning& tu, const ds_camera* cams, const uint64_t* seeds, int32_t n_views,
+                 int32_t S, const ds_view_out* out, const ds_view_gin* gin);
+
 // Library-wide count of kernel launches (every launch site adds to it).
 void note_launches(int n);
 long long launches_total();

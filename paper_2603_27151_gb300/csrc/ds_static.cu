@@ -70,12 +70,16 @@ cudaError_t scratch_address(unsigned char** out) {
 
 thread_local ds::ViewTable t_vt;   // host staging of the kernel parameter table
 
-bool valid_cam(const ds_camera& c) {
-    const float* f = &c.fx;
-    for (int i = 0; i < 17; ++i)
-        if (!(f[i] == f[i]) || f[i] == __builtin_inff() || f[i] == -__builtin_inff()) return false;
-    return c.fx != 0.f && c.fy != 0.f && c.near_z > 0.f && c.width >= 1 && c.height >= 1 &&
-           c.width <= DS_MAX_RESOLUTION && c.height <= DS_MAX_RESOLUTION;
+// Every caller pointer must be device memory of the current device (or
+// managed memory): a host or foreign-device pointer would be dereferenced by
+// the kernels.  cudaPointerGetAttributes allocates nothing.
+bool on_current_device(const void* p, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 ds_status reject(ds_status code, const std::string& msg) {
@@ -95,21 +99,28 @@ extern "C" DS_API ds_status ds_raster_forward_noalloc(const float* verts, const 
         return reject(DS_ERR_INVALID_ARG, "T, grid_n or C out of range");
     if (n_views < 1 || n_views > DS_MAX_VIEWS || S < 1 || S > DS_MAX_SAMPLES)
         return reject(DS_ERR_INVALID_ARG, "n_views or S out of range");
-    if (mode != DS_MODE_STOCHASTIC && mode != DS_MODE_THRESHOLD_HALF) return reject(DS_ERR_INVALID_ARG, "bad mode");
+    if (mode != DS_MODE_STOCHASTIC && mode != DS_MODE_THRESHOLD_HALF)
+        return reject(DS_ERR_INVALID_ARG, "bad mode (flag bits such as DS_NO_SYNC are not accepted here)");
     if (mode == DS_MODE_STOCHASTIC && !seeds) return reject(DS_ERR_INVALID_ARG, "seeds is NULL");
     const int V = (grid_n + 1) * (grid_n + 2) / 2;
     if ((long long)T * V * C > kMaxTexFloats)
         return reject(DS_ERR_INVALID_ARG, "T*V*C exceeds the no-alloc limit of 2^20 texture values");
     if ((long long)n_views * T > kMaxViewTris)
         return reject(DS_ERR_INVALID_ARG, "n_views*T exceeds the no-alloc limit of 65536");
+    if (ds::check_outputs(out, n_views) != DS_OK) return DS_ERR_INVALID_ARG;   // message set
     long long tiles = 0;
     for (int v = 0; v < n_views; ++v) {
-        if (!valid_cam(cams[v])) return reject(DS_ERR_INVALID_ARG, "camera " + std::to_string(v) + " is invalid");
-        if (!out[v].gbuf || !out[v].color || ((uintptr_t)out[v].gbuf & 15))
-            return reject(DS_ERR_INVALID_ARG, "view output buffer is NULL or gbuf is not 16-byte aligned");
+        if (!ds::finite_cam(cams[v])) return reject(DS_ERR_INVALID_ARG, "camera " + std::to_string(v) + " is invalid");
         tiles += (long long)((cams[v].width + kTileEdge - 1) / kTileEdge) * ((cams[v].height + kTileEdge - 1) / kTileEdge);
     }
     if (tiles > kMaxTiles) return reject(DS_ERR_INVALID_ARG, "the views exceed the no-alloc limit of 65536 tiles");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return reject(DS_ERR_CUDA, "cudaGetDevice failed");
+    bool dev_ok = on_current_device(verts, dev) && on_current_device(tex, dev);
+    for (int v = 0; v < n_views && dev_ok; ++v)
+        dev_ok = on_current_device(out[v].gbuf, dev) && on_current_device(out[v].color, dev) &&
+                 (!out[v].n_front || on_current_device(out[v].n_front, dev));
+    if (!dev_ok) return reject(DS_ERR_INVALID_ARG, "an input or output is not device memory of the current device");
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     unsigned char* base = nullptr;
@@ -118,39 +129,9 @@ extern "C" DS_API ds_status ds_raster_forward_noalloc(const float* verts, const 
 
     // ---- views and soup over the scratch array
     ds::ViewTable& vt = t_vt;
-    std::memset(&vt, 0, sizeof(vt));
-    vt.n = n_views;
-    vt.S = S;
-    vt.n_groups = (S + ds::kSampleGroup - 1) / ds::kSampleGroup;
-    vt.tile_w = vt.tile_h = kTileEdge;
-    vt.chunk = ds::kChunk;
-    int tile_base = 0, item_base = 0;
-    for (int v = 0; v < n_views; ++v) {
-        ds::ViewDesc& d = vt.v[v];
-        const ds_camera& c = cams[v];
-        d.cam.fx = c.fx;
-        d.cam.fy = c.fy;
-        d.cam.cx = c.cx;
-        d.cam.cy = c.cy;
-        for (int i = 0; i < 9; ++i) d.cam.R[i] = c.R[i];
-        for (int i = 0; i < 3; ++i) d.cam.t[i] = c.t[i];
-        d.cam.near_z = c.near_z;
-        d.W = c.width;
-        d.H = c.height;
-        d.tiles_x = (c.width + kTileEdge - 1) / kTileEdge;
-        d.tiles_y = (c.height + kTileEdge - 1) / kTileEdge;
-        d.tile_base = tile_base;
-        d.item_base = item_base;
-        tile_base += d.tiles_x * d.tiles_y;
-        item_base += d.tiles_x * d.tiles_y * vt.n_groups;
-        const uint64_t sd = seeds ? seeds[v] : 0ull;
-        d.seed_lo = (uint32_t)sd;
-        d.seed_hi = (uint32_t)(sd >> 32);
-        d.gbuf = out[v].gbuf;
-        d.color = out[v].color;
-        d.n_front = out[v].n_front;
-    }
-    vt.n_items = item_base;
+    const ds_tuning tu{kTileEdge, 0, 0, ds::kChunk};
+    ds::build_table(vt, tu, cams, seeds, n_views, S, out, nullptr);
+    const int tile_base = vt.v[n_views - 1].tile_base + vt.v[n_views - 1].tiles_x * vt.v[n_views - 1].tiles_y;
 
     ds::SoupDev sd;
     sd.verts = verts;

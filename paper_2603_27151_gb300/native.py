@@ -470,18 +470,46 @@ class Context:
 def raster_forward_noalloc(verts, tex, grid_n, cams, seeds, S, mode, bg, gbufs, colors, n_fronts=None,
                            stream=None):
     """ds_raster_forward_noalloc: the forward pass on a soup given directly,
-    with no context and no allocation (library-internal fixed scratch)."""
+    with no context and no allocation (library-internal fixed scratch).
+    verts [T,3,3] and tex [T,V,C] float32 CUDA tensors on one device; per
+    view v: gbufs[v] int32 [S,H,W,4], colors[v] float32 [S,C-1,H,W] and
+    optional n_fronts[v] int32 [S,H,W], all contiguous on that device.  The
+    call runs with that device current."""
+    import torch
     n = len(cams)
+    dev = verts.device
+    for name, t, dt in (("verts", verts, torch.float32), ("tex", tex, torch.float32)):
+        if not (t.is_cuda and t.device == dev and t.is_contiguous() and t.dtype == dt):
+            raise ValueError("%s must be a contiguous %s tensor on %s" % (name, dt, dev))
+    if tex.dim() != 3:
+        raise ValueError("tex must be [T, V, C]")
     T, V, C = tex.shape
+    if tuple(verts.shape) != (T, 3, 3):
+        raise ValueError("verts must be [T, 3, 3] with T = tex.shape[0]")
+    if V != (grid_n + 1) * (grid_n + 2) // 2:
+        raise ValueError("tex.shape[1] = %d is not (grid_n+1)(grid_n+2)/2 for grid_n = %d" % (V, grid_n))
+    if len(gbufs) != n or len(colors) != n or (n_fronts is not None and len(n_fronts) != n):
+        raise ValueError("one output buffer per camera is required")
+    for v, c in enumerate(cams):
+        H, W = int(c.height), int(c.width)
+        want = [(gbufs[v], (S, H, W, 4), torch.int32), (colors[v], (S, C - 1, H, W), torch.float32)]
+        if n_fronts is not None and n_fronts[v] is not None:
+            want.append((n_fronts[v], (S, H, W), torch.int32))
+        for t, shape, dt in want:
+            if not (t.is_cuda and t.device == dev and t.is_contiguous() and t.dtype == dt and tuple(t.shape) == shape):
+                raise ValueError("view %d: output must be a contiguous %s tensor %s on %s" % (v, dt, shape, dev))
     sd = (ctypes.c_uint64 * n)(*[int(x) for x in (seeds if seeds is not None else [0] * n)])
     bga = np.ascontiguousarray(bg, np.float32)
+    if bga.size != C - 1:
+        raise ValueError("bg must hold C-1 = %d values" % (C - 1))
     outs = (ds_view_out * n)()
     for v in range(n):
         outs[v].gbuf = gbufs[v].data_ptr()
         outs[v].color = colors[v].data_ptr()
         outs[v].n_front = n_fronts[v].data_ptr() if n_fronts is not None and n_fronts[v] is not None else None
-    _check(load().ds_raster_forward_noalloc(_ptr(verts), _ptr(tex), T, grid_n, C, cameras(cams), sd, n, S, mode,
-                                            bga.ctypes.data_as(ctypes.c_void_p), outs, _stream(stream)))
+    with torch.cuda.device(dev):
+        _check(load().ds_raster_forward_noalloc(_ptr(verts), _ptr(tex), T, grid_n, C, cameras(cams), sd, n, S, mode,
+                                                bga.ctypes.data_as(ctypes.c_void_p), outs, _stream(stream)))
 
 
 def level_V(R: int) -> int:

@@ -153,19 +153,36 @@ def _source_sha1() -> str:
     return h.hexdigest()
 
 
-def _traffic(kernel: str, pixel_samples: int):
-    """DRAM bytes per launch of `kernel` from the committed ncu capture,
-    scaled to this launch's pixel-samples; None when the kernels changed
-    since the capture (source hash differs) or the kernel was not captured."""
+def _capture():
+    """The committed ncu capture of the tile kernels (DRAM bytes and issue
+    counters), or None when the kernels changed since (source hash differs)."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
     except (OSError, ValueError):
         return None
-    if d.get("source_sha1") != _source_sha1() or kernel not in d.get("bytes", {}):
+    return d if d.get("source_sha1") == _source_sha1() else None
+
+
+def _traffic(kernel: str, pixel_samples: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture,
+    scaled to this launch's pixel-samples; None when the kernels changed
+    since the capture (source hash differs) or the kernel was not captured."""
+    d = _capture()
+    if d is None or kernel not in d.get("bytes", {}):
         return None
     return d["bytes"][kernel] * pixel_samples / d["pixel_samples"]
+
+
+def _counters(kernel: str):
+    """Issue and pipe counters of `kernel` from the same capture (the bound
+    the kernel actually hits: issue slots, ALU/FMA/FP64 pipes, active lanes),
+    or None as for _traffic."""
+    d = _capture()
+    if d is None or kernel not in d.get("counters", {}):
+        return None
+    return dict(d["counters"][kernel], source=d.get("profile"))
 
 
 # ---------------------------------------------------------------- the GPU step
@@ -243,24 +260,45 @@ class Workload:
         self.ctx.status()
 
     def algorithmic_bytes(self):
-        """Minimum HBM bytes each stage must move per launch (the algorithmic bytes of the roofline)."""
+        """Minimum HBM bytes each stage must move per launch: the per-unit
+        bytes of the scope table's measurement section (T triangles, V
+        texels of C channels, C_o = C - 1 colour channels, P pixels, S
+        samples, K bin pairs), with every triangle counted as visible and as
+        a winner (upper bounds of T_vis and T_win).  Implementation traffic
+        (staged set-up records, geometry records, texel re-reads) is not
+        algorithmic and is not counted."""
         sc, S = self.sc, self.S
         T, V, C = sc.tex.shape
         Co = C - 1
         P = sum(c.width * c.height for c in sc.cams)
         nv = len(sc.cams)
         K = self.pairs
+        loss = (P * 4 * Co + P * S * (4 * Co + 4)) if self.fused else 0   # fused epilogue: target in, dL/dC and l out
+        fwd_raster = T * V * 4 + T * V * Co * 4 + 2 * K * 12 + P * S * (16 + 4 * Co)
+        bwd_raster = P * S * (16 + 4 * Co + 4) + 2 * (36 * T + T * V * C * 4) + T * V * 4 + 2 * K * 12
         return {
-            "activate": T * V * C * 4 * 2 + T * V * 4,
-            "setup": nv * T * (36 + 64 + 4 + 16 + 4),
-            "raster_fwd": (K * (8 + 64) + T * V * 4 + T * V * C * 4 + P * S * (16 + 4 * Co)
-                           + ((P * 4 * Co + P * S * (4 * Co + 4)) if self.fused else 0)),   # + loss epilogue
-            "train": (K * (8 + 64) + T * V * 4 + T * V * C * 4 * 3 + P * S * (16 + 4 * Co) + P * 4 * Co
-                      + P * S * (4 * Co + 4) + 36 * T * 2 + nv * T * 208),
-            "raster_bwd": K * (8 + 64) + P * S * (16 + 4 * Co + 4) + T * V * C * 4 * 3 + 36 * T * 2 + nv * T * 208,
-            "edge_bwd": P * S * (16 + 8 * Co) + nv * T * (64 + 208) + 36 * T * 2,
-            "geom": nv * T * (36 + 208),
+            "activate": T * V * C * 4 * 2,
+            "setup": nv * T * 36,
+            "raster_fwd": fwd_raster + loss,
+            "train": fwd_raster + loss + bwd_raster,
+            "raster_bwd": bwd_raster,
+            "edge_bwd": P * S * (16 + 8 * Co) + 2 * 36 * T,
+            "geom": nv * T * 36,
         }
+
+    def step_bytes(self):
+        """Algorithmic bytes of one forward + backward step, as the scope
+        table's measurement section states them: forward 36 T + T V 4 +
+        T V C_o 4 + 2 K 12 + P S (16 + 4 C_o); backward P S (16 + 8 C_o + 4)
+        + 2 (36 T + T V C 4) + T V 4."""
+        sc, S = self.sc, self.S
+        T, V, C = sc.tex.shape
+        Co = C - 1
+        P = sum(c.width * c.height for c in sc.cams)
+        K = self.pairs
+        fwd = 36 * T + T * V * 4 + T * V * Co * 4 + 2 * K * 12 + P * S * (16 + 4 * Co)
+        bwd = P * S * (16 + 8 * Co + 4) + 2 * (36 * T + T * V * C * 4) + T * V * 4
+        return fwd + bwd
 
 
 def _plain_leg(wl, steps: int):
@@ -739,44 +777,75 @@ def _gpu_arm(args):
     wl.ctx.profile(True)
     launches0 = N.kernel_launches()
     stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]   # one pair per step
     barrier()
     with ClockSampler(local) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
+        evs[0].record(stream)
+        for k in range(args.steps):
             wl.step()
-        e1.record(stream)
+            evs[k + 1].record(stream)
         torch.cuda.synchronize()
     launches = N.kernel_launches() - launches0
     wl.check()
     wl.ctx.profile(False)
     prof = wl.ctx.profile_read()
-    ms = e0.elapsed_time(e1)
+    ms = evs[0].elapsed_time(evs[-1])
+    step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     t_max = max_over_ranks(ms, world, dev)
     barrier()
 
     # ---- end to end through the public API with host buffers.  Every step
     # copies its inputs (vertices, texture logits, targets) from pinned host
-    # memory and reads its loss back to the host.  The inputs are double
-    # buffered: step k+1's copies run on a copy stream while step k computes
-    # (two borrowed soups over the two buffers), as a training data loader
-    # would prefetch.
+    # memory and its results (the texture and vertex gradients and the loss)
+    # back to pinned host memory, and the host reads the loss.
+    #  serial:    copy in -> step -> copy out on one stream, then the host
+    #             waits: nothing overlaps;
+    #  pipelined: inputs and gradients double buffered: step k+1's inputs
+    #             are copied on a copy stream while step k computes, and step
+    #             k's gradients are copied out on a third stream while step
+    #             k+1 computes, as a training loop with a prefetching loader
+    #             and an asynchronous parameter server would run.
     hv = wl.verts.cpu().pin_memory()
     ht = wl.tex.cpu().pin_memory()
     htg = [x.cpu().pin_memory() for x in wl.targets]
-    hl = torch.zeros(1, dtype=torch.float32).pin_memory()
     h2d = hv.numel() * 4 + ht.numel() * 4 + sum(x.numel() * 4 for x in htg)
-    bufs = [(wl.verts, wl.tex, wl.targets, wl.sid)]
+    hgt = [torch.empty(wl.gt.shape, dtype=torch.float32).pin_memory() for _ in range(2)]
+    hgv = [torch.empty(wl.gv.shape, dtype=torch.float32).pin_memory() for _ in range(2)]
+    hl = [torch.zeros(1, dtype=torch.float32).pin_memory() for _ in range(2)]
+    d2h = wl.gt.numel() * 4 + wl.gv.numel() * 4 + 4
+    comp = torch.cuda.current_stream()
+
+    barrier()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        wl.verts.copy_(hv, non_blocking=True)
+        wl.tex.copy_(ht, non_blocking=True)
+        for d, h in zip(wl.targets, htg):
+            d.copy_(h, non_blocking=True)
+        wl.step()
+        hgt[0].copy_(wl.gt, non_blocking=True)
+        hgv[0].copy_(wl.gv, non_blocking=True)
+        hl[0].copy_(wl.loss, non_blocking=True)
+        comp.synchronize()
+        _ = float(hl[0][0])
+    e2e_serial_s = time.perf_counter() - t0
+    wl.check()
+    e2e_serial_s = max_over_ranks(e2e_serial_s, world, dev)
+
+    home = (wl.verts, wl.tex, wl.targets, wl.sid, wl.gt, wl.gv, wl.loss)
+    bufs = [home]
     v2, t2 = torch.empty_like(wl.verts), torch.empty_like(wl.tex)
     bufs.append((v2, t2, [torch.empty_like(x) for x in wl.targets],
-                 wl.ctx.soup_upload(v2, t2, wl.sc.grid_n, borrow=True)))
-    comp = torch.cuda.current_stream()
-    copy = torch.cuda.Stream()
+                 wl.ctx.soup_upload(v2, t2, wl.sc.grid_n, borrow=True),
+                 torch.empty_like(wl.gt), torch.empty_like(wl.gv), torch.zeros_like(wl.loss)))
+    copy, back = torch.cuda.Stream(), torch.cuda.Stream()
     copied = [torch.cuda.Event(), torch.cuda.Event()]
     freed = [torch.cuda.Event(), torch.cuda.Event()]
+    stepped = [torch.cuda.Event(), torch.cuda.Event()]
+    readback = [torch.cuda.Event(), torch.cuda.Event()]
 
     def load_inputs(b):
-        v, t, tg, _ = bufs[b]
+        v, t, tg = bufs[b][:3]
         with torch.cuda.stream(copy):
             copy.wait_event(freed[b])   # the step that last read buffer b has finished
             v.copy_(hv, non_blocking=True)
@@ -787,6 +856,7 @@ def _gpu_arm(args):
 
     for b in range(2):
         freed[b].record(comp)
+        readback[b].record(comp)
     barrier()
     t0 = time.perf_counter()
     load_inputs(0)
@@ -795,16 +865,26 @@ def _gpu_arm(args):
         if k + 1 < args.steps:
             load_inputs(1 - b)
         comp.wait_event(copied[b])
-        wl.verts, wl.tex, wl.targets, wl.sid = bufs[b]
+        comp.wait_event(readback[b])    # step k-2's gradients have left buffer b
+        wl.verts, wl.tex, wl.targets, wl.sid, wl.gt, wl.gv, wl.loss = bufs[b]
         wl.step()
         freed[b].record(comp)
-        hl.copy_(wl.loss, non_blocking=True)
-        comp.synchronize()
-        _ = float(hl[0])
-    e2e_s = time.perf_counter() - t0
+        stepped[b].record(comp)
+        with torch.cuda.stream(back):
+            back.wait_event(stepped[b])
+            hgt[b].copy_(wl.gt, non_blocking=True)
+            hgv[b].copy_(wl.gv, non_blocking=True)
+            hl[b].copy_(wl.loss, non_blocking=True)
+            readback[b].record(back)
+        if k >= 1:                      # step k-1's results are on the host
+            readback[1 - b].synchronize()
+            _ = float(hl[1 - b][0])
+    readback[(args.steps - 1) % 2].synchronize()
+    _ = float(hl[(args.steps - 1) % 2][0])
+    e2e_pipe_s = time.perf_counter() - t0
     wl.check()
-    wl.verts, wl.tex, wl.targets, wl.sid = bufs[0]
-    e2e_s = max_over_ranks(e2e_s, world, dev)
+    wl.verts, wl.tex, wl.targets, wl.sid, wl.gt, wl.gv, wl.loss = home
+    e2e_pipe_s = max_over_ranks(e2e_pipe_s, world, dev)
     barrier()
 
     extras = {}
@@ -830,12 +910,26 @@ def _gpu_arm(args):
                    "bin_pairs": wl.pairs, "l2": "inputs larger than L2 (about 3 GB touched per step)",
                    "tuning": tuning,
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "e2e": {"value": frags_total / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 4},
+        "ms_per_step_dist": {"mean": ms / args.steps, "median": float(np.median(step_ms)),
+                             "p10": float(np.percentile(step_ms, 10)), "p90": float(np.percentile(step_ms, 90)),
+                             "min": float(min(step_ms)), "max": float(max(step_ms)),
+                             "what": "one CUDA event pair per timed step (rank 0)"},
+        "e2e": {"value": frags_total / e2e_serial_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h,
+                "what": "serial: inputs copied in, the step, texture and vertex gradients and the loss copied "
+                        "out, host waits; nothing overlaps"},
+        "e2e_pipelined": {"value": frags_total / e2e_pipe_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                          "d2h_bytes_per_step": d2h,
+                          "what": "the same copies double buffered: inputs of step k+1 and gradients of step k "
+                                  "move on two copy streams while the next step computes"},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind,
                      "traffic": _traffic(dom, wl.pixel_samples),
-                     "algorithmic_bytes": algo[dom], "launch_ms": per_launch_ms},
+                     "algorithmic_bytes": algo[dom], "launch_ms": per_launch_ms,
+                     "step_bytes": wl.step_bytes(),
+                     "step_frac": wl.step_bytes() / (t_max / args.steps / 1e3) / 1e9 / peak,
+                     "counters": _counters(dom)},
         "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
         "clocks": clk.summary(),
     }

@@ -54,9 +54,9 @@ def test_two_gloo_ranks_aggregate_like_the_bench():
 
 
 def test_traffic_lookup_scales_and_checks_the_source_hash(tmp_path, monkeypatch):
-    """The DRAM traffic of the committed capture is scaled to a launch by its
-    pixel-samples, and withheld (null) once the tile kernels' sources differ
-    from the captured ones."""
+    """The DRAM traffic and counters of a capture are scaled to a launch by its
+    pixel-samples and reported while the tile kernels' sources hash to the
+    captured ones; withheld (null) once they differ."""
     import importlib.util
     import json
     import os
@@ -64,18 +64,20 @@ def test_traffic_lookup_scales_and_checks_the_source_hash(tmp_path, monkeypatch)
     spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(root, "bench.py"))
     B = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(B)
-    d = json.load(open(os.path.join(root, "profiles", "dram_traffic.json")))
-    assert d["source_sha1"] == B._source_sha1()       # the committed capture matches the committed kernels
-    got = B._traffic("raster_bwd", 2 * d["pixel_samples"])
-    assert got == 2 * d["bytes"]["raster_bwd"]
-    assert B._traffic("no_such_kernel", 1) is None
-    # a copy of the tree whose tile kernel differs: no traffic
     fake = tmp_path / "repo"
     (fake / "profiles").mkdir(parents=True)
     (fake / "paper_2603_27151_gb300" / "csrc").mkdir(parents=True)
     for n in B.TILE_KERNEL_SOURCES:
         src = open(os.path.join(root, "paper_2603_27151_gb300", "csrc", n), "rb").read()
-        (fake / "paper_2603_27151_gb300" / "csrc" / n).write_bytes(src + (b"// changed\n" if n == "ds_raster.cu" else b""))
-    (fake / "profiles" / "dram_traffic.json").write_text(json.dumps(d))
+        (fake / "paper_2603_27151_gb300" / "csrc" / n).write_bytes(src)
     monkeypatch.setattr(B, "ROOT", str(fake))
-    assert B._traffic("raster_bwd", d["pixel_samples"]) is None
+    d = {"source_sha1": B._source_sha1(), "pixel_samples": 1000, "bytes": {"raster_bwd": 5000},
+         "counters": {"raster_bwd": {"issue_active": 0.5}}, "profile": "profiles/x.md"}
+    (fake / "profiles" / "dram_traffic.json").write_text(json.dumps(d))
+    assert B._traffic("raster_bwd", 2000) == 10000
+    assert B._traffic("no_such_kernel", 1) is None
+    assert B._counters("raster_bwd") == {"issue_active": 0.5, "source": "profiles/x.md"}
+    # a tile kernel changed after the capture: no traffic, no counters
+    p = fake / "paper_2603_27151_gb300" / "csrc" / "ds_raster.cu"
+    p.write_bytes(p.read_bytes() + b"// changed\n")
+    assert B._traffic("raster_bwd", 1000) is None and B._counters("raster_bwd") is None

@@ -56,9 +56,9 @@ def lib():
         L.or_activate.restype = None; L.or_activate.argtypes = [P, i64, P]
         L.or_forward.restype = ctypes.c_int
         L.or_forward.argtypes = [P, P, i32, i32, i32, P, P, P, i32, i32, i32, P, P, i32, i32,
-                                 P, P, P, P, P, P]
+                                 P, P, P, P, P, P, i32]
         L.or_backward.restype = ctypes.c_int
-        L.or_backward.argtypes = [P, P, i32, i32, i32, P, P, i32, i32, P, P, P, P, P, u32, i32, i32, P, P]
+        L.or_backward.argtypes = [P, P, i32, i32, i32, P, P, i32, i32, P, P, P, P, P, u32, i32, i32, P, P, i32]
         L.or_compose.restype = None; L.or_compose.argtypes = [P, i32, i32, i32, i32, P]
         L.or_coverage.restype = None; L.or_coverage.argtypes = [P, i64, i32, P]
         L.or_edge_ratios.restype = None; L.or_edge_ratios.argtypes = [P, i32, P, P, i32, P]
@@ -289,9 +289,11 @@ def soup_rebuild(verts, levels, r_min: int, r_max: int, plan):
 
 # ---------------------------------------------------------------- full passes
 def forward(verts, tex, grid_n, cams, seeds, S=1, mode=MODE_STOCHASTIC, bg=None,
-            order=None, rows=None):
+            order=None, rows=None, scan=False):
     """Brute-force forward.  Returns one dict per view with tri_id [S,H,W],
-    bary [S,H,W,2], depth [S,H,W], n_front, n_cover [S,H,W], color [S,C-1,H,W]."""
+    bary [S,H,W,2], depth [S,H,W], n_front, n_cover [S,H,W], color [S,C-1,H,W].
+    scan=True: the same results through object-order candidate lists (the
+    bbox-scan timing mode)."""
     verts = _c(verts, np.float32); tex = _c(tex, np.float32)
     T, V, C = tex.shape
     cf, wh = _cams(cams)
@@ -305,7 +307,7 @@ def forward(verts, tex, grid_n, cams, seeds, S=1, mode=MODE_STOCHASTIC, bg=None,
     r0, r1 = (0, -1) if rows is None else rows
     rc = lib().or_forward(_p(verts), _p(tex), T, grid_n, C, _p(cf), _p(wh), _p(seeds), len(cams),
                           S, mode, _p(bg), _p(order_a), r0, r1,
-                          _p(tri), _p(bary), _p(depth), _p(nf), _p(nc), _p(color))
+                          _p(tri), _p(bary), _p(depth), _p(nf), _p(nc), _p(color), int(bool(scan)))
     assert rc == 0, rc
     out, o, oc = [], 0, 0
     for c in cams:
@@ -321,10 +323,11 @@ def forward(verts, tex, grid_n, cams, seeds, S=1, mode=MODE_STOCHASTIC, bg=None,
     return out
 
 
-def backward(verts, tex, grid_n, cams, S, fwd, grad_color, score_w, flags=G_ALL, rows=None):
+def backward(verts, tex, grid_n, cams, S, fwd, grad_color, score_w, flags=G_ALL, rows=None, scan=False):
     """Algorithm A1 step 2 plus vertex gradients, FP64 accumulation.
     fwd: list of per-view dicts (tri_id, bary, color); grad_color: list of
-    [S,C-1,H,W]; score_w: list of [S,H,W].  Returns (grad_tex, grad_verts)."""
+    [S,C-1,H,W]; score_w: list of [S,H,W].  Returns (grad_tex, grad_verts).
+    scan=True: object-order candidate lists, identical results (timing mode)."""
     verts = _c(verts, np.float32); tex = _c(tex, np.float32)
     T, V, C = tex.shape
     cf, wh = _cams(cams)
@@ -336,7 +339,8 @@ def backward(verts, tex, grid_n, cams, S, fwd, grad_color, score_w, flags=G_ALL,
     gt = np.zeros(tex.shape, np.float64); gv = np.zeros(verts.shape, np.float64)
     r0, r1 = (0, -1) if rows is None else rows
     rc = lib().or_backward(_p(verts), _p(tex), T, grid_n, C, _p(cf), _p(wh), len(cams), S,
-                           _p(tri), _p(bary), _p(col), _p(gc), _p(sw), flags, r0, r1, _p(gt), _p(gv))
+                           _p(tri), _p(bary), _p(col), _p(gc), _p(sw), flags, r0, r1, _p(gt), _p(gv),
+                           int(bool(scan)))
     assert rc == 0, rc
     return gt, gv
 

@@ -303,12 +303,76 @@ static void o_activate(const float* tex, size_t n, float* act)
 void or_activate(const float* tex, int64_t n, float* act) { o_activate(tex, (size_t)n, act); }
 
 /* ------------------------------------------------------------------------ */
+/* Object-order candidate lists (the bbox-scan mode, used to time the        */
+/* oracle; results identical to the brute-force loops)                      */
+/* ------------------------------------------------------------------------ */
+
+/* Every live triangle scans the pixel rectangle of its bounding box within
+ * rows [r0, r1) and appends its index to the list of each pixel there, in
+ * ascending triangle order.  A pixel's list then holds exactly the
+ * triangles that pass the brute-force loop's rectangle test, in the order
+ * that loop visits them, so every result (and every FP64 summation order)
+ * is the same.  off has (r1 - r0) W + 1 entries; returns 0, or -2 when out
+ * of memory. */
+typedef struct { int32_t* off; int32_t* idx; } OCand;
+
+static int o_candidates(const OTri* tri, int T, int W, int r0, int r1, OCand* c)
+{
+    const size_t npix = (size_t)(r1 > r0 ? r1 - r0 : 0) * W;
+    c->off = (int32_t*)calloc(npix + 1, sizeof(int32_t));
+    c->idx = NULL;
+    if (!c->off) return -2;
+    for (int t = 0; t < T; ++t) {
+        const OTri* o = &tri[t];
+        if (!o->live) continue;
+        const int y0 = o->py0 > r0 ? o->py0 : r0, y1 = o->py1 < r1 - 1 ? o->py1 : r1 - 1;
+        for (int y = y0; y <= y1; ++y)
+            for (int x = o->px0; x <= o->px1; ++x) c->off[(size_t)(y - r0) * W + x + 1]++;
+    }
+    for (size_t i = 0; i < npix; ++i) c->off[i + 1] += c->off[i];
+    c->idx = (int32_t*)malloc(sizeof(int32_t) * (size_t)(c->off[npix] > 0 ? c->off[npix] : 1));
+    int32_t* fill = (int32_t*)malloc(sizeof(int32_t) * (npix > 0 ? npix : 1));
+    if (!c->idx || !fill) {
+        free(c->idx); free(fill); free(c->off);
+        c->off = NULL; c->idx = NULL;
+        return -2;
+    }
+    memcpy(fill, c->off, sizeof(int32_t) * npix);
+    for (int t = 0; t < T; ++t) {
+        const OTri* o = &tri[t];
+        if (!o->live) continue;
+        const int y0 = o->py0 > r0 ? o->py0 : r0, y1 = o->py1 < r1 - 1 ? o->py1 : r1 - 1;
+        for (int y = y0; y <= y1; ++y)
+            for (int x = o->px0; x <= o->px1; ++x) c->idx[fill[(size_t)(y - r0) * W + x]++] = t;
+    }
+    free(fill);
+    return 0;
+}
+
+static void o_candidates_free(OCand* c) { free(c->off); free(c->idx); c->off = NULL; c->idx = NULL; }
+
+/* Sigmoid of the texels of every triangle on a candidate list that has not
+ * been activated yet (done[t] marks the activated ones). */
+static void o_activate_candidates(const OCand* c, size_t n_entries, const float* tex, size_t VC, float* act,
+                                  unsigned char* done)
+{
+    for (size_t i = 0; i < n_entries; ++i) {
+        const int t = c->idx[i];
+        if (done[t]) continue;
+        o_activate(tex + (size_t)t * VC, VC, act + (size_t)t * VC);
+        done[t] = 1;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Forward: Eq. 5 by brute force (Algorithm A1, step 1)                      */
 /* ------------------------------------------------------------------------ */
 
 /* For every view, pixel row in [row0, row1) (all rows if row1 < 0), pixel and
  * mask sample: the foremost covered fragment whose opacity exceeds its
- * threshold.  Outputs per view are concatenated: [S][H][W] for tri_id, depth,
+ * threshold.  scan != 0: the per-pixel loops visit the pixel's object-order
+ * candidate list (o_candidates) instead of all T triangles, and only those
+ * triangles are activated; the results are identical (timing mode).  Outputs per view are concatenated: [S][H][W] for tri_id, depth,
  * n_front, n_cover; [S][H][W][2] for bary; [S][C-1][H][W] for color.
  * order (may be NULL) is the order in which triangles are visited. */
 int or_forward(const float* verts, const float* tex, int32_t T, int32_t N, int32_t C,
@@ -316,26 +380,35 @@ int or_forward(const float* verts, const float* tex, int32_t T, int32_t N, int32
                int32_t S, int32_t mode, const float* bg, const int32_t* order,
                int32_t row0, int32_t row1,
                int32_t* tri_id, float* bary, float* depth, int32_t* n_front, int32_t* n_cover,
-               float* color)
+               float* color, int32_t scan)
 {
     const int V = V_of(N), Co = C - 1;
     float* act = (float*)malloc(sizeof(float) * (size_t)T * V * C);
     OTri* tri = (OTri*)malloc(sizeof(OTri) * (size_t)(T > 0 ? T : 1));
-    if (!act || !tri) { free(act); free(tri); return -2; }
-    o_activate(tex, (size_t)T * V * C, act);
+    unsigned char* done = scan ? (unsigned char*)calloc((size_t)(T > 0 ? T : 1), 1) : NULL;
+    if (!act || !tri || (scan && !done)) { free(act); free(tri); free(done); return -2; }
+    if (!scan) o_activate(tex, (size_t)T * V * C, act);
     size_t off = 0, coff = 0;
     for (int v = 0; v < n_views; ++v) {
         const int W = wh[2 * v], H = wh[2 * v + 1];
         const float* cam = cams + 17 * v;
         for (int t = 0; t < T; ++t) o_setup(verts + 9 * (size_t)t, cam, W, H, &tri[t]);
         int r0 = row1 < 0 ? 0 : row0, r1 = row1 < 0 ? H : (row1 < H ? row1 : H);
+        if (r1 < r0) r1 = r0;   /* a band below this view: no rows */
+        OCand cand = {NULL, NULL};
+        if (scan) {
+            if (o_candidates(tri, T, W, r0, r1, &cand)) { free(act); free(tri); free(done); return -2; }
+            o_activate_candidates(&cand, (size_t)cand.off[(size_t)(r1 - r0) * W], tex, (size_t)V * C, act, done);
+        }
         for (int s = 0; s < S; ++s)
         for (int py = r0; py < r1; ++py)
         for (int px = 0; px < W; ++px) {
             int bt = -1;
             float brho = 0.0f, bD = INFINITY, bb1 = 0.0f, bb2 = 0.0f;
-            for (int n = 0; n < T; ++n) {
-                int t = order ? order[n] : n;
+            const int32_t* cl = scan ? cand.idx + cand.off[(size_t)(py - r0) * W + px] : NULL;
+            const int ncand = scan ? cand.off[(size_t)(py - r0) * W + px + 1] - cand.off[(size_t)(py - r0) * W + px] : T;
+            for (int n = 0; n < ncand; ++n) {
+                int t = cl ? cl[n] : (order ? order[n] : n);
                 const OTri* o = &tri[t];
                 if (!o->live || px < o->px0 || px > o->px1 || py < o->py0 || py > o->py1) continue;
                 int64_t E[3];
@@ -350,7 +423,8 @@ int or_forward(const float* verts, const float* tex, int32_t T, int32_t N, int32
                 }
             }
             int nf = 0, nc = 0;
-            for (int t = 0; t < T; ++t) {
+            for (int n = 0; n < ncand; ++n) {
+                const int t = cl ? cl[n] : n;
                 const OTri* o = &tri[t];
                 if (!o->live || px < o->px0 || px > o->px1 || py < o->py0 || py > o->py1) continue;
                 int64_t E[3];
@@ -374,11 +448,13 @@ int or_forward(const float* verts, const float* tex, int32_t T, int32_t N, int32
                 }
             }
         }
+        o_candidates_free(&cand);
         off += (size_t)S * H * W;
         coff += (size_t)S * Co * H * W;
     }
     free(act);
     free(tri);
+    free(done);
     return 0;
 }
 
@@ -492,20 +568,27 @@ int or_backward(const float* verts, const float* tex, int32_t T, int32_t N, int3
                 const float* cams, const int32_t* wh, int32_t n_views, int32_t S,
                 const int32_t* tri_id, const float* bary, const float* color,
                 const float* grad_color, const float* score_w, uint32_t flags,
-                int32_t row0, int32_t row1, double* grad_tex, double* grad_verts)
+                int32_t row0, int32_t row1, double* grad_tex, double* grad_verts, int32_t scan)
 {
     const int V = V_of(N), Co = C - 1;
     float* act = (float*)malloc(sizeof(float) * (size_t)T * V * C);
     OTri* tri = (OTri*)malloc(sizeof(OTri) * (size_t)(T > 0 ? T : 1));
     double* g = (double*)malloc(sizeof(double) * (size_t)(Co > 0 ? Co : 1));
-    if (!act || !tri || !g) { free(act); free(tri); free(g); return -2; }
-    o_activate(tex, (size_t)T * V * C, act);
+    unsigned char* done = scan ? (unsigned char*)calloc((size_t)(T > 0 ? T : 1), 1) : NULL;
+    if (!act || !tri || !g || (scan && !done)) { free(act); free(tri); free(g); free(done); return -2; }
+    if (!scan) o_activate(tex, (size_t)T * V * C, act);
     size_t off = 0, coff = 0;
     for (int v = 0; v < n_views; ++v) {
         const int W = wh[2 * v], H = wh[2 * v + 1];
         const float* cam = cams + 17 * v;
         for (int t = 0; t < T; ++t) o_setup(verts + 9 * (size_t)t, cam, W, H, &tri[t]);
         int r0 = row1 < 0 ? 0 : row0, r1 = row1 < 0 ? H : (row1 < H ? row1 : H);
+        if (r1 < r0) r1 = r0;   /* a band below this view: no rows */
+        OCand cand = {NULL, NULL};
+        if (scan) {
+            if (o_candidates(tri, T, W, r0, r1, &cand)) { free(act); free(tri); free(g); free(done); return -2; }
+            o_activate_candidates(&cand, (size_t)cand.off[(size_t)(r1 - r0) * W], tex, (size_t)V * C, act, done);
+        }
         const size_t HW = (size_t)H * W;
         for (int s = 0; s < S; ++s)
         for (int py = r0; py < r1; ++py)
@@ -527,7 +610,10 @@ int or_backward(const float* verts, const float* tex, int32_t T, int32_t N, int3
                 double w = score_w[pix];
                 float rs = 0.0f;
                 int has = o_winner_key(tri, ts, px, py, &rs);
-                for (int t = 0; t < T; ++t) {
+                const int32_t* cl = scan ? cand.idx + cand.off[(size_t)(py - r0) * W + px] : NULL;
+                const int ncand = scan ? cand.off[(size_t)(py - r0) * W + px + 1] - cand.off[(size_t)(py - r0) * W + px] : T;
+                for (int n = 0; n < ncand; ++n) {
+                    const int t = cl ? cl[n] : n;
                     const OTri* o = &tri[t];
                     if (t == ts || !o->live || px < o->px0 || px > o->px1 || py < o->py0 || py > o->py1) continue;
                     int64_t E[3];
@@ -673,12 +759,14 @@ int or_backward(const float* verts, const float* tex, int32_t T, int32_t N, int3
                 }
             }
         }
+        o_candidates_free(&cand);
         off += (size_t)S * HW;
         coff += (size_t)S * Co * HW;
     }
     free(act);
     free(tri);
     free(g);
+    free(done);
     return 0;
 }
 

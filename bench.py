@@ -185,6 +185,15 @@ def _counters(kernel: str):
     return dict(d["counters"][kernel], source=d.get("profile"))
 
 
+def workload_config(world: int) -> dict:
+    """The bench line's config: the workload alone (the same for both arms)."""
+    sc = I.large_batch()
+    return {"workload": WORKLOAD, "triangles": sc.T, "views": len(sc.cams), "samples": sc.samples,
+            "pixel_samples_per_step": sum(c.width * c.height for c in sc.cams) * sc.samples,
+            "l2": "inputs larger than L2 (about 3 GB touched per step)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 # ---------------------------------------------------------------- the GPU step
 class Workload:
     def __init__(self, rank: int, device: str, views: int = 0, fused: bool = True):
@@ -905,11 +914,8 @@ def _gpu_arm(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded soups, cameras, targets)",
-        "config": {"workload": WORKLOAD, "triangles": wl.sc.T, "views": len(wl.sc.cams), "samples": wl.S,
-                   "fragments_per_step": wl.fragments, "pixel_samples_per_step": wl.pixel_samples,
-                   "bin_pairs": wl.pairs, "l2": "inputs larger than L2 (about 3 GB touched per step)",
-                   "tuning": tuning,
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": workload_config(world),
+        "workload_stats": {"fragments_per_step": wl.fragments, "bin_pairs": wl.pairs, "tuning": tuning},
         "ms_per_step_dist": {"mean": ms / args.steps, "median": float(np.median(step_ms)),
                              "p10": float(np.percentile(step_ms, 10)), "p90": float(np.percentile(step_ms, 90)),
                              "min": float(min(step_ms)), "max": float(max(step_ms)),
@@ -955,7 +961,16 @@ def _gpu_arm(args):
 
 
 # ---------------------------------------------------------------- CPU oracle
+# The CPU baseline times the oracle in its bbox-scan (object-order) mode,
+# whose results equal the brute-force oracle's bit for bit, on bands of rows
+# of the workload's first view (1920x1080, S = 4, forward + L2 loss +
+# backward with every gradient term); the targets of those rows are rendered
+# beforehand, untimed.  Both the cpu_baseline of the GPU arm and the
+# reference arm time this same sample: rows ROW0, ROW0 + 1, ... of view 0,
+# one row per process.
 _ORACLE_SCENES = {}
+CPU_VIEW = 0
+CPU_ROW0 = 400
 
 
 def _oracle_init():
@@ -967,26 +982,39 @@ def _oracle_init():
     _ORACLE_SCENES["tsc"] = I.large_batch(soup_seed=12)
 
 
-def _oracle_rows(job):
-    """One bounded sample: forward + backward of the oracle on a band of rows
-    of one view (L2 loss against the target soup's binary-opacity render)."""
+def _oracle_target(job):
+    """Untimed: the target colours [C-1, r1-r0, W] of rows [r0, r1) of a view
+    (the target soup's binary-opacity render, Eq. 3)."""
     import oracle as O
-    view, r0, r1, seed = job
+    if not _ORACLE_SCENES:
+        _oracle_init()
+    view, r0, r1 = job
     sc, tsc = _ORACLE_SCENES["sc"], _ORACLE_SCENES["tsc"]
+    tg = O.forward(tsc.verts, tsc.tex, tsc.grid_n, [sc.cams[view]], np.zeros(1, np.uint64), S=1,
+                   mode=O.MODE_THRESHOLD_HALF, bg=sc.bg, rows=(r0, r1), scan=True)[0]
+    return tg["color"][0][:, r0:r1].copy()
+
+
+def _oracle_rows(job):
+    """One timed unit: forward + L2 loss + backward of the oracle (bbox-scan
+    mode) on rows [r0, r1) of one view against precomputed target rows.
+    Returns (fragments, seconds)."""
+    import oracle as O
+    if not _ORACLE_SCENES:
+        _oracle_init()
+    view, r0, r1, seed, tgt = job
+    sc = _ORACLE_SCENES["sc"]
     cam = sc.cams[view]
-    t0 = time.perf_counter()
-    f = O.forward(sc.verts, sc.tex, sc.grid_n, [cam], np.array([seed], np.uint64), S=sc.samples, bg=sc.bg,
-                  rows=(r0, r1))[0]
-    tg = O.forward(tsc.verts, tsc.tex, tsc.grid_n, [cam], np.zeros(1, np.uint64), S=1,
-                   mode=O.MODE_THRESHOLD_HALF, bg=sc.bg, rows=(r0, r1))[0]
     S = sc.samples
-    diff = f["color"] - tg["color"][0][None]
-    band = np.zeros(diff.shape[2], bool)
-    band[r0:r1] = True
-    diff[:, :, ~band] = 0.0
-    ell = (diff.astype(np.float64) ** 2).sum(1)
-    O.backward(sc.verts, sc.tex, sc.grid_n, [cam], S, [f], [(2.0 * diff / S).astype(np.float32)],
-               [(ell / S).astype(np.float32)], rows=(r0, r1))
+    t0 = time.perf_counter()
+    f = O.forward(sc.verts, sc.tex, sc.grid_n, [cam], np.array([seed], np.uint64), S=S, bg=sc.bg,
+                  rows=(r0, r1), scan=True)[0]
+    d = f["color"][:, :, r0:r1] - tgt[None]                     # the band only
+    gc = np.zeros(f["color"].shape, np.float32)
+    gc[:, :, r0:r1] = 2.0 * d / S
+    sw = np.zeros(f["tri_id"].shape, np.float32)
+    sw[:, r0:r1] = (d.astype(np.float64) ** 2).sum(1) / S
+    O.backward(sc.verts, sc.tex, sc.grid_n, [cam], S, [f], [gc], [sw], rows=(r0, r1), scan=True)
     frags = int(f["n_cover"][:, r0:r1].sum())
     return frags, time.perf_counter() - t0
 
@@ -1002,10 +1030,13 @@ def oracle_pool(cores: int):
     return mp.get_context("spawn").Pool(cores, initializer=_oracle_init)
 
 
-def oracle_sample(pool, cores: int, view: int = 0, start_row: int = 400, seed: int = 13):
-    """One row per process of `view`; fragments/s over the wall time of the
-    sample."""
-    jobs = [(view, start_row + k, start_row + k + 1, seed) for k in range(cores)]
+def oracle_sample(pool, cores: int, start_row: int, seed: int = 13):
+    """Rows start_row .. start_row + cores - 1 of view CPU_VIEW, one per
+    process; fragments/s over the wall time of the timed pass (targets
+    rendered before, untimed)."""
+    rows = [(CPU_VIEW, start_row + k, start_row + k + 1) for k in range(cores)]
+    tg = pool.map(_oracle_target, rows)
+    jobs = [r + (seed, t) for r, t in zip(rows, tg)]
     t0 = time.perf_counter()
     res = pool.map(_oracle_rows, jobs)
     wall = time.perf_counter() - t0
@@ -1013,13 +1044,36 @@ def oracle_sample(pool, cores: int, view: int = 0, start_row: int = 400, seed: i
     return frags / wall, wall, frags
 
 
-def cpu_baseline_entry():
+def oracle_one_core(start_row: int, n_rows: int, seed: int = 13):
+    """The same unit on one core, in this process: rows start_row ..
+    start_row + n_rows - 1 one after another."""
+    frags = 0
+    secs = 0.0
+    for k in range(n_rows):
+        r = (CPU_VIEW, start_row + k, start_row + k + 1)
+        tg = _oracle_target(r)
+        f, t = _oracle_rows(r + (seed, tg))
+        frags += f
+        secs += t
+    return frags / secs, secs, frags
+
+
+def cpu_baseline_entry(fragments_per_step=None):
     cores = _cores()
     with oracle_pool(cores) as pool:
-        v, wall, frags = oracle_sample(pool, cores)
-    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d rows of a 1920x1080 view (one row per process, S=4, fwd+bwd incl. the target render), "
-                      "%d fragments in %.1f s wall" % (cores, frags, wall)}
+        v, wall, frags = oracle_sample(pool, cores, CPU_ROW0)
+    v1, secs1, frags1 = oracle_one_core(CPU_ROW0, 2)
+    out = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle (bbox-scan mode, results equal to brute force)",
+           "sample": "rows %d-%d of view %d (1920x1080), one row per process, S=4, forward + L2 loss + backward "
+                     "(all gradient terms), targets rendered before, untimed: %d fragments in %.2f s wall"
+                     % (CPU_ROW0, CPU_ROW0 + cores - 1, CPU_VIEW, frags, wall),
+           "cores_1": {"value": v1, "unit": UNIT, "cores": 1,
+                       "sample": "rows %d-%d of the same view on one core: %d fragments in %.2f s"
+                                 % (CPU_ROW0, CPU_ROW0 + 1, frags1, secs1)}}
+    if fragments_per_step:
+        out["extrapolated_s_per_step"] = {"cores": fragments_per_step / v, "cores_1": fragments_per_step / v1,
+                                          "what": "extrapolated: the step's fragments at the sampled rate"}
+    return out
 
 
 def _reference_arm(args):
@@ -1029,23 +1083,25 @@ def _reference_arm(args):
     cores = _cores()
     for _ in range(args.warmup):
         pass   # the oracle has no warm-up state; warm-up samples would only repeat the work
-    # each step: one row per process of a 960x540 view of the workload
-    # (view 4), so that --steps K stays within a few minutes
+    # each step: the next band of rows of the workload's first view, one row
+    # per process (the rows the GPU arm's cpu_baseline times come first)
     vals, walls, total = [], [], 0
     with oracle_pool(cores) as pool:
         for k in range(args.steps):
-            v, wall, frags = oracle_sample(pool, cores, view=4, start_row=150 + 7 * k)
+            v, wall, frags = oracle_sample(pool, cores, start_row=CPU_ROW0 + cores * k)
             vals.append(v)
             walls.append(wall)
             total += frags
     value = total / sum(walls)
+    sample = ("per step %d rows of view %d (1920x1080), one row per process, from row %d on, S=4, forward + L2 "
+              "loss + backward; oracle in bbox-scan mode" % (cores, CPU_VIEW, CPU_ROW0))
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded soups, cameras, targets)",
-            "config": {"workload": WORKLOAD, "sample": "per step %d rows of view 4 (960x540), one per process" % cores},
+            "config": workload_config(world),
             "impl": "reference",
-            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value, "unit": UNIT,
-                             "sample": "per step %d rows of a 960x540 view of the workload, S=4, fwd+bwd" % cores},
+            "cpu_baseline": {"kind": "oracle (bbox-scan mode)", "cores": cores, "value": value, "unit": UNIT,
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -1084,6 +1140,10 @@ def main():
         cpu = cpu_baseline_entry()   # before the first GPU call (spawned workers)
     line = _gpu_arm(args)
     if line is not None:
+        if cpu is not None:
+            f = line["workload_stats"]["fragments_per_step"]
+            cpu["extrapolated_s_per_step"] = {"cores": f / cpu["value"], "cores_1": f / cpu["cores_1"]["value"],
+                                              "what": "extrapolated: the step's fragments at the sampled rate"}
         line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
 

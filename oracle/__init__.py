@@ -331,11 +331,13 @@ def backward(verts, tex, grid_n, cams, S, fwd, grad_color, score_w, flags=G_ALL,
     verts = _c(verts, np.float32); tex = _c(tex, np.float32)
     T, V, C = tex.shape
     cf, wh = _cams(cams)
-    tri = _c(np.concatenate([f["tri_id"].ravel() for f in fwd]), np.int32)
-    bary = _c(np.concatenate([f["bary"].ravel() for f in fwd]), np.float32)
-    col = _c(np.concatenate([f["color"].ravel() for f in fwd]), np.float32)
-    gc = _c(np.concatenate([g.ravel() for g in grad_color]), np.float32)
-    sw = _c(np.concatenate([w.ravel() for w in score_w]), np.float32)
+    def cat(arrays, dt):   # one view: no copy
+        return _c(arrays[0].reshape(-1) if len(arrays) == 1 else np.concatenate([a.ravel() for a in arrays]), dt)
+    tri = cat([f["tri_id"] for f in fwd], np.int32)
+    bary = cat([f["bary"] for f in fwd], np.float32)
+    col = cat([f["color"] for f in fwd], np.float32)
+    gc = cat(list(grad_color), np.float32)
+    sw = cat(list(score_w), np.float32)
     gt = np.zeros(tex.shape, np.float64); gv = np.zeros(verts.shape, np.float64)
     r0, r1 = (0, -1) if rows is None else rows
     rc = lib().or_backward(_p(verts), _p(tex), T, grid_n, C, _p(cf), _p(wh), len(cams), S,

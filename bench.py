@@ -507,6 +507,124 @@ def _loss_optim_leg(wl, reps: int = 10):
                     "the texture logits + VectorAdam on the vertices"}
 
 
+# ---------------------------------------------------------------- the small configurations
+def _config_scenes(name: str):
+    """(scene, target scene) of the 64-triangle plain workload ("plain
+    small") or of the 2,000-triangle batched views ("batched views")."""
+    if name == "plain_small":
+        return I.plain_small(), I.plain_small(soup_seed=1)
+    return I.batched_views(), I.batched_views(soup_seed=4)
+
+
+def _oracle_view(job):
+    """CPU oracle (bbox-scan mode) on one whole view of a small
+    configuration: forward + L2 loss + backward with every gradient term,
+    the target rendered first, untimed.  Returns (fragments, seconds)."""
+    import oracle as O
+    name, v = job
+    sc, tsc = _config_scenes(name)
+    cam, S = sc.cams[v], sc.samples
+    tg = O.forward(tsc.verts, tsc.tex, tsc.grid_n, [cam], np.zeros(1, np.uint64), S=1,
+                   mode=O.MODE_THRESHOLD_HALF, bg=sc.bg, scan=True)[0]["color"][0]
+    t0 = time.perf_counter()
+    f = O.forward(sc.verts, sc.tex, sc.grid_n, [cam], sc.seeds[v:v + 1], S=S, bg=sc.bg, scan=True)[0]
+    d = f["color"] - tg[None]
+    gc = (2.0 * d / S).astype(np.float32)
+    sw = ((d.astype(np.float64) ** 2).sum(1) / S).astype(np.float32)
+    O.backward(sc.verts, sc.tex, sc.grid_n, [cam], S, [f], [gc], [sw], scan=True)
+    return int(f["n_cover"].sum()), time.perf_counter() - t0
+
+
+def _config_cpu(name: str, n_views: int):
+    """The oracle on the whole configuration: every view on its own process
+    (all cores), and the same views one after another on one core."""
+    import oracle as O
+    O.build()
+    jobs = [(name, v) for v in range(n_views)]
+    cores = min(_cores(), n_views)
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_view, jobs[:1])                  # workers warm (library loaded)
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_view, jobs)
+        wall = time.perf_counter() - t0
+    frags = sum(r[0] for r in res)
+    one = [_oracle_view(j) for j in jobs]
+    f1, s1 = sum(r[0] for r in one), sum(r[1] for r in one)
+    return {"value": frags / wall, "unit": UNIT, "cores": cores, "seconds": wall,
+            "cores_1": {"value": f1 / s1, "unit": UNIT, "cores": 1, "seconds": s1},
+            "kind": "oracle (bbox-scan mode), whole configuration, forward + L2 loss + backward"}
+
+
+def _config_leg(name: str, device: str, steps: int, tune: bool = True):
+    """fwd+bwd fragments/s of a small configuration on the GPU (one fused
+    training pass over all views per step, autotuned launch parameters),
+    on the plain path (one view per call, default launch parameters) and in
+    the CPU oracle.  CUDA events over ``steps`` steps after 5 warm-up
+    steps; the inputs stay resident (these configurations fit in L2, so the
+    numbers are L2-resident by construction)."""
+    import torch
+    from paper_2603_27151_gb300 import autotune
+    from paper_2603_27151_gb300 import native as N
+    sc, tsc = _config_scenes(name)
+    S, C = sc.samples, sc.C
+    ctx = N.Context(torch.cuda.current_device())
+    verts, tex = torch.from_numpy(sc.verts).to(device), torch.from_numpy(sc.tex).to(device)
+    sid = ctx.soup_upload(verts, tex, sc.grid_n, borrow=True)
+    tv, tt = torch.from_numpy(tsc.verts).to(device), torch.from_numpy(tsc.tex).to(device)
+    tsid = ctx.soup_upload(tv, tt, tsc.grid_n)
+    tg, tc, _ = N.alloc_outputs(sc.cams, 1, C, device)
+    ctx.raster_forward(tsid, sc.cams, None, 1, N.DS_MODE_THRESHOLD_HALF, sc.bg, tg, tc)
+    targets = [c[0].contiguous() for c in tc]
+    g, col, _ = N.alloc_outputs(sc.cams, S, C, device)
+    gcol = [torch.empty_like(c) for c in col]
+    sw = [torch.empty((S, c.height, c.width), device=device) for c in sc.cams]
+    loss = torch.zeros(1, device=device)
+    gt, gv = torch.zeros_like(tex), torch.zeros_like(verts)
+    fragments = ctx.fragment_count(sid, sc.cams) * S
+
+    def batched():
+        loss.zero_()
+        ctx.train_l2(sid, sc.cams, sc.seeds, S, N.DS_MODE_STOCHASTIC, sc.bg, g, col, targets, gcol, sw, 1.0 / S,
+                     loss, N.DS_G_ALL | N.DS_OVERWRITE, gv, gt)
+
+    def plain():
+        loss.zero_()
+        for v in range(len(sc.cams)):
+            one = slice(v, v + 1)
+            ctx.train_l2(sid, sc.cams[one], sc.seeds[one], S, N.DS_MODE_STOCHASTIC, sc.bg, g[one], col[one],
+                         targets[one], gcol[one], sw[one], 1.0 / S, loss,
+                         N.DS_G_ALL | (N.DS_OVERWRITE if v == 0 else 0), gv, gt)
+
+    def timed(fn):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    ctx.set_tuning()
+    plain_ms = timed(plain)
+    tuning = None
+    if tune:
+        batched()
+        tuning = autotune.tuned(ctx, sid, sc.T, sc.grid_n, C, sc.cams, sc.seeds, S, N.DS_MODE_STOCHASTIC, sc.bg, g,
+                                col, gcol, sw, gv, gt, reps=3, targets=targets, scale=1.0 / S)
+    batched_ms = timed(batched)
+    ctx.close()
+    px = sum(c.width * c.height for c in sc.cams)
+    return {"gpu": {"value": fragments / (batched_ms / 1e3), "unit": UNIT, "ms_per_step": batched_ms,
+                    "tuning": tuning},
+            "gpu_plain": {"value": fragments / (plain_ms / 1e3), "unit": UNIT, "ms_per_step": plain_ms},
+            "batched_speedup": plain_ms / batched_ms,
+            "fragments_per_step": fragments, "pixel_samples_per_step": px * S, "views": len(sc.cams),
+            "triangles": sc.T}
+
+
 def widened_cases():
     """One launch of each kernel of the widened rows on a case larger than L2
     (for profiler captures; prints one check line, not a bench line): deferred
@@ -711,13 +829,35 @@ def _train_leg(device: str, iters: int, fused: bool = True):
                     "one CUDA graph per step vs the same step launched eagerly"}
 
 
-def _serve_leg(device: str, seconds: float, plain: bool):
-    """Replay the Poisson request stream (16 resident soups, 2000 requests/s,
-    resolutions 256^2 .. 1920x1080, forward with binary opacity)."""
+def _request_fragments(device, soups, reqs):
+    """Covered (pixel, triangle) pairs of each request's view (|F| of Eq. 1,
+    one sample), counted by the library on a separate context, summed over
+    the requests."""
+    import torch
+    from paper_2603_27151_gb300 import native as N
+    ctx = N.Context(torch.cuda.current_device())
+    total = 0
+    by_soup = {}
+    for (_, k, cam, _) in reqs:
+        by_soup.setdefault(k, []).append(cam)
+    for k, cams in by_soup.items():
+        sc = soups[k]
+        v, t = torch.from_numpy(sc.verts).to(device), torch.from_numpy(sc.tex).to(device)
+        sid = ctx.soup_upload(v, t, sc.grid_n, borrow=True)
+        for i in range(0, len(cams), 64):
+            total += ctx.fragment_count(sid, cams[i:i + 64])
+        ctx.soup_free(sid)
+    ctx.close()
+    return total
+
+
+def _serve_run(device, soups, reqs, plain: bool, time_scale: float = 1.0):
+    """Replay ``reqs`` through the batching server (4 worker streams, up to
+    16 same-soup requests per launch, 8 GiB admission budget) or the plain
+    server (one stream, one request per launch)."""
     import torch
     from paper_2603_27151_gb300 import native as N
     from paper_2603_27151_gb300.serve import SlotPool, replay
-    soups, reqs = I.serving_workload(duration=seconds)
     if plain:
         srv = N.Server(torch.cuda.current_device(), n_streams=1, mem_budget=8 << 30, max_batch=1,
                        reserve_pairs=1 << 22)
@@ -731,19 +871,57 @@ def _serve_leg(device: str, seconds: float, plain: bool):
     warm = [(0.0, k, I.look_at(np.array([0.0, -3.0, 0.5]), w, h), 1) for k in range(len(soups))
             for (w, h) in I.SERVE_RESOLUTIONS]
     replay(srv, ids, warm * 2, pool, time_scale=0.0)
-    r = replay(srv, ids, reqs, pool)
+    r = replay(srv, ids, reqs, pool, time_scale=time_scale)
     srv.close()
+    return r
+
+
+def _serve_stats(r, fragments: int, offered):
     lat = r["latency_ms"]
     n = len(lat)
     bytes_per_px = 16 + 4 * 7
+    out_bytes = float(r["pixels"].sum()) * bytes_per_px
     return {"requests": n, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "frames_per_s": n / r["span_s"],
             "pixels_per_s": float(r["pixels"].sum()) / r["span_s"],
-            "output_gbs": float(r["pixels"].sum()) * bytes_per_px / r["span_s"] / 1e9,
-            "hbm_frac": float(r["pixels"].sum()) * bytes_per_px / r["span_s"] / 1e9 / _peaks()[0],
-            "mean_batch": float(r["batch"].mean()), "offered_rps": len(reqs) / seconds,
-            "what": ("plain: one stream, one request per launch" if plain else
-                     "4 worker streams, up to 16 same-soup requests per launch, 8 GiB admission budget")}
+            "fragments_per_s": fragments / r["span_s"],
+            "output_gbs": out_bytes / r["span_s"] / 1e9,
+            "hbm_frac": out_bytes / r["span_s"] / 1e9 / _peaks()[0],
+            "mean_batch": float(r["batch"].mean()), "offered_rps": offered}
+
+
+def _serve_leg(device: str, seconds: float, plain: bool):
+    """Replay the Poisson request stream (16 resident soups, 2000 requests/s,
+    resolutions 256^2 .. 1920x1080, forward with binary opacity)."""
+    soups, reqs = I.serving_workload(duration=seconds)
+    r = _serve_run(device, soups, reqs, plain)
+    out = _serve_stats(r, _request_fragments(device, soups, reqs), len(reqs) / seconds)
+    out["what"] = ("plain: one stream, one request per launch" if plain else
+                   "4 worker streams, up to 16 same-soup requests per launch, 8 GiB admission budget")
+    return out
+
+
+def _serve_sweep(device: str):
+    """The same stream at higher Poisson rates, and closed loop (every request
+    submitted at once: the server saturated), through the batching server and
+    the plain server.  fragments/s counts the covered (pixel, triangle)
+    pairs of the served views; hbm_frac is the output bytes (G-buffer and
+    colour) per second over the measured HBM bandwidth."""
+    out = []
+    for rate, secs in ((8000.0, 2.5), (20000.0, 1.5), (None, 0.0)):
+        if rate is None:
+            soups, reqs = I.serving_workload(rate=4000.0, duration=1.0, arrival_seed=41)
+            scale, offered = 0.0, "closed loop (all submitted at once)"
+        else:
+            soups, reqs = I.serving_workload(rate=rate, duration=secs, arrival_seed=41)
+            scale, offered = 1.0, len(reqs) / secs
+        frags = _request_fragments(device, soups, reqs)
+        row = {"offered_rps": offered}
+        for plain in (False, True):
+            r = _serve_run(device, soups, reqs, plain, time_scale=scale)
+            row["plain" if plain else "batching"] = _serve_stats(r, frags, offered)
+        out.append(row)
+    return out
 
 
 def _gpu_arm(args):
@@ -943,6 +1121,11 @@ def _gpu_arm(args):
         line["plain_path"] = extras["plain_path"]
         line["plain_path"]["batched_speedup"] = value / world / extras["plain_path"]["value"]
     if not args.views and not args.no_extras and world == 1:
+        for name in ("plain_small", "batched_views"):
+            leg = _config_leg(name, dev, 200 if name == "plain_small" else 50)
+            if not args.no_cpu_baseline:
+                leg["cpu_oracle"] = _config_cpu(name, leg["views"])
+            line[name] = leg
         line["shade"] = _shade_leg(wl, max(5, args.steps // 4))
         line["adapt"] = _adapt_leg(wl)
         line["loss_optim"] = _loss_optim_leg(wl)
@@ -957,6 +1140,7 @@ def _gpu_arm(args):
         if args.serve_seconds > 0:
             line["serve"] = _serve_leg(dev, args.serve_seconds, plain=False)
             line["serve_plain"] = _serve_leg(dev, args.serve_seconds, plain=True)
+            line["serve_sweep"] = _serve_sweep(dev)
     return line
 
 

@@ -195,7 +195,8 @@ DS_API ds_status ds_levels_resample(const float* src, int32_t T, int32_t r_src, 
 
 /* Forward pass (Eq. 5; Algorithm A1 step 1) for n_views views of one soup:
  * sigmoid activation of the texture (Sec. 3.3), triangle set-up, radix-sorted
- * binning of triangles into 16x16 pixel tiles, then per pixel and sample the
+ * binning of triangles into tiles of 256 pixels (8x32, 16x16 or 32x8: a
+ * launch parameter of the context, see ds_set_tuning), then per pixel and sample the
  * foremost covered fragment whose interpolated opacity exceeds its threshold
  * (fixed tie-break: larger perspective-correct inverse depth first, then the
  * lower triangle index), and the mesh-colour decode of its C-1 colour
@@ -462,7 +463,8 @@ DS_API ds_status ds_fragment_count(ds_ctx* ctx, int32_t soup_id, const ds_camera
 
 /* Sizes of the context's current binning plan (the last forward, backward or
  * fragment count): *pairs = (tile, triangle) pairs after binning, *tiles =
- * 16x16 tiles over all views.  Host values; never synchronises. */
+ * tiles (of the context's tile shape) over all views.  Host values; never
+ * synchronises. */
 DS_API ds_status ds_plan_stats(ds_ctx* ctx, int64_t* pairs, int64_t* tiles);
 
 /* Read and clear the context's device status word (synchronises the

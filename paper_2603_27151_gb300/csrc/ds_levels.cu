@@ -90,61 +90,166 @@ __host__ __device__ inline int stage_floats(int r_min, int r_max, int C) {
     return n;
 }
 
-// One CTA per triangle.  Stage the triangle's levels in shared memory, then
-// for every (finest vertex, channel group) sum the levels' values at the
-// vertex from the coarsest up (FP32, the oracle's order) and write the
-// composed logits, or their sigmoid with the planar opacity copy.  kVec:
-// groups of four channels (C % 4 == 0, 16-byte aligned levels and output),
-// else one channel per item.
-template <bool kAct, bool kVec>
+// Sigmoid of Sec. 3.3 with the reciprocal of (1 + e^-x) taken by the
+// correctly rounded reciprocal: the same value as pinned_sigmoid's IEEE
+// division 1 / (1 + e^-x) (both round 1/y to nearest; y >= 1).
+__device__ __forceinline__ float sigmoid_rcp(float th) { return __frcp_rn(__fadd_rn(1.0f, pinned_exp(-th))); }
+
+// Tap of one coarse level at one finest vertex, shared by every triangle:
+// corner texel indices k0 | k1 << 10 | k2 << 20 (| 1 << 30 when the vertex
+// coincides with level vertex k0) and the interpolation weights (wa, wb) of
+// the decode (R3), exact multiples of 2^-(r_max - R).
+struct Tap {
+    uint32_t k;
+    float wa, wb;
+};
+
+__device__ __forceinline__ Tap make_tap(int R, int i, int j, int Nf, int r_max) {
+    const int NR = 1 << R, sh = r_max - R, m = (1 << sh) - 1;
+    Tap tp;
+    if (!(i & m) && !(j & m)) {
+        tp.k = (uint32_t)texel_index(NR, i >> sh, j >> sh) | (1u << 30);
+        tp.wa = tp.wb = 0.f;
+        return tp;
+    }
+    const float inv = __frcp_rn((float)Nf);   // exact power of two
+    const Cell cl = find_cell(NR, __fmul_rn((float)i, inv), __fmul_rn((float)j, inv));
+    tp.k = (uint32_t)cl.k0 | ((uint32_t)cl.k1 << 10) | ((uint32_t)cl.k2 << 20);
+    tp.wa = cl.wa;
+    tp.wb = cl.wb;
+    return tp;
+}
+
+// Channels c..c+3 of level grid zl at a tap (the coinciding vertex, or the
+// decode's interpolation in FP32 in the decode's order).
+__device__ __forceinline__ float4 tap_value(const float* zl, const Tap& tp, int C, int c) {
+    const float4 a0 = *reinterpret_cast<const float4*>(zl + (size_t)(tp.k & 1023u) * C + c);
+    if (tp.k >> 30) return a0;
+    const float4 a1 = *reinterpret_cast<const float4*>(zl + (size_t)((tp.k >> 10) & 1023u) * C + c);
+    const float4 a2 = *reinterpret_cast<const float4*>(zl + (size_t)((tp.k >> 20) & 1023u) * C + c);
+    return make_float4(interp(a0.x, a1.x, a2.x, tp.wa, tp.wb), interp(a0.y, a1.y, a2.y, tp.wa, tp.wb),
+                       interp(a0.z, a1.z, a2.z, tp.wa, tp.wb), interp(a0.w, a1.w, a2.w, tp.wa, tp.wb));
+}
+
+// 16-byte asynchronous copy global -> shared (cp.async, completion by
+// commit/wait groups: no spin loop).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Issue the copies of triangle t's levels r_min..r_max into the stage zs.
+__device__ __forceinline__ void stage_levels(float* zs, const float* __restrict__ levels, int t, int T, int r_min,
+                                             int r_max, int C) {
+    size_t off = 0;   // offset of level R in `levels`
+    int so = 0;       // offset of level R in zs
+    for (int R = r_min; R <= r_max; ++R) {
+        const int n = level_V(R) * C;
+        const float* g = levels + off + (size_t)t * n;
+        for (int k = threadIdx.x; k < n / 4; k += blockDim.x) cp_async16(zs + so + 4 * k, g + 4 * k);
+        off += (size_t)T * n;
+        so += n;
+    }
+}
+
+// Persistent CTAs (grid-stride over triangles), C % 4 == 0 and 16-byte
+// aligned levels and output.  Shared memory: the taps of the coarse levels
+// at every finest vertex (computed once per CTA: they do not depend on the
+// triangle), then two stages of one triangle's levels.  While the CTA sums
+// triangle t from one stage, the asynchronous copies of its next triangle
+// fill the other.  Each thread takes finest vertices; for every group of
+// four channels the levels' values are summed from the coarsest up (FP32,
+// the oracle's order), then activated and written.
+template <bool kAct>
 __global__ void __launch_bounds__(256) k_compose(const float* __restrict__ levels, int T, int r_min, int r_max, int C,
                                                  float* __restrict__ out, float* __restrict__ act_a) {
+    extern __shared__ __align__(16) float smem[];
+    const int Nf = 1 << r_max, Vf = level_V(r_max), L = r_max - r_min;   // L coarse levels
+    Tap* taps = reinterpret_cast<Tap*>(smem);                              // [L][Vf]
+    const int tap_floats = (3 * L * Vf + 3) & ~3;
+    const int sf = stage_floats(r_min, r_max, C);
+    float* const stage0 = smem + tap_floats;   // stage b at stage0 + b * sf
+    int t = blockIdx.x;
+    if (t < T) stage_levels(stage0, levels, t, T, r_min, r_max, C);
+    cp_async_commit();
+    for (int q = threadIdx.x; q < L * Vf; q += blockDim.x) {
+        const int l = q / Vf, v = q - l * Vf;
+        int i, j;
+        texel_ij(Nf, v, i, j);
+        taps[q] = make_tap(r_min + l, i, j, Nf, r_max);
+    }
+    int buf = 0;
+    for (; t < T; t += gridDim.x) {
+        const int tn = t + gridDim.x;
+        if (tn < T) stage_levels(stage0 + (buf ^ 1) * sf, levels, tn, T, r_min, r_max, C);
+        cp_async_commit();
+        cp_async_wait<1>();   // this thread's copies of triangle t have landed
+        __syncthreads();      // everyone's (and the taps)
+        const float* zs = stage0 + buf * sf;
+        const float* fine = zs + sf - Vf * C;   // the finest level's slab
+        for (int v = threadIdx.x; v < Vf; v += blockDim.x) {
+            for (int c = 0; c < C; c += 4) {
+                int so = 0;
+                float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int l = 0; l < L; ++l) {
+                    const float4 y = tap_value(zs + so, taps[l * Vf + v], C, c);
+                    z = l == 0 ? y : add4(z, y);
+                    so += level_V(r_min + l) * C;
+                }
+                const float4 y = *reinterpret_cast<const float4*>(fine + (size_t)v * C + c);
+                z = L == 0 ? y : add4(z, y);
+                if (kAct) {
+                    z = make_float4(sigmoid_rcp(z.x), sigmoid_rcp(z.y), sigmoid_rcp(z.z), sigmoid_rcp(z.w));
+                    if (c + 4 == C && act_a) act_a[(size_t)t * Vf + v] = z.w;
+                }
+                __stcs(reinterpret_cast<float4*>(out + ((size_t)t * Vf + v) * C + c), z);
+            }
+        }
+        __syncthreads();      // stage[buf] is refilled next round
+        buf ^= 1;
+    }
+    cp_async_wait<0>();
+}
+
+// Any C or alignment: one CTA per triangle, the levels staged with plain
+// loads, one (finest vertex, channel) per item; the same sum in the same
+// order.
+template <bool kAct>
+__global__ void __launch_bounds__(256) k_compose_scalar(const float* __restrict__ levels, int T, int r_min, int r_max,
+                                                        int C, float* __restrict__ out, float* __restrict__ act_a) {
     extern __shared__ __align__(16) float zs[];   // levels r_min..r_max of triangle t, one after the other
     const int t = blockIdx.x;
     {
-        size_t off = 0;   // offset of level R in `levels`
-        int so = 0;       // offset of level R in zs
+        size_t off = 0;
+        int so = 0;
         for (int R = r_min; R <= r_max; ++R) {
             const int n = level_V(R) * C;
             const float* g = levels + off + (size_t)t * n;
-            if (kVec) {
-                for (int k = threadIdx.x; k < n / 4; k += blockDim.x)
-                    reinterpret_cast<float4*>(zs + so)[k] = __ldcs(reinterpret_cast<const float4*>(g) + k);
-            } else {
-                for (int k = threadIdx.x; k < n; k += blockDim.x) zs[so + k] = __ldcs(g + k);
-            }
+            for (int k = threadIdx.x; k < n; k += blockDim.x) zs[so + k] = __ldcs(g + k);
             off += (size_t)T * n;
             so += n;
         }
     }
     __syncthreads();
     const int Nf = 1 << r_max, Vf = level_V(r_max);
-    const int per = kVec ? C / 4 : C;   // items per vertex
-    for (int it = threadIdx.x; it < Vf * per; it += blockDim.x) {
-        const int v = it / per, c = (it - v * per) * (kVec ? 4 : 1);
+    for (int it = threadIdx.x; it < Vf * C; it += blockDim.x) {
+        const int v = it / C, c = it - v * C;
         int i, j;
         texel_ij(Nf, v, i, j);
-        float4 z = level_at<kVec>(zs, r_min, C, c, i, j, Nf, r_max);
+        float z = level_at<false>(zs, r_min, C, c, i, j, Nf, r_max).x;
         int so = level_V(r_min) * C;
         for (int R = r_min + 1; R <= r_max; ++R) {
-            z = add4(z, level_at<kVec>(zs + so, R, C, c, i, j, Nf, r_max));
+            z = __fadd_rn(z, level_at<false>(zs + so, R, C, c, i, j, Nf, r_max).x);
             so += level_V(R) * C;
         }
-        float* o = out + ((size_t)t * Vf + v) * C + c;
-        if (kVec) {
-            if (kAct) {
-                z = make_float4(pinned_sigmoid(z.x), pinned_sigmoid(z.y), pinned_sigmoid(z.z), pinned_sigmoid(z.w));
-                if (c + 4 == C && act_a) act_a[(size_t)t * Vf + v] = z.w;
-            }
-            __stcs(reinterpret_cast<float4*>(o), z);
-        } else {
-            float y = z.x;
-            if (kAct) {
-                y = pinned_sigmoid(y);
-                if (c == C - 1 && act_a) act_a[(size_t)t * Vf + v] = y;
-            }
-            *o = y;
+        if (kAct) {
+            z = pinned_sigmoid(z);
+            if (c == C - 1 && act_a) act_a[(size_t)t * Vf + v] = z;
         }
+        out[((size_t)t * Vf + v) * C + c] = z;
     }
 }
 
@@ -268,20 +373,30 @@ cudaError_t launch_compose(const float* levels, int T, int r_min, int r_max, int
             k_compose_single<true><<<flat_grid(n), 256, 0, st>>>(levels, n, C, out, act_a);
         else
             k_compose_single<false><<<flat_grid(n), 256, 0, st>>>(levels, n, C, out, nullptr);
+    } else if ((C % 4 == 0) && ((uintptr_t)levels % 16 == 0) && ((uintptr_t)out % 16 == 0)) {
+        const int Vf = level_V(r_max), L = r_max - r_min;
+        const size_t smem = sizeof(float) * ((size_t)((3 * L * Vf + 3) & ~3) + 2 * (size_t)stage_floats(r_min, r_max, C));
+        auto run = [&](auto kernel) {
+            cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            int per_sm = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smem);
+            if (e != cudaSuccess) return e;
+            const int grid = persistent_grid(T, per_sm < 1 ? 1 : per_sm);
+            kernel<<<grid, 256, smem, st>>>(levels, T, r_min, r_max, C, out, act ? act_a : nullptr);
+            return cudaSuccess;
+        };
+        cudaError_t e = act ? run(k_compose<true>) : run(k_compose<false>);
+        if (e != cudaSuccess) return e;
     } else {
         const size_t smem = sizeof(float) * (size_t)stage_floats(r_min, r_max, C);
-        const bool vec = (C % 4 == 0) && ((uintptr_t)levels % 16 == 0) && ((uintptr_t)out % 16 == 0);
         auto run = [&](auto kernel) {
             cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             kernel<<<T, 256, smem, st>>>(levels, T, r_min, r_max, C, out, act ? act_a : nullptr);
             return cudaSuccess;
         };
-        cudaError_t e;
-        if (act)
-            e = vec ? run(k_compose<true, true>) : run(k_compose<true, false>);
-        else
-            e = vec ? run(k_compose<false, true>) : run(k_compose<false, false>);
+        cudaError_t e = act ? run(k_compose_scalar<true>) : run(k_compose_scalar<false>);
         if (e != cudaSuccess) return e;
     }
     note_launches(1);

@@ -11,6 +11,14 @@
 //    mask-induced boundaries inside it.
 //  k_grad_finish: adds the FP64 accumulators to the caller's FP32 gradients.
 //
+// Lane use: the walks are warp-synchronous (a warp steps through the tile's
+// staged triangles, or through the samples of its pixels), and a small
+// triangle covers few of a warp's 32 pixels.  The expensive work found on
+// the way -- the opacity lookup and scatter of a fragment in front of a
+// winner, the texture and interior terms of a pixel's distinct winners, an
+// edge side -- is therefore queued per warp in shared memory and evaluated
+// 32 jobs at a time, every lane busy.
+//
 // Scatter: lanes holding the same target (texel cell or triangle) in
 // consecutive lanes are summed in registers first (warp_run_sum); only the
 // first lane of each run issues the atomics, which accumulate in FP64 so that
@@ -164,30 +172,6 @@ __device__ __forceinline__ void ray_bary(const GeomRec* g, const DevCam& cam, fl
 }
 
 // ------------------------------------------------------------ texture scatter
-// Opacity-channel score gradient g of one lane's fragment (cell cl of
-// triangle t), chained through the interpolation weights and the sigmoid.
-__device__ __forceinline__ void scatter_alpha_run(const SoupDev& s, double* acc_tex, bool act, int t, const Cell& cl,
-                                                  float g) {
-    float v[3] = {0.f, 0.f, 0.f};
-    unsigned long long key = lane_sentinel();
-    if (act) {
-        v[0] = g * (1.0f - cl.wa - cl.wb);
-        v[1] = g * cl.wa;
-        v[2] = g * cl.wb;
-        key = ((unsigned long long)(unsigned)t << 20) | ((unsigned)cl.k0 << 1) | (cl.lower ? 1u : 0u);
-    }
-    const bool head = warp_run_sum<3>(key, v);
-    if (act && head) {
-        const float* aa = s.act_a + (size_t)t * s.V;
-        const int ks[3] = {cl.k0, cl.k1, cl.k2};
-#pragma unroll
-        for (int m = 0; m < 3; ++m) {
-            const float a = __ldg(aa + ks[m]);
-            atomicAdd(acc_tex + ((size_t)t * s.V + ks[m]) * s.C + (s.C - 1), (double)(v[m] * a * (1.0f - a)));
-        }
-    }
-}
-
 // Winner terms of one sample: colour gradient (C-1 channels) and the +w/alpha
 // opacity score, merged into one pass over the corner texels, four channels
 // at a time.  G receives dL/d(b1, b2) of the colour (for the interior term).
@@ -323,14 +307,66 @@ __device__ __forceinline__ void interior_grad(const GeomRec* g, const DevCam& ca
 // (Algorithm A1 2(b), G-buffer recomputation): walk the tile's list again and
 // scatter -w/(1 - alpha) to the opacity texels of the fragments in front.
 // `staged`: the whole list is already in shared memory (one chunk).
+//
+// The walk is warp-synchronous over the staged triangles, and a small
+// triangle covers few of a warp's pixels, so the opacity lookup and the
+// scatter of a fragment in front are not done where it is found: each lane
+// appends (triangle, barycentrics, summed score weight) to the warp's ring
+// in shared memory, and whenever 32 jobs wait the warp evaluates them with
+// every lane busy (the rest after the walk).
+struct ScoreJob {
+    int t;
+    float b1, b2;
+    float gw;   // sum of the score weights of the samples whose winner lies behind
+};
+constexpr int kScoreRing = 64;   // up to 31 waiting jobs + 32 new ones
+
+// Evaluate n <= 32 jobs of the ring from `head`: opacity at the fragment,
+// g = -gw / (1 - alpha), chained through the interpolation weights and the
+// sigmoid (a (1 - a) at each corner texel), summed over runs of lanes on
+// the same cell, one FP64 atomic per corner and run.
+__device__ __forceinline__ void score_batch(const SoupDev& s, double* __restrict__ acc_tex, const ScoreJob* ring,
+                                            int head, int n) {
+    const int lane = threadIdx.x & 31;
+    const bool act = lane < n;
+    ScoreJob jb{0, 0.f, 0.f, 0.f};
+    if (act) jb = ring[(head + lane) & (kScoreRing - 1)];
+    Cell cl;
+    cl.k0 = cl.k1 = cl.k2 = 0;
+    cl.wa = cl.wb = 0.f;
+    cl.lower = true;
+    float v[3] = {0.f, 0.f, 0.f};
+    unsigned long long key = lane_sentinel();
+    if (act) {
+        cl = find_cell(s.N, jb.b1, jb.b2);
+        const float* aa = s.act_a + (size_t)jb.t * s.V;
+        const float a0 = __ldg(aa + cl.k0), a1 = __ldg(aa + cl.k1), a2 = __ldg(aa + cl.k2);
+        const float alpha = interp(a0, a1, a2, cl.wa, cl.wb);
+        const float g = -jb.gw / (1.0f - alpha);
+        v[0] = g * (1.0f - cl.wa - cl.wb) * (a0 * (1.0f - a0));
+        v[1] = g * cl.wa * (a1 * (1.0f - a1));
+        v[2] = g * cl.wb * (a2 * (1.0f - a2));
+        key = ((unsigned long long)(unsigned)jb.t << 20) | ((unsigned)cl.k0 << 1) | (cl.lower ? 1u : 0u);
+    }
+    const bool head_lane = warp_run_sum<3>(key, v);
+    if (act && head_lane) {
+        const int ks[3] = {cl.k0, cl.k1, cl.k2};
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+            atomicAdd(acc_tex + ((size_t)jb.t * s.V + ks[m]) * s.C + (s.C - 1), (double)v[m]);
+    }
+}
+
 template <int SG, int TW>
 __device__ __forceinline__ void score_walk(TileStage& sm, const SetupRec* __restrict__ recs,
                                            const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
                                            uint2 rg, int DB, int chunk, size_t vbase, const WorkItem& wi,
                                            const SoupDev& s, double* __restrict__ acc_tex, int tid, int lx, int ly,
                                            int warp, bool staged, bool any_score, const int (&wt)[SG],
-                                           const float (&wrho)[SG], const float (&wsc)[SG]) {
+                                           const float (&wrho)[SG], const float (&wsc)[SG], ScoreJob* ring) {
     constexpr int TH = kTilePix / TW;
+    const unsigned lt = (1u << (tid & 31)) - 1u;
+    int head = 0, count = 0;   // the warp's ring (same values in every lane)
     bool warp_done = !__any_sync(kFullMask, any_score);
     if (__syncthreads_or(!warp_done)) {
         for (uint32_t c0 = rg.x; c0 < rg.y; c0 += (uint32_t)chunk) {
@@ -357,88 +393,126 @@ __device__ __forceinline__ void score_walk(TileStage& sm, const SetupRec* __rest
                         }
                     }
                     const int t = h2.y;
-                    bool act = false;
-                    float g = 0.f;
-                    Cell cl;
-                    cl.k0 = cl.k1 = cl.k2 = 0;
-                    cl.wa = cl.wb = 0.f;
-                    cl.lower = true;
+                    bool need = false;
+                    float gw = 0.f, b1 = 0.f, b2 = 0.f;
                     long long E[3];
                     if (any_score && tile_cover(sm, j, lx, ly, E)) {
                         const Frag f = make_frag(E[0], E[1], E[2], sm.kk[j][0], sm.kk[j][1], sm.kk[j][2]);
-                        bool need = false;
 #pragma unroll
                         for (int q = 0; q < SG; ++q)
-                            need = need || (wsc[q] != 0.f && t != wt[q] &&
-                                            (wt[q] < 0 || in_front(f.rho, t, wrho[q], wt[q])));
+                            if (wsc[q] != 0.f && t != wt[q] && (wt[q] < 0 || in_front(f.rho, t, wrho[q], wt[q]))) {
+                                need = true;
+                                gw += wsc[q];
+                            }
                         if (need) {
                             const float r = __frcp_rn(f.rho);
-                            cl = find_cell(s.N, __fmul_rn(f.q1, r), __fmul_rn(f.q2, r));
-                            const float* aa = s.act_a + (size_t)t * s.V;
-                            const float alpha = interp(__ldg(aa + cl.k0), __ldg(aa + cl.k1), __ldg(aa + cl.k2), cl.wa, cl.wb);
-                            const float inv = 1.0f / (1.0f - alpha);
-#pragma unroll
-                            for (int q = 0; q < SG; ++q)
-                                if (wsc[q] != 0.f && t != wt[q] && (wt[q] < 0 || in_front(f.rho, t, wrho[q], wt[q])))
-                                    g -= wsc[q] * inv;
-                            act = true;
+                            b1 = __fmul_rn(f.q1, r);
+                            b2 = __fmul_rn(f.q2, r);
                         }
                     }
-                    if (__any_sync(kFullMask, act)) scatter_alpha_run(s, acc_tex, act, t, cl, g);
+                    const unsigned bal = __ballot_sync(kFullMask, need);
+                    if (bal) {
+                        if (need) ring[(head + count + __popc(bal & lt)) & (kScoreRing - 1)] = ScoreJob{t, b1, b2, gw};
+                        count += __popc(bal);
+                        __syncwarp();
+                        if (count >= 32) {
+                            score_batch(s, acc_tex, ring, head, 32);
+                            head = (head + 32) & (kScoreRing - 1);
+                            count -= 32;
+                            __syncwarp();
+                        }
+                    }
                 }
             }
             if (__syncthreads_and(warp_done)) break;
         }
     }
+    if (count > 0) score_batch(s, acc_tex, ring, head, count);
+    __syncwarp();
 }
 
 // Winner terms of every sample: colour (Algorithm A1 2(a)), +w/alpha
 // (2(b)) and the interior vertex term (first term of Eq. 8), once per
-// distinct winner of the pixel's samples.
-template <int SG>
+// distinct winner of a pixel's samples.  The warp's (pixel, distinct winner)
+// jobs are compacted into a list in shared memory, sample by sample (the
+// jobs of one sample index keep the pixels' lane order, so that runs of
+// neighbouring pixels on the same triangle stay adjacent), and evaluated 32
+// at a time: every lane of a round works on a job, instead of the warp
+// stepping through every sample index with only the lanes whose sample
+// holds a new winner active.
+struct WinnerJob {
+    int code;     // source lane | sample index << 5 | sample mask << 8
+    int t;        // winner triangle
+    float wsum;   // sum of the score weights of the samples in the mask
+};
+constexpr int kWinnerJobsPerWarp = kSampleGroup * 32;
+
+// Per-warp scratch of the backward tile kernels: the score ring during the
+// walk, then the winner jobs (the same warp uses them one after the other).
+union WarpJobs {
+    ScoreJob ring[kScoreRing];
+    WinnerJob winners[kWinnerJobsPerWarp];
+};
+
+template <int SG, int TW>
 __device__ __forceinline__ void winner_terms(const SoupDev& s, double* __restrict__ acc_tex,
                                              double* __restrict__ acc_verts, const GeomRec* __restrict__ vgeom,
-                                             const DevCam& cam, const ViewDesc& V, int s0, int ns, size_t HW,
-                                             size_t pix, int px, int py, bool valid, bool do_tex, bool do_score,
-                                             bool do_int, const int (&wt)[SG], const float (&wsc)[SG]) {
-    const size_t sstride = (size_t)(s.C - 1) * HW;
-    const float* gcol0 = V.grad_color + (size_t)s0 * sstride + pix;
+                                             const DevCam& cam, const ViewDesc& V, const WorkItem& wi, int s0, int ns,
+                                             size_t HW, bool valid, bool do_tex, bool do_score, bool do_int,
+                                             const int (&wt)[SG], const float (&wsc)[SG], WinnerJob* jobs) {
+    constexpr int TH = kTilePix / TW;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    int base = 0;
 #pragma unroll
     for (int q = 0; q < SG; ++q) {
-        bool act = valid && q < ns && wt[q] >= 0;
+        bool first = valid && q < ns && wt[q] >= 0;
         int msk = 0;
         float wsum = 0.f;
 #pragma unroll
         for (int r = 0; r < SG; ++r) {
-            if (r < q && r < ns && wt[r] == wt[q]) act = false;   // handled with sample r
+            if (r < q && r < ns && wt[r] == wt[q]) first = false;   // handled with sample r
             if (r >= q && r < ns && wt[r] == wt[q]) {
                 msk |= 1 << r;
                 wsum += wsc[r];
             }
         }
-        // barycentrics read again here (L1-resident) rather than kept in
-        // registers through the walk
+        const unsigned bal = __ballot_sync(kFullMask, first);
+        if (first) jobs[base + __popc(bal & lt)] = WinnerJob{lane | (q << 5) | (msk << 8), wt[q], wsum};
+        base += __popc(bal);
+    }
+    __syncwarp();
+    const size_t sstride = (size_t)(s.C - 1) * HW;
+    for (int r0 = 0; r0 < base; r0 += 32) {
+        const bool act = r0 + lane < base;
+        WinnerJob jb{0, 0, 0.f};
+        if (act) jb = jobs[r0 + lane];
+        const int src = warp * 32 + (jb.code & 31), q = (jb.code >> 5) & 7, msk = jb.code >> 8;
+        const int px = wi.tx * TW + (src & (TW - 1)), py = wi.ty * TH + src / TW;
+        const size_t pix = (size_t)py * V.W + px;
         float b1 = 0.f, b2 = 0.f;
         if (act) {
             const int4 gb = reinterpret_cast<const int4*>(V.gbuf)[(s0 + q) * HW + pix];
             b1 = __int_as_float(gb.y);
             b2 = __int_as_float(gb.z);
         }
+        const float* gcol0 = V.grad_color + (size_t)s0 * sstride + pix;
         float G[2];
         if (do_int)
-            winner_texture<true, SG>(s, acc_tex, act, wt[q], b1, b2, gcol0, sstride, msk, HW, wsum, do_tex,
+            winner_texture<true, SG>(s, acc_tex, act, jb.t, b1, b2, gcol0, sstride, msk, HW, jb.wsum, do_tex,
                                      do_score, G);
         else if (do_tex || do_score)
-            winner_texture<false, SG>(s, acc_tex, act, wt[q], b1, b2, gcol0, sstride, msk, HW, wsum, do_tex,
+            winner_texture<false, SG>(s, acc_tex, act, jb.t, b1, b2, gcol0, sstride, msk, HW, jb.wsum, do_tex,
                                       do_score, G);
         if (do_int) {
             float gv[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) gv[k] = 0.f;
-            if (act) interior_grad(vgeom + wt[q], cam, px, py, G, gv);
-            scatter_verts_run(acc_verts, act, wt[q], gv);
+            if (act) interior_grad(vgeom + jb.t, cam, px, py, G, gv);
+            scatter_verts_run(acc_verts, act, jb.t, gv);
         }
     }
+    __syncwarp();   // the list is rewritten by the next work item
 }
 
 template <int SG, int TW>
@@ -448,6 +522,7 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_BWD)
                  const uint2* __restrict__ ranges, int DB, uint32_t flags, const GeomRec* __restrict__ geom,
                  double* __restrict__ acc_tex, double* __restrict__ acc_verts, int* __restrict__ counter) {
     __shared__ TileStage sm;
+    __shared__ WarpJobs s_jobs[kTilePix / 32];
     __shared__ int s_item;
     const int tid = threadIdx.x;
     constexpr int TH = kTilePix / TW;
@@ -497,9 +572,9 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_BWD)
 
         const uint2 rg = ranges[V.tile_base + wi.ty * V.tiles_x + wi.tx];
         score_walk<SG, TW>(sm, recs, keys, vals, rg, DB, vt.chunk, (size_t)wi.v * s.T, wi, s, acc_tex, tid, lx, ly,
-                           warp, false, any_score, wt, wrho, wsc);
-        winner_terms<SG>(s, acc_tex, acc_verts, geom + (size_t)wi.v * s.T, view_cam(vt, wi.v), V, s0, ns, HW, pix, px,
-                         py, valid, do_tex, do_score, do_int, wt, wsc);
+                           warp, false, any_score, wt, wrho, wsc, s_jobs[warp].ring);
+        winner_terms<SG, TW>(s, acc_tex, acc_verts, geom + (size_t)wi.v * s.T, view_cam(vt, wi.v), V, wi, s0, ns, HW,
+                             valid, do_tex, do_score, do_int, wt, wsc, s_jobs[warp].winners);
         __syncthreads();
     }
 }
@@ -519,6 +594,7 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_TRAIN)
                    float* __restrict__ loss, uint32_t flags, const GeomRec* __restrict__ geom,
                    double* __restrict__ acc_tex, double* __restrict__ acc_verts, int* __restrict__ counter) {
     __shared__ TileStage sm;
+    __shared__ WarpJobs s_jobs[kTilePix / 32];
     __shared__ int s_item;
     __shared__ float s_loss[kTilePix / 32];
     const int tid = threadIdx.x;
@@ -582,9 +658,9 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_TRAIN)
 
         // ---- Algorithm A1 step 2 (texture, score, interior)
         score_walk<SG, TW>(sm, recs, keys, vals, rg, DB, vt.chunk, (size_t)wi.v * s.T, wi, s, acc_tex, tid, lx, ly,
-                           warp, fits, any_score, bt, brho, wsc);
-        winner_terms<SG>(s, acc_tex, acc_verts, geom + (size_t)wi.v * s.T, view_cam(vt, wi.v), V, s0, ns, HW, pix, px,
-                         py, valid, do_tex, do_score, do_int, bt, wsc);
+                           warp, fits, any_score, bt, brho, wsc, s_jobs[warp].ring);
+        winner_terms<SG, TW>(s, acc_tex, acc_verts, geom + (size_t)wi.v * s.T, view_cam(vt, wi.v), V, wi, s0, ns, HW,
+                             valid, do_tex, do_score, do_int, bt, wsc, s_jobs[warp].winners);
         __syncthreads();
     }
     // ---- the loss: one atomic per CTA

@@ -21,6 +21,8 @@
 //    CTA per triangle, levels in shared memory, FP32 from the FP64
 //    accumulator of the finest grid;
 //  - k_resample: one level's grid sampled at another level's vertices.
+#include <cuda_fp16.h>
+
 #include "ds_internal.h"
 
 namespace ds {
@@ -98,37 +100,28 @@ __device__ __forceinline__ float sigmoid_rcp(float th) { return __frcp_rn(__fadd
 // Tap of one coarse level at one finest vertex, shared by every triangle:
 // corner texel indices k0 | k1 << 10 | k2 << 20 (| 1 << 30 when the vertex
 // coincides with level vertex k0) and the interpolation weights (wa, wb) of
-// the decode (R3), exact multiples of 2^-(r_max - R).
-struct Tap {
-    uint32_t k;
-    float wa, wb;
-};
-
-__device__ __forceinline__ Tap make_tap(int R, int i, int j, int Nf, int r_max) {
+// the decode (R3) as two halves: they are multiples of 2^-(r_max - R) in
+// [0, 1] with r_max - R <= 5, exact in FP16.
+__device__ __forceinline__ uint2 make_tap(int R, int i, int j, int Nf, int r_max) {
     const int NR = 1 << R, sh = r_max - R, m = (1 << sh) - 1;
-    Tap tp;
-    if (!(i & m) && !(j & m)) {
-        tp.k = (uint32_t)texel_index(NR, i >> sh, j >> sh) | (1u << 30);
-        tp.wa = tp.wb = 0.f;
-        return tp;
-    }
+    if (!(i & m) && !(j & m)) return make_uint2((uint32_t)texel_index(NR, i >> sh, j >> sh) | (1u << 30), 0u);
     const float inv = __frcp_rn((float)Nf);   // exact power of two
     const Cell cl = find_cell(NR, __fmul_rn((float)i, inv), __fmul_rn((float)j, inv));
-    tp.k = (uint32_t)cl.k0 | ((uint32_t)cl.k1 << 10) | ((uint32_t)cl.k2 << 20);
-    tp.wa = cl.wa;
-    tp.wb = cl.wb;
-    return tp;
+    const __half2 w = __floats2half2_rn(cl.wa, cl.wb);
+    return make_uint2((uint32_t)cl.k0 | ((uint32_t)cl.k1 << 10) | ((uint32_t)cl.k2 << 20),
+                      *reinterpret_cast<const uint32_t*>(&w));
 }
 
 // Channels c..c+3 of level grid zl at a tap (the coinciding vertex, or the
 // decode's interpolation in FP32 in the decode's order).
-__device__ __forceinline__ float4 tap_value(const float* zl, const Tap& tp, int C, int c) {
-    const float4 a0 = *reinterpret_cast<const float4*>(zl + (size_t)(tp.k & 1023u) * C + c);
-    if (tp.k >> 30) return a0;
-    const float4 a1 = *reinterpret_cast<const float4*>(zl + (size_t)((tp.k >> 10) & 1023u) * C + c);
-    const float4 a2 = *reinterpret_cast<const float4*>(zl + (size_t)((tp.k >> 20) & 1023u) * C + c);
-    return make_float4(interp(a0.x, a1.x, a2.x, tp.wa, tp.wb), interp(a0.y, a1.y, a2.y, tp.wa, tp.wb),
-                       interp(a0.z, a1.z, a2.z, tp.wa, tp.wb), interp(a0.w, a1.w, a2.w, tp.wa, tp.wb));
+__device__ __forceinline__ float4 tap_value(const float* zl, uint2 tp, int C, int c) {
+    const float4 a0 = *reinterpret_cast<const float4*>(zl + (size_t)(tp.x & 1023u) * C + c);
+    if (tp.x >> 30) return a0;
+    const float4 a1 = *reinterpret_cast<const float4*>(zl + (size_t)((tp.x >> 10) & 1023u) * C + c);
+    const float4 a2 = *reinterpret_cast<const float4*>(zl + (size_t)((tp.x >> 20) & 1023u) * C + c);
+    const float2 w = __half22float2(*reinterpret_cast<const __half2*>(&tp.y));
+    return make_float4(interp(a0.x, a1.x, a2.x, w.x, w.y), interp(a0.y, a1.y, a2.y, w.x, w.y),
+                       interp(a0.z, a1.z, a2.z, w.x, w.y), interp(a0.w, a1.w, a2.w, w.x, w.y));
 }
 
 // 16-byte asynchronous copy global -> shared (cp.async, completion by
@@ -141,12 +134,12 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Issue the copies of triangle t's levels r_min..r_max into the stage zs.
-__device__ __forceinline__ void stage_levels(float* zs, const float* __restrict__ levels, int t, int T, int r_min,
+// Issue the copies of triangle t's coarse levels r_min..r_max-1 into zs.
+__device__ __forceinline__ void stage_coarse(float* zs, const float* __restrict__ levels, int t, int T, int r_min,
                                              int r_max, int C) {
     size_t off = 0;   // offset of level R in `levels`
     int so = 0;       // offset of level R in zs
-    for (int R = r_min; R <= r_max; ++R) {
+    for (int R = r_min; R < r_max; ++R) {
         const int n = level_V(R) * C;
         const float* g = levels + off + (size_t)t * n;
         for (int k = threadIdx.x; k < n / 4; k += blockDim.x) cp_async16(zs + so + 4 * k, g + 4 * k);
@@ -158,22 +151,27 @@ __device__ __forceinline__ void stage_levels(float* zs, const float* __restrict_
 // Persistent CTAs (grid-stride over triangles), C % 4 == 0 and 16-byte
 // aligned levels and output.  Shared memory: the taps of the coarse levels
 // at every finest vertex (computed once per CTA: they do not depend on the
-// triangle), then two stages of one triangle's levels.  While the CTA sums
-// triangle t from one stage, the asynchronous copies of its next triangle
-// fill the other.  Each thread takes finest vertices; for every group of
-// four channels the levels' values are summed from the coarsest up (FP32,
-// the oracle's order), then activated and written.
+// triangle), then two stages of one triangle's coarse levels, filled by
+// asynchronous copies one triangle ahead.  Items are (finest vertex, group
+// of four channels); an item's finest-level values stream from global
+// memory (issued before the coarse levels are read), the coarse levels'
+// values at the vertex come from the stage, and the sum runs from the
+// coarsest level up (FP32, the oracle's order) before the sigmoid.  The
+// small stages keep five CTAs resident per SM.
 template <bool kAct>
-__global__ void __launch_bounds__(256) k_compose(const float* __restrict__ levels, int T, int r_min, int r_max, int C,
-                                                 float* __restrict__ out, float* __restrict__ act_a) {
+__global__ void __launch_bounds__(256, 5) k_compose(const float* __restrict__ levels, int T, int r_min, int r_max,
+                                                    int C, float* __restrict__ out, float* __restrict__ act_a) {
     extern __shared__ __align__(16) float smem[];
-    const int Nf = 1 << r_max, Vf = level_V(r_max), L = r_max - r_min;   // L coarse levels
-    Tap* taps = reinterpret_cast<Tap*>(smem);                              // [L][Vf]
-    const int tap_floats = (3 * L * Vf + 3) & ~3;
-    const int sf = stage_floats(r_min, r_max, C);
-    float* const stage0 = smem + tap_floats;   // stage b at stage0 + b * sf
+    const int Nf = 1 << r_max, Vf = level_V(r_max), L = r_max - r_min;   // L >= 1 coarse levels
+    uint2* taps = reinterpret_cast<uint2*>(smem);                           // [L][Vf]
+    const int tap_floats = (2 * L * Vf + 3) & ~3;
+    const int sf = stage_floats(r_min, r_max - 1, C);                      // coarse levels of one triangle
+    float* const stage0 = smem + tap_floats;                               // stage b at stage0 + b * sf
+    size_t fine_off = 0;                                                   // the finest level in `levels`
+    for (int R = r_min; R < r_max; ++R) fine_off += (size_t)T * level_V(R) * C;
+    const int per = C / 4;
     int t = blockIdx.x;
-    if (t < T) stage_levels(stage0, levels, t, T, r_min, r_max, C);
+    if (t < T) stage_coarse(stage0, levels, t, T, r_min, r_max, C);
     cp_async_commit();
     for (int q = threadIdx.x; q < L * Vf; q += blockDim.x) {
         const int l = q / Vf, v = q - l * Vf;
@@ -184,29 +182,27 @@ __global__ void __launch_bounds__(256) k_compose(const float* __restrict__ level
     int buf = 0;
     for (; t < T; t += gridDim.x) {
         const int tn = t + gridDim.x;
-        if (tn < T) stage_levels(stage0 + (buf ^ 1) * sf, levels, tn, T, r_min, r_max, C);
+        if (tn < T) stage_coarse(stage0 + (buf ^ 1) * sf, levels, tn, T, r_min, r_max, C);
         cp_async_commit();
         cp_async_wait<1>();   // this thread's copies of triangle t have landed
         __syncthreads();      // everyone's (and the taps)
         const float* zs = stage0 + buf * sf;
-        const float* fine = zs + sf - Vf * C;   // the finest level's slab
-        for (int v = threadIdx.x; v < Vf; v += blockDim.x) {
-            for (int c = 0; c < C; c += 4) {
-                int so = 0;
-                float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                for (int l = 0; l < L; ++l) {
-                    const float4 y = tap_value(zs + so, taps[l * Vf + v], C, c);
-                    z = l == 0 ? y : add4(z, y);
-                    so += level_V(r_min + l) * C;
-                }
-                const float4 y = *reinterpret_cast<const float4*>(fine + (size_t)v * C + c);
-                z = L == 0 ? y : add4(z, y);
-                if (kAct) {
-                    z = make_float4(sigmoid_rcp(z.x), sigmoid_rcp(z.y), sigmoid_rcp(z.z), sigmoid_rcp(z.w));
-                    if (c + 4 == C && act_a) act_a[(size_t)t * Vf + v] = z.w;
-                }
-                __stcs(reinterpret_cast<float4*>(out + ((size_t)t * Vf + v) * C + c), z);
+        const float* fine = levels + fine_off + (size_t)t * Vf * C;
+        for (int it = threadIdx.x; it < Vf * per; it += blockDim.x) {
+            const int v = it / per, c = (it - v * per) * 4;
+            const float4 y = __ldcs(reinterpret_cast<const float4*>(fine + (size_t)v * C + c));
+            float4 z = tap_value(zs, taps[v], C, c);
+            int so = level_V(r_min) * C;
+            for (int l = 1; l < L; ++l) {
+                z = add4(z, tap_value(zs + so, taps[l * Vf + v], C, c));
+                so += level_V(r_min + l) * C;
             }
+            z = add4(z, y);
+            if (kAct) {
+                z = make_float4(sigmoid_rcp(z.x), sigmoid_rcp(z.y), sigmoid_rcp(z.z), sigmoid_rcp(z.w));
+                if (c + 4 == C && act_a) act_a[(size_t)t * Vf + v] = z.w;
+            }
+            __stcs(reinterpret_cast<float4*>(out + ((size_t)t * Vf + v) * C + c), z);
         }
         __syncthreads();      // stage[buf] is refilled next round
         buf ^= 1;
@@ -375,7 +371,7 @@ cudaError_t launch_compose(const float* levels, int T, int r_min, int r_max, int
             k_compose_single<false><<<flat_grid(n), 256, 0, st>>>(levels, n, C, out, nullptr);
     } else if ((C % 4 == 0) && ((uintptr_t)levels % 16 == 0) && ((uintptr_t)out % 16 == 0)) {
         const int Vf = level_V(r_max), L = r_max - r_min;
-        const size_t smem = sizeof(float) * ((size_t)((3 * L * Vf + 3) & ~3) + 2 * (size_t)stage_floats(r_min, r_max, C));
+        const size_t smem = sizeof(float) * ((size_t)((2 * L * Vf + 3) & ~3) + 2 * (size_t)stage_floats(r_min, r_max - 1, C));
         auto run = [&](auto kernel) {
             cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;

@@ -485,8 +485,12 @@ __device__ __forceinline__ void winner_terms(const SoupDev& s, double* __restric
     const size_t sstride = (size_t)(s.C - 1) * HW;
     for (int r0 = 0; r0 < base; r0 += 32) {
         const bool act = r0 + lane < base;
+        // the round in triangle order (one run of interior atomics per triangle)
+        unsigned skey = act ? (unsigned)jobs[r0 + lane].t : 0xffffffffu;
+        int pos = lane;
+        warp_sort32(skey, pos);
         WinnerJob jb{0, 0, 0.f};
-        if (act) jb = jobs[r0 + lane];
+        if (act) jb = jobs[r0 + pos];
         const int src = warp * 32 + (jb.code & 31), q = (jb.code >> 5) & 7, msk = jb.code >> 8;
         const int px = wi.tx * TW + (src & (TW - 1)), py = wi.ty * TH + src / TW;
         const size_t pix = (size_t)py * V.W + px;

@@ -309,6 +309,25 @@ __device__ __forceinline__ bool warp_run_sum(unsigned long long key, float (&v)[
     return head;
 }
 
+// Sort (key, val) ascending over the 32 lanes of the warp (bitonic network,
+// 15 compare-exchange steps by shuffles; equal keys never swap).  All 32
+// lanes must call it.
+__device__ __forceinline__ void warp_sort32(unsigned& key, int& val) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const unsigned ok = __shfl_xor_sync(kFullMask, key, j);
+            const int ov = __shfl_xor_sync(kFullMask, val, j);
+            const bool up = (lane & k) == 0, lower = (lane & j) == 0;
+            if (lower == up ? ok < key : ok > key) {
+                key = ok;
+                val = ov;
+            }
+        }
+}
+
 // Tile-kernel dispatch on the sample group (1, 2 or 4 samples per CTA) and
 // the tile width (8, 16 or 32 pixels): calls f(IntPair<SG, TW>{}).
 template <int A, int B>

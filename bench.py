@@ -375,10 +375,19 @@ def _shade_leg(wl, steps: int):
     grgb = [torch.randn_like(r) for r in rgb]
     gfeat = [torch.empty_like(c) for c in wl.col]
     gp = torch.empty_like(params)
-    fwd = lambda: wl.ctx.shade_forward(cams, params, wl.col, rgb)
+    N = wl.N
+    path0 = wl.ctx.get_shade_path()
+
+    def fwd_path(path):
+        def f():
+            wl.ctx.set_shade_path(path)
+            wl.ctx.shade_forward(cams, params, wl.col, rgb)
+        return f
     bwd = lambda: wl.ctx.shade_backward(cams, params, wl.col, grgb, gfeat, gp, overwrite=True)
     out = {}
-    for name, fn, flops in (("forward", fwd, SHADE_FWD_FLOPS), ("backward", bwd, SHADE_BWD_FLOPS)):
+    for name, fn, flops in (("forward", fwd_path(N.DS_SHADE_CUDA_CORES), SHADE_FWD_FLOPS),
+                            ("forward_tensor_cores", fwd_path(N.DS_SHADE_TENSOR_CORES), SHADE_FWD_FLOPS),
+                            ("backward", bwd, SHADE_BWD_FLOPS)):
         for _ in range(3):
             fn()
         torch.cuda.synchronize()
@@ -395,8 +404,17 @@ def _shade_leg(wl, steps: int):
                                   "unit": "TFLOP/s", "frac": tflops / FP32_PEAK_TFLOPS,
                                   "peak_kind": "nominal FP32 FMA rate at 2070 MHz",
                                   "algorithmic_flops_per_pixel_sample": flops}}
+    wl.ctx.set_shade_path(path0)
+    wl.ctx.status()
+    # the tensor-core forward's algorithmic work on the tensor pipe: 3
+    # layers x 3 TF32 products of 128 x 16 x 16 per tile of 128
+    tc = out["forward_tensor_cores"]
+    tc["roofline_tensor"] = {"what": "3 x TF32-split MMAs (3 products per layer) on the kind::tf32 path",
+                             "mma_flops_per_pixel_sample": 3 * 3 * 2 * 16 * 16}
     out["pixel_samples"] = wl.pixel_samples
-    out["what"] = "16-16-16-3 MLP on 7 features + SH2 of the view direction, RGBA blend (FP32)"
+    out["what"] = ("16-16-16-3 MLP on 7 features + SH2 of the view direction, RGBA blend; forward on the CUDA "
+                   "cores (FP32 FMA) and on the tensor cores (tcgen05 kind::tf32, hi/lo split), backward on "
+                   "the CUDA cores")
     return out
 
 

@@ -407,6 +407,21 @@ DS_API ds_status ds_shade_backward(ds_ctx* ctx, int32_t n_views, int32_t S, cons
                                    const float* const* grad_rgbs, float* const* grad_feats,
                                    float* grad_params, uint32_t flags, void* stream);
 
+/* Which kernel ds_shade_forward runs on this context (no paper counterpart:
+ * two implementations of the same forward of Sec. 3.3's MLP):
+ *  DS_SHADE_CUDA_CORES: FP32 fused multiply-adds on the CUDA cores;
+ *  DS_SHADE_TENSOR_CORES: the three layers as tcgen05 MMAs of kind::tf32 on
+ *    the 5th-generation tensor cores, every operand split into a TF32 high
+ *    part and the remainder (x w ~ x_lo w_hi + x_hi w_lo + x_hi w_hi), FP32
+ *    accumulation in tensor memory; about FP32 accuracy.  A launch whose wait
+ *    for its MMAs runs out (about a second) stops, and the next
+ *    ds_ctx_status returns DS_ERR_TIMEOUT.
+ * Host calls; DS_ERR_INVALID_ARG for another value. */
+#define DS_SHADE_CUDA_CORES 0
+#define DS_SHADE_TENSOR_CORES 1
+DS_API ds_status ds_set_shade_path(ds_ctx* ctx, int32_t path);
+DS_API ds_status ds_get_shade_path(ds_ctx* ctx, int32_t* path);
+
 /* The paper's photometric loss lambda L1 + (1 - lambda) L_SSIM (Eq. 10, Sec.
  * 3.4; lambda = 0.8), per pixel, with its upstream gradients for
  * ds_raster_backward.  SSIM per channel with an 11 x 11 Gaussian window

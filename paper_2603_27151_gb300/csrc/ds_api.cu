@@ -118,8 +118,10 @@ struct ds_ctx {
     uint32_t* h_word = nullptr;   // pinned host words
     Plan plan;
     ds_tuning tune{16, -1, 0, 256};   // tile shape, depth bits, grid, staging chunk
+    int32_t shade_path = DS_SHADE_CUDA_CORES;   // kernel of ds_shade_forward
     cudaStream_t last_stream = nullptr;
-    ds::ViewTable* vt = nullptr;   // host staging of the kernel parameter table (~9 KB)
+    ds::ViewTable* vt = nullptr;   // host staging of the kernel parameter tables (~9 KB each): [0] the
+                                   // call's views, [1] the same views in the edge kernel's tiles
 
     // optional stage profiler: CUDA events around each pipeline stage
     struct ProfRec {
@@ -321,6 +323,30 @@ int total_tiles(const ds::ViewTable& vt) {
     return d.tile_base + d.tiles_x * d.tiles_y;
 }
 
+// The edge kernel reads G-buffers, colours and set-up records but no bins, so
+// its pixel partition need not be the binning tiles: it runs on 32 x 8
+// tiles, in which a warp covers one row of 32 pixels and every per-pixel load
+// of a warp is one contiguous 128-byte line (the binning tiles of 8 x 32 cut
+// a warp's pixels into four 32-byte segments of four lines).
+constexpr int kEdgeTileW = 32;
+
+void retile(const ds::ViewTable& vt, int tw, ds::ViewTable& out) {
+    out = vt;
+    out.tile_w = tw;
+    out.tile_h = ds::kTilePix / tw;
+    int tile_base = 0, item_base = 0;
+    for (int v = 0; v < vt.n; ++v) {
+        ds::ViewDesc& d = out.v[v];
+        d.tiles_x = (d.W + out.tile_w - 1) / out.tile_w;
+        d.tiles_y = (d.H + out.tile_h - 1) / out.tile_h;
+        d.tile_base = tile_base;
+        d.item_base = item_base;
+        tile_base += d.tiles_x * d.tiles_y;
+        item_base += d.tiles_x * d.tiles_y * out.n_groups;
+    }
+    out.n_items = item_base;
+}
+
 // Activation, set-up and binning of `vt`'s views into the context's plan.
 ds_status prepare(ds_ctx* c, int32_t soup_id, Soup& s, const ds_camera* cams, const ds::ViewTable& vt, bool sync,
                   cudaStream_t st) {
@@ -432,7 +458,7 @@ ds_status ds_create(ds_ctx** out, int32_t device) {
     if (device < 0 || device >= n) return fail(DS_ERR_INVALID_ARG, "bad device index");
     ds_ctx* c = new (std::nothrow) ds_ctx();
     if (!c) return fail(DS_ERR_OOM, "host allocation failed");
-    c->vt = new (std::nothrow) ds::ViewTable();
+    c->vt = new (std::nothrow) ds::ViewTable[2]();
     if (!c->vt) {
         delete c;
         return fail(DS_ERR_OOM, "host allocation failed");
@@ -441,13 +467,13 @@ ds_status ds_create(ds_ctx** out, int32_t device) {
     DeviceGuard g(device);
     if (cudaHostAlloc(reinterpret_cast<void**>(&c->h_word), 64, cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();
-        delete c->vt;
+        delete[] c->vt;
         delete c;
         return fail(DS_ERR_CUDA, "cudaHostAlloc failed");
     }
     if (c->misc.ensure(256, "context words") != DS_OK) {
         cudaFreeHost(c->h_word);
-        delete c->vt;
+        delete[] c->vt;
         delete c;
         return DS_ERR_OOM;
     }
@@ -474,7 +500,7 @@ void ds_destroy(ds_ctx* c) {
         cudaEventDestroy(r.b);
     }
     for (cudaEvent_t e : c->prof_pool) cudaEventDestroy(e);
-    delete c->vt;
+    delete[] c->vt;
     delete c;
 }
 
@@ -753,8 +779,10 @@ ds_status backward_impl(ds_ctx* c, Soup& s, uint32_t grad_flags, float* grad_ver
     if (want_verts && (gflags & DS_G_EDGE)) {
         StageScope p(c, ds::kStEdgeBwd, st);
         DS_TRY_CUDA(cudaMemsetAsync(c->d_counter() + 3, 0, 4, st));
-        DS_TRY_CUDA(ds::launch_edge_bwd(vt, sd, c->recs.as<ds::SetupRec>(), c->geom.as<ds::GeomRec>(), acc_verts,
-                                        c->d_counter() + 3, grid, st));
+        ds::ViewTable& ve = c->vt[1];
+        retile(vt, kEdgeTileW, ve);
+        DS_TRY_CUDA(ds::launch_edge_bwd(ve, sd, c->recs.as<ds::SetupRec>(), c->geom.as<ds::GeomRec>(), acc_verts,
+                                        c->d_counter() + 3, tile_grid(c, ve), st));
     }
     {
         StageScope p(c, ds::kStFinish, st);
@@ -989,6 +1017,7 @@ ds_status ds_ctx_status(ds_ctx* c) {
     DS_TRY_CUDA(cudaMemcpy(&st, c->d_status(), 4, cudaMemcpyDeviceToHost));
     DS_TRY_CUDA(cudaMemset(c->d_status(), 0, 4));
     if (st & 1) return fail(DS_ERR_CAPACITY, "bin capacity exceeded in a DS_NO_SYNC forward");
+    if (st & 2) return fail(DS_ERR_TIMEOUT, "a tensor-core shading launch timed out waiting for its MMAs");
     return DS_OK;
 }
 
@@ -1100,7 +1129,27 @@ ds_status ds_shade_forward(ds_ctx* c, int32_t n_views, int32_t S, const ds_camer
         if (!rgbs[i]) return fail(DS_ERR_INVALID_ARG, "rgbs[" + std::to_string(i) + "] is NULL");
         v[i].rgb = rgbs[i];
     }
-    DS_TRY_CUDA(ds::launch_shade_fwd(v.data(), n_views, S, params, static_cast<cudaStream_t>(stream)));
+    if (c->shade_path == DS_SHADE_TENSOR_CORES)
+        DS_TRY_CUDA(ds::launch_shade_fwd_tc(v.data(), n_views, S, params, c->d_status(),
+                                            static_cast<cudaStream_t>(stream)));
+    else
+        DS_TRY_CUDA(ds::launch_shade_fwd(v.data(), n_views, S, params, static_cast<cudaStream_t>(stream)));
+    c->last_stream = static_cast<cudaStream_t>(stream);
+    return DS_OK;
+}
+
+ds_status ds_set_shade_path(ds_ctx* c, int32_t path) {
+    if (!c) return fail(DS_ERR_INVALID_ARG, "NULL context");
+    if (path != DS_SHADE_CUDA_CORES && path != DS_SHADE_TENSOR_CORES) return fail(DS_ERR_INVALID_ARG, "bad shade path");
+    std::lock_guard<std::mutex> lk(c->mu);
+    c->shade_path = path;
+    return DS_OK;
+}
+
+ds_status ds_get_shade_path(ds_ctx* c, int32_t* path) {
+    if (!c || !path) return fail(DS_ERR_INVALID_ARG, "NULL argument");
+    std::lock_guard<std::mutex> lk(c->mu);
+    *path = c->shade_path;
     return DS_OK;
 }
 

@@ -408,6 +408,228 @@ __global__ void __launch_bounds__(kThreads) k_shade_finish(const float* __restri
     out[k] = overwrite ? (float)a : (float)((double)out[k] + a);
 }
 
+// ---------------------------------------------------------------------------
+// Forward on the tensor cores: the three layers as tcgen05.mma of kind::tf32
+// (Blackwell 5th-generation tensor cores; operands in shared memory, the
+// FP32 accumulator in tensor memory).  A tile is 128 pixel-samples, one per
+// thread and one TMEM lane each (M = 128); N = 16 hidden units (the 3 outputs
+// padded to 16); K = 16 inputs in two MMAs of K = 8.  TF32 keeps 10 mantissa
+// bits, so every operand is split into hi = the TF32 truncation and lo = the
+// remainder (exact in FP32) and each product is taken as
+// x_lo w_hi + x_hi w_lo + x_hi w_hi (the x_lo w_lo term, about 2^-21 of the
+// product, is dropped): six MMAs per layer, issued by one thread and
+// completed on an mbarrier.  Per layer the 128 threads read their row of the
+// accumulator (tcgen05.ld), add the bias, apply the activation, and write the
+// next layer's hi/lo operand rows back to shared memory.
+namespace tc {
+
+constexpr int kRows = 128;   // pixel-samples per tile = TMEM lanes = M
+constexpr uint32_t kTmemCols = 32;   // smallest allocation; the accumulator uses 16 columns
+// Instruction descriptor of kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32
+// (bits 7-9 and 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 in bits
+// 17-22, M >> 4 in bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+
+// Byte offset of element (r, k) of an R x 16 K-major TF32 operand in the
+// canonical layout without swizzle: core matrices of 8 rows x 16 bytes
+// (4 values), 128 bytes each; the two core matrices of one MMA's K = 8 are
+// 128 bytes apart (leading-dimension offset), successive 8-row groups 512
+// bytes apart (stride-dimension offset).
+__device__ __forceinline__ uint32_t op_off(int r, int k) {
+    return (uint32_t)(((((r >> 3) << 2) + (k >> 2)) << 7) + ((r & 7) << 4) + ((k & 3) << 2));
+}
+
+// Shared-memory matrix descriptor: start address, leading and stride byte
+// offsets (all >> 4), descriptor version 1 (bit 46), no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(512u >> 4) << 32) |
+           (1ull << 46);
+}
+
+__device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+struct Smem {
+    uint8_t w[6][1024];   // W1 hi, W1 lo, W2 hi, W2 lo, W3 hi, W3 lo (N 16 x K 16)
+    uint8_t a[2][8192];   // the layer's input rows: hi, lo (M 128 x K 16)
+    float bias[36];       // b1 [16], b2 [16], b3 [3]
+    unsigned long long bar;
+    uint32_t tmem;
+};
+
+// Store one operand row (16 values) as its TF32 hi and lo parts.
+__device__ __forceinline__ void store_row(Smem& sm, int r, const float (&x)[16]) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        uint32_t h[4], l[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            h[e] = __float_as_uint(x[4 * c + e]) & 0xFFFFE000u;
+            l[e] = __float_as_uint(x[4 * c + e] - __uint_as_float(h[e]));
+        }
+        *reinterpret_cast<uint4*>(sm.a[0] + op_off(r, 4 * c)) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4*>(sm.a[1] + op_off(r, 4 * c)) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+}
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+}
+
+// Layer L: D = A_lo W_hi + A_hi W_lo + A_hi W_hi (small terms first), then
+// the commit that arrives on the barrier when the MMAs are complete.  One
+// thread.
+__device__ __forceinline__ void issue_layer(Smem& sm, int L, uint32_t d) {
+    const uint32_t a0 = saddr(sm.a[0]), a1 = saddr(sm.a[1]), b0 = saddr(sm.w[2 * L]), b1 = saddr(sm.w[2 * L + 1]);
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        mma(d, smem_desc(a1 + 256 * s), smem_desc(b0 + 256 * s), s);
+        mma(d, smem_desc(a0 + 256 * s), smem_desc(b1 + 256 * s), 1);
+    }
+#pragma unroll
+    for (int s = 0; s < 2; ++s) mma(d, smem_desc(a0 + 256 * s), smem_desc(b0 + 256 * s), 1);
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(saddr(&sm.bar))
+                 : "memory");
+}
+
+// Wait for phase `parity` of the barrier, for at most about 2^31 SM clocks.
+__device__ __forceinline__ bool wait_bar(const Smem& sm, uint32_t parity) {
+    const uint32_t b = saddr(&sm.bar);
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(b), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > (1ll << 31)) return false;
+    }
+}
+
+// This thread's accumulator row (TMEM lane = thread), 16 columns.
+__device__ __forceinline__ void load_row(uint32_t tmem, float (&v)[16]) {
+    uint32_t r[16];
+    const uint32_t ta = tmem + ((uint32_t)(threadIdx.x & ~31) << 16);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(ta));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Generic-proxy writes of the operand rows -> visible to the MMAs; prior
+// tcgen05 loads ordered before the barrier that follows.
+__device__ __forceinline__ void before_sync() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+
+}  // namespace tc
+
+// One tile of 128 pixel-samples per round, persistent CTAs of 128 threads;
+// tiles never straddle views (view v owns tiles blk0 .. blk0 + ceil(S HW /
+// 128) - 1).  A wait for the MMAs that runs out (about a second) sets bit 1
+// of *status, and the CTA releases its tensor memory and returns.
+__global__ void __launch_bounds__(tc::kRows) k_shade_fwd_tc(const __grid_constant__ ShadeTable t,
+                                                          const float* __restrict__ params, int* __restrict__ status) {
+    using namespace tc;
+    extern __shared__ uint8_t smem_raw[];
+    Smem& sm = *reinterpret_cast<Smem*>(smem_raw + ((1024u - (saddr(smem_raw) & 1023u)) & 1023u));
+    const int tid = threadIdx.x, warp = tid >> 5;
+    // weights -> TF32 hi/lo operand tiles (W3's 3 rows padded with zeros)
+    for (int q = tid; q < 3 * 256; q += kRows) {
+        const int L = q >> 8, n = (q >> 4) & 15, k = q & 15;
+        const int o = L == 0 ? oW1 : (L == 1 ? oW2 : oW3);
+        const float w = (L < 2 || n < kOut) ? __ldg(params + o + n * 16 + k) : 0.f;
+        const uint32_t h = __float_as_uint(w) & 0xFFFFE000u;
+        *reinterpret_cast<uint32_t*>(sm.w[2 * L] + op_off(n, k)) = h;
+        *reinterpret_cast<uint32_t*>(sm.w[2 * L + 1] + op_off(n, k)) = __float_as_uint(w - __uint_as_float(h));
+    }
+    if (tid < 36) sm.bias[tid] = tid < 16 ? __ldg(params + oB1 + tid) : (tid < 32 ? __ldg(params + oB2 + tid - 16)
+                                                                                  : (tid < 35 ? __ldg(params + oB3 + tid - 32) : 0.f));
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(saddr(&sm.bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(saddr(&sm.tmem)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    before_sync();
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = sm.tmem;
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < t.n_blocks && ok; tile += gridDim.x) {
+        const ShadeView& V = t.v[find_view(t, tile)];
+        const int idx = (tile - V.blk0) * kRows + tid;
+        const bool valid = idx < t.S * V.HW;
+        const int s = valid ? idx / V.HW : 0, p = valid ? idx - s * V.HW : 0;
+        float f[kFeat], x[16];
+#pragma unroll
+        for (int c = 0; c < kFeat; ++c) f[c] = valid ? __ldcs(V.feat + ((size_t)s * kFeat + c) * V.HW + p) : 0.f;
+        float sh[kSH];
+        sh_of_pixel(V, p % V.W, p / V.W, sh);
+#pragma unroll
+        for (int c = 0; c < kFeat; ++c) x[c] = f[c];
+#pragma unroll
+        for (int c = 0; c < kSH; ++c) x[kFeat + c] = valid ? sh[c] : 0.f;
+        float o[kOut];
+#pragma unroll
+        for (int L = 0; L < 3; ++L) {
+            store_row(sm, tid, x);
+            before_sync();
+            __syncthreads();
+            if (tid == 0) issue_layer(sm, L, tmem);
+            ok = __syncthreads_and(wait_bar(sm, phase));
+            phase ^= 1u;
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            float d[16];
+            load_row(tmem, d);
+            if (L < 2) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) x[i] = fmaxf(d[i] + sm.bias[16 * L + i], 0.f);
+            } else {
+#pragma unroll
+                for (int c = 0; c < kOut; ++c) o[c] = sigmoidf_(d[c] + sm.bias[32 + c]);
+            }
+        }
+        if (!ok) break;
+        if (valid) {
+            const float A = f[3];
+#pragma unroll
+            for (int c = 0; c < kOut; ++c)
+                __stcs(V.rgb + ((size_t)s * kOut + c) * V.HW + p, fmaf(A, f[c], (1.0f - A) * o[c]));
+        }
+        before_sync();
+        __syncthreads();   // the operand rows and the accumulator are reused by the next tile
+    }
+    if (!ok) {
+        // a layer's MMAs did not complete in time: record it, give them one
+        // more bounded wait, then release the tensor memory and return
+        if (tid == 0) atomicOr(status, 2);
+        wait_bar(sm, phase ^ 1u);
+    }
+    before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
 void fill_table(ShadeTable& t, const ShadeView* views, int n, int S, bool overwrite) {
     t.n = n;
     t.S = S;
@@ -446,6 +668,33 @@ cudaError_t launch_shade_fwd(const ShadeView* views, int n, int S, const float* 
     fill_table(t, views, n, S, false);
     if (t.n_blocks == 0 || S == 0) return cudaSuccess;
     k_shade_fwd<<<t.n_blocks, kThreads, 0, st>>>(t, params);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shade_fwd_tc(const ShadeView* views, int n, int S, const float* params, int* status,
+                                cudaStream_t st) {
+    ShadeTable t;
+    t.n = n;
+    t.S = S;
+    t.overwrite = 0;
+    int blk = 0;
+    for (int i = 0; i < n; ++i) {
+        t.v[i] = views[i];
+        t.v[i].HW = views[i].W * views[i].H;
+        t.v[i].blk0 = blk;
+        blk += (int)(((long long)S * t.v[i].HW + tc::kRows - 1) / tc::kRows);
+    }
+    t.n_blocks = blk;
+    if (t.n_blocks == 0) return cudaSuccess;
+    const size_t smem = sizeof(tc::Smem) + 1024;   // + room to align the operand tiles to 1 KB
+    cudaError_t e = cudaFuncSetAttribute(k_shade_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shade_fwd_tc, tc::kRows, smem)) != cudaSuccess)
+        return e;
+    per_sm = per_sm < 1 ? 1 : (per_sm > 16 ? 16 : per_sm);   // 16 x 32 TMEM columns = all 512
+    k_shade_fwd_tc<<<persistent_grid(t.n_blocks, per_sm), tc::kRows, smem, st>>>(t, params, status);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -27,6 +27,7 @@ DS_REUSE_FORWARD = 0x100
 DS_OVERWRITE = 0x200
 DS_SHADE_N_PARAMS = 595
 DS_COPY, DS_BORROW, DS_STATIC = 0, 1, 2
+DS_SHADE_CUDA_CORES, DS_SHADE_TENSOR_CORES = 0, 1
 ERRORS = {-1: "DS_ERR_INVALID_ARG", -2: "DS_ERR_OOM", -3: "DS_ERR_CUDA", -4: "DS_ERR_CAPACITY",
           -5: "DS_ERR_TIMEOUT", -6: "DS_ERR_NOT_FOUND", -7: "DS_ERR_BUSY"}
 
@@ -166,6 +167,10 @@ def load():
     L.ds_loss_l1_ssim.restype = i32
     L.ds_shade_forward.argtypes = [P, i32, i32, P, P, P, P, P]
     L.ds_shade_forward.restype = i32
+    L.ds_set_shade_path.argtypes = [P, i32]
+    L.ds_set_shade_path.restype = i32
+    L.ds_get_shade_path.argtypes = [P, ctypes.POINTER(i32)]
+    L.ds_get_shade_path.restype = i32
     L.ds_shade_backward.argtypes = [P, i32, i32, P, P, P, P, P, P, u32, P]
     L.ds_shade_backward.restype = i32
     _lib = L
@@ -289,6 +294,16 @@ class Context:
             gin[v].score_w = score_ws[v].data_ptr() if score_ws is not None and score_ws[v] is not None else None
         _check(load().ds_raster_backward(self.h, soup_id, ca, n, S, fwd, gin, flags,
                                          _ptr(grad_verts), _ptr(grad_tex), _stream(stream)))
+
+    def set_shade_path(self, path: int):
+        """Kernel of shade_forward: DS_SHADE_CUDA_CORES (FP32 FMA) or
+        DS_SHADE_TENSOR_CORES (tcgen05, TF32 split into hi + lo)."""
+        _check(load().ds_set_shade_path(self.h, int(path)))
+
+    def get_shade_path(self) -> int:
+        p = ctypes.c_int32(-1)
+        _check(load().ds_get_shade_path(self.h, ctypes.byref(p)))
+        return p.value
 
     def shade_forward(self, cams, params, feats, rgbs, stream=None):
         """Deferred shading (ds_shade_forward): feats[v] float32 [S,7,H,W] ->

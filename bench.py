@@ -1260,6 +1260,72 @@ def oracle_one_core(start_row: int, n_rows: int, seed: int = 13):
     return frags / secs, secs, frags
 
 
+def _train_cpu_job(job):
+    """CPU oracle (bbox-scan mode) on rows [r0, r1) of one training view
+    (20,000 triangles, 1024x768, S = 1): forward + L2 loss + backward against
+    the reference soup's render of those rows (rendered first, untimed).
+    Returns seconds."""
+    import oracle as O
+    r0, r1 = job
+    if "train" not in _ORACLE_SCENES:
+        _ORACLE_SCENES["train"] = I.training_setup()
+    sc, ref = _ORACLE_SCENES["train"]
+    cam = sc.cams[0]
+    tg = O.forward(ref.verts, ref.tex, ref.grid_n, [cam], np.zeros(1, np.uint64), S=1,
+                   mode=O.MODE_THRESHOLD_HALF, bg=sc.bg, rows=(r0, r1), scan=True)[0]["color"][0][:, r0:r1]
+    t0 = time.perf_counter()
+    f = O.forward(sc.verts, sc.tex, sc.grid_n, [cam], np.array([9], np.uint64), S=1, bg=sc.bg, rows=(r0, r1),
+                  scan=True)[0]
+    d = f["color"][:, :, r0:r1] - tg[None]
+    gc = np.zeros(f["color"].shape, np.float32)
+    gc[:, :, r0:r1] = 2.0 * d
+    sw = np.zeros(f["tri_id"].shape, np.float32)
+    sw[:, r0:r1] = (d.astype(np.float64) ** 2).sum(1)
+    O.backward(sc.verts, sc.tex, sc.grid_n, [cam], 1, [f], [gc], [sw], rows=(r0, r1), scan=True)
+    return time.perf_counter() - t0
+
+
+def _serve_cpu_job(job):
+    """CPU oracle forward (bbox-scan mode, binary opacity, S = 1) of rows
+    [r0, r1) of one served request.  Returns (seconds, rows of the frame)."""
+    import oracle as O
+    k, cam, seed, r0, r1 = job
+    if "serve" not in _ORACLE_SCENES:
+        _ORACLE_SCENES["serve"] = I.serving_workload(duration=0.0)[0]
+    sc = _ORACLE_SCENES["serve"][k]
+    t0 = time.perf_counter()
+    O.forward(sc.verts, sc.tex, sc.grid_n, [cam], np.array([seed], np.uint64), S=1, mode=O.MODE_THRESHOLD_HALF,
+              bg=sc.bg, rows=(r0, r1), scan=True)
+    return time.perf_counter() - t0, cam.height
+
+
+def cpu_config_estimates():
+    """The oracle on the training step and on the serving stream, extrapolated
+    from bounded samples (marked "extrapolated"): one row band per process."""
+    cores = _cores()
+    with mp.get_context("spawn").Pool(cores) as pool:
+        bands = [(300 + 2 * k, 302 + 2 * k) for k in range(cores)]
+        secs = pool.map(_train_cpu_job, bands)
+        s_per_row = float(np.mean(secs)) / 2
+        rows_per_step = 4 * 768
+        train = {"iters_per_s": 1.0 / (s_per_row * rows_per_step / cores), "cores": cores,
+                 "iters_per_s_cores_1": 1.0 / (s_per_row * rows_per_step),
+                 "kind": "oracle (bbox-scan mode), extrapolated",
+                 "sample": "%d bands of 2 rows of a 1024x768 training view, forward + L2 + backward, S=1" % cores}
+        _, reqs = I.serving_workload(duration=0.05, arrival_seed=40)
+        jobs = []
+        for i, (_, k, cam, seed) in enumerate(reqs[:2 * cores]):
+            r0 = cam.height // 2
+            jobs.append((k, cam, seed, r0, r0 + 2))
+        res = pool.map(_serve_cpu_job, jobs)
+        frame_s = float(np.mean([t / 2 * h for t, h in res]))
+        serve = {"frames_per_s": cores / frame_s, "cores": cores, "frames_per_s_cores_1": 1.0 / frame_s,
+                 "kind": "oracle (bbox-scan mode), extrapolated",
+                 "sample": "2 middle rows of each of %d requests of the stream (frames of 256x256 .. 1920x1080), "
+                           "forward with binary opacity" % len(jobs)}
+    return {"train": train, "serve": serve}
+
+
 def cpu_baseline_entry(fragments_per_step=None):
     cores = _cores()
     with oracle_pool(cores) as pool:
@@ -1338,8 +1404,11 @@ def main():
         return
     world, rank, _ = _dist()
     cpu = None
+    cpu_est = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.views:
         cpu = cpu_baseline_entry()   # before the first GPU call (spawned workers)
+        if not args.no_extras:
+            cpu_est = cpu_config_estimates()
     line = _gpu_arm(args)
     if line is not None:
         if cpu is not None:
@@ -1347,6 +1416,11 @@ def main():
             cpu["extrapolated_s_per_step"] = {"cores": f / cpu["value"], "cores_1": f / cpu["cores_1"]["value"],
                                               "what": "extrapolated: the step's fragments at the sampled rate"}
         line["cpu_baseline"] = cpu
+        if cpu_est is not None:
+            if "train" in line:
+                line["train"]["cpu_oracle"] = cpu_est["train"]
+            if "serve" in line:
+                line["serve"]["cpu_oracle"] = cpu_est["serve"]
         print(json.dumps(line), flush=True)
 
 

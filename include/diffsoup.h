@@ -438,6 +438,23 @@ DS_API ds_status ds_loss_l1_ssim(int32_t n_views, int32_t S, int32_t C, const in
                                  float* const* grad_colors, float* const* score_ws, float lambda, float scale,
                                  float* loss, void* stream);
 
+/* Forward pass of views of different soups in one launch (Eq. 5; Algorithm
+ * A1 step 1, as ds_raster_forward): view v renders soup soup_ids[v] (host
+ * [n_views]) with camera cams[v] and seed seeds[v]; the set-up records of
+ * all views are binned together and the persistent tile kernel serves every
+ * view's tiles in one launch, each tile reading its view's soup.  Every
+ * output (triangle ids index the view's own soup, barycentrics, depths,
+ * colours, n_front) equals that of ds_raster_forward on the view alone: the
+ * per-view arithmetic, mask thresholds and tie-breaks are the same.  The
+ * soups must share grid_n and C (DS_ERR_INVALID_ARG otherwise).  The paper
+ * has no counterpart: this serves the continuous-batching render server,
+ * which batches queued requests for different resident soups.  Other
+ * arguments, flags and errors as ds_raster_forward; the call leaves no plan
+ * that a later ds_raster_backward can reuse. */
+DS_API ds_status ds_raster_forward_multi(ds_ctx* ctx, const int32_t* soup_ids, const ds_camera* cams,
+                                         const uint64_t* seeds, int32_t n_views, int32_t S, uint32_t mode,
+                                         const float* bg, const ds_view_out* out, void* stream);
+
 /* Forward pass for callers that cannot allocate device memory: the same
  * computation and outputs as ds_raster_forward (Eq. 5, Algorithm A1 step 1),
  * on a soup passed directly (verts [T][3][3], tex [T][V][C] logits, as in
@@ -526,9 +543,10 @@ DS_API ds_status ds_autotune(ds_ctx* ctx, int32_t soup_id, const ds_camera* cams
  * resident soups (the inference use of Eq. 5 and Eq. 3; the paper measures
  * the rendering speed of the optimised soups, Sec. 4).  One scheduler thread
  * and n_streams workers, each a context with its own CUDA stream.  A free
- * worker takes the oldest queued request and every other queued request for
- * the same soup, mode and background (up to max_batch views) into one forward
- * launch; requests that arrive while batches run join the next one, and the
+ * worker takes the oldest queued request and every other queued request with
+ * the same mode, background and texture shape (grid_n, C), whatever its soup
+ * (up to max_batch views), into one ds_raster_forward_multi launch; requests
+ * that arrive while batches run join the next one, and the
  * batches of different workers overlap on the device.  Admission by device
  * memory: a batch is launched only while the scratch estimate of all batches
  * in flight stays within mem_budget bytes (a batch of one request is always

@@ -347,11 +347,19 @@ void retile(const ds::ViewTable& vt, int tw, ds::ViewTable& out) {
     out.n_items = item_base;
 }
 
-// Activation, set-up and binning of `vt`'s views into the context's plan.
-ds_status prepare(ds_ctx* c, int32_t soup_id, Soup& s, const ds_camera* cams, const ds::ViewTable& vt, bool sync,
-                  cudaStream_t st) {
-    const ds::SoupDev sd = soup_dev(s);
-    const size_t nvt = (size_t)vt.n * s.T;
+// Activation, set-up and binning of `vt`'s views into the context's plan;
+// view v is of soup *soups[v] (the same soup for every view but in a
+// multi-soup forward, whose plan is keyed by plan_soup = -1).
+ds_status prepare(ds_ctx* c, int32_t plan_soup, Soup* const* soups, const ds_camera* cams, ds::ViewTable& vt,
+                  bool sync, cudaStream_t st) {
+    ds::SoupDev sds[DS_MAX_VIEWS];
+    const ds::SoupDev* sdp[DS_MAX_VIEWS];
+    for (int v = 0; v < vt.n; ++v) {
+        sds[v] = soup_dev(*soups[v]);
+        sdp[v] = &sds[v];
+    }
+    ds::set_view_soups(vt, sdp);
+    const size_t nvt = (size_t)ds::view_records(vt);
     const int n_tiles = total_tiles(vt);
     c->plan.valid = false;
     DS_TRY(c->recs.ensure(sizeof(ds::SetupRec) * nvt, "set-up records"));
@@ -362,17 +370,21 @@ ds_status prepare(ds_ctx* c, int32_t soup_id, Soup& s, const ds_camera* cams, co
     DS_TRY(c->ranges.ensure(8 * (size_t)n_tiles, "tile ranges"));
     DS_TRY(ensure_scan(c, (int64_t)nvt));
 
-    if (!(s.fixed && s.act_valid)) {
+    for (int v = 0; v < vt.n; ++v) {
+        Soup& s = *soups[v];
+        bool seen = false;   // activate each soup once
+        for (int u = 0; u < v && !seen; ++u) seen = soups[u] == soups[v];
+        if (seen || (s.fixed && s.act_valid)) continue;
         StageScope p(c, ds::kStActivate, st);
         if (s.levels())
-            DS_TRY_CUDA(ds::launch_compose(s.tex, s.T, s.r_min, s.r_max, s.C, sd.act, true, sd.act_a, st));
+            DS_TRY_CUDA(ds::launch_compose(s.tex, s.T, s.r_min, s.r_max, s.C, sds[v].act, true, sds[v].act_a, st));
         else
-            DS_TRY_CUDA(ds::launch_activate(sd, st));
+            DS_TRY_CUDA(ds::launch_activate(sds[v], st));
         s.act_valid = s.fixed;
     }
     {
         StageScope p(c, ds::kStSetup, st);
-        DS_TRY_CUDA(ds::launch_setup(vt, sd, c->recs.as<ds::SetupRec>(), c->counts.as<uint32_t>(), c->tbox.as<int4>(),
+        DS_TRY_CUDA(ds::launch_setup(vt, c->recs.as<ds::SetupRec>(), c->counts.as<uint32_t>(), c->tbox.as<int4>(),
                                      c->zkeys.as<uint32_t>(), st));
     }
     {
@@ -402,7 +414,7 @@ ds_status prepare(ds_ctx* c, int32_t soup_id, Soup& s, const ds_camera* cams, co
     const int DB = std::min(c->tune.depth_bits >= 0 ? c->tune.depth_bits : 16, 32 - tile_bits);
     {
         StageScope p(c, ds::kStEmit, st);
-        DS_TRY_CUDA(ds::launch_emit(vt, s.T, c->recs.as<ds::SetupRec>(), c->counts.as<uint32_t>(), c->offs.as<uint32_t>(),
+        DS_TRY_CUDA(ds::launch_emit(vt, c->recs.as<ds::SetupRec>(), c->counts.as<uint32_t>(), c->offs.as<uint32_t>(),
                                     c->tbox.as<int4>(), c->zkeys.as<uint32_t>(), DB, c->keys[0].as<uint32_t>(),
                                     c->vals[0].as<uint32_t>(), kcap, c->d_status(), st));
     }
@@ -420,7 +432,7 @@ ds_status prepare(ds_ctx* c, int32_t soup_id, Soup& s, const ds_camera* cams, co
     }
 
     c->plan.valid = true;
-    c->plan.soup = soup_id;
+    c->plan.soup = plan_soup;
     c->plan.devcam = cams == nullptr;
     c->plan.n_views = vt.n;
     if (cams)
@@ -432,6 +444,14 @@ ds_status prepare(ds_ctx* c, int32_t soup_id, Soup& s, const ds_camera* cams, co
     c->plan.kcap = kcap;
     c->plan.n_tiles = n_tiles;
     return DS_OK;
+}
+
+// Every view of one soup.
+ds_status prepare(ds_ctx* c, int32_t soup_id, Soup& s, const ds_camera* cams, ds::ViewTable& vt, bool sync,
+                  cudaStream_t st) {
+    Soup* soups[DS_MAX_VIEWS];
+    for (int v = 0; v < vt.n; ++v) soups[v] = &s;
+    return prepare(c, soup_id, soups, cams, vt, sync, st);
 }
 
 bool plan_matches(const ds_ctx* c, int32_t soup_id, const ds_camera* cams, int32_t n_views) {
@@ -867,6 +887,52 @@ ds_status ds_raster_forward(ds_ctx* c, int32_t soup_id, const ds_camera* cams, c
     c->last_stream = st;
     build_table(*c->vt, c->tune, cams, seeds, n_views, S, out, nullptr);   // calls on one context are serialised
     return forward_impl(c, soup_id, *s, cams, mode, bg, out, st);
+}
+
+ds_status ds_raster_forward_multi(ds_ctx* c, const int32_t* soup_ids, const ds_camera* cams, const uint64_t* seeds,
+                                  int32_t n_views, int32_t S, uint32_t mode, const float* bg, const ds_view_out* out,
+                                  void* stream) {
+    if (!c) return fail(DS_ERR_INVALID_ARG, "NULL context");
+    if (!soup_ids) return fail(DS_ERR_INVALID_ARG, "soup_ids is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    DS_TRY(check_views(cams, n_views, S));
+    DS_TRY(check_mode(mode, seeds != nullptr));
+    if (!bg) return fail(DS_ERR_INVALID_ARG, "bg is NULL");
+    DS_TRY(check_outputs(out, n_views));
+    Soup* soups[DS_MAX_VIEWS];
+    for (int v = 0; v < n_views; ++v) {
+        DS_TRY(get_soup(c, soup_ids[v], &soups[v]));
+        if (soups[v]->N != soups[0]->N || soups[v]->C != soups[0]->C)
+            return fail(DS_ERR_INVALID_ARG, "the soups of one multi-soup forward must share grid_n and C");
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    ds::ViewTable& vt = *c->vt;
+    build_table(vt, c->tune, cams, seeds, n_views, S, out, nullptr);
+    DS_TRY(prepare(c, -1, soups, cams, vt, (mode & DS_NO_SYNC) == 0, st));
+    const Soup& s0 = *soups[0];
+    ds::Bg b{};
+    for (int i = 0; i < s0.C - 1; ++i) b.c[i] = bg[i];
+    const ds::SoupDev sd = soup_dev(s0);   // N, C, V; the views read their own soups
+    const int grid = tile_grid(c, vt);
+    {
+        StageScope p(c, ds::kStRasterFwd, st);
+        DS_TRY_CUDA(cudaMemsetAsync(c->d_counter(), 0, 4, st));
+        DS_TRY_CUDA(ds::launch_raster_fwd(vt, sd, c->recs.as<ds::SetupRec>(), c->keys[c->plan.res].as<uint32_t>(),
+                                          c->vals[c->plan.res].as<uint32_t>(), c->ranges.as<uint2>(), c->plan.DB,
+                                          mode & 0xffu, b, c->d_counter(), grid, st, false, 0.f, nullptr, true));
+    }
+    bool want_front = false;
+    for (int v = 0; v < vt.n; ++v) want_front = want_front || out[v].n_front;
+    if (want_front) {
+        StageScope p(c, ds::kStCount, st);
+        DS_TRY_CUDA(cudaMemsetAsync(c->d_counter() + 1, 0, 4, st));
+        DS_TRY_CUDA(ds::launch_raster_count(vt, sd, c->recs.as<ds::SetupRec>(), c->keys[c->plan.res].as<uint32_t>(),
+                                            c->vals[c->plan.res].as<uint32_t>(), c->ranges.as<uint2>(), c->plan.DB, 0,
+                                            nullptr, c->d_counter() + 1, grid, st));
+    }
+    return DS_OK;
 }
 
 ds_status ds_raster_forward_devcam(ds_ctx* c, int32_t soup_id, const int32_t* wh, const ds_camera* cams,

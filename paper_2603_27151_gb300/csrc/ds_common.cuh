@@ -46,6 +46,14 @@ struct ViewDesc {
     const float* grad_color;
     const float* score_w;
     const float* target;   // fused training pass: [C-1][H][W] target image
+    // The view's soup and the index of its first set-up record: the call's
+    // soup and v * T in a single-soup call; one soup per view in a
+    // multi-soup forward (ds_raster_forward_multi), records concatenated.
+    const float* s_verts;
+    float* s_act;
+    float* s_act_a;
+    int s_T;
+    long long rec_base;
 };
 
 struct ViewTable {

@@ -65,21 +65,30 @@ int radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1,
 
 // ---- set-up and binning (ds_setup.cu)
 cudaError_t launch_activate(const SoupDev& s, cudaStream_t st);
-cudaError_t launch_setup(const ViewTable& vt, const SoupDev& s, SetupRec* recs, uint32_t* counts,
-                         int4* tbox, uint32_t* zkeys, cudaStream_t st);
-cudaError_t launch_emit(const ViewTable& vt, int T, const SetupRec* recs, const uint32_t* counts,
-                        const uint32_t* offs, const int4* tbox, const uint32_t* zkeys, int DB,
-                        uint32_t* keys, uint32_t* vals, uint32_t cap, int* status,
-                        cudaStream_t st);
+// The views' soups (ViewDesc s_*, rec_base): one soup for every view, or
+// soups[v] for view v (records of the views concatenated in view order);
+// view_records = the number of set-up records of the table.
+void set_view_soups(ViewTable& vt, const SoupDev& s);
+void set_view_soups(ViewTable& vt, const SoupDev* const* soups);
+long long view_records(const ViewTable& vt);
+// One set-up record (and tile count, tile box, depth key) per (view,
+// triangle of the view's soup), at rec_base + triangle.
+cudaError_t launch_setup(const ViewTable& vt, SetupRec* recs, uint32_t* counts, int4* tbox, uint32_t* zkeys,
+                         cudaStream_t st);
+cudaError_t launch_emit(const ViewTable& vt, const SetupRec* recs, const uint32_t* counts, const uint32_t* offs,
+                        const int4* tbox, const uint32_t* zkeys, int DB, uint32_t* keys, uint32_t* vals,
+                        uint32_t cap, int* status, cudaStream_t st);
 cudaError_t launch_tile_ranges(const uint32_t* keys, const uint32_t* count, uint32_t kcap, int DB,
                                uint2* ranges, cudaStream_t st);
 
 // ---- forward rasteriser (ds_raster.cu)
+// multi: every view reads its own soup (ViewDesc s_*, rec_base) instead of s
+// (s then supplies N, C and V, which the views' soups share).
 cudaError_t launch_raster_fwd(const ViewTable& vt, const SoupDev& s, const SetupRec* recs,
                               const uint32_t* keys, const uint32_t* vals, const uint2* ranges,
                               int DB, uint32_t mode, const Bg& bg, int* counter, int grid,
                               cudaStream_t st, bool with_loss = false, float scale = 0.f,
-                              float* loss = nullptr);
+                              float* loss = nullptr, bool multi = false);
 // mode 0: n_front into the views' n_front buffers; mode 1: add the number of
 // covered fragments (one sample) to *total.
 cudaError_t launch_raster_count(const ViewTable& vt, const SoupDev& s, const SetupRec* recs,

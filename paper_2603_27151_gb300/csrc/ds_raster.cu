@@ -13,9 +13,11 @@ namespace ds {
 // kLoss: the epilogue also evaluates the per-pixel L2 loss against the
 // view's target and writes the upstream gradients and score weights (the
 // first half of the fused training pass; same arithmetic as ds_loss_l2).
-template <int SG, int TW, bool kLoss>
+// kMulti: the views are of different soups (ViewDesc s_act, s_act_a,
+// rec_base; the soups share N, C and V, given by s).
+template <int SG, int TW, bool kLoss, bool kMulti>
 __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
-    k_raster_fwd(const __grid_constant__ ViewTable vt, const SoupDev s, const SetupRec* __restrict__ recs,
+    k_raster_fwd(const __grid_constant__ ViewTable vt, const SoupDev soup, const SetupRec* __restrict__ recs,
                  const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
                  const uint2* __restrict__ ranges, int DB, uint32_t mode, const Bg bg, float scale,
                  float* __restrict__ loss, int* __restrict__ counter) {
@@ -33,6 +35,14 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
         if (item >= vt.n_items) break;
         const WorkItem wi = decode_item(vt, item);
         const ViewDesc& V = vt.v[wi.v];
+        SoupDev s = soup;
+        size_t vbase = (size_t)wi.v * soup.T;
+        if (kMulti) {
+            s.act = V.s_act;
+            s.act_a = V.s_act_a;
+            s.T = V.s_T;
+            vbase = (size_t)V.rec_base;
+        }
         const int px = wi.tx * TW + lx, py = wi.ty * TH + ly;
         const bool valid = px < V.W && py < V.H;
         const int s0 = wi.g * kSampleGroup;
@@ -50,7 +60,7 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
         }
 
         const uint2 rg = ranges[V.tile_base + wi.ty * V.tiles_x + wi.tx];
-        forward_walk<SG, TW>(sm, recs, keys, vals, rg, DB, vt.chunk, (size_t)wi.v * s.T, wi, s, tid, lx, ly, warp, valid,
+        forward_walk<SG, TW>(sm, recs, keys, vals, rg, DB, vt.chunk, vbase, wi, s, tid, lx, ly, warp, valid,
                              px, py, ns, seed, stochastic, bt, brho, bb1, bb2, bD);
 
         if (valid) {
@@ -120,6 +130,7 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
         const int s0 = wi.g * kSampleGroup;
         const int ns = mode == 0 ? min(SG, vt.S - s0) : 1;
         const size_t HW = (size_t)V.H * V.W, pix = (size_t)py * V.W + px;
+        const size_t vbase = (size_t)V.rec_base;   // the view's records (per-view soups)
 
         int wt[SG], cnt[SG];
         float wrho[SG];
@@ -130,8 +141,8 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
             cnt[q] = 0;
             if (mode == 0 && valid && q < ns) {
                 wt[q] = reinterpret_cast<const int4*>(V.gbuf)[(s0 + q) * HW + pix].x;
-                if (wt[q] < 0 || wt[q] >= s.T) wt[q] = -1;
-                if (wt[q] >= 0) wrho[q] = winner_rho(recs + (size_t)wi.v * s.T + wt[q], px, py);
+                if (wt[q] < 0 || wt[q] >= V.s_T) wt[q] = -1;
+                if (wt[q] >= 0) wrho[q] = winner_rho(recs + vbase + wt[q], px, py);
             }
         }
         const uint2 rg = ranges[V.tile_base + wi.ty * V.tiles_x + wi.tx];
@@ -140,8 +151,7 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
             const int n = (int)min((uint32_t)vt.chunk, rg.y - c0);
             __syncthreads();
             if (tid < n)
-                stage_triangle<TW>(sm, tid, recs, (size_t)wi.v * s.T, keys[c0 + tid], vals[c0 + tid], DB, wi.tx * TW,
-                               wi.ty * TH);
+                stage_triangle<TW>(sm, tid, recs, vbase, keys[c0 + tid], vals[c0 + tid], DB, wi.tx * TW, wi.ty * TH);
             __syncthreads();
             if (!warp_done) {
                 for (int j = 0; j < n; ++j) {
@@ -196,15 +206,22 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
 
 cudaError_t launch_raster_fwd(const ViewTable& vt, const SoupDev& s, const SetupRec* recs, const uint32_t* keys,
                               const uint32_t* vals, const uint2* ranges, int DB, uint32_t mode, const Bg& bg,
-                              int* counter, int grid, cudaStream_t st, bool with_loss, float scale, float* loss) {
+                              int* counter, int grid, cudaStream_t st, bool with_loss, float scale, float* loss,
+                              bool multi) {
     dispatch_tile(vt.tile_w, vt.S == 1 ? 1 : (vt.S == 2 ? 2 : 4), [&](auto P) {
         constexpr int SG = decltype(P)::sg, TW = decltype(P)::tw;
         if (with_loss)
-            k_raster_fwd<SG, TW, true><<<resident_grid(k_raster_fwd<SG, TW, true>, vt.n_items, grid), kTilePix, 0,
-                                         st>>>(vt, s, recs, keys, vals, ranges, DB, mode, bg, scale, loss, counter);
+            k_raster_fwd<SG, TW, true, false><<<resident_grid(k_raster_fwd<SG, TW, true, false>, vt.n_items, grid),
+                                                kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, bg, scale,
+                                                                   loss, counter);
+        else if (multi)
+            k_raster_fwd<SG, TW, false, true><<<resident_grid(k_raster_fwd<SG, TW, false, true>, vt.n_items, grid),
+                                                kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, bg, scale,
+                                                                   loss, counter);
         else
-            k_raster_fwd<SG, TW, false><<<resident_grid(k_raster_fwd<SG, TW, false>, vt.n_items, grid), kTilePix, 0,
-                                          st>>>(vt, s, recs, keys, vals, ranges, DB, mode, bg, scale, loss, counter);
+            k_raster_fwd<SG, TW, false, false><<<resident_grid(k_raster_fwd<SG, TW, false, false>, vt.n_items, grid),
+                                                 kTilePix, 0, st>>>(vt, s, recs, keys, vals, ranges, DB, mode, bg, scale,
+                                                                    loss, counter);
     });
     note_launches(1);
     return cudaGetLastError();

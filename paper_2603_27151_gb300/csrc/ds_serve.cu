@@ -3,10 +3,11 @@
 // Soups stay resident on the device.  Requests (one view each) are queued
 // without blocking; a scheduler thread hands them to k workers, each a
 // library context on its own stream.  When a worker is free it takes the
-// oldest queued request together with any other queued requests for the same
-// soup (up to max_batch views, one forward launch), so requests that arrive
-// while others are on the GPU join the next batch, and batches on different
-// streams overlap on the device.  Admission is by device memory: a batch is
+// oldest queued request together with the other queued requests that share
+// its mode, background and texture shape (grid_n, C), whatever their soup
+// (up to max_batch views, one multi-soup forward launch), so requests that
+// arrive while others are on the GPU join the next batch, and batches on
+// different streams overlap on the device.  Admission is by device memory: a batch is
 // launched only if the scratch estimate of all in-flight batches stays within
 // the budget (a lone request is always admitted).  Completion is signalled by
 // a host function enqueued behind each batch (no polling).
@@ -53,8 +54,8 @@ struct Batch {
     ds_server* srv = nullptr;
     Worker* w = nullptr;
     std::vector<Request*> reqs;
+    std::vector<int32_t> soup_ids;   // each request's soup, as ids in the worker's context
     size_t bytes = 0;
-    int32_t soup_id = -1;   // the soup's id in the worker's context
 };
 
 struct Worker {
@@ -144,8 +145,8 @@ ds_status launch(ds_server* s, Worker& w, Batch& b) {
     }
     const Request* r0 = b.reqs[0];
     std::lock_guard<std::mutex> cl(w.call_mu);
-    ds_status st = ds_raster_forward(w.ctx, b.soup_id, cams.data(), seeds.data(), n, 1, r0->mode | DS_NO_SYNC,
-                                     r0->bg, outs.data(), w.stream);
+    ds_status st = ds_raster_forward_multi(w.ctx, b.soup_ids.data(), cams.data(), seeds.data(), n, 1,
+                                           r0->mode | DS_NO_SYNC, r0->bg, outs.data(), w.stream);
     if (st != DS_OK) return st;
     if (cudaLaunchHostFunc(w.stream, batch_done, &b) != cudaSuccess) {
         cudaGetLastError();
@@ -182,8 +183,8 @@ void scheduler(ds_server* s) {
                     outs[i] = b->reqs[i]->out;
                 }
                 const Request* r0 = b->reqs[0];
-                st = ds_raster_forward(w.ctx, b->soup_id, cams.data(), seeds.data(), n, 1, r0->mode, r0->bg,
-                                       outs.data(), w.stream);
+                st = ds_raster_forward_multi(w.ctx, b->soup_ids.data(), cams.data(), seeds.data(), n, 1, r0->mode,
+                                             r0->bg, outs.data(), w.stream);
                 if (st == DS_OK && cudaStreamSynchronize(w.stream) != cudaSuccess) st = DS_ERR_CUDA;
                 const int64_t t = now_ns();
                 for (Request* r : b->reqs) r->t_done = t;
@@ -212,24 +213,28 @@ void scheduler(ds_server* s) {
                     break;
                 }
             Request* first = s->queue.front();
+            const ServerSoup& fs = s->soups[first->soup];
             Batch& b = w->batch;
             b.srv = s;
             b.w = w;
             b.reqs.clear();
+            b.soup_ids.clear();
             b.bytes = 0;
+            const size_t wi = (size_t)(w - s->workers.data());
             for (auto it = s->queue.begin(); it != s->queue.end() && (int)b.reqs.size() < s->max_batch;) {
                 Request* r = *it;
-                const bool same = r->soup == first->soup && r->mode == first->mode &&
+                const ServerSoup& rs = s->soups[r->soup];
+                const bool same = r->mode == first->mode && rs.N == fs.N && rs.C == fs.C &&
                                   std::memcmp(r->bg, first->bg, sizeof(r->bg)) == 0;
                 if (same && (b.reqs.empty() || s->in_flight + b.bytes + r->bytes <= s->budget)) {
                     b.reqs.push_back(r);
+                    b.soup_ids.push_back(rs.ids[wi]);
                     b.bytes += r->bytes;
                     it = s->queue.erase(it);
                 } else {
                     ++it;
                 }
             }
-            b.soup_id = s->soups[first->soup].ids[w - s->workers.data()];
             const int64_t t = now_ns();
             for (Request* r : b.reqs) {
                 r->state = kRunning;

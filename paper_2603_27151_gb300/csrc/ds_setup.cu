@@ -77,15 +77,23 @@ constexpr int kExactTileLimit = 64;   // bbox tile counts above this skip the pe
 // the oriented edge functions with the top-left fill rule (Eq. 1 fragments),
 // the perspective factors k_i, the tile rectangle and the number of tiles
 // whose pixel centres the triangle may cover.
-__global__ void k_setup(const __grid_constant__ ViewTable vt, const SoupDev s,
+// The view of set-up record `gid` (records of view v start at rec_base).
+__device__ __forceinline__ int view_of_record(const ViewTable& vt, long long gid) {
+    int v = 0;
+    for (int i = 1; i < vt.n; ++i)
+        if (vt.v[i].rec_base <= gid) v = i;
+    return v;
+}
+
+__global__ void k_setup(const __grid_constant__ ViewTable vt, long long n_records,
                         SetupRec* __restrict__ recs, uint32_t* __restrict__ counts,
                         int4* __restrict__ tbox, uint32_t* __restrict__ zkeys) {
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (gid >= (long long)vt.n * s.T) return;
-    const int v = (int)(gid / s.T), t = (int)(gid - (long long)v * s.T);
+    if (gid >= n_records) return;
+    const int v = view_of_record(vt, gid), t = (int)(gid - vt.v[v].rec_base);
     const DevCam& cam = view_cam(vt, v);
     const int W = vt.v[v].W, H = vt.v[v].H;
-    const float* p = s.verts + 9LL * t;
+    const float* p = vt.v[v].s_verts + 9LL * t;
 
     int X[3], Y[3];
     float w[3];
@@ -169,30 +177,50 @@ __global__ void k_setup(const __grid_constant__ ViewTable vt, const SoupDev s,
     zkeys[gid] = zk;
 }
 
-cudaError_t launch_setup(const ViewTable& vt, const SoupDev& s, SetupRec* recs, uint32_t* counts,
-                         int4* tbox, uint32_t* zkeys, cudaStream_t st) {
-    const long long n = (long long)vt.n * s.T;
+long long view_records(const ViewTable& vt) {
+    return vt.n > 0 ? vt.v[vt.n - 1].rec_base + vt.v[vt.n - 1].s_T : 0;
+}
+
+void set_view_soups(ViewTable& vt, const SoupDev* const* soups) {
+    long long rb = 0;
+    for (int v = 0; v < vt.n; ++v) {
+        const SoupDev& s = *soups[v];
+        ViewDesc& d = vt.v[v];
+        d.s_verts = s.verts;
+        d.s_act = s.act;
+        d.s_act_a = s.act_a;
+        d.s_T = s.T;
+        d.rec_base = rb;
+        rb += s.T;
+    }
+}
+
+void set_view_soups(ViewTable& vt, const SoupDev& s) {
+    const SoupDev* one[DS_MAX_VIEWS];
+    for (int v = 0; v < vt.n; ++v) one[v] = &s;
+    set_view_soups(vt, one);
+}
+
+cudaError_t launch_setup(const ViewTable& vt, SetupRec* recs, uint32_t* counts, int4* tbox, uint32_t* zkeys,
+                         cudaStream_t st) {
+    const long long n = view_records(vt);
+    if (n <= 0) return cudaSuccess;
     const int grid = (int)((n + 255) / 256);
-    k_setup<<<grid, 256, 0, st>>>(vt, s, recs, counts, tbox, zkeys);
+    k_setup<<<grid, 256, 0, st>>>(vt, n, recs, counts, tbox, zkeys);
     note_launches(1);
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- emission
-// Key of a (tile, triangle) pair: global tile index in the high bits, the top
-// DB bits of the triangle's nearest vertex depth (a positive float, so its bit
-// pattern orders like its value) in the low bits.  Sorting the keys orders
-// each tile's list front to back, which lets the rasteriser stop early.
-__global__ void k_emit(const __grid_constant__ ViewTable vt, int T, const SetupRec* __restrict__ recs,
+__global__ void k_emit(const __grid_constant__ ViewTable vt, long long n_records, const SetupRec* __restrict__ recs,
                        const uint32_t* __restrict__ counts, const uint32_t* __restrict__ offs,
                        const int4* __restrict__ tbox, const uint32_t* __restrict__ zkeys, int DB,
                        uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, uint32_t cap,
                        int* __restrict__ status) {
     const long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (gid >= (long long)vt.n * T) return;
+    if (gid >= n_records) return;
     const uint32_t cnt = counts[gid];
     if (cnt == 0) return;
-    const int v = (int)(gid / T), t = (int)(gid - (long long)v * T);
+    const int v = view_of_record(vt, gid), t = (int)(gid - vt.v[v].rec_base);
     const int4 box = tbox[gid];
     const SetupRec r = load_rec(recs + gid);
     const uint32_t dbits = DB > 0 ? ((zkeys[gid] & 0x7fffffffu) >> (31 - DB)) : 0u;
@@ -215,12 +243,13 @@ __global__ void k_emit(const __grid_constant__ ViewTable vt, int T, const SetupR
     if (over) atomicOr(status, 1);
 }
 
-cudaError_t launch_emit(const ViewTable& vt, int T, const SetupRec* recs, const uint32_t* counts,
-                        const uint32_t* offs, const int4* tbox, const uint32_t* zkeys, int DB,
-                        uint32_t* keys, uint32_t* vals, uint32_t cap, int* status, cudaStream_t st) {
-    const long long n = (long long)vt.n * T;
+cudaError_t launch_emit(const ViewTable& vt, const SetupRec* recs, const uint32_t* counts, const uint32_t* offs,
+                        const int4* tbox, const uint32_t* zkeys, int DB, uint32_t* keys, uint32_t* vals,
+                        uint32_t cap, int* status, cudaStream_t st) {
+    const long long n = view_records(vt);
+    if (n <= 0) return cudaSuccess;
     const int grid = (int)((n + 255) / 256);
-    k_emit<<<grid, 256, 0, st>>>(vt, T, recs, counts, offs, tbox, zkeys, DB, keys, vals, cap, status);
+    k_emit<<<grid, 256, 0, st>>>(vt, n, recs, counts, offs, tbox, zkeys, DB, keys, vals, cap, status);
     note_launches(1);
     return cudaGetLastError();
 }

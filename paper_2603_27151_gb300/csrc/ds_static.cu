@@ -182,7 +182,8 @@ extern "C" DS_API ds_status ds_raster_forward_noalloc(const float* verts, const 
     const size_t nvt = (size_t)n_views * T;
     NA_TRY(cudaMemsetAsync(misc, 0, 256, st));
     NA_TRY(ds::launch_activate(sd, st));
-    NA_TRY(ds::launch_setup(vt, sd, recs, counts, tbox, zkeys, st));
+    ds::set_view_soups(vt, sd);
+    NA_TRY(ds::launch_setup(vt, recs, counts, tbox, zkeys, st));
     NA_TRY(ds::scan_exclusive(counts, offs, (int64_t)nvt, dK, sc, st));
     uint32_t K = 0;   // the one data-dependent size, read back into host stack memory
     NA_TRY(cudaMemcpyAsync(&K, dK, sizeof(K), cudaMemcpyDeviceToHost, st));
@@ -193,7 +194,7 @@ extern "C" DS_API ds_status ds_raster_forward_noalloc(const float* verts, const 
     int tile_bits = 0;
     while (tile_bits < 32 && (1ull << tile_bits) < (unsigned long long)tile_base) ++tile_bits;
     const int DB = tile_bits <= 16 ? 16 : 32 - tile_bits;
-    NA_TRY(ds::launch_emit(vt, T, recs, counts, offs, tbox, zkeys, DB, keys[0], vals[0], (uint32_t)kMaxPairs, status, st));
+    NA_TRY(ds::launch_emit(vt, recs, counts, offs, tbox, zkeys, DB, keys[0], vals[0], (uint32_t)kMaxPairs, status, st));
     cudaError_t se = cudaSuccess;
     const int res = ds::radix_sort_pairs(keys[0], vals[0], keys[1], vals[1], dK, K, tile_bits + DB, hist, hist_scan, sc,
                                          st, &se);

@@ -92,6 +92,8 @@ def load():
     L.ds_soup_free.argtypes = [P, i32]
     L.ds_soup_free.restype = i32
     L.ds_raster_forward.argtypes = [P, i32, P, P, i32, i32, u32, P, P, P]
+    L.ds_raster_forward_multi.argtypes = [P, P, P, P, i32, i32, u32, P, P, P]
+    L.ds_raster_forward_multi.restype = i32
     L.ds_raster_forward.restype = i32
     L.ds_raster_backward.argtypes = [P, i32, P, i32, i32, P, P, u32, P, P, P]
     L.ds_raster_backward.restype = i32
@@ -280,6 +282,22 @@ class Context:
             outs[v].n_front = n_fronts[v].data_ptr() if n_fronts is not None and n_fronts[v] is not None else None
         _check(load().ds_raster_forward(self.h, soup_id, ca, sd, n, S, mode,
                                         bga.ctypes.data_as(ctypes.c_void_p), outs, _stream(stream)))
+
+    def raster_forward_multi(self, soup_ids, cams, seeds, S, mode, bg, gbufs, colors, n_fronts=None, stream=None):
+        """Views of different soups in one launch (ds_raster_forward_multi):
+        view v renders soup soup_ids[v]; outputs as raster_forward."""
+        n = len(cams)
+        ids = (ctypes.c_int32 * n)(*[int(x) for x in soup_ids])
+        ca = cameras(cams)
+        sd = (ctypes.c_uint64 * n)(*[int(x) for x in (seeds if seeds is not None else [0] * n)])
+        bga = np.ascontiguousarray(bg, np.float32)
+        outs = (ds_view_out * n)()
+        for v in range(n):
+            outs[v].gbuf = gbufs[v].data_ptr()
+            outs[v].color = colors[v].data_ptr()
+            outs[v].n_front = n_fronts[v].data_ptr() if n_fronts is not None and n_fronts[v] is not None else None
+        _check(load().ds_raster_forward_multi(self.h, ids, ca, sd, n, S, mode, bga.ctypes.data_as(ctypes.c_void_p),
+                                              outs, _stream(stream)))
 
     def raster_backward(self, soup_id, cams, S, gbufs, colors, grad_colors, score_ws, flags,
                         grad_verts=None, grad_tex=None, stream=None):

@@ -1232,11 +1232,12 @@ def oracle_pool(cores: int):
     return mp.get_context("spawn").Pool(cores, initializer=_oracle_init)
 
 
-def oracle_sample(pool, cores: int, start_row: int, seed: int = 13):
-    """Rows start_row .. start_row + cores - 1 of view CPU_VIEW, one per
-    process; fragments/s over the wall time of the timed pass (targets
-    rendered before, untimed)."""
-    rows = [(CPU_VIEW, start_row + k, start_row + k + 1) for k in range(cores)]
+def oracle_sample(pool, cores: int, start_row: int, seed: int = 13, rows_per_process: int = 1):
+    """Rows start_row .. start_row + cores * rows_per_process - 1 of view
+    CPU_VIEW, one band of rows_per_process rows per process; fragments/s over
+    the wall time of the timed pass (targets rendered before, untimed)."""
+    n = rows_per_process
+    rows = [(CPU_VIEW, start_row + n * k, start_row + n * (k + 1)) for k in range(cores)]
     tg = pool.map(_oracle_target, rows)
     jobs = [r + (seed, t) for r, t in zip(rows, tg)]
     t0 = time.perf_counter()
@@ -1326,18 +1327,25 @@ def cpu_config_estimates():
     return {"train": train, "serve": serve}
 
 
+# Rows per process of the CPU baseline's sample (about 10-20 s of CPU work
+# in all on 16 cores) and of each step of the reference arm.
+CPU_ROWS_BASELINE = 20
+CPU_ROWS_STEP = 4
+
+
 def cpu_baseline_entry(fragments_per_step=None):
     cores = _cores()
+    n = CPU_ROWS_BASELINE
     with oracle_pool(cores) as pool:
-        v, wall, frags = oracle_sample(pool, cores, CPU_ROW0)
-    v1, secs1, frags1 = oracle_one_core(CPU_ROW0, 2)
+        v, wall, frags = oracle_sample(pool, cores, CPU_ROW0, rows_per_process=n)
+    v1, secs1, frags1 = oracle_one_core(CPU_ROW0, n)
     out = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle (bbox-scan mode, results equal to brute force)",
-           "sample": "rows %d-%d of view %d (1920x1080), one row per process, S=4, forward + L2 loss + backward "
+           "sample": "rows %d-%d of view %d (1920x1080), %d rows per process, S=4, forward + L2 loss + backward "
                      "(all gradient terms), targets rendered before, untimed: %d fragments in %.2f s wall"
-                     % (CPU_ROW0, CPU_ROW0 + cores - 1, CPU_VIEW, frags, wall),
+                     % (CPU_ROW0, CPU_ROW0 + n * cores - 1, CPU_VIEW, n, frags, wall),
            "cores_1": {"value": v1, "unit": UNIT, "cores": 1,
                        "sample": "rows %d-%d of the same view on one core: %d fragments in %.2f s"
-                                 % (CPU_ROW0, CPU_ROW0 + 1, frags1, secs1)}}
+                                 % (CPU_ROW0, CPU_ROW0 + n - 1, frags1, secs1)}}
     if fragments_per_step:
         out["extrapolated_s_per_step"] = {"cores": fragments_per_step / v, "cores_1": fragments_per_step / v1,
                                           "what": "extrapolated: the step's fragments at the sampled rate"}
@@ -1354,15 +1362,17 @@ def _reference_arm(args):
     # each step: the next band of rows of the workload's first view, one row
     # per process (the rows the GPU arm's cpu_baseline times come first)
     vals, walls, total = [], [], 0
+    n = CPU_ROWS_STEP
     with oracle_pool(cores) as pool:
         for k in range(args.steps):
-            v, wall, frags = oracle_sample(pool, cores, start_row=CPU_ROW0 + cores * k)
+            start = CPU_ROW0 + (n * cores * k) % (1080 - CPU_ROW0 - n * cores)
+            v, wall, frags = oracle_sample(pool, cores, start_row=start, rows_per_process=n)
             vals.append(v)
             walls.append(wall)
             total += frags
     value = total / sum(walls)
-    sample = ("per step %d rows of view %d (1920x1080), one row per process, from row %d on, S=4, forward + L2 "
-              "loss + backward; oracle in bbox-scan mode" % (cores, CPU_VIEW, CPU_ROW0))
+    sample = ("per step %d rows of view %d (1920x1080), %d rows per process, from row %d on, S=4, forward + L2 "
+              "loss + backward; oracle in bbox-scan mode" % (n * cores, CPU_VIEW, n, CPU_ROW0))
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded soups, cameras, targets)",

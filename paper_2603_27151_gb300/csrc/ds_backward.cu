@@ -29,9 +29,6 @@
 
 namespace ds {
 
-__device__ __forceinline__ unsigned long long lane_sentinel() {
-    return 0xffffffffffff0000ull | (threadIdx.x & 31);
-}
 
 // ------------------------------------------------------------ small vectors
 struct f3 {
@@ -301,134 +298,6 @@ __device__ __forceinline__ void interior_grad(const GeomRec* g, const DevCam& ca
         out[3 * m + 1] = gw.y;
         out[3 * m + 2] = gw.z;
     }
-}
-
-// Eq. 9 for every covered fragment in front of the winner of each sample
-// (Algorithm A1 2(b), G-buffer recomputation): walk the tile's list again and
-// scatter -w/(1 - alpha) to the opacity texels of the fragments in front.
-// `staged`: the whole list is already in shared memory (one chunk).
-//
-// The walk is warp-synchronous over the staged triangles, and a small
-// triangle covers few of a warp's pixels, so the opacity lookup and the
-// scatter of a fragment in front are not done where it is found: each lane
-// appends (triangle, barycentrics, summed score weight) to the warp's ring
-// in shared memory, and whenever 32 jobs wait the warp evaluates them with
-// every lane busy (the rest after the walk).
-struct ScoreJob {
-    int t;
-    float b1, b2;
-    float gw;   // sum of the score weights of the samples whose winner lies behind
-};
-constexpr int kScoreRing = 64;   // up to 31 waiting jobs + 32 new ones
-
-// Evaluate n <= 32 jobs of the ring from `head`: opacity at the fragment,
-// g = -gw / (1 - alpha), chained through the interpolation weights and the
-// sigmoid (a (1 - a) at each corner texel), summed over runs of lanes on
-// the same cell, one FP64 atomic per corner and run.
-__device__ __forceinline__ void score_batch(const SoupDev& s, double* __restrict__ acc_tex, const ScoreJob* ring,
-                                            int head, int n) {
-    const int lane = threadIdx.x & 31;
-    const bool act = lane < n;
-    ScoreJob jb{0, 0.f, 0.f, 0.f};
-    if (act) jb = ring[(head + lane) & (kScoreRing - 1)];
-    Cell cl;
-    cl.k0 = cl.k1 = cl.k2 = 0;
-    cl.wa = cl.wb = 0.f;
-    cl.lower = true;
-    float v[3] = {0.f, 0.f, 0.f};
-    unsigned long long key = lane_sentinel();
-    if (act) {
-        cl = find_cell(s.N, jb.b1, jb.b2);
-        const float* aa = s.act_a + (size_t)jb.t * s.V;
-        const float a0 = __ldg(aa + cl.k0), a1 = __ldg(aa + cl.k1), a2 = __ldg(aa + cl.k2);
-        const float alpha = interp(a0, a1, a2, cl.wa, cl.wb);
-        const float g = -jb.gw / (1.0f - alpha);
-        v[0] = g * (1.0f - cl.wa - cl.wb) * (a0 * (1.0f - a0));
-        v[1] = g * cl.wa * (a1 * (1.0f - a1));
-        v[2] = g * cl.wb * (a2 * (1.0f - a2));
-        key = ((unsigned long long)(unsigned)jb.t << 20) | ((unsigned)cl.k0 << 1) | (cl.lower ? 1u : 0u);
-    }
-    const bool head_lane = warp_run_sum<3>(key, v);
-    if (act && head_lane) {
-        const int ks[3] = {cl.k0, cl.k1, cl.k2};
-#pragma unroll
-        for (int m = 0; m < 3; ++m)
-            atomicAdd(acc_tex + ((size_t)jb.t * s.V + ks[m]) * s.C + (s.C - 1), (double)v[m]);
-    }
-}
-
-template <int SG, int TW>
-__device__ __forceinline__ void score_walk(TileStage& sm, const SetupRec* __restrict__ recs,
-                                           const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
-                                           uint2 rg, int DB, int chunk, size_t vbase, const WorkItem& wi,
-                                           const SoupDev& s, double* __restrict__ acc_tex, int tid, int lx, int ly,
-                                           int warp, bool staged, bool any_score, const int (&wt)[SG],
-                                           const float (&wrho)[SG], const float (&wsc)[SG], ScoreJob* ring) {
-    constexpr int TH = kTilePix / TW;
-    const unsigned lt = (1u << (tid & 31)) - 1u;
-    int head = 0, count = 0;   // the warp's ring (same values in every lane)
-    bool warp_done = !__any_sync(kFullMask, any_score);
-    if (__syncthreads_or(!warp_done)) {
-        for (uint32_t c0 = rg.x; c0 < rg.y; c0 += (uint32_t)chunk) {
-            const int n = (int)min((uint32_t)chunk, rg.y - c0);
-            __syncthreads();
-            if (!staged) {
-                if (tid < n)
-                    stage_triangle<TW>(sm, tid, recs, vbase, keys[c0 + tid], vals[c0 + tid], DB, wi.tx * TW,
-                                       wi.ty * TH);
-                __syncthreads();
-            }
-            if (!warp_done) {
-                for (int j = 0; j < n; ++j) {
-                    const int4 h2 = sm.h2[j];
-                    if (!((h2.w >> warp) & 1)) continue;   // covers none of this warp's pixels
-                    if (DB > 0) {   // without depth bits the bound is infinite
-                        bool ldone = true;
-#pragma unroll
-                        for (int q = 0; q < SG; ++q)
-                            if (wsc[q] != 0.f) ldone = ldone && wt[q] >= 0 && wrho[q] > __int_as_float(h2.z);
-                        if (__all_sync(kFullMask, ldone)) {
-                            warp_done = true;
-                            break;
-                        }
-                    }
-                    const int t = h2.y;
-                    bool need = false;
-                    float gw = 0.f, b1 = 0.f, b2 = 0.f;
-                    long long E[3];
-                    if (any_score && tile_cover(sm, j, lx, ly, E)) {
-                        const Frag f = make_frag(E[0], E[1], E[2], sm.kk[j][0], sm.kk[j][1], sm.kk[j][2]);
-#pragma unroll
-                        for (int q = 0; q < SG; ++q)
-                            if (wsc[q] != 0.f && t != wt[q] && (wt[q] < 0 || in_front(f.rho, t, wrho[q], wt[q]))) {
-                                need = true;
-                                gw += wsc[q];
-                            }
-                        if (need) {
-                            const float r = __frcp_rn(f.rho);
-                            b1 = __fmul_rn(f.q1, r);
-                            b2 = __fmul_rn(f.q2, r);
-                        }
-                    }
-                    const unsigned bal = __ballot_sync(kFullMask, need);
-                    if (bal) {
-                        if (need) ring[(head + count + __popc(bal & lt)) & (kScoreRing - 1)] = ScoreJob{t, b1, b2, gw};
-                        count += __popc(bal);
-                        __syncwarp();
-                        if (count >= 32) {
-                            score_batch(s, acc_tex, ring, head, 32);
-                            head = (head + 32) & (kScoreRing - 1);
-                            count -= 32;
-                            __syncwarp();
-                        }
-                    }
-                }
-            }
-            if (__syncthreads_and(warp_done)) break;
-        }
-    }
-    if (count > 0) score_batch(s, acc_tex, ring, head, count);
-    __syncwarp();
 }
 
 // Winner terms of every sample: colour (Algorithm A1 2(a)), +w/alpha
@@ -831,8 +700,10 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_EDGE)
             if (tp < 0 || tp >= s.T) tp = -1;
             const float* col = V.color + (size_t)sq * Co * HW;
             const float* gc = V.grad_color + (size_t)sq * Co * HW;
-            // ---- this lane's jobs: slot 2*dir + side (fixed slots keep the
-            // register arrays at constant indices)
+            // ---- this lane's jobs: slot dir for the pixel's own side, 2 + dir
+            // for the neighbour's (the two own-side jobs share the pixel's
+            // winner and sit next to each other: one run of atomics); fixed
+            // slots keep the register arrays at constant indices
             EdgeJob sl[4];
             bool vl[4] = {false, false, false, false};
             // winners of the right and lower neighbours, and the pair terms
@@ -867,12 +738,12 @@ __global__ void __launch_bounds__(kTilePix, DS_MINB_EDGE)
                 const float phi = phid[dir];
                 if (phi == 0.f) continue;
                 if (tp >= 0) {
-                    sl[2 * dir] = EdgeJob{px | (py << 16), tp, tq, phi, dir == 0 ? 0 : 2};
-                    vl[2 * dir] = true;
+                    sl[dir] = EdgeJob{px | (py << 16), tp, tq, phi, dir == 0 ? 0 : 2};
+                    vl[dir] = true;
                 }
                 if (tq >= 0) {
-                    sl[2 * dir + 1] = EdgeJob{qx | (qy << 16), tq, tp, -phi, dir == 0 ? 1 : 3};
-                    vl[2 * dir + 1] = true;
+                    sl[2 + dir] = EdgeJob{qx | (qy << 16), tq, tp, -phi, dir == 0 ? 1 : 3};
+                    vl[2 + dir] = true;
                 }
             }
             const int nmine = (int)vl[0] + (int)vl[1] + (int)vl[2] + (int)vl[3];

@@ -410,33 +410,42 @@ __global__ void __launch_bounds__(kThreads) k_shade_finish(const float* __restri
 
 // ---------------------------------------------------------------------------
 // Forward on the tensor cores: the three layers as tcgen05.mma of kind::tf32
-// (Blackwell 5th-generation tensor cores; operands in shared memory, the
-// FP32 accumulator in tensor memory).  A tile is 128 pixel-samples, one per
-// thread and one TMEM lane each (M = 128); N = 16 hidden units (the 3 outputs
-// padded to 16); K = 16 inputs in two MMAs of K = 8.  TF32 keeps 10 mantissa
-// bits, so every operand is split into hi = the TF32 truncation and lo = the
-// remainder (exact in FP32) and each product is taken as
-// x_lo w_hi + x_hi w_lo + x_hi w_hi (the x_lo w_lo term, about 2^-21 of the
+// (Blackwell 5th-generation tensor cores).  A tile is 128 pixel-samples, one
+// per thread and one tensor-memory lane each (M = 128); N = 16 hidden units
+// (the 3 outputs padded to 16); K = 16 inputs in two MMAs of K = 8.  TF32
+// keeps 10 mantissa bits, so every operand is split into hi = the TF32
+// truncation and lo = the remainder (exact in FP32) and each product is taken
+// as x_lo w_hi + x_hi w_lo + x_hi w_hi (the x_lo w_lo term, about 2^-21 of the
 // product, is dropped): six MMAs per layer, issued by one thread and
-// completed on an mbarrier.  Per layer the 128 threads read their row of the
-// accumulator (tcgen05.ld), add the bias, apply the activation, and write the
-// next layer's hi/lo operand rows back to shared memory.
+// completed on an mbarrier.
+//
+// The layer inputs (operand A) live in tensor memory beside the FP32
+// accumulator: each thread writes its row with tcgen05.st and the MMAs read A
+// from there, so shared memory carries only the 6 KB of weight tiles (B).
+// With A in shared memory every MMA re-read 4 KB of it, and the shared-memory
+// bandwidth, not the tensor cores, set the kernel's speed.  Per layer the 128
+// threads read their accumulator row (tcgen05.ld), add the bias, apply the
+// activation and write the next layer's hi/lo row.
 namespace tc {
 
 constexpr int kRows = 128;   // pixel-samples per tile = TMEM lanes = M
-constexpr uint32_t kTmemCols = 32;   // smallest allocation; the accumulator uses 16 columns
+// Tensor-memory columns of a CTA: the accumulator D in 0..15, A hi in 16..31,
+// A lo in 32..47 (one 32-bit TF32 value per column and lane).
+constexpr uint32_t kTmemCols = 64;
+constexpr uint32_t kColD = 0, kColAh = 16, kColAl = 32;
+constexpr int kMaxCtasPerSm = 512 / (int)kTmemCols;   // the SM's 512 columns, none left waiting
 // Instruction descriptor of kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32
 // (bits 7-9 and 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 in bits
 // 17-22, M >> 4 in bits 24-28.
 constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
 
-// Byte offset of element (r, k) of an R x 16 K-major TF32 operand in the
-// canonical layout without swizzle: core matrices of 8 rows x 16 bytes
-// (4 values), 128 bytes each; the two core matrices of one MMA's K = 8 are
-// 128 bytes apart (leading-dimension offset), successive 8-row groups 512
-// bytes apart (stride-dimension offset).
-__device__ __forceinline__ uint32_t op_off(int r, int k) {
-    return (uint32_t)(((((r >> 3) << 2) + (k >> 2)) << 7) + ((r & 7) << 4) + ((k & 3) << 2));
+// Byte offset of element (n, k) of a 16 x 16 K-major TF32 operand in shared
+// memory in the canonical layout without swizzle: core matrices of 8 rows x
+// 16 bytes (4 values), 128 bytes each; the two core matrices of one MMA's
+// K = 8 are 128 bytes apart (leading-dimension offset), the two 8-row groups
+// 512 bytes apart (stride-dimension offset).
+__device__ __forceinline__ uint32_t op_off(int n, int k) {
+    return (uint32_t)(((((n >> 3) << 2) + (k >> 2)) << 7) + ((n & 7) << 4) + ((k & 3) << 2));
 }
 
 // Shared-memory matrix descriptor: start address, leading and stride byte
@@ -450,47 +459,62 @@ __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cv
 
 struct Smem {
     uint8_t w[6][1024];   // W1 hi, W1 lo, W2 hi, W2 lo, W3 hi, W3 lo (N 16 x K 16)
-    uint8_t a[2][8192];   // the layer's input rows: hi, lo (M 128 x K 16)
     float bias[36];       // b1 [16], b2 [16], b3 [3]
     unsigned long long bar;
     uint32_t tmem;
 };
 
-// Store one operand row (16 values) as its TF32 hi and lo parts.
-__device__ __forceinline__ void store_row(Smem& sm, int r, const float (&x)[16]) {
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        uint32_t h[4], l[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            h[e] = __float_as_uint(x[4 * c + e]) & 0xFFFFE000u;
-            l[e] = __float_as_uint(x[4 * c + e] - __uint_as_float(h[e]));
-        }
-        *reinterpret_cast<uint4*>(sm.a[0] + op_off(r, 4 * c)) = make_uint4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<uint4*>(sm.a[1] + op_off(r, 4 * c)) = make_uint4(l[0], l[1], l[2], l[3]);
-    }
+// TF32 hi part (truncation to 10 mantissa bits) and FP32 remainder.
+__device__ __forceinline__ void split(float x, uint32_t& h, uint32_t& l) {
+    h = __float_as_uint(x) & 0xFFFFE000u;
+    l = __float_as_uint(x - __uint_as_float(h));
 }
 
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t accumulate) {
+// 16 columns of this thread's lane from column `col` on (warp w owns lanes
+// 32w .. 32w + 31, the lane field sits in bits 16-31 of the address).
+__device__ __forceinline__ uint32_t lane_addr(uint32_t tmem, uint32_t col) {
+    return tmem + ((uint32_t)(threadIdx.x & ~31) << 16) + col;
+}
+
+__device__ __forceinline__ void st8(uint32_t ta, const uint32_t (&r)[8]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n" ::"r"(ta), "r"(r[0]),
+                 "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+
+// Write eight values of this thread's operand row, K = 8 half .. 8 half + 7,
+// as their hi and lo parts into tensor memory.
+__device__ __forceinline__ void store_half(uint32_t tmem, int half, const uint32_t (&h)[8], const uint32_t (&l)[8]) {
+    st8(lane_addr(tmem, kColAh + 8 * half), h);
+    st8(lane_addr(tmem, kColAl + 8 * half), l);
+}
+
+__device__ __forceinline__ void split8(const float* x, uint32_t (&h)[8], uint32_t (&l)[8]) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) split(x[i], h[i], l[i]);
+}
+
+__device__ __forceinline__ void mma(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t accumulate) {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+        "r"(a_tmem), "l"(b), "r"(kIdesc), "r"(accumulate));
 }
 
 // Layer L: D = A_lo W_hi + A_hi W_lo + A_hi W_hi (small terms first), then
 // the commit that arrives on the barrier when the MMAs are complete.  One
 // thread.
-__device__ __forceinline__ void issue_layer(Smem& sm, int L, uint32_t d) {
-    const uint32_t a0 = saddr(sm.a[0]), a1 = saddr(sm.a[1]), b0 = saddr(sm.w[2 * L]), b1 = saddr(sm.w[2 * L + 1]);
+__device__ __forceinline__ void issue_layer(Smem& sm, int L, uint32_t tmem) {
+    const uint32_t b0 = saddr(sm.w[2 * L]), b1 = saddr(sm.w[2 * L + 1]);
+    const uint32_t d = tmem + kColD;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
-        mma(d, smem_desc(a1 + 256 * s), smem_desc(b0 + 256 * s), s);
-        mma(d, smem_desc(a0 + 256 * s), smem_desc(b1 + 256 * s), 1);
+        mma(d, tmem + kColAl + 8 * s, smem_desc(b0 + 256 * s), s);
+        mma(d, tmem + kColAh + 8 * s, smem_desc(b1 + 256 * s), 1);
     }
 #pragma unroll
-    for (int s = 0; s < 2; ++s) mma(d, smem_desc(a0 + 256 * s), smem_desc(b0 + 256 * s), 1);
+    for (int s = 0; s < 2; ++s) mma(d, tmem + kColAh + 8 * s, smem_desc(b0 + 256 * s), 1);
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(saddr(&sm.bar))
                  : "memory");
 }
@@ -511,34 +535,38 @@ __device__ __forceinline__ bool wait_bar(const Smem& sm, uint32_t parity) {
     }
 }
 
-// This thread's accumulator row (TMEM lane = thread), 16 columns.
+// This thread's accumulator row, 16 columns.
 __device__ __forceinline__ void load_row(uint32_t tmem, float (&v)[16]) {
     uint32_t r[16];
-    const uint32_t ta = tmem + ((uint32_t)(threadIdx.x & ~31) << 16);
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(ta));
+        : "r"(lane_addr(tmem, kColD)));
     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Generic-proxy writes of the operand rows -> visible to the MMAs; prior
-// tcgen05 loads ordered before the barrier that follows.
+// This thread's tensor-memory stores complete, and they and its earlier
+// tensor-memory loads ordered before the barrier that follows.
 __device__ __forceinline__ void before_sync() {
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
 }
 
 }  // namespace tc
 
-// One tile of 128 pixel-samples per round, persistent CTAs of 128 threads;
-// tiles never straddle views (view v owns tiles blk0 .. blk0 + ceil(S HW /
-// 128) - 1).  A wait for the MMAs that runs out (about a second) sets bit 1
-// of *status, and the CTA releases its tensor memory and returns.
-__global__ void __launch_bounds__(tc::kRows) k_shade_fwd_tc(const __grid_constant__ ShadeTable t,
+// Per round a CTA takes one tile: 128 consecutive pixels of one view (tiles
+// never straddle views: view v owns tiles blk0 .. blk0 + ceil(HW / 128) - 1)
+// and all S mask samples of them in turn.  The SH encoding of the pixel and
+// its hi/lo split are computed once per tile; per sample the thread writes
+// its input row (7 features, then the 9 SH values) and the three layers
+// run.  The next sample's features are loaded before the current sample's
+// MMAs.  Persistent CTAs of 128 threads.  A wait for the MMAs that runs out
+// (about a second) sets bit 1 of *status, and the CTA releases its tensor
+// memory and returns.
+__global__ void __launch_bounds__(tc::kRows, tc::kMaxCtasPerSm) k_shade_fwd_tc(const __grid_constant__ ShadeTable t,
                                                           const float* __restrict__ params, int* __restrict__ status) {
     using namespace tc;
     extern __shared__ uint8_t smem_raw[];
@@ -549,9 +577,10 @@ __global__ void __launch_bounds__(tc::kRows) k_shade_fwd_tc(const __grid_constan
         const int L = q >> 8, n = (q >> 4) & 15, k = q & 15;
         const int o = L == 0 ? oW1 : (L == 1 ? oW2 : oW3);
         const float w = (L < 2 || n < kOut) ? __ldg(params + o + n * 16 + k) : 0.f;
-        const uint32_t h = __float_as_uint(w) & 0xFFFFE000u;
+        uint32_t h, l;
+        split(w, h, l);
         *reinterpret_cast<uint32_t*>(sm.w[2 * L] + op_off(n, k)) = h;
-        *reinterpret_cast<uint32_t*>(sm.w[2 * L + 1] + op_off(n, k)) = __float_as_uint(w - __uint_as_float(h));
+        *reinterpret_cast<uint32_t*>(sm.w[2 * L + 1] + op_off(n, k)) = l;
     }
     if (tid < 36) sm.bias[tid] = tid < 16 ? __ldg(params + oB1 + tid) : (tid < 32 ? __ldg(params + oB2 + tid - 16)
                                                                                   : (tid < 35 ? __ldg(params + oB3 + tid - 32) : 0.f));
@@ -565,6 +594,8 @@ __global__ void __launch_bounds__(tc::kRows) k_shade_fwd_tc(const __grid_constan
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
+    // the weight tiles (generic-proxy writes) visible to the MMAs
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     before_sync();
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -573,48 +604,73 @@ __global__ void __launch_bounds__(tc::kRows) k_shade_fwd_tc(const __grid_constan
     bool ok = true;
     for (int tile = blockIdx.x; tile < t.n_blocks && ok; tile += gridDim.x) {
         const ShadeView& V = t.v[find_view(t, tile)];
-        const int idx = (tile - V.blk0) * kRows + tid;
-        const bool valid = idx < t.S * V.HW;
-        const int s = valid ? idx / V.HW : 0, p = valid ? idx - s * V.HW : 0;
-        float f[kFeat], x[16];
+        const int p = (tile - V.blk0) * kRows + tid;
+        const bool valid = p < V.HW;
+        const int py = valid ? p / V.W : 0, px = valid ? p - py * V.W : 0;
+        // input columns 8..15 (SH bands 1..8), split once for all samples;
+        // column 7 is the constant band
+        uint32_t shh[8], shl[8];
+        {
+            float sh[kSH];
+            sh_of_pixel(V, px, py, sh);
+            split8(sh + 1, shh, shl);
+        }
+        const float* fp = V.feat + (valid ? p : 0);
+        float fn[kFeat];
 #pragma unroll
-        for (int c = 0; c < kFeat; ++c) f[c] = valid ? __ldcs(V.feat + ((size_t)s * kFeat + c) * V.HW + p) : 0.f;
-        float sh[kSH];
-        sh_of_pixel(V, p % V.W, p / V.W, sh);
+        for (int c = 0; c < kFeat; ++c) fn[c] = valid ? __ldcs(fp + (size_t)c * V.HW) : 0.f;
+        for (int s = 0; s < t.S; ++s) {
+            float f[kFeat];
 #pragma unroll
-        for (int c = 0; c < kFeat; ++c) x[c] = f[c];
+            for (int c = 0; c < kFeat; ++c) f[c] = fn[c];
+            if (s + 1 < t.S) {
 #pragma unroll
-        for (int c = 0; c < kSH; ++c) x[kFeat + c] = valid ? sh[c] : 0.f;
-        float o[kOut];
+                for (int c = 0; c < kFeat; ++c)
+                    fn[c] = valid ? __ldcs(fp + ((size_t)(s + 1) * kFeat + c) * V.HW) : 0.f;
+            }
+            {
+                const float x[8] = {f[0], f[1], f[2], f[3], f[4], f[5], f[6], kC0};
+                uint32_t h[8], l[8];
+                split8(x, h, l);
+                store_half(tmem, 0, h, l);
+                store_half(tmem, 1, shh, shl);
+            }
+            float o[kOut];
 #pragma unroll
-        for (int L = 0; L < 3; ++L) {
-            store_row(sm, tid, x);
-            before_sync();
-            __syncthreads();
-            if (tid == 0) issue_layer(sm, L, tmem);
-            ok = __syncthreads_and(wait_bar(sm, phase));
-            phase ^= 1u;
+            for (int L = 0; L < 3; ++L) {
+                // the rows are complete and every thread's reads of the
+                // previous accumulator are done: the next MMAs may start
+                before_sync();
+                __syncthreads();
+                if (tid == 0) issue_layer(sm, L, tmem);
+                ok = __syncthreads_and(wait_bar(sm, phase));
+                phase ^= 1u;
+                if (!ok) break;
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                float d[16];
+                load_row(tmem, d);
+                if (L < 2) {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) d[i] = fmaxf(d[i] + sm.bias[16 * L + i], 0.f);
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        uint32_t h[8], l[8];
+                        split8(d + 8 * half, h, l);
+                        store_half(tmem, half, h, l);
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < kOut; ++c) o[c] = sigmoidf_(d[c] + sm.bias[32 + c]);
+                }
+            }
             if (!ok) break;
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            float d[16];
-            load_row(tmem, d);
-            if (L < 2) {
+            if (valid) {
+                const float A = f[3];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) x[i] = fmaxf(d[i] + sm.bias[16 * L + i], 0.f);
-            } else {
-#pragma unroll
-                for (int c = 0; c < kOut; ++c) o[c] = sigmoidf_(d[c] + sm.bias[32 + c]);
+                for (int c = 0; c < kOut; ++c)
+                    __stcs(V.rgb + ((size_t)s * kOut + c) * V.HW + p, fmaf(A, f[c], (1.0f - A) * o[c]));
             }
         }
-        if (!ok) break;
-        if (valid) {
-            const float A = f[3];
-#pragma unroll
-            for (int c = 0; c < kOut; ++c)
-                __stcs(V.rgb + ((size_t)s * kOut + c) * V.HW + p, fmaf(A, f[c], (1.0f - A) * o[c]));
-        }
-        before_sync();
-        __syncthreads();   // the operand rows and the accumulator are reused by the next tile
     }
     if (!ok) {
         // a layer's MMAs did not complete in time: record it, give them one
@@ -672,6 +728,49 @@ cudaError_t launch_shade_fwd(const ShadeView* views, int n, int S, const float* 
     return cudaGetLastError();
 }
 
+// Launch shape of k_shade_fwd_tc: dynamic shared memory and CTAs per SM.
+// Each CTA holds kTmemCols of the SM's 512 tensor-memory columns, so at most
+// kMaxCtasPerSm may be resident at once (a further CTA's allocation would
+// wait for a CTA to finish); the shared-memory request is padded so that no
+// more fit, and the residency is the least of what shared memory, registers
+// and threads allow.  Computed here from the kernel's attributes: the
+// runtime's occupancy query answers 1 for this kernel although more CTAs fit.
+bool tc_launch_shape(size_t* dyn_smem, int* per_sm) {
+    static size_t c_smem = 0;
+    static int c_per_sm = 0;
+    if (c_per_sm > 0) {
+        *dyn_smem = c_smem;
+        *per_sm = c_per_sm;
+        return true;
+    }
+    cudaFuncAttributes fa;
+    int dev = 0, smem_sm = 0, reserved = 0, regs_sm = 0, thr_sm = 0;
+    if (cudaFuncGetAttributes(&fa, k_shade_fwd_tc) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const size_t fixed = fa.sharedSizeBytes + (size_t)reserved;
+    size_t smem = sizeof(tc::Smem) + 1024;   // + room to align the weight tiles to 1 KB
+    const size_t at_least = (size_t)smem_sm / (tc::kMaxCtasPerSm + 1) + 1;   // kMaxCtasPerSm + 1 do not fit
+    if (smem + fixed < at_least) smem = at_least - fixed;
+    const int by_smem = (int)((size_t)smem_sm / (smem + fixed));
+    const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;   // allocated per warp in units of 256
+    const int by_regs = regs_warp > 0 ? regs_sm / (regs_warp * (tc::kRows / 32)) : tc::kMaxCtasPerSm;
+    const int by_thr = thr_sm / tc::kRows;
+    int n = by_smem < by_regs ? by_smem : by_regs;
+    n = n < by_thr ? n : by_thr;
+    if (n < 1 || n > tc::kMaxCtasPerSm) return false;
+    c_smem = smem;
+    c_per_sm = n;
+    *dyn_smem = smem;
+    *per_sm = n;
+    return true;
+}
+
 cudaError_t launch_shade_fwd_tc(const ShadeView* views, int n, int S, const float* params, int* status,
                                 cudaStream_t st) {
     ShadeTable t;
@@ -683,17 +782,15 @@ cudaError_t launch_shade_fwd_tc(const ShadeView* views, int n, int S, const floa
         t.v[i] = views[i];
         t.v[i].HW = views[i].W * views[i].H;
         t.v[i].blk0 = blk;
-        blk += (int)(((long long)S * t.v[i].HW + tc::kRows - 1) / tc::kRows);
+        blk += (t.v[i].HW + tc::kRows - 1) / tc::kRows;
     }
     t.n_blocks = blk;
     if (t.n_blocks == 0) return cudaSuccess;
-    const size_t smem = sizeof(tc::Smem) + 1024;   // + room to align the operand tiles to 1 KB
+    size_t smem = 0;
+    int per_sm = 0;
+    if (!tc_launch_shape(&smem, &per_sm)) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(k_shade_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_shade_fwd_tc, tc::kRows, smem)) != cudaSuccess)
-        return e;
-    per_sm = per_sm < 1 ? 1 : (per_sm > 16 ? 16 : per_sm);   // 16 x 32 TMEM columns = all 512
     k_shade_fwd_tc<<<persistent_grid(t.n_blocks, per_sm), tc::kRows, smem, st>>>(t, params, status);
     note_launches(1);
     return cudaGetLastError();

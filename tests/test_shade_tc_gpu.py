@@ -54,8 +54,8 @@ def _shade(ctx, path, cams, params, feats):
 
 @pytest.mark.parametrize("S", [1, 3, 4])
 def test_tensor_core_forward_matches_the_oracle_and_the_cuda_cores(ctx, S):
-    """Three views (96x64, 37x23, 300x17): tiles of 128 pixel-samples with
-    ragged ends in every view."""
+    """Three views (96x64, 37x23, 300x17): tiles of 128 pixels, each taking
+    all S samples, with ragged ends in every view."""
     from paper_2603_27151_gb300 import native as N
     eyes = I.sphere_eyes(3, 3.0, np.random.default_rng(4))
     cams = [I.look_at(eyes[0], 96, 64), I.look_at(eyes[1], 37, 23), I.look_at(eyes[2], 300, 17)]
@@ -101,7 +101,7 @@ def test_shade_path_setting(ctx):
 
 def test_tensor_core_forward_full_size_batch(ctx):
     """The 1080p batch's colour features (4 x 1920x1080 + 4 x 960x540, S = 4,
-    41.5 M pixel-samples, 324,000 tiles) in one launch: windows at corners
+    41.5 M pixel-samples, 81,000 tiles of 128 pixels) in one launch: windows at corners
     and the centre against the oracle on cropped cameras, everything against
     the CUDA-core kernel."""
     import torch

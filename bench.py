@@ -360,6 +360,11 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # columns of W1 ((48 + 256 + 112) multiply-adds) + the weight gradients (560).
 SHADE_FWD_FLOPS = 2 * 560
 SHADE_BWD_FLOPS = 2 * 560 + 2 * (48 + 256 + 112) + 2 * 560
+# Algorithmic bytes per pixel-sample of the shading forward: 7 feature floats
+# read, 3 colour floats written.
+SHADE_FWD_BYTES = 4 * (7 + 3)
+# Nominal dense TF32 tensor rate of a GB300 (half the bf16 rate).
+TF32_NOMINAL_TFLOPS = 1125.0
 
 
 def _shade_leg(wl, steps: int):
@@ -385,8 +390,8 @@ def _shade_leg(wl, steps: int):
         return f
     bwd = lambda: wl.ctx.shade_backward(cams, params, wl.col, grgb, gfeat, gp, overwrite=True)
     out = {}
-    for name, fn, flops in (("forward", fwd_path(N.DS_SHADE_CUDA_CORES), SHADE_FWD_FLOPS),
-                            ("forward_tensor_cores", fwd_path(N.DS_SHADE_TENSOR_CORES), SHADE_FWD_FLOPS),
+    for name, fn, flops in (("forward", fwd_path(N.DS_SHADE_TENSOR_CORES), SHADE_FWD_FLOPS),
+                            ("forward_cuda_cores", fwd_path(N.DS_SHADE_CUDA_CORES), SHADE_FWD_FLOPS),
                             ("backward", bwd, SHADE_BWD_FLOPS)):
         for _ in range(3):
             fn()
@@ -406,15 +411,23 @@ def _shade_leg(wl, steps: int):
                                   "algorithmic_flops_per_pixel_sample": flops}}
     wl.ctx.set_shade_path(path0)
     wl.ctx.status()
-    # the tensor-core forward's algorithmic work on the tensor pipe: 3
-    # layers x 3 TF32 products of 128 x 16 x 16 per tile of 128
-    tc = out["forward_tensor_cores"]
-    tc["roofline_tensor"] = {"what": "3 x TF32-split MMAs (3 products per layer) on the kind::tf32 path",
-                             "mma_flops_per_pixel_sample": 3 * 3 * 2 * 16 * 16}
+    # The tensor-core forward: at 28 flops per byte the MLP sits below the
+    # TF32 ridge point (about 160 flops per byte), so its roofline is the
+    # HBM one: 40 bytes per pixel-sample against the measured copy rate.
+    hbm_peak, hbm_kind = _peaks()
+    tc = out["forward"]
+    gbs = SHADE_FWD_BYTES * wl.pixel_samples / (tc["ms"] / 1e3) / 1e9
+    tc["roofline_flops"] = tc["roofline"]
+    tc["roofline_flops"].update(peak=TF32_NOMINAL_TFLOPS, frac=tc["roofline"]["achieved"] / TF32_NOMINAL_TFLOPS,
+                                bound="tensor", peak_kind="nominal dense TF32 rate")
+    tc["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                      "peak_kind": hbm_kind, "algorithmic_bytes_per_pixel_sample": SHADE_FWD_BYTES}
+    tc["mma"] = {"what": "per layer and tile of 128: 6 TF32 MMAs of 128 x 16 x 8 (3 products x 2 K-chunks) + 1 "
+                         "for the bias; layer inputs in tensor memory", "mma_per_pixel_sample": 3 * 7 / 128}
     out["pixel_samples"] = wl.pixel_samples
-    out["what"] = ("16-16-16-3 MLP on 7 features + SH2 of the view direction, RGBA blend; forward on the CUDA "
-                   "cores (FP32 FMA) and on the tensor cores (tcgen05 kind::tf32, hi/lo split), backward on "
-                   "the CUDA cores")
+    out["what"] = ("16-16-16-3 MLP on 7 features + SH2 of the view direction, RGBA blend; forward on the tensor "
+                   "cores (tcgen05 kind::tf32, hi/lo split; the default path) and on the CUDA cores (FP32 FMA), "
+                   "backward on the CUDA cores")
     return out
 
 

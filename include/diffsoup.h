@@ -416,7 +416,8 @@ DS_API ds_status ds_shade_backward(ds_ctx* ctx, int32_t n_views, int32_t S, cons
  *    accumulation in tensor memory; about FP32 accuracy.  A launch whose wait
  *    for its MMAs runs out (about a second) stops, and the next
  *    ds_ctx_status returns DS_ERR_TIMEOUT.
- * Host calls; DS_ERR_INVALID_ARG for another value. */
+ * A new context uses DS_SHADE_TENSOR_CORES (the faster of the two on
+ * sm_103a).  Host calls; DS_ERR_INVALID_ARG for another value. */
 #define DS_SHADE_CUDA_CORES 0
 #define DS_SHADE_TENSOR_CORES 1
 DS_API ds_status ds_set_shade_path(ds_ctx* ctx, int32_t path);

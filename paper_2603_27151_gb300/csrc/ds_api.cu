@@ -118,7 +118,7 @@ struct ds_ctx {
     uint32_t* h_word = nullptr;   // pinned host words
     Plan plan;
     ds_tuning tune{16, -1, 0, 256};   // tile shape, depth bits, grid, staging chunk
-    int32_t shade_path = DS_SHADE_CUDA_CORES;   // kernel of ds_shade_forward
+    int32_t shade_path = DS_SHADE_TENSOR_CORES;   // kernel of ds_shade_forward
     cudaStream_t last_stream = nullptr;
     ds::ViewTable* vt = nullptr;   // host staging of the kernel parameter tables (~9 KB each): [0] the
                                    // call's views, [1] the same views in the edge kernel's tiles

@@ -429,10 +429,12 @@ __global__ void __launch_bounds__(kThreads) k_shade_finish(const float* __restri
 namespace tc {
 
 constexpr int kRows = 128;   // pixel-samples per tile = TMEM lanes = M
-// Tensor-memory columns of a CTA: the accumulator D in 0..15, A hi in 16..31,
-// A lo in 32..47 (one 32-bit TF32 value per column and lane).
+// Tensor-memory columns of a CTA (one 32-bit value per column and lane): the
+// accumulator D in 0..15, A hi in 16..31, A lo in 32..47, and in 48..55 the
+// constant K-chunk (1, 1, 0, ..., 0) that adds the bias rows (b hi, b lo) of
+// the bias tile.
 constexpr uint32_t kTmemCols = 64;
-constexpr uint32_t kColD = 0, kColAh = 16, kColAl = 32;
+constexpr uint32_t kColD = 0, kColAh = 16, kColAl = 32, kColOne = 48;
 constexpr int kMaxCtasPerSm = 512 / (int)kTmemCols;   // the SM's 512 columns, none left waiting
 // Instruction descriptor of kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32
 // (bits 7-9 and 10-12 = 2), both K-major (bits 15, 16 = 0), N >> 3 in bits
@@ -459,7 +461,7 @@ __device__ __forceinline__ uint32_t saddr(const void* p) { return (uint32_t)__cv
 
 struct Smem {
     uint8_t w[6][1024];   // W1 hi, W1 lo, W2 hi, W2 lo, W3 hi, W3 lo (N 16 x K 16)
-    float bias[36];       // b1 [16], b2 [16], b3 [3]
+    uint8_t b[3][1024];   // bias tiles of the three layers: K = 0 b hi, K = 1 b lo, else 0
     unsigned long long bar;
     uint32_t tmem;
 };
@@ -501,9 +503,9 @@ __device__ __forceinline__ void mma(uint32_t d, uint32_t a_tmem, uint64_t b, uin
         "r"(a_tmem), "l"(b), "r"(kIdesc), "r"(accumulate));
 }
 
-// Layer L: D = A_lo W_hi + A_hi W_lo + A_hi W_hi (small terms first), then
-// the commit that arrives on the barrier when the MMAs are complete.  One
-// thread.
+// Layer L: D = A_lo W_hi + A_hi W_lo + A_hi W_hi (small terms first) + the
+// bias, then the commit that arrives on the barrier when the MMAs are
+// complete.  One thread.
 __device__ __forceinline__ void issue_layer(Smem& sm, int L, uint32_t tmem) {
     const uint32_t b0 = saddr(sm.w[2 * L]), b1 = saddr(sm.w[2 * L + 1]);
     const uint32_t d = tmem + kColD;
@@ -515,6 +517,7 @@ __device__ __forceinline__ void issue_layer(Smem& sm, int L, uint32_t tmem) {
     }
 #pragma unroll
     for (int s = 0; s < 2; ++s) mma(d, tmem + kColAh + 8 * s, smem_desc(b0 + 256 * s), 1);
+    mma(d, tmem + kColOne, smem_desc(saddr(sm.b[L])), 1);
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(saddr(&sm.bar))
                  : "memory");
 }
@@ -555,6 +558,10 @@ __device__ __forceinline__ void before_sync() {
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
 }
 
+// Logistic function from the hardware exponential and the correctly rounded
+// reciprocal (a few 1e-7 from the exact value on [0, 1]).
+__device__ __forceinline__ float sigmoid(float z) { return __frcp_rn(1.0f + __expf(-z)); }
+
 }  // namespace tc
 
 // Per round a CTA takes one tile: 128 consecutive pixels of one view (tiles
@@ -582,8 +589,14 @@ __global__ void __launch_bounds__(tc::kRows, tc::kMaxCtasPerSm) k_shade_fwd_tc(c
         *reinterpret_cast<uint32_t*>(sm.w[2 * L] + op_off(n, k)) = h;
         *reinterpret_cast<uint32_t*>(sm.w[2 * L + 1] + op_off(n, k)) = l;
     }
-    if (tid < 36) sm.bias[tid] = tid < 16 ? __ldg(params + oB1 + tid) : (tid < 32 ? __ldg(params + oB2 + tid - 16)
-                                                                                  : (tid < 35 ? __ldg(params + oB3 + tid - 32) : 0.f));
+    for (int q = tid; q < 3 * 256; q += kRows) {
+        const int L = q >> 8, n = (q >> 4) & 15, k = q & 15;
+        const int o = L == 0 ? oB1 : (L == 1 ? oB2 : oB3);
+        const float b = (k < 2 && (L < 2 || n < kOut)) ? __ldg(params + o + n) : 0.f;
+        uint32_t h, l;
+        split(b, h, l);
+        *reinterpret_cast<uint32_t*>(sm.b[L] + op_off(n, k)) = k == 0 ? h : (k == 1 ? l : 0u);
+    }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(saddr(&sm.bar)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -600,6 +613,11 @@ __global__ void __launch_bounds__(tc::kRows, tc::kMaxCtasPerSm) k_shade_fwd_tc(c
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = sm.tmem;
+    {
+        const uint32_t one = __float_as_uint(1.0f);
+        const uint32_t r[8] = {one, one, 0u, 0u, 0u, 0u, 0u, 0u};
+        st8(lane_addr(tmem, kColOne), r);
+    }
     uint32_t phase = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < t.n_blocks && ok; tile += gridDim.x) {
@@ -651,7 +669,7 @@ __global__ void __launch_bounds__(tc::kRows, tc::kMaxCtasPerSm) k_shade_fwd_tc(c
                 load_row(tmem, d);
                 if (L < 2) {
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) d[i] = fmaxf(d[i] + sm.bias[16 * L + i], 0.f);
+                    for (int i = 0; i < 16; ++i) d[i] = fmaxf(d[i], 0.f);
 #pragma unroll
                     for (int half = 0; half < 2; ++half) {
                         uint32_t h[8], l[8];
@@ -660,7 +678,7 @@ __global__ void __launch_bounds__(tc::kRows, tc::kMaxCtasPerSm) k_shade_fwd_tc(c
                     }
                 } else {
 #pragma unroll
-                    for (int c = 0; c < kOut; ++c) o[c] = sigmoidf_(d[c] + sm.bias[32 + c]);
+                    for (int c = 0; c < kOut; ++c) o[c] = sigmoid(d[c]);
                 }
             }
             if (!ok) break;

@@ -315,7 +315,7 @@ class Context:
 
     def set_shade_path(self, path: int):
         """Kernel of shade_forward: DS_SHADE_CUDA_CORES (FP32 FMA) or
-        DS_SHADE_TENSOR_CORES (tcgen05, TF32 split into hi + lo)."""
+        DS_SHADE_TENSOR_CORES (tcgen05, TF32 split into hi + lo; the default)."""
         _check(load().ds_set_shade_path(self.h, int(path)))
 
     def get_shade_path(self) -> int:

@@ -42,12 +42,13 @@ def _to(x):
 def _shade(ctx, path, cams, params, feats):
     import torch
     from paper_2603_27151_gb300 import native as N
+    path0 = ctx.get_shade_path()
     ctx.set_shade_path(path)
     f = [_to(x) for x in feats]
     rgb = [torch.full((x.shape[0], 3, x.shape[2], x.shape[3]), -1.0, device="cuda") for x in feats]
     ctx.shade_forward(cams, _to(params.astype(np.float32)), f, rgb)
     torch.cuda.synchronize()
-    ctx.set_shade_path(N.DS_SHADE_CUDA_CORES)
+    ctx.set_shade_path(path0)
     ctx.status()                                   # no timed-out MMA wait
     return [r.cpu().numpy() for r in rgb]
 
@@ -67,6 +68,7 @@ def test_tensor_core_forward_matches_the_oracle_and_the_cuda_cores(ctx, S):
     for v, c in enumerate(cams):
         ref = SH.shade(feats[v], c, params)
         assert np.abs(tc[v] - ref).max() <= 1e-5, (v, float(np.abs(tc[v] - ref).max()))
+        assert np.abs(cc[v] - ref).max() <= 1e-5, (v, float(np.abs(cc[v] - ref).max()))
         assert np.abs(tc[v] - cc[v]).max() <= 1e-5, v
 
 
@@ -89,14 +91,23 @@ def test_tensor_core_forward_special_cases(ctx):
 
 
 def test_shade_path_setting(ctx):
+    """A new context shades on the tensor cores; the setting persists and
+    rejects unknown paths."""
     from paper_2603_27151_gb300 import native as N
+    fresh = N.Context(0)
+    try:
+        assert fresh.get_shade_path() == N.DS_SHADE_TENSOR_CORES
+    finally:
+        fresh.close()
+    path0 = ctx.get_shade_path()
+    ctx.set_shade_path(N.DS_SHADE_CUDA_CORES)
+    assert ctx.get_shade_path() == N.DS_SHADE_CUDA_CORES
+    with pytest.raises(N.DsError):
+        ctx.set_shade_path(7)
     assert ctx.get_shade_path() == N.DS_SHADE_CUDA_CORES
     ctx.set_shade_path(N.DS_SHADE_TENSOR_CORES)
     assert ctx.get_shade_path() == N.DS_SHADE_TENSOR_CORES
-    with pytest.raises(N.DsError):
-        ctx.set_shade_path(7)
-    assert ctx.get_shade_path() == N.DS_SHADE_TENSOR_CORES
-    ctx.set_shade_path(N.DS_SHADE_CUDA_CORES)
+    ctx.set_shade_path(path0)
 
 
 def test_tensor_core_forward_full_size_batch(ctx):
@@ -120,7 +131,7 @@ def test_tensor_core_forward_full_size_batch(ctx):
         ctx.shade_forward(sc.cams, p, col, rgb)
         torch.cuda.synchronize()
         out[path] = rgb
-    ctx.set_shade_path(N.DS_SHADE_CUDA_CORES)
+    ctx.set_shade_path(N.DS_SHADE_TENSOR_CORES)
     ctx.status()
     for v, c in enumerate(sc.cams):
         d = (out[N.DS_SHADE_TENSOR_CORES][v] - out[N.DS_SHADE_CUDA_CORES][v]).abs().max().item()

@@ -659,7 +659,8 @@ def _config_leg(name: str, device: str, steps: int, tune: bool = True):
 def widened_cases():
     """One launch of each kernel of the widened rows on a case larger than L2
     (for profiler captures; prints one check line, not a bench line): deferred
-    shading forward and backward of two 1920x1080 views at S = 4; the L1 +
+    shading forward (tensor cores, then CUDA cores) and backward of two
+    1920x1080 views at S = 4; the L1 +
     SSIM loss of the same images (7 channels); the level composition
     (standalone and inside the activation of a level soup, 20,000 triangles,
     levels 2..5) and its adjoint; coverage counts of the 2-view G-buffers; one
@@ -681,7 +682,10 @@ def widened_cases():
     gf = [torch.empty_like(f) for f in feats]
     params = init_params(1)
     gp = torch.empty_like(params)
-    ctx.shade_forward(cams, params, feats, rgb)
+    ctx.shade_forward(cams, params, feats, rgb)                 # tensor cores (the default)
+    ctx.set_shade_path(N.DS_SHADE_CUDA_CORES)
+    ctx.shade_forward(cams, params, feats, rgb)                 # FP32 FMA
+    ctx.set_shade_path(N.DS_SHADE_TENSOR_CORES)
     ctx.shade_backward(cams, params, feats, grgb, gf, gp, overwrite=True)
     tg = [torch.rand((7, c.height, c.width), generator=gen, device=dev) for c in cams]
     sw = [torch.empty((S, c.height, c.width), device=dev) for c in cams]
@@ -706,6 +710,7 @@ def widened_cases():
     m, v = torch.zeros_like(x), torch.zeros_like(x)
     N.adam_step(x, gx, m, v, 0.05, 1)
     torch.cuda.synchronize()
+    ctx.status()
     print("widened cases ok: loss %.6g, |grad params| %.6g, |grad levels| %.6g, coverage %d"
           % (float(loss), float(gp.abs().sum()), float(gt.abs().sum()), int(counts.sum())))
 

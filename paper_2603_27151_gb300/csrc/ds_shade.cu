@@ -202,6 +202,13 @@ struct BwdSmem {
 };
 static_assert(sizeof(float) * kGroups * kParams <= sizeof(float) * (2 * kThreads * kRow + 16), "reduction buffer");
 
+// The sample-independent part of the first layer (16 values per pixel) kept
+// in the 4 pad columns of the thread's X, H1, H2 and D1 rows (the reducers
+// read columns 0..15 only).
+__device__ __forceinline__ float* upad(BwdSmem& sm, int tid, int q) {
+    return q == 0 ? &sm.X[tid][16] : q == 1 ? &sm.H1[tid][16] : q == 2 ? &sm.H2[tid][16] : &sm.D1[tid][16];
+}
+
 __device__ __forceinline__ void store4(float* dst, const float* v) {
     *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
 }
@@ -238,14 +245,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_shade_bwd(const __grid_constant
         const ShadeView& V = t.v[find_view(t, b)];
         const int p = (b - V.blk0) * kThreads + tid;
         const bool valid = p < V.HW;
-        float u[kHid];
         {
             // the SH columns 8..15 of the input row are the same for every
             // sample (column 7, the constant band, is stored with the features)
             float sh[kSH + 3] = {};
+            float u[kHid];
             if (valid) {
                 sh_of_pixel(V, p % V.W, p / V.W, sh);
                 first_layer_sh(sp, sh, u);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) store4(upad(sm, tid, q), u + 4 * q);
             }
 #pragma unroll
             for (int q = 0; q < 2; ++q) store4(&sm.X[tid][8 + 4 * q], sh + 1 + 4 * q);
@@ -253,64 +262,86 @@ __global__ void __launch_bounds__(kThreads, 2) k_shade_bwd(const __grid_constant
         for (int s = 0; s < t.S; ++s) {
             // Rows are staged as soon as they are known; the ReLU masks of
             // the hidden layers stay in registers as bits.
-            float d1[kHid], d2[kHid], d3[4];
+            float d1[kHid], d3[4];
             if (valid) {
-                float f[1][kFeat], h1[1][kHid], h2[1][kHid], o[1][kOut];
+                float f[kFeat];
 #pragma unroll
-                for (int c = 0; c < kFeat; ++c) f[0][c] = __ldg(V.feat + ((size_t)s * kFeat + c) * V.HW + p);
+                for (int c = 0; c < kFeat; ++c) f[c] = __ldg(V.feat + ((size_t)s * kFeat + c) * V.HW + p);
                 {
-                    const float x4[4] = {f[0][4], f[0][5], f[0][6], kC0};
-                    store4(&sm.X[tid][0], f[0]);
+                    const float x4[4] = {f[4], f[5], f[6], kC0};
+                    store4(&sm.X[tid][0], f);
                     store4(&sm.X[tid][4], x4);
                 }
-                mlp<1>(sp, u, f, h1, h2, o);
+                // Forward.  h1 as in the forward kernel; then each h2 unit in
+                // turn is staged and folded into the output accumulators, so
+                // that h2 never sits in registers as a whole (the same FMA
+                // order per output as the forward kernel).
                 unsigned m1 = 0, m2 = 0;
+                float h1[kHid];
 #pragma unroll
-                for (int k = 0; k < kHid; ++k) {
-                    m1 |= (h1[0][k] > 0.f ? 1u : 0u) << k;
-                    m2 |= (h2[0][k] > 0.f ? 1u : 0u) << k;
+                for (int i = 0; i < kHid; ++i) {
+                    const float4 w0 = *reinterpret_cast<const float4*>(sp + oW1 + i * kIn);
+                    const float4 w1 = *reinterpret_cast<const float4*>(sp + oW1 + i * kIn + 4);
+                    float a = upad(sm, tid, i >> 2)[i & 3];
+                    a = fmaf(w0.x, f[0], a); a = fmaf(w0.y, f[1], a);
+                    a = fmaf(w0.z, f[2], a); a = fmaf(w0.w, f[3], a);
+                    a = fmaf(w1.x, f[4], a); a = fmaf(w1.y, f[5], a);
+                    a = fmaf(w1.z, f[6], a);
+                    h1[i] = fmaxf(a, 0.f);
+                    m1 |= (h1[i] > 0.f ? 1u : 0u) << i;
                 }
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    store4(&sm.H1[tid][4 * q], h1[0] + 4 * q);
-                    store4(&sm.H2[tid][4 * q], h2[0] + 4 * q);
+                for (int q = 0; q < 4; ++q) store4(&sm.H1[tid][4 * q], h1 + 4 * q);
+                float o[kOut];
+#pragma unroll
+                for (int c = 0; c < kOut; ++c) o[c] = sp[oB3 + c];
+#pragma unroll
+                for (int i = 0; i < kHid; ++i) {
+                    float a = sp[oB2 + i];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 w = *reinterpret_cast<const float4*>(sp + oW2 + i * kHid + 4 * q);
+                        a = fmaf(w.x, h1[4 * q + 0], a); a = fmaf(w.y, h1[4 * q + 1], a);
+                        a = fmaf(w.z, h1[4 * q + 2], a); a = fmaf(w.w, h1[4 * q + 3], a);
+                    }
+                    const float h2 = fmaxf(a, 0.f);
+                    m2 |= (h2 > 0.f ? 1u : 0u) << i;
+                    sm.H2[tid][i] = h2;
+#pragma unroll
+                    for (int c = 0; c < kOut; ++c) o[c] = fmaf(sp[oW3 + c * kHid + i], h2, o[c]);
                 }
+#pragma unroll
+                for (int c = 0; c < kOut; ++c) o[c] = sigmoidf_(o[c]);
                 float g[kOut];
 #pragma unroll
                 for (int c = 0; c < kOut; ++c) g[c] = __ldcs(V.grad_rgb + ((size_t)s * kOut + c) * V.HW + p);
-                const float A = f[0][3];
+                const float A = f[3];
                 float gA = 0.f;
 #pragma unroll
                 for (int c = 0; c < kOut; ++c) {
-                    gA = fmaf(g[c], f[0][c] - o[0][c], gA);
+                    gA = fmaf(g[c], f[c] - o[c], gA);
                     const float go = (1.0f - A) * g[c];
-                    d3[c] = go * o[0][c] * (1.0f - o[0][c]);
+                    d3[c] = go * o[c] * (1.0f - o[c]);
                 }
                 d3[3] = 0.f;
-                // d2 = (W3^T d3) * [z2 > 0]
-#pragma unroll
-                for (int j = 0; j < kHid; ++j) d2[j] = 0.f;
-#pragma unroll
-                for (int c = 0; c < kOut; ++c)
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float4 w = *reinterpret_cast<const float4*>(sp + oW3 + c * kHid + 4 * q);
-                        d2[4 * q + 0] = fmaf(w.x, d3[c], d2[4 * q + 0]); d2[4 * q + 1] = fmaf(w.y, d3[c], d2[4 * q + 1]);
-                        d2[4 * q + 2] = fmaf(w.z, d3[c], d2[4 * q + 2]); d2[4 * q + 3] = fmaf(w.w, d3[c], d2[4 * q + 3]);
-                    }
-#pragma unroll
-                for (int j = 0; j < kHid; ++j) d2[j] = (m2 >> j) & 1u ? d2[j] : 0.f;
-                // d1 = (W2^T d2) * [z1 > 0]
+                // d2_j = (W3^T d3)_j [z2_j > 0], staged as soon as known and
+                // folded into d1 = W2^T d2 (then masked by [z1 > 0])
 #pragma unroll
                 for (int k = 0; k < kHid; ++k) d1[k] = 0.f;
 #pragma unroll
-                for (int j = 0; j < kHid; ++j)
+                for (int j = 0; j < kHid; ++j) {
+                    float dj = 0.f;
+#pragma unroll
+                    for (int c = 0; c < kOut; ++c) dj = fmaf(sp[oW3 + c * kHid + j], d3[c], dj);
+                    dj = (m2 >> j) & 1u ? dj : 0.f;
+                    sm.D2[tid][j] = dj;
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const float4 w = *reinterpret_cast<const float4*>(sp + oW2 + j * kHid + 4 * q);
-                        d1[4 * q + 0] = fmaf(w.x, d2[j], d1[4 * q + 0]); d1[4 * q + 1] = fmaf(w.y, d2[j], d1[4 * q + 1]);
-                        d1[4 * q + 2] = fmaf(w.z, d2[j], d1[4 * q + 2]); d1[4 * q + 3] = fmaf(w.w, d2[j], d1[4 * q + 3]);
+                        d1[4 * q + 0] = fmaf(w.x, dj, d1[4 * q + 0]); d1[4 * q + 1] = fmaf(w.y, dj, d1[4 * q + 1]);
+                        d1[4 * q + 2] = fmaf(w.z, dj, d1[4 * q + 2]); d1[4 * q + 3] = fmaf(w.w, dj, d1[4 * q + 3]);
                     }
+                }
 #pragma unroll
                 for (int k = 0; k < kHid; ++k) d1[k] = (m1 >> k) & 1u ? d1[k] : 0.f;
                 // feature gradient: blend terms + (W1^T d1)[0:7]
@@ -330,10 +361,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_shade_bwd(const __grid_constant
 #pragma unroll
                     for (int c = 0; c < kOut; ++c) gf[c] = fmaf(A, g[c], gf[c]);
                     gf[3] += gA;
+                    float* dst = V.grad_feat + (size_t)s * kFeat * V.HW + p;
+                    if (t.overwrite) {
 #pragma unroll
-                    for (int c = 0; c < kFeat; ++c) {
-                        float* dst = V.grad_feat + ((size_t)s * kFeat + c) * V.HW + p;
-                        *dst = t.overwrite ? gf[c] : *dst + gf[c];
+                        for (int c = 0; c < kFeat; ++c) dst[(size_t)c * V.HW] = gf[c];
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < kFeat; ++c) dst[(size_t)c * V.HW] += gf[c];
                     }
                 }
             } else {
@@ -346,15 +380,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_shade_bwd(const __grid_constant
                     store4(&sm.H2[tid][4 * q], z4);
                 }
 #pragma unroll
-                for (int k = 0; k < kHid; ++k) d1[k] = d2[k] = 0.f;
+                for (int k = 0; k < kHid; ++k) d1[k] = 0.f;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) d3[c] = 0.f;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) store4(&sm.D2[tid][4 * q], z4);
             }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                store4(&sm.D1[tid][4 * q], d1 + 4 * q);
-                store4(&sm.D2[tid][4 * q], d2 + 4 * q);
-            }
+            for (int q = 0; q < 4; ++q) store4(&sm.D1[tid][4 * q], d1 + 4 * q);
             store4(&sm.D3[tid][0], d3);
             __syncthreads();
             if (reducer) {

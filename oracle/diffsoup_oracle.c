@@ -24,9 +24,12 @@
  *                             order independence, Monte Carlo selection frequencies)
  *   or_backward (tex, score)  pinned (expectation == finite differences of Eq. 7)
  *   or_backward (interior) .. pinned (finite differences at fixed visibility)
- *   or_backward (edge) ...... partly pinned: sign/magnitude against a supersampled
- *                             finite difference; the absolute weighting is
- *                             "parity unpinned" (the paper prints no formula).
+ *   or_backward (edge) ...... pinned against derivatives, not against the paper
+ *                             (which prints no formula): silhouette term = finite
+ *                             differences of the area-coverage loss over sub-pixel
+ *                             placements (about 1%); implicit term unbiased for
+ *                             the closed-form expected loss of a moving opacity
+ *                             field.
  *   or_expected ............. pinned (finite differences; Monte Carlo of or_forward)
  *   or_compose .............. pinned (affine reproduction, closed-form hat function,
  *                             level-0 barycentrics, identity, constants, the FP64 sum

@@ -560,8 +560,10 @@ def test_silhouette_gradient_matches_antialiased_finite_differences(O, verts):
             fd_sum[q] += (aa_loss(vp) - aa_loss(vm)) / 2e-5
     cos = g_sum @ fd_sum / (np.linalg.norm(g_sum) * np.linalg.norm(fd_sum))
     ratio = np.linalg.norm(g_sum) / np.linalg.norm(fd_sum)
-    assert cos > 0.98, (cos, g_sum, fd_sum)
-    assert abs(ratio - 1.0) < 0.06, (ratio, g_sum, fd_sum)
+    # measured: cos 0.99999 and ratios 1.004 / 1.002 for the two cases, so
+    # the absolute weight of the silhouette term is pinned to about 1%
+    assert cos > 0.9995, (cos, g_sum, fd_sum)
+    assert abs(ratio - 1.0) < 0.015, (ratio, g_sum, fd_sum)
     # weighting each pair axis by the squared normal component keeps every
     # crossing's contribution bounded: the estimate barely moves with the
     # sub-pixel placement (weighting the other axis is also unbiased on
@@ -645,5 +647,10 @@ def test_implicit_boundary_gradient_is_unbiased_for_a_moving_opacity_field(O):
     g = np.mean(acc, 0)
     cos = g @ fd / (np.linalg.norm(g) * np.linalg.norm(fd))
     ratio = np.linalg.norm(g) / np.linalg.norm(fd)
-    assert cos > 0.98, (cos, g, fd)
-    assert abs(ratio - (W - 1) / W) < 0.06, (ratio, g, fd)
+    assert cos > 0.995, (cos, g, fd)
+    assert abs(ratio - (W - 1) / W) < 0.025, (ratio, g, fd)
+    # unbiasedness component by component: each mean within 4 standard
+    # errors of the expected derivative (measured: |z| <= 1.7)
+    se = np.std(acc, 0, ddof=1) / math.sqrt(len(acc))
+    z = (g - fd * (W - 1) / W) / se
+    assert np.all(np.abs(z) < 4.0), z

@@ -14,6 +14,12 @@
 // with a 10-pixel halo, the five moments (separable blur) and ssim, G1..G3
 // are formed on the tile plus a 5-pixel halo, and G1..G3 are blurred back
 // onto the tile -- one pass, no intermediate maps in HBM.
+//
+// The blurs are issue-bound, so their operands are interleaved in shared
+// memory as pairs that take the same weight -- (x, y), (x^2, y^2), (G1, G2)
+// -- and each tap of a pair is one packed FP32 multiply-add (fma.rn.f32x2,
+// the weight duplicated in both halves); x y and G3 stay scalar.  Every
+// output keeps the order and rounding of its scalar FMA chain.
 #include <cmath>
 #include <new>
 
@@ -41,18 +47,29 @@ struct SsimTable {
     int n, S, Co, n_tiles;
     float lambda, scale;
     float w[kTaps];
+    float2 wd[kTaps];   // (w, w)
     SsimView v[DS_MAX_VIEWS];
 };
 
 struct SsimSmem {
-    float X[kIY][kIX], Y[kIY][kIX];
+    float2 XY[kIY][kIX];            // (x, y)
     union {
-        float HM[5][kIY][kMX];   // horizontal pass of x, y, x^2, y^2, xy
-        float HG[3][kMY][kTX];   // horizontal pass of G1..G3
+        struct {
+            float2 a[kIY][kMX];     // horizontal pass of (x, y)
+            float2 b[kIY][kMX];     // of (x^2, y^2)
+            float c[kIY][kMX];      // of x y
+        } hm;
+        struct {
+            float2 a[kMY][kTX];     // horizontal pass of (G1, G2)
+            float b[kMY][kTX];      // of G3
+        } hg;
     };
-    float G[3][kMY][kMX];
-    float St[kTY][kTX];          // ssim of the tile's pixels (this channel)
+    float2 Ga[kMY][kMX];            // (G1, G2)
+    float Gb[kMY][kMX];             // G3
+    float St[kTY][kTX];             // ssim of the tile's pixels (this channel)
 };
+
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
 __global__ void __launch_bounds__(256) k_loss_l1_ssim(const __grid_constant__ SsimTable t, float* __restrict__ loss) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -92,8 +109,7 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(const __grid_constant__ Ss
             const int k = tid + 256 * i;
             if (k < kIX * kIY) {
                 const int r = k / kIX, q = k - r * kIX;
-                sm.X[r][q] = px[i];
-                sm.Y[r][q] = py[i];
+                sm.XY[r][q] = make_float2(px[i], py[i]);
             }
         }
     };
@@ -103,54 +119,53 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(const __grid_constant__ Ss
     for (int c = 0; c < t.Co; ++c) {
         if (c + 1 < t.Co) load_regs(c + 1);
         // 2. horizontal pass of the five moments, two neighbouring outputs
-        //    per thread sharing their window (read and written as float2:
-        //    the pair starts at an even column)
+        //    per thread sharing their window (the pair starts at an even
+        //    column: two input pairs per 16-byte read)
         for (int k = tid; k < kIY * (kMX / 2); k += 256) {
             const int r = k / (kMX / 2), q = 2 * (k - r * (kMX / 2));
-            float a[2][5] = {};
+            float2 A[2] = {}, B[2] = {};
+            float Cxy[2] = {0.f, 0.f};
 #pragma unroll
             for (int jj = 0; jj <= kTaps; jj += 2) {
-                const float2 x2 = *reinterpret_cast<const float2*>(&sm.X[r][q + jj]);
-                const float2 y2 = *reinterpret_cast<const float2*>(&sm.Y[r][q + jj]);
+                const float4 in = *reinterpret_cast<const float4*>(&sm.XY[r][q + jj]);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int j = jj + h;
-                    const float x = h ? x2.y : x2.x, y = h ? y2.y : y2.x;
-                    const float xx = x * x, yy = y * y, xy = x * y;
+                    const float2 v = h ? make_float2(in.z, in.w) : make_float2(in.x, in.y);
+                    const float2 sq = __fmul2_rn(v, v);
+                    const float xy = v.x * v.y;
 #pragma unroll
                     for (int o = 0; o < 2; ++o) {
                         const int tap = j - o;
                         if (tap < 0 || tap >= kTaps) continue;
-                        const float w = t.w[tap];
-                        a[o][0] = fmaf(w, x, a[o][0]);
-                        a[o][1] = fmaf(w, y, a[o][1]);
-                        a[o][2] = fmaf(w, xx, a[o][2]);
-                        a[o][3] = fmaf(w, yy, a[o][3]);
-                        a[o][4] = fmaf(w, xy, a[o][4]);
+                        A[o] = ffma2(t.wd[tap], v, A[o]);
+                        B[o] = ffma2(t.wd[tap], sq, B[o]);
+                        Cxy[o] = fmaf(t.w[tap], xy, Cxy[o]);
                     }
                 }
             }
-#pragma unroll
-            for (int u = 0; u < 5; ++u) *reinterpret_cast<float2*>(&sm.HM[u][r][q]) = make_float2(a[0][u], a[1][u]);
+            *reinterpret_cast<float4*>(&sm.hm.a[r][q]) = make_float4(A[0].x, A[0].y, A[1].x, A[1].y);
+            *reinterpret_cast<float4*>(&sm.hm.b[r][q]) = make_float4(B[0].x, B[0].y, B[1].x, B[1].y);
+            *reinterpret_cast<float2*>(&sm.hm.c[r][q]) = make_float2(Cxy[0], Cxy[1]);
         }
         __syncthreads();
         // 3. vertical pass (two rows per thread), ssim and its derivatives
         //    w.r.t. the raw moments
         for (int k = tid; k < (kMY / 2) * kMX; k += 256) {
             const int rp = k / kMX, q = k - rp * kMX, r0 = 2 * rp;
-            float m[2][5] = {};
+            float2 A[2] = {}, B[2] = {};
+            float Cxy[2] = {0.f, 0.f};
 #pragma unroll
             for (int j = 0; j <= kTaps; ++j) {
-                float hv[5];
-#pragma unroll
-                for (int u = 0; u < 5; ++u) hv[u] = sm.HM[u][r0 + j][q];
+                const float2 ha = sm.hm.a[r0 + j][q], hb = sm.hm.b[r0 + j][q];
+                const float hc = sm.hm.c[r0 + j][q];
 #pragma unroll
                 for (int o = 0; o < 2; ++o) {
                     const int tap = j - o;
                     if (tap < 0 || tap >= kTaps) continue;
-                    const float w = t.w[tap];
-#pragma unroll
-                    for (int u = 0; u < 5; ++u) m[o][u] = fmaf(w, hv[u], m[o][u]);
+                    A[o] = ffma2(t.wd[tap], ha, A[o]);
+                    B[o] = ffma2(t.wd[tap], hb, B[o]);
+                    Cxy[o] = fmaf(t.w[tap], hc, Cxy[o]);
                 }
             }
 #pragma unroll
@@ -159,17 +174,17 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(const __grid_constant__ Ss
                 const int gy = y0 - kR + r, gx = x0 - kR + q;
                 float g1 = 0.f, g2 = 0.f, g3 = 0.f;
                 if (gx >= 0 && gx < V.W && gy >= 0 && gy < V.H) {
-                    const float mx = m[o][0], my = m[o][1];
-                    const float A = 2.f * mx * my + kC1;
-                    const float B = 2.f * (m[o][4] - mx * my) + kC2;
+                    const float mx = A[o].x, my = A[o].y;
+                    const float A_ = 2.f * mx * my + kC1;
+                    const float B_ = 2.f * (Cxy[o] - mx * my) + kC2;
                     const float Cc = mx * mx + my * my + kC1;
-                    const float D = (m[o][2] - mx * mx) + (m[o][3] - my * my) + kC2;
+                    const float D = (B[o].x - mx * mx) + (B[o].y - my * my) + kC2;
                     // one reciprocal, 1/(Cc D)^2, gives ssim and its quotients by A, B, Cc, D
-                    const float ab = A * B, cd = Cc * D;
+                    const float ab = A_ * B_, cd = Cc * D;
                     const float inv = 1.0f / (cd * cd);
                     const float ssim = ab * cd * inv;
-                    const float sA = B * cd * inv, sB = A * cd * inv;   // ssim / A, ssim / B
-                    const float sCc = ab * D * inv, sD = ab * Cc * inv;  // ssim / Cc, ssim / D
+                    const float sA = B_ * cd * inv, sB = A_ * cd * inv;   // ssim / A, ssim / B
+                    const float sCc = ab * D * inv, sD = ab * Cc * inv;    // ssim / Cc, ssim / D
                     const float dmu = 2.f * my * sA - 2.f * mx * sCc;
                     const float dvar = -sD;
                     const float dcov = 2.f * sB;
@@ -178,54 +193,55 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(const __grid_constant__ Ss
                     g3 = dcov;
                     if (r >= kR && r < kR + kTY && q >= kR && q < kR + kTX) sm.St[r - kR][q - kR] = ssim;
                 }
-                sm.G[0][r][q] = g1; sm.G[1][r][q] = g2; sm.G[2][r][q] = g3;
+                sm.Ga[r][q] = make_float2(g1, g2);
+                sm.Gb[r][q] = g3;
             }
         }
         __syncthreads();
-        // 4. horizontal pass of G1..G3 (over the HM buffer), two outputs per
-        //    thread (float2 reads and writes)
+        // 4. horizontal pass of G1..G3 (over the moments' buffer), two
+        //    outputs per thread
         for (int k = tid; k < kMY * (kTX / 2); k += 256) {
             const int r = k / (kTX / 2), q = 2 * (k - r * (kTX / 2));
-            float a[2][3] = {};
+            float2 A[2] = {};
+            float Bg[2] = {0.f, 0.f};
 #pragma unroll
             for (int jj = 0; jj <= kTaps; jj += 2) {
-                float2 g2[3];
-#pragma unroll
-                for (int u = 0; u < 3; ++u) g2[u] = *reinterpret_cast<const float2*>(&sm.G[u][r][q + jj]);
+                const float4 ga = *reinterpret_cast<const float4*>(&sm.Ga[r][q + jj]);
+                const float2 gb = *reinterpret_cast<const float2*>(&sm.Gb[r][q + jj]);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int j = jj + h;
+                    const float2 va = h ? make_float2(ga.z, ga.w) : make_float2(ga.x, ga.y);
+                    const float vb = h ? gb.y : gb.x;
 #pragma unroll
                     for (int o = 0; o < 2; ++o) {
                         const int tap = j - o;
                         if (tap < 0 || tap >= kTaps) continue;
-                        const float w = t.w[tap];
-#pragma unroll
-                        for (int u = 0; u < 3; ++u) a[o][u] = fmaf(w, h ? g2[u].y : g2[u].x, a[o][u]);
+                        A[o] = ffma2(t.wd[tap], va, A[o]);
+                        Bg[o] = fmaf(t.w[tap], vb, Bg[o]);
                     }
                 }
             }
-#pragma unroll
-            for (int u = 0; u < 3; ++u) *reinterpret_cast<float2*>(&sm.HG[u][r][q]) = make_float2(a[0][u], a[1][u]);
+            *reinterpret_cast<float4*>(&sm.hg.a[r][q]) = make_float4(A[0].x, A[0].y, A[1].x, A[1].y);
+            *reinterpret_cast<float2*>(&sm.hg.b[r][q]) = make_float2(Bg[0], Bg[1]);
         }
         __syncthreads();
         // 5. vertical pass onto the tile (four rows of one column per thread):
         //    gradient and the loss terms
         {
             const int q = tid % kTX, r0 = 4 * (tid / kTX);
-            float b[4][3] = {};
+            float2 A[4] = {};
+            float Bg[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int j = 0; j < kTaps + 3; ++j) {
-                float hv[3];
-#pragma unroll
-                for (int u = 0; u < 3; ++u) hv[u] = sm.HG[u][r0 + j][q];
+                const float2 ha = sm.hg.a[r0 + j][q];
+                const float hb = sm.hg.b[r0 + j][q];
 #pragma unroll
                 for (int o = 0; o < 4; ++o) {
                     const int tap = j - o;
                     if (tap < 0 || tap >= kTaps) continue;
-                    const float w = t.w[tap];
-#pragma unroll
-                    for (int u = 0; u < 3; ++u) b[o][u] = fmaf(w, hv[u], b[o][u]);
+                    A[o] = ffma2(t.wd[tap], ha, A[o]);
+                    Bg[o] = fmaf(t.w[tap], hb, Bg[o]);
                 }
             }
 #pragma unroll
@@ -233,12 +249,13 @@ __global__ void __launch_bounds__(256) k_loss_l1_ssim(const __grid_constant__ Ss
                 const int r = r0 + o;
                 const int gy = y0 + r, gx = x0 + q;
                 if (gx >= V.W || gy >= V.H) continue;
-                const float x = sm.X[r + 2 * kR][q + 2 * kR], y = sm.Y[r + 2 * kR][q + 2 * kR];
+                const float2 xy = sm.XY[r + 2 * kR][q + 2 * kR];
+                const float x = xy.x, y = xy.y;
                 const float d = x - y;
                 l1[o] += fabsf(d);
                 ss[o] += sm.St[r][q];
                 if (V.grad_color) {
-                    const float dsum = b[o][0] + 2.f * x * b[o][1] + y * b[o][2];
+                    const float dsum = A[o].x + 2.f * x * A[o].y + y * Bg[o];
                     const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
                     const float gval = (t.lambda * sg - (1.f - t.lambda) * dsum) / (float)t.Co;
                     V.grad_color[((size_t)s * t.Co + c) * HW + (size_t)gy * V.W + gx] = t.scale * gval;
@@ -294,7 +311,10 @@ cudaError_t launch_loss_l1_ssim(int n_views, int S, int Co, const int* hw, const
         w[j] = std::exp(-k * k / (2.0 * 1.5 * 1.5));
         sum += w[j];
     }
-    for (int j = 0; j < kTaps; ++j) t->w[j] = (float)(w[j] / sum);
+    for (int j = 0; j < kTaps; ++j) {
+        t->w[j] = (float)(w[j] / sum);
+        t->wd[j] = make_float2(t->w[j], t->w[j]);
+    }
     int tile = 0;
     for (int v = 0; v < n_views; ++v) {
         SsimView& d = t->v[v];

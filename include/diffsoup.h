@@ -416,10 +416,17 @@ DS_API ds_status ds_shade_backward(ds_ctx* ctx, int32_t n_views, int32_t S, cons
  *    accumulation in tensor memory; about FP32 accuracy.  A launch whose wait
  *    for its MMAs runs out (about a second) stops, and the next
  *    ds_ctx_status returns DS_ERR_TIMEOUT.
+ *  DS_SHADE_TENSOR_CORES_WAIT_TEST: diagnostic, for testing the bounded
+ *    wait on a GPU: the tensor-core kernel with its MMAs never issued, so
+ *    that every CTA's wait runs out (twice about 2^31 SM clocks, about 2 s
+ *    in all); the output is left unwritten, the tensor memory is released,
+ *    the next ds_ctx_status returns DS_ERR_TIMEOUT and the context stays
+ *    usable.
  * A new context uses DS_SHADE_TENSOR_CORES (the faster of the two on
  * sm_103a).  Host calls; DS_ERR_INVALID_ARG for another value. */
 #define DS_SHADE_CUDA_CORES 0
 #define DS_SHADE_TENSOR_CORES 1
+#define DS_SHADE_TENSOR_CORES_WAIT_TEST 2
 DS_API ds_status ds_set_shade_path(ds_ctx* ctx, int32_t path);
 DS_API ds_status ds_get_shade_path(ds_ctx* ctx, int32_t* path);
 

@@ -1195,9 +1195,10 @@ ds_status ds_shade_forward(ds_ctx* c, int32_t n_views, int32_t S, const ds_camer
         if (!rgbs[i]) return fail(DS_ERR_INVALID_ARG, "rgbs[" + std::to_string(i) + "] is NULL");
         v[i].rgb = rgbs[i];
     }
-    if (c->shade_path == DS_SHADE_TENSOR_CORES)
+    if (c->shade_path == DS_SHADE_TENSOR_CORES || c->shade_path == DS_SHADE_TENSOR_CORES_WAIT_TEST)
         DS_TRY_CUDA(ds::launch_shade_fwd_tc(v.data(), n_views, S, params, c->d_status(),
-                                            static_cast<cudaStream_t>(stream)));
+                                            static_cast<cudaStream_t>(stream),
+                                            c->shade_path == DS_SHADE_TENSOR_CORES_WAIT_TEST));
     else
         DS_TRY_CUDA(ds::launch_shade_fwd(v.data(), n_views, S, params, static_cast<cudaStream_t>(stream)));
     c->last_stream = static_cast<cudaStream_t>(stream);
@@ -1206,7 +1207,8 @@ ds_status ds_shade_forward(ds_ctx* c, int32_t n_views, int32_t S, const ds_camer
 
 ds_status ds_set_shade_path(ds_ctx* c, int32_t path) {
     if (!c) return fail(DS_ERR_INVALID_ARG, "NULL context");
-    if (path != DS_SHADE_CUDA_CORES && path != DS_SHADE_TENSOR_CORES) return fail(DS_ERR_INVALID_ARG, "bad shade path");
+    if (path != DS_SHADE_CUDA_CORES && path != DS_SHADE_TENSOR_CORES && path != DS_SHADE_TENSOR_CORES_WAIT_TEST)
+        return fail(DS_ERR_INVALID_ARG, "bad shade path");
     std::lock_guard<std::mutex> lk(c->mu);
     c->shade_path = path;
     return DS_OK;

@@ -159,9 +159,10 @@ struct ShadeView {
 };
 cudaError_t launch_shade_fwd(const ShadeView* views, int n, int S, const float* params, cudaStream_t st);
 // The same forward on the tensor cores (tcgen05, TF32 split into hi + lo);
-// a timed-out wait for the MMAs sets bit 1 of *status (device).
+// a timed-out wait for the MMAs sets bit 1 of *status (device).  no_mma:
+// the MMAs are never issued, so every wait runs out (tests the bounded wait).
 cudaError_t launch_shade_fwd_tc(const ShadeView* views, int n, int S, const float* params, int* status,
-                                cudaStream_t st);
+                                cudaStream_t st, bool no_mma = false);
 // Backward: writes one partial of the 595 parameter gradients per CTA into
 // `partial` (shade_partial_floats(grid) floats) and, if grad_params is set,
 // reduces them into it.

@@ -605,7 +605,9 @@ __device__ __forceinline__ float sigmoid(float z) { return __frcp_rn(1.0f + __ex
 // run.  The next sample's features are loaded before the current sample's
 // MMAs.  Persistent CTAs of 128 threads.  A wait for the MMAs that runs out
 // (about a second) sets bit 1 of *status, and the CTA releases its tensor
-// memory and returns.
+// memory and returns.  kNoMma: the MMAs are never issued, so that every wait
+// runs out (for testing the bounded wait on a GPU).
+template <bool kNoMma>
 __global__ void __launch_bounds__(tc::kRows, tc::kMaxCtasPerSm) k_shade_fwd_tc(const __grid_constant__ ShadeTable t,
                                                           const float* __restrict__ params, int* __restrict__ status) {
     using namespace tc;
@@ -693,7 +695,7 @@ __global__ void __launch_bounds__(tc::kRows, tc::kMaxCtasPerSm) k_shade_fwd_tc(c
                 // previous accumulator are done: the next MMAs may start
                 before_sync();
                 __syncthreads();
-                if (tid == 0) issue_layer(sm, L, tmem);
+                if (tid == 0 && !kNoMma) issue_layer(sm, L, tmem);
                 ok = __syncthreads_and(wait_bar(sm, phase));
                 phase ^= 1u;
                 if (!ok) break;
@@ -796,7 +798,7 @@ bool tc_launch_shape(size_t* dyn_smem, int* per_sm) {
     }
     cudaFuncAttributes fa;
     int dev = 0, smem_sm = 0, reserved = 0, regs_sm = 0, thr_sm = 0;
-    if (cudaFuncGetAttributes(&fa, k_shade_fwd_tc) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+    if (cudaFuncGetAttributes(&fa, k_shade_fwd_tc<false>) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
@@ -823,7 +825,7 @@ bool tc_launch_shape(size_t* dyn_smem, int* per_sm) {
 }
 
 cudaError_t launch_shade_fwd_tc(const ShadeView* views, int n, int S, const float* params, int* status,
-                                cudaStream_t st) {
+                                cudaStream_t st, bool no_mma) {
     ShadeTable t;
     t.n = n;
     t.S = S;
@@ -840,9 +842,12 @@ cudaError_t launch_shade_fwd_tc(const ShadeView* views, int n, int S, const floa
     size_t smem = 0;
     int per_sm = 0;
     if (!tc_launch_shape(&smem, &per_sm)) return cudaErrorInvalidConfiguration;
-    cudaError_t e = cudaFuncSetAttribute(k_shade_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the diagnostic instantiation is launched with the production one's
+    // shape (its shared-memory padding keeps the same residency cap)
+    auto kernel = no_mma ? k_shade_fwd_tc<true> : k_shade_fwd_tc<false>;
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_shade_fwd_tc<<<persistent_grid(t.n_blocks, per_sm), tc::kRows, smem, st>>>(t, params, status);
+    kernel<<<persistent_grid(t.n_blocks, per_sm), tc::kRows, smem, st>>>(t, params, status);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -27,7 +27,7 @@ DS_REUSE_FORWARD = 0x100
 DS_OVERWRITE = 0x200
 DS_SHADE_N_PARAMS = 595
 DS_COPY, DS_BORROW, DS_STATIC = 0, 1, 2
-DS_SHADE_CUDA_CORES, DS_SHADE_TENSOR_CORES = 0, 1
+DS_SHADE_CUDA_CORES, DS_SHADE_TENSOR_CORES, DS_SHADE_TENSOR_CORES_WAIT_TEST = 0, 1, 2
 ERRORS = {-1: "DS_ERR_INVALID_ARG", -2: "DS_ERR_OOM", -3: "DS_ERR_CUDA", -4: "DS_ERR_CAPACITY",
           -5: "DS_ERR_TIMEOUT", -6: "DS_ERR_NOT_FOUND", -7: "DS_ERR_BUSY"}
 
@@ -315,7 +315,10 @@ class Context:
 
     def set_shade_path(self, path: int):
         """Kernel of shade_forward: DS_SHADE_CUDA_CORES (FP32 FMA) or
-        DS_SHADE_TENSOR_CORES (tcgen05, TF32 split into hi + lo; the default)."""
+        DS_SHADE_TENSOR_CORES (tcgen05, TF32 split into hi + lo; the default);
+        DS_SHADE_TENSOR_CORES_WAIT_TEST runs the tensor-core kernel without its
+        MMAs so that its bounded waits run out (DS_ERR_TIMEOUT at the next
+        status check)."""
         _check(load().ds_set_shade_path(self.h, int(path)))
 
     def get_shade_path(self) -> int:

@@ -110,6 +110,33 @@ def test_shade_path_setting(ctx):
     ctx.set_shade_path(path0)
 
 
+def test_tensor_core_wait_runs_out_and_the_context_recovers(ctx):
+    """The bounded wait of the tensor-core kernel on the GPU: with the MMAs
+    never issued, every CTA's wait for them runs out (about 2 s), the CTA
+    releases its tensor memory and returns without writing, the status check
+    reports DS_ERR_TIMEOUT once, and the same context then shades correctly."""
+    import torch
+    from paper_2603_27151_gb300 import native as N
+    cams = [I.look_at([0.0, -3.0, 0.5], 64, 32)]
+    rng = np.random.default_rng(12)
+    feats = [rng.uniform(0, 1, (2, 7, 32, 64)).astype(np.float32)]
+    params = _params(13)
+    path0 = ctx.get_shade_path()
+    ctx.set_shade_path(N.DS_SHADE_TENSOR_CORES_WAIT_TEST)
+    assert ctx.get_shade_path() == N.DS_SHADE_TENSOR_CORES_WAIT_TEST
+    rgb = [torch.full((2, 3, 32, 64), -1.0, device="cuda")]
+    ctx.shade_forward(cams, _to(params.astype(np.float32)), [_to(feats[0])], rgb)
+    torch.cuda.synchronize()
+    ctx.set_shade_path(path0)
+    with pytest.raises(N.DsError) as e:
+        ctx.status()
+    assert e.value.code == -5                      # DS_ERR_TIMEOUT
+    assert bool((rgb[0] == -1.0).all())            # nothing written
+    ctx.status()                                   # reported once
+    got = _shade(ctx, N.DS_SHADE_TENSOR_CORES, cams, params, feats)
+    assert np.abs(got[0] - SH.shade(feats[0], cams[0], params)).max() <= 1e-5
+
+
 def test_tensor_core_forward_full_size_batch(ctx):
     """The 1080p batch's colour features (4 x 1920x1080 + 4 x 960x540, S = 4,
     41.5 M pixel-samples, 81,000 tiles of 128 pixels) in one launch: windows at corners

@@ -1266,16 +1266,12 @@ def oracle_sample(pool, cores: int, start_row: int, seed: int = 13, rows_per_pro
 
 
 def oracle_one_core(start_row: int, n_rows: int, seed: int = 13):
-    """The same unit on one core, in this process: rows start_row ..
-    start_row + n_rows - 1 one after another."""
-    frags = 0
-    secs = 0.0
-    for k in range(n_rows):
-        r = (CPU_VIEW, start_row + k, start_row + k + 1)
-        tg = _oracle_target(r)
-        f, t = _oracle_rows(r + (seed, tg))
-        frags += f
-        secs += t
+    """The unit of one process of oracle_sample on one core, in this process:
+    the band of rows start_row .. start_row + n_rows - 1 in one call (the
+    oracle's per-call candidate scan is paid once per band, as there)."""
+    r = (CPU_VIEW, start_row, start_row + n_rows)
+    tg = _oracle_target(r)
+    frags, secs = _oracle_rows(r + (seed, tg))
     return frags / secs, secs, frags
 
 
@@ -1347,7 +1343,7 @@ def cpu_config_estimates():
 
 # Rows per process of the CPU baseline's sample (about 10-20 s of CPU work
 # in all on 16 cores) and of each step of the reference arm.
-CPU_ROWS_BASELINE = 20
+CPU_ROWS_BASELINE = 40
 CPU_ROWS_STEP = 4
 
 

@@ -227,6 +227,38 @@ DS_API ds_status ds_raster_backward(ds_ctx* ctx, int32_t soup_id, const ds_camer
                              const ds_view_gin* gin, uint32_t grad_flags, float* grad_verts,
                              float* grad_tex, void* stream);
 
+/* Adam state of a texture for ds_raster_backward_adam (Sec. 3.4; the
+ * supplementary "Hyperparameters" train the texture features with Adam):
+ *  m, v  (device) first and second moments, float32, one value per texture
+ *        value in the soup's texture layout (levels back to back for a level
+ *        soup), owned by the caller;
+ *  lr, beta1 in [0, 1), beta2 in [0, 1), eps >= 0; step t >= 1 (the bias
+ *  corrections use 1 - beta^t). */
+typedef struct ds_adam_args {
+    float* m;
+    float* v;
+    float lr, beta1, beta2, eps;
+    int64_t step;
+} ds_adam_args;
+
+/* ds_raster_backward with one Adam step of the soup's texture fused into
+ * the gradient finish: the texture gradient of this call (the terms of
+ * grad_flags, as ds_raster_backward would write with DS_OVERWRITE) is never
+ * written; each value's gradient, rounded to FP32 exactly as written there,
+ * updates the soup's texture in place together with m and v, with the
+ * roundings of ds_adam_step at dim = 1, so that the result is bit-identical
+ * to ds_raster_backward (DS_OVERWRITE) followed by ds_adam_step.  For a level
+ * soup the update applies to the levels (in the adjoint's epilogue).  The
+ * texture updated is the soup's own storage: the caller's tensor for a soup
+ * uploaded with borrowing, the context's copy otherwise.  grad_verts as in
+ * ds_raster_backward.  DS_ERR_INVALID_ARG for a NULL tex_adam, m or v, bad
+ * hyperparameters, step < 1, no DS_G_TEX or DS_G_SCORE in grad_flags, or a
+ * static soup (DS_STATIC). */
+DS_API ds_status ds_raster_backward_adam(ds_ctx* ctx, int32_t soup_id, const ds_camera* cams,
+                                         int32_t n_views, int32_t S, const ds_view_out* fwd,
+                                         const ds_view_gin* gin, uint32_t grad_flags, float* grad_verts,
+                                         const ds_adam_args* tex_adam, void* stream);
+
 /* The two passes with the cameras and seeds in DEVICE memory (ds_camera[n]
  * and uint64[n], read by the kernels), the view sizes on the host
  * (wh [n][2] = width, height).  Otherwise as ds_raster_forward /

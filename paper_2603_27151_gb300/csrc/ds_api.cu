@@ -737,14 +737,14 @@ struct FusedL2 {
 // `fused` the forward has not run: the fused kernel renders, evaluates the
 // loss and takes the texture, score and interior terms in one pass.
 ds_status backward_impl(ds_ctx* c, Soup& s, uint32_t grad_flags, float* grad_verts, float* grad_tex, cudaStream_t st,
-                        const FusedL2* fused = nullptr) {
+                        const FusedL2* fused = nullptr, const ds::AdamTex* tex_adam = nullptr) {
     ds::ViewTable& vt = *c->vt;
     const int n_views = vt.n;
     const ds::SoupDev sd = soup_dev(s);
     const int grid = tile_grid(c, vt);
     const uint32_t gflags = grad_flags & DS_G_ALL;
     const size_t n_tex = (size_t)s.T * s.V * s.C, n_verts = 9 * (size_t)s.T;
-    const bool want_tex = grad_tex && (gflags & (DS_G_TEX | DS_G_SCORE));
+    const bool want_tex = (grad_tex || tex_adam) && (gflags & (DS_G_TEX | DS_G_SCORE));
     const bool want_verts = grad_verts && (gflags & (DS_G_INTERIOR | DS_G_EDGE));
     const bool overwrite = (grad_flags & DS_OVERWRITE) != 0;
     double* acc_tex = nullptr;
@@ -806,7 +806,11 @@ ds_status backward_impl(ds_ctx* c, Soup& s, uint32_t grad_flags, float* grad_ver
     }
     {
         StageScope p(c, ds::kStFinish, st);
-        if (want_tex && s.levels())
+        if (want_tex && tex_adam && s.levels())
+            DS_TRY_CUDA(ds::launch_restrict_adam(acc_tex, s.T, s.r_min, s.r_max, s.C, *tex_adam, st));
+        else if (want_tex && tex_adam)
+            DS_TRY_CUDA(ds::launch_grad_finish_adam(acc_tex, *tex_adam, (long long)n_tex, st));
+        else if (want_tex && s.levels())
             DS_TRY_CUDA(ds::launch_restrict(acc_tex, s.T, s.r_min, s.r_max, s.C, grad_tex, overwrite, st));
         else if (want_tex)
             DS_TRY_CUDA(ds::launch_grad_finish(acc_tex, grad_tex, (long long)n_tex, overwrite, st));
@@ -968,6 +972,34 @@ ds_status ds_raster_backward(ds_ctx* c, int32_t soup_id, const ds_camera* cams, 
     if (!((grad_flags & DS_REUSE_FORWARD) && plan_matches(c, soup_id, cams, n_views)))
         DS_TRY(prepare(c, soup_id, *s, cams, *c->vt, true, st));
     return backward_impl(c, *s, grad_flags, grad_verts, grad_tex, st);
+}
+
+ds_status ds_raster_backward_adam(ds_ctx* c, int32_t soup_id, const ds_camera* cams, int32_t n_views, int32_t S,
+                                  const ds_view_out* fwd, const ds_view_gin* gin, uint32_t grad_flags,
+                                  float* grad_verts, const ds_adam_args* tex_adam, void* stream) {
+    if (!c) return fail(DS_ERR_INVALID_ARG, "NULL context");
+    if (!tex_adam || !tex_adam->m || !tex_adam->v) return fail(DS_ERR_INVALID_ARG, "NULL Adam state");
+    if (tex_adam->step < 1) return fail(DS_ERR_INVALID_ARG, "step must be >= 1");
+    if (!(tex_adam->beta1 >= 0.f && tex_adam->beta1 < 1.f && tex_adam->beta2 >= 0.f && tex_adam->beta2 < 1.f &&
+          tex_adam->eps >= 0.f) || !std::isfinite(tex_adam->lr))
+        return fail(DS_ERR_INVALID_ARG, "bad hyperparameters");
+    if (!(grad_flags & (DS_G_TEX | DS_G_SCORE))) return fail(DS_ERR_INVALID_ARG, "no texture gradient term selected");
+    std::lock_guard<std::mutex> lk(c->mu);
+    DeviceGuard g(c->device);
+    Soup* s = nullptr;
+    DS_TRY(get_soup(c, soup_id, &s));
+    if (s->fixed) return fail(DS_ERR_INVALID_ARG, "the soup is static (DS_STATIC): its texture cannot be updated");
+    DS_TRY(check_views(cams, n_views, S));
+    DS_TRY(check_gin(fwd, gin, n_views, grad_flags));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    build_table(*c->vt, c->tune, cams, nullptr, n_views, S, fwd, gin);
+    if (!((grad_flags & DS_REUSE_FORWARD) && plan_matches(c, soup_id, cams, n_views)))
+        DS_TRY(prepare(c, soup_id, *s, cams, *c->vt, true, st));
+    const ds::AdamTex at{const_cast<float*>(s->tex), tex_adam->m, tex_adam->v,
+                         ds::make_adam(tex_adam->lr, tex_adam->beta1, tex_adam->beta2, tex_adam->eps,
+                                       (long long)tex_adam->step)};
+    return backward_impl(c, *s, grad_flags, grad_verts, nullptr, st, nullptr, &at);
 }
 
 ds_status ds_raster_backward_devcam(ds_ctx* c, int32_t soup_id, const int32_t* wh, const ds_camera* cams,

@@ -795,6 +795,20 @@ __global__ void k_grad_finish(const double* __restrict__ acc, float* __restrict_
     }
 }
 
+// The texture finish with Adam fused (Sec. 3.4): the step's gradient of value
+// i, rounded to FP32 as the plain finish writes it, moves x, m, v at once.
+__global__ void k_grad_finish_adam(const double* __restrict__ acc, float* __restrict__ x, float* __restrict__ m,
+                                   float* __restrict__ v, long long n, AdamDev a) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+        float xi = x[i], mi = m[i], vi = v[i];
+        adam_apply(xi, mi, vi, (float)(0.0 + __ldcs(acc + i)), a);
+        x[i] = xi;
+        m[i] = mi;
+        v[i] = vi;
+    }
+}
+
 cudaError_t launch_geom(const ViewTable& vt, const SoupDev& s, GeomRec* geom, cudaStream_t st) {
     const long long n = (long long)vt.n * s.T;
     k_geom<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(vt, s, geom);
@@ -843,6 +857,15 @@ cudaError_t launch_grad_finish(const double* acc, float* out, long long n, bool 
     long long g = (n + 255) / 256;
     if (g > 152 * 8) g = 152 * 8;
     k_grad_finish<<<(unsigned)g, 256, 0, st>>>(acc, out, n, overwrite ? 1 : 0);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_finish_adam(const double* acc, const AdamTex& adam, long long n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    long long g = (n + 255) / 256;
+    if (g > 152 * 8) g = 152 * 8;
+    k_grad_finish_adam<<<(unsigned)g, 256, 0, st>>>(acc, adam.x, adam.m, adam.v, n, adam.a);
     note_launches(1);
     return cudaGetLastError();
 }

@@ -303,4 +303,23 @@ __device__ __forceinline__ SetupRec load_rec(const SetupRec* p) {
     return r;
 }
 
+// Adam (Sec. 3.4; supplementary "Hyperparameters"): the step's scalars, with
+// the bias corrections c1 = 1/(1 - b1^t), c2 = 1/(1 - b2^t) formed on the host.
+struct AdamDev {
+    float lr, b1, b2, eps, c1, c2;
+};
+
+// One value's Adam step:
+//   m <- b1 m + (1 - b1) g,  v <- b2 v + (1 - b2) g^2,
+//   x <- x - lr (m c1) / (sqrt(v c2) + eps),
+// every rounding fixed by an explicit intrinsic, so that each kernel that
+// applies it (the optimiser step, the fused gradient finishes) gives the
+// same bits for the same gradient.
+__device__ __forceinline__ void adam_apply(float& x, float& m, float& v, float g, const AdamDev& a) {
+    m = __fmaf_rn(a.b1, m, __fmul_rn(1.0f - a.b1, g));
+    v = __fmaf_rn(a.b2, v, __fmul_rn(1.0f - a.b2, __fmul_rn(g, g)));
+    const float u = __fdiv_rn(__fmul_rn(a.lr, __fmul_rn(m, a.c1)), __fadd_rn(__fsqrt_rn(__fmul_rn(v, a.c2)), a.eps));
+    x = __fsub_rn(x, u);
+}
+
 }  // namespace ds

@@ -96,6 +96,19 @@ cudaError_t launch_raster_count(const ViewTable& vt, const SoupDev& s, const Set
                                 int DB, int mode, unsigned long long* total, int* counter,
                                 int grid, cudaStream_t st);
 
+// The scalars of Adam step t (t >= 1), bias corrections in FP64 on the host.
+AdamDev make_adam(float lr, float b1, float b2, float eps, long long t);
+
+// An Adam update fused into a gradient finish: the texture x and its moments
+// m, v (device, the texture's layout) take the step instead of a gradient
+// being written.
+struct AdamTex {
+    float* x;
+    float* m;
+    float* v;
+    AdamDev a;
+};
+
 // ---- backward (ds_backward.cu)
 cudaError_t launch_geom(const ViewTable& vt, const SoupDev& s, GeomRec* geom, cudaStream_t st);
 cudaError_t launch_raster_bwd(const ViewTable& vt, const SoupDev& s, const SetupRec* recs,
@@ -113,6 +126,9 @@ cudaError_t launch_edge_bwd(const ViewTable& vt, const SoupDev& s, const SetupRe
 // out[i] = (overwrite ? 0 : out[i]) + acc[i] (FP64 accumulators into FP32 gradients)
 cudaError_t launch_grad_finish(const double* acc, float* out, long long n, bool overwrite,
                                cudaStream_t st);
+// The texture finish with Adam fused: g = (float) acc[i] is the step's
+// gradient of value i, applied to adam.x/m/v (no gradient is written).
+cudaError_t launch_grad_finish_adam(const double* acc, const AdamTex& adam, long long n, cudaStream_t st);
 
 // Multi-resolution grids (levels r_min..r_max, level R = [T][V_R][C], stored
 // one after the other).  Composition of the finest grid's logits (act: the
@@ -123,6 +139,10 @@ cudaError_t launch_compose(const float* levels, int T, int r_min, int r_max, int
                            float* act_a, cudaStream_t st);
 cudaError_t launch_restrict(const double* fine, int T, int r_min, int r_max, int C, float* out, bool overwrite,
                             cudaStream_t st);
+// The adjoint with Adam fused: each level value's gradient is applied to
+// adam.x/m/v (the levels' layout) instead of being written.
+cudaError_t launch_restrict_adam(const double* fine, int T, int r_min, int r_max, int C, const AdamTex& adam,
+                                 cudaStream_t st);
 cudaError_t launch_resample(const float* src, int T, int r_src, int C, float* dst, int r_dst, cudaStream_t st);
 
 // Adaptive control of primitives (ds_adapt.cu).

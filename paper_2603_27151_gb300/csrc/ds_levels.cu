@@ -265,9 +265,12 @@ __global__ void __launch_bounds__(256) k_compose_single(const float* __restrict_
 
 // Adjoint of the composition for one triangle per CTA.  fine: FP64 gradient
 // of the composed logits [T][V_f][C]; out: the level gradients (same layout
-// as the levels), written or accumulated.
+// as the levels), written or accumulated.  kAdam: no gradient is written;
+// each level value's gradient takes its Adam step on adam.x/m/v (same
+// layout) where the plain kernel would store it.
+template <bool kAdam>
 __global__ void __launch_bounds__(256) k_restrict(const double* __restrict__ fine, int T, int r_min, int r_max, int C,
-                                                  float* __restrict__ out, int overwrite) {
+                                                  float* __restrict__ out, int overwrite, AdamTex adam) {
     extern __shared__ float sm[];
     const int t = blockIdx.x;
     const int Vf = level_V(r_max);
@@ -285,7 +288,7 @@ __global__ void __launch_bounds__(256) k_restrict(const double* __restrict__ fin
     {
         // the finest level: eight loads in flight per thread before they are used
         const double* src = fine + (size_t)t * Vf * C;
-        float* dst = out + off[r_max - r_min] + (size_t)t * Vf * C;
+        float* dst = kAdam ? nullptr : out + off[r_max - r_min] + (size_t)t * Vf * C;
         const int n = Vf * C;
         for (int k0 = threadIdx.x; k0 < n; k0 += 8 * blockDim.x) {
             double g[8];
@@ -299,7 +302,16 @@ __global__ void __launch_bounds__(256) k_restrict(const double* __restrict__ fin
                 const int k = k0 + u * blockDim.x;
                 if (k < n) {
                     A[k] = (float)g[u];
-                    dst[k] = overwrite ? (float)g[u] : (float)((double)dst[k] + g[u]);
+                    if (kAdam) {
+                        const size_t i = off[r_max - r_min] + (size_t)t * Vf * C + k;
+                        float x = adam.x[i], m = adam.m[i], v = adam.v[i];
+                        adam_apply(x, m, v, (float)g[u], adam.a);
+                        adam.x[i] = x;
+                        adam.m[i] = m;
+                        adam.v[i] = v;
+                    } else {
+                        dst[k] = overwrite ? (float)g[u] : (float)((double)dst[k] + g[u]);
+                    }
                 }
             }
         }
@@ -307,7 +319,7 @@ __global__ void __launch_bounds__(256) k_restrict(const double* __restrict__ fin
     __syncthreads();
     for (int R = r_max - 1; R >= r_min; --R) {
         const int N = 1 << R, Nfine = 2 * N, V = level_V(R);
-        float* dst = out + off[R - r_min] + (size_t)t * V * C;
+        float* dst = kAdam ? nullptr : out + off[R - r_min] + (size_t)t * V * C;
         for (int k = threadIdx.x; k < V * C; k += blockDim.x) {
             const int u = k / C, c = k - u * C;
             int a, b;
@@ -323,7 +335,16 @@ __global__ void __launch_bounds__(256) k_restrict(const double* __restrict__ fin
             }
             acc = fmaf(0.5f, half, acc);
             B[k] = acc;
-            dst[k] = overwrite ? acc : dst[k] + acc;
+            if (kAdam) {
+                const size_t i = off[R - r_min] + (size_t)t * V * C + k;
+                float x = adam.x[i], m = adam.m[i], v = adam.v[i];
+                adam_apply(x, m, v, acc, adam.a);
+                adam.x[i] = x;
+                adam.m[i] = m;
+                adam.v[i] = v;
+            } else {
+                dst[k] = overwrite ? acc : dst[k] + acc;
+            }
         }
         __syncthreads();
         float* tmp = A;
@@ -399,14 +420,25 @@ cudaError_t launch_compose(const float* levels, int T, int r_min, int r_max, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_restrict(const double* fine, int T, int r_min, int r_max, int C, float* out, bool overwrite,
-                            cudaStream_t st) {
+template <bool kAdam>
+static cudaError_t run_restrict(const double* fine, int T, int r_min, int r_max, int C, float* out, bool overwrite,
+                                const AdamTex& adam, cudaStream_t st) {
     const size_t smem = sizeof(float) * (size_t)(level_V(r_max) + level_V(r_max > 0 ? r_max - 1 : 0)) * C;
-    cudaError_t e = cudaFuncSetAttribute(k_restrict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_restrict<kAdam>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_restrict<<<T, 256, smem, st>>>(fine, T, r_min, r_max, C, out, overwrite ? 1 : 0);
+    k_restrict<kAdam><<<T, 256, smem, st>>>(fine, T, r_min, r_max, C, out, overwrite ? 1 : 0, adam);
     note_launches(1);
     return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(const double* fine, int T, int r_min, int r_max, int C, float* out, bool overwrite,
+                            cudaStream_t st) {
+    return run_restrict<false>(fine, T, r_min, r_max, C, out, overwrite, AdamTex{}, st);
+}
+
+cudaError_t launch_restrict_adam(const double* fine, int T, int r_min, int r_max, int C, const AdamTex& adam,
+                                 cudaStream_t st) {
+    return run_restrict<true>(fine, T, r_min, r_max, C, nullptr, true, adam, st);
 }
 
 cudaError_t launch_resample(const float* src, int T, int r_src, int C, float* dst, int r_dst, cudaStream_t st) {

@@ -13,53 +13,44 @@ namespace ds {
 
 namespace {
 
-struct AdamArgs {
-    float lr, b1, b2, eps, c1, c2;
-};
-
-__device__ __forceinline__ float adam_update(float m, float v, const AdamArgs& a) {
-    return a.lr * (m * a.c1) / (sqrtf(v * a.c2) + a.eps);
-}
-
 // dim = 1, four values per thread.
 __global__ void __launch_bounds__(256) k_adam4(float4* __restrict__ x, const float4* __restrict__ g,
                                                float4* __restrict__ m, float4* __restrict__ v, long long n4,
-                                               AdamArgs a) {
+                                               AdamDev a) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4;
          i += (long long)gridDim.x * blockDim.x) {
         const float4 gi = __ldcs(g + i);
         float4 mi = m[i], vi = v[i], xi = x[i];
-        float* mp = &mi.x; float* vp = &vi.x; float* xp = &xi.x;
-        const float* gp = &gi.x;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            mp[k] = a.b1 * mp[k] + (1.0f - a.b1) * gp[k];
-            vp[k] = a.b2 * vp[k] + (1.0f - a.b2) * gp[k] * gp[k];
-            xp[k] -= adam_update(mp[k], vp[k], a);
-        }
+        adam_apply(xi.x, mi.x, vi.x, gi.x, a);
+        adam_apply(xi.y, mi.y, vi.y, gi.y, a);
+        adam_apply(xi.z, mi.z, vi.z, gi.z, a);
+        adam_apply(xi.w, mi.w, vi.w, gi.w, a);
         m[i] = mi;
         v[i] = vi;
         x[i] = xi;
     }
 }
 
-// Any dim (1..4): one vector per thread.
+// Any dim (1..4): one vector per thread; the second moment from the squared
+// norm of the vector's gradient (VectorAdam), the same roundings as
+// adam_apply (which it equals for dim = 1).
 __global__ void __launch_bounds__(256) k_adam_vec(float* __restrict__ x, const float* __restrict__ g,
                                                   float* __restrict__ m, float* __restrict__ v, long long n_vec,
-                                                  int dim, AdamArgs a) {
+                                                  int dim, AdamDev a) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_vec;
          i += (long long)gridDim.x * blockDim.x) {
         float gv[4], g2 = 0.f;
         for (int k = 0; k < dim; ++k) {
             gv[k] = __ldcs(g + i * dim + k);
-            g2 += gv[k] * gv[k];
+            g2 = __fmaf_rn(gv[k], gv[k], g2);
         }
-        const float vi = a.b2 * v[i] + (1.0f - a.b2) * g2;
+        const float vi = __fmaf_rn(a.b2, v[i], __fmul_rn(1.0f - a.b2, g2));
         v[i] = vi;
+        const float den = __fadd_rn(__fsqrt_rn(__fmul_rn(vi, a.c2)), a.eps);
         for (int k = 0; k < dim; ++k) {
-            const float mi = a.b1 * m[i * dim + k] + (1.0f - a.b1) * gv[k];
+            const float mi = __fmaf_rn(a.b1, m[i * dim + k], __fmul_rn(1.0f - a.b1, gv[k]));
             m[i * dim + k] = mi;
-            x[i * dim + k] -= adam_update(mi, vi, a);
+            x[i * dim + k] = __fsub_rn(x[i * dim + k], __fdiv_rn(__fmul_rn(a.lr, __fmul_rn(mi, a.c1)), den));
         }
     }
 }
@@ -72,15 +63,20 @@ int grid_for(long long n) {
 
 }  // namespace
 
-cudaError_t launch_adam(float* x, const float* g, float* m, float* v, long long n, int dim, float lr, float b1,
-                        float b2, float eps, long long t, cudaStream_t st) {
-    AdamArgs a;
+AdamDev make_adam(float lr, float b1, float b2, float eps, long long t) {
+    AdamDev a;
     a.lr = lr;
     a.b1 = b1;
     a.b2 = b2;
     a.eps = eps;
     a.c1 = (float)(1.0 / (1.0 - std::pow((double)b1, (double)t)));
     a.c2 = (float)(1.0 / (1.0 - std::pow((double)b2, (double)t)));
+    return a;
+}
+
+cudaError_t launch_adam(float* x, const float* g, float* m, float* v, long long n, int dim, float lr, float b1,
+                        float b2, float eps, long long t, cudaStream_t st) {
+    const AdamDev a = make_adam(lr, b1, b2, eps, t);
     if (n == 0) return cudaSuccess;
     const bool vec4 = dim == 1 && n % 4 == 0 && ((uintptr_t)x | (uintptr_t)g | (uintptr_t)m | (uintptr_t)v) % 16 == 0;
     if (vec4)

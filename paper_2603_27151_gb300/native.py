@@ -44,6 +44,11 @@ class ds_camera(ctypes.Structure):
                 ("R", ctypes.c_float * 9), ("t", ctypes.c_float * 3), ("near_z", ctypes.c_float)]
 
 
+class ds_adam_args(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_void_p), ("v", ctypes.c_void_p), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("step", ctypes.c_int64)]
+
+
 class ds_view_out(ctypes.Structure):
     _fields_ = [("gbuf", ctypes.c_void_p), ("color", ctypes.c_void_p), ("n_front", ctypes.c_void_p)]
 
@@ -97,6 +102,8 @@ def load():
     L.ds_raster_forward.restype = i32
     L.ds_raster_backward.argtypes = [P, i32, P, i32, i32, P, P, u32, P, P, P]
     L.ds_raster_backward.restype = i32
+    L.ds_raster_backward_adam.argtypes = [P, i32, P, i32, i32, P, P, u32, P, ctypes.POINTER(ds_adam_args), P]
+    L.ds_raster_backward_adam.restype = i32
     L.ds_fragment_count.argtypes = [P, i32, P, i32, ctypes.POINTER(ctypes.c_int64), P]
     L.ds_fragment_count.restype = i32
     L.ds_ctx_status.argtypes = [P]
@@ -312,6 +319,29 @@ class Context:
             gin[v].score_w = score_ws[v].data_ptr() if score_ws is not None and score_ws[v] is not None else None
         _check(load().ds_raster_backward(self.h, soup_id, ca, n, S, fwd, gin, flags,
                                          _ptr(grad_verts), _ptr(grad_tex), _stream(stream)))
+
+    def raster_backward_adam(self, soup_id, cams, S, gbufs, colors, grad_colors, score_ws, flags, m, v,
+                             lr: float, step: int, grad_verts=None, beta1: float = 0.9, beta2: float = 0.999,
+                             eps: float = 1e-8, stream=None):
+        """ds_raster_backward_adam: the backward with one Adam step of the
+        soup's own texture fused into the gradient finish (no texture gradient
+        is written); m, v: float32 CUDA tensors of the texture's size."""
+        import torch
+        for t in (m, v):
+            if t is None or t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
+                raise ValueError("m and v must be contiguous float32 CUDA tensors")
+        n = len(cams)
+        ca = cameras(cams)
+        fwd = (ds_view_out * n)()
+        gin = (ds_view_gin * n)()
+        for k in range(n):
+            fwd[k].gbuf = gbufs[k].data_ptr()
+            fwd[k].color = colors[k].data_ptr() if colors is not None else None
+            gin[k].grad_color = grad_colors[k].data_ptr() if grad_colors is not None else None
+            gin[k].score_w = score_ws[k].data_ptr() if score_ws is not None and score_ws[k] is not None else None
+        args = ds_adam_args(m.data_ptr(), v.data_ptr(), float(lr), float(beta1), float(beta2), float(eps), int(step))
+        _check(load().ds_raster_backward_adam(self.h, soup_id, ca, n, S, fwd, gin, flags, _ptr(grad_verts),
+                                              ctypes.byref(args), _stream(stream)))
 
     def set_shade_path(self, path: int):
         """Kernel of shade_forward: DS_SHADE_CUDA_CORES (FP32 FMA) or

@@ -263,14 +263,32 @@ __global__ void __launch_bounds__(256) k_compose_single(const float* __restrict_
     }
 }
 
+// The adjoint's value k of level R (N = 2^R subdivisions) from the gradient
+// G of level R + 1 ([V][C]): the hat function of the coarse vertex on the
+// fine grid, weight 1 at the coincident vertex and 1/2 at its six
+// neighbours.
+__device__ __forceinline__ float restrict_value(const float* G, int N, int k, int C) {
+    const int Nfine = 2 * N;
+    const int u = k / C, c = k - u * C;
+    int a, b;
+    texel_ij(N, u, a, b);
+    const int x = 2 * a, y = 2 * b;
+    float acc = G[(size_t)texel_index(Nfine, x, y) * C + c];
+    float half = 0.f;
+    const int dx[6] = {1, -1, 0, 0, 1, -1}, dy[6] = {0, 0, 1, -1, -1, 1};
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+        const int xi = x + dx[e], yi = y + dy[e];
+        if (xi >= 0 && yi >= 0 && xi + yi <= Nfine) half += G[(size_t)texel_index(Nfine, xi, yi) * C + c];
+    }
+    return fmaf(0.5f, half, acc);
+}
+
 // Adjoint of the composition for one triangle per CTA.  fine: FP64 gradient
 // of the composed logits [T][V_f][C]; out: the level gradients (same layout
-// as the levels), written or accumulated.  kAdam: no gradient is written;
-// each level value's gradient takes its Adam step on adam.x/m/v (same
-// layout) where the plain kernel would store it.
-template <bool kAdam>
+// as the levels), written or accumulated.
 __global__ void __launch_bounds__(256) k_restrict(const double* __restrict__ fine, int T, int r_min, int r_max, int C,
-                                                  float* __restrict__ out, int overwrite, AdamTex adam) {
+                                                  float* __restrict__ out, int overwrite) {
     extern __shared__ float sm[];
     const int t = blockIdx.x;
     const int Vf = level_V(r_max);
@@ -288,7 +306,7 @@ __global__ void __launch_bounds__(256) k_restrict(const double* __restrict__ fin
     {
         // the finest level: eight loads in flight per thread before they are used
         const double* src = fine + (size_t)t * Vf * C;
-        float* dst = kAdam ? nullptr : out + off[r_max - r_min] + (size_t)t * Vf * C;
+        float* dst = out + off[r_max - r_min] + (size_t)t * Vf * C;
         const int n = Vf * C;
         for (int k0 = threadIdx.x; k0 < n; k0 += 8 * blockDim.x) {
             double g[8];
@@ -302,54 +320,97 @@ __global__ void __launch_bounds__(256) k_restrict(const double* __restrict__ fin
                 const int k = k0 + u * blockDim.x;
                 if (k < n) {
                     A[k] = (float)g[u];
-                    if (kAdam) {
-                        const size_t i = off[r_max - r_min] + (size_t)t * Vf * C + k;
-                        float x = adam.x[i], m = adam.m[i], v = adam.v[i];
-                        adam_apply(x, m, v, (float)g[u], adam.a);
-                        adam.x[i] = x;
-                        adam.m[i] = m;
-                        adam.v[i] = v;
-                    } else {
-                        dst[k] = overwrite ? (float)g[u] : (float)((double)dst[k] + g[u]);
-                    }
+                    dst[k] = overwrite ? (float)g[u] : (float)((double)dst[k] + g[u]);
                 }
             }
         }
     }
     __syncthreads();
     for (int R = r_max - 1; R >= r_min; --R) {
-        const int N = 1 << R, Nfine = 2 * N, V = level_V(R);
-        float* dst = kAdam ? nullptr : out + off[R - r_min] + (size_t)t * V * C;
+        const int V = level_V(R);
+        float* dst = out + off[R - r_min] + (size_t)t * V * C;
         for (int k = threadIdx.x; k < V * C; k += blockDim.x) {
-            const int u = k / C, c = k - u * C;
-            int a, b;
-            texel_ij(N, u, a, b);
-            const int x = 2 * a, y = 2 * b;
-            float acc = A[(size_t)texel_index(Nfine, x, y) * C + c];
-            float half = 0.f;
-            const int dx[6] = {1, -1, 0, 0, 1, -1}, dy[6] = {0, 0, 1, -1, -1, 1};
-#pragma unroll
-            for (int e = 0; e < 6; ++e) {
-                const int xi = x + dx[e], yi = y + dy[e];
-                if (xi >= 0 && yi >= 0 && xi + yi <= Nfine) half += A[(size_t)texel_index(Nfine, xi, yi) * C + c];
-            }
-            acc = fmaf(0.5f, half, acc);
+            const float acc = restrict_value(A, 1 << R, k, C);
             B[k] = acc;
-            if (kAdam) {
-                const size_t i = off[R - r_min] + (size_t)t * V * C + k;
-                float x = adam.x[i], m = adam.m[i], v = adam.v[i];
-                adam_apply(x, m, v, acc, adam.a);
-                adam.x[i] = x;
-                adam.m[i] = m;
-                adam.v[i] = v;
-            } else {
-                dst[k] = overwrite ? acc : dst[k] + acc;
-            }
+            dst[k] = overwrite ? acc : dst[k] + acc;
         }
         __syncthreads();
         float* tmp = A;
         A = B;
         B = tmp;
+    }
+}
+
+// The adjoint with the levels' Adam step fused (Sec. 3.4): one triangle per
+// CTA.  The gradients of all its levels (the FP32 values the plain adjoint
+// writes with overwrite) are formed in shared memory, level after level;
+// then each level's block of the triangle -- contiguous in the levels'
+// layout -- takes its Adam step as a float4 stream of x, m and v, so that
+// the gradient never reaches memory.
+__global__ void __launch_bounds__(256) k_restrict_adam(const double* __restrict__ fine, int T, int r_min, int r_max,
+                                                       int C, AdamTex adam) {
+    extern __shared__ float sm[];   // the levels' gradients of this triangle, finest first
+    const int t = blockIdx.x;
+    size_t off[6];
+    int soff[6];
+    {
+        size_t o = 0;
+        int so = 0;
+        for (int R = r_min; R <= r_max; ++R) {
+            off[R - r_min] = o;
+            o += (size_t)T * level_V(R) * C;
+        }
+        for (int R = r_max; R >= r_min; --R) {
+            soff[R - r_min] = so;
+            so += level_V(R) * C;
+        }
+    }
+    {
+        const int n = level_V(r_max) * C;
+        const double* src = fine + (size_t)t * n;
+        float* G = sm + soff[r_max - r_min];
+        for (int k0 = threadIdx.x; k0 < n; k0 += 8 * blockDim.x) {
+            double g[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int k = k0 + u * blockDim.x;
+                g[u] = k < n ? __ldcs(src + k) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int k = k0 + u * blockDim.x;
+                if (k < n) G[k] = (float)g[u];
+            }
+        }
+    }
+    __syncthreads();
+    for (int R = r_max - 1; R >= r_min; --R) {
+        const float* Gf = sm + soff[R + 1 - r_min];
+        float* G = sm + soff[R - r_min];
+        const int n = level_V(R) * C;
+        for (int k = threadIdx.x; k < n; k += blockDim.x) G[k] = restrict_value(Gf, 1 << R, k, C);
+        __syncthreads();
+    }
+    // Adam over each level's block, four values per access (the block starts
+    // on a 16-byte boundary: C and the level offsets are multiples of 4)
+    for (int R = r_max; R >= r_min; --R) {
+        const int n4 = level_V(R) * C / 4;
+        const size_t base4 = (off[R - r_min] + (size_t)t * level_V(R) * C) / 4;
+        const float4* G4 = reinterpret_cast<const float4*>(sm + soff[R - r_min]);
+        float4* X = reinterpret_cast<float4*>(adam.x) + base4;
+        float4* M = reinterpret_cast<float4*>(adam.m) + base4;
+        float4* Vv = reinterpret_cast<float4*>(adam.v) + base4;
+        for (int q = threadIdx.x; q < n4; q += blockDim.x) {
+            const float4 g = G4[q];
+            float4 x = X[q], m = __ldcs(M + q), v = __ldcs(Vv + q);
+            adam_apply(x.x, m.x, v.x, g.x, adam.a);
+            adam_apply(x.y, m.y, v.y, g.y, adam.a);
+            adam_apply(x.z, m.z, v.z, g.z, adam.a);
+            adam_apply(x.w, m.w, v.w, g.w, adam.a);
+            X[q] = x;
+            __stcs(M + q, m);
+            __stcs(Vv + q, v);
+        }
     }
 }
 
@@ -420,25 +481,28 @@ cudaError_t launch_compose(const float* levels, int T, int r_min, int r_max, int
     return cudaGetLastError();
 }
 
-template <bool kAdam>
-static cudaError_t run_restrict(const double* fine, int T, int r_min, int r_max, int C, float* out, bool overwrite,
-                                const AdamTex& adam, cudaStream_t st) {
+cudaError_t launch_restrict(const double* fine, int T, int r_min, int r_max, int C, float* out, bool overwrite,
+                            cudaStream_t st) {
     const size_t smem = sizeof(float) * (size_t)(level_V(r_max) + level_V(r_max > 0 ? r_max - 1 : 0)) * C;
-    cudaError_t e = cudaFuncSetAttribute(k_restrict<kAdam>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_restrict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_restrict<kAdam><<<T, 256, smem, st>>>(fine, T, r_min, r_max, C, out, overwrite ? 1 : 0, adam);
+    k_restrict<<<T, 256, smem, st>>>(fine, T, r_min, r_max, C, out, overwrite ? 1 : 0);
     note_launches(1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_restrict(const double* fine, int T, int r_min, int r_max, int C, float* out, bool overwrite,
-                            cudaStream_t st) {
-    return run_restrict<false>(fine, T, r_min, r_max, C, out, overwrite, AdamTex{}, st);
-}
-
 cudaError_t launch_restrict_adam(const double* fine, int T, int r_min, int r_max, int C, const AdamTex& adam,
                                  cudaStream_t st) {
-    return run_restrict<true>(fine, T, r_min, r_max, C, nullptr, true, adam, st);
+    if (C % 4 != 0 || (((uintptr_t)adam.x | (uintptr_t)adam.m | (uintptr_t)adam.v) & 15) != 0)
+        return cudaErrorInvalidValue;
+    size_t per_tri = 0;
+    for (int R = r_min; R <= r_max; ++R) per_tri += (size_t)level_V(R) * C;
+    const size_t smem = sizeof(float) * per_tri;
+    cudaError_t e = cudaFuncSetAttribute(k_restrict_adam, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_restrict_adam<<<T, 256, smem, st>>>(fine, T, r_min, r_max, C, adam);
+    note_launches(1);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_resample(const float* src, int T, int r_src, int C, float* dst, int r_dst, cudaStream_t st) {

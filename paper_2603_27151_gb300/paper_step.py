@@ -11,6 +11,9 @@ library (Sec. 3.3-3.4; supplementary "Hyperparameters"):
      rasteriser backward to the level textures and vertices (Alg. A1, Eq. 8);
   5. VectorAdam for the vertices, Adam for the level textures and the MLP,
      learning rates annealed exponentially by 100x over ``total_steps``.
+     In ``step`` the level textures' Adam update runs inside the
+     rasteriser backward's gradient finish (ds_raster_backward_adam), so
+     their gradient is never written to memory.
 
 Every stage is a kernel of the library; PyTorch only holds the tensors.
 """
@@ -49,10 +52,12 @@ class PaperStep:
         self.step_no = 0
         self.rng = np.random.default_rng(seed)
 
-    def gradients(self, view_ids, seeds):
+    def gradients(self, view_ids, seeds, tex_adam=None):
         """Steps 1-4 for the given views and mask seeds: fills g_verts, g_tex,
         g_params and loss (the sum over views of the mean over samples of the
-        summed per-pixel loss); returns the shaded RGB images."""
+        summed per-pixel loss); returns the shaded RGB images.  tex_adam =
+        (lr, step): the level textures take that Adam step in the backward
+        instead, and g_tex is left as it was."""
         cams = [self.cams[k] for k in view_ids]
         S, dev = self.S, self.dev
         g, col, _ = N.alloc_outputs(cams, S, self.C, dev)
@@ -66,20 +71,23 @@ class PaperStep:
         N.loss_l1_ssim(rgb, [self.targets[k] for k in view_ids], g_rgb, sw, self.loss, lam=self.lam, scale=1.0 / S)
         g_col = [torch.empty_like(c) for c in col]
         self.ctx.shade_backward(cams, self.params, col, g_rgb, g_col, self.g_params, overwrite=True)
-        self.ctx.raster_backward(self.sid, cams, S, g, col, g_col, sw,
-                                 N.DS_G_ALL | N.DS_REUSE_FORWARD | N.DS_OVERWRITE, self.g_verts, self.g_tex)
+        flags = N.DS_G_ALL | N.DS_REUSE_FORWARD | N.DS_OVERWRITE
+        if tex_adam is None:
+            self.ctx.raster_backward(self.sid, cams, S, g, col, g_col, sw, flags, self.g_verts, self.g_tex)
+        else:
+            self.ctx.raster_backward_adam(self.sid, cams, S, g, col, g_col, sw, flags, self.m["tex"], self.v["tex"],
+                                          tex_adam[0], tex_adam[1], grad_verts=self.g_verts)
         return rgb
 
     def step(self):
         """One step on ``per_step`` random views; returns the loss (host float)."""
         ids = self.rng.choice(len(self.cams), size=self.per_step, replace=False)
         seeds = self.rng.integers(0, 2 ** 63, size=self.per_step, dtype=np.uint64)
-        self.gradients(ids, seeds)
         self.step_no += 1
         anneal = 100.0 ** (-(self.step_no - 1) / self.total)
+        self.gradients(ids, seeds, tex_adam=(self.lr["tex"] * anneal, self.step_no))
         N.adam_step(self.verts, self.g_verts, self.m["verts"], self.v["verts"], self.lr["verts"] * anneal,
                     self.step_no, dim=3)
-        N.adam_step(self.tex, self.g_tex, self.m["tex"], self.v["tex"], self.lr["tex"] * anneal, self.step_no)
         N.adam_step(self.params, self.g_params, self.m["mlp"], self.v["mlp"], self.lr["mlp"] * anneal, self.step_no)
         return float(self.loss)
 

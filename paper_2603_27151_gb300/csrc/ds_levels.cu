@@ -341,14 +341,15 @@ __global__ void __launch_bounds__(256) k_restrict(const double* __restrict__ fin
     }
 }
 
-// The adjoint with the levels' Adam step fused (Sec. 3.4): one triangle per
-// CTA.  The gradients of all its levels (the FP32 values the plain adjoint
-// writes with overwrite) are formed in shared memory, level after level;
-// then each level's block of the triangle -- contiguous in the levels'
-// layout -- takes its Adam step as a float4 stream of x, m and v, so that
-// the gradient never reaches memory.
-__global__ void __launch_bounds__(256) k_restrict_adam(const double* __restrict__ fine, int T, int r_min, int r_max,
-                                                       int C, AdamTex adam) {
+// The adjoint staged in shared memory, one triangle per CTA: the gradients
+// of all its levels (the FP32 values k_restrict writes with overwrite) are
+// formed there level after level; then each level's block of the triangle --
+// contiguous in the levels' layout -- leaves as a float4 stream: written to
+// `out` (kAdam false), or, with the levels' Adam step fused (Sec. 3.4),
+// applied to x, m and v so that the gradient never reaches memory.
+template <bool kAdam>
+__global__ void __launch_bounds__(256) k_restrict_staged(const double* __restrict__ fine, int T, int r_min, int r_max,
+                                                         int C, float* __restrict__ out, AdamTex adam) {
     extern __shared__ float sm[];   // the levels' gradients of this triangle, finest first
     const int t = blockIdx.x;
     size_t off[6];
@@ -391,12 +392,17 @@ __global__ void __launch_bounds__(256) k_restrict_adam(const double* __restrict_
         for (int k = threadIdx.x; k < n; k += blockDim.x) G[k] = restrict_value(Gf, 1 << R, k, C);
         __syncthreads();
     }
-    // Adam over each level's block, four values per access (the block starts
-    // on a 16-byte boundary: C and the level offsets are multiples of 4)
+    // each level's block, four values per access (the block starts on a
+    // 16-byte boundary: C and the level offsets are multiples of 4)
     for (int R = r_max; R >= r_min; --R) {
         const int n4 = level_V(R) * C / 4;
         const size_t base4 = (off[R - r_min] + (size_t)t * level_V(R) * C) / 4;
         const float4* G4 = reinterpret_cast<const float4*>(sm + soff[R - r_min]);
+        if (!kAdam) {
+            float4* O = reinterpret_cast<float4*>(out) + base4;
+            for (int q = threadIdx.x; q < n4; q += blockDim.x) __stcs(O + q, G4[q]);
+            continue;
+        }
         float4* X = reinterpret_cast<float4*>(adam.x) + base4;
         float4* M = reinterpret_cast<float4*>(adam.m) + base4;
         float4* Vv = reinterpret_cast<float4*>(adam.v) + base4;
@@ -481,8 +487,25 @@ cudaError_t launch_compose(const float* levels, int T, int r_min, int r_max, int
     return cudaGetLastError();
 }
 
+template <bool kAdam>
+static cudaError_t run_staged(const double* fine, int T, int r_min, int r_max, int C, float* out, const AdamTex& adam,
+                              cudaStream_t st) {
+    size_t per_tri = 0;
+    for (int R = r_min; R <= r_max; ++R) per_tri += (size_t)level_V(R) * C;
+    const size_t smem = sizeof(float) * per_tri;
+    cudaError_t e = cudaFuncSetAttribute(k_restrict_staged<kAdam>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_restrict_staged<kAdam><<<T, 256, smem, st>>>(fine, T, r_min, r_max, C, out, adam);
+    note_launches(1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_restrict(const double* fine, int T, int r_min, int r_max, int C, float* out, bool overwrite,
                             cudaStream_t st) {
+    // overwrite with a 16-byte-aligned output and C a multiple of 4: the
+    // staged kernel (float4 stores); otherwise the per-level one
+    if (overwrite && C % 4 == 0 && ((uintptr_t)out & 15) == 0)
+        return run_staged<false>(fine, T, r_min, r_max, C, out, AdamTex{}, st);
     const size_t smem = sizeof(float) * (size_t)(level_V(r_max) + level_V(r_max > 0 ? r_max - 1 : 0)) * C;
     cudaError_t e = cudaFuncSetAttribute(k_restrict, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -495,14 +518,7 @@ cudaError_t launch_restrict_adam(const double* fine, int T, int r_min, int r_max
                                  cudaStream_t st) {
     if (C % 4 != 0 || (((uintptr_t)adam.x | (uintptr_t)adam.m | (uintptr_t)adam.v) & 15) != 0)
         return cudaErrorInvalidValue;
-    size_t per_tri = 0;
-    for (int R = r_min; R <= r_max; ++R) per_tri += (size_t)level_V(R) * C;
-    const size_t smem = sizeof(float) * per_tri;
-    cudaError_t e = cudaFuncSetAttribute(k_restrict_adam, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_restrict_adam<<<T, 256, smem, st>>>(fine, T, r_min, r_max, C, adam);
-    note_launches(1);
-    return cudaGetLastError();
+    return run_staged<true>(fine, T, r_min, r_max, C, nullptr, adam, st);
 }
 
 cudaError_t launch_resample(const float* src, int T, int r_src, int C, float* dst, int r_dst, cudaStream_t st) {

@@ -232,11 +232,14 @@ DS_API ds_status ds_raster_backward(ds_ctx* ctx, int32_t soup_id, const ds_camer
  *  m, v  (device) first and second moments, float32, one value per texture
  *        value in the soup's texture layout (levels back to back for a level
  *        soup), owned by the caller;
+ *  n     the number of floats in each of m and v: must equal the soup's
+ *        texture size (T V C, or the levels' total), else DS_ERR_INVALID_ARG;
  *  lr, beta1 in [0, 1), beta2 in [0, 1), eps >= 0; step t >= 1 (the bias
  *  corrections use 1 - beta^t). */
 typedef struct ds_adam_args {
     float* m;
     float* v;
+    int64_t n;
     float lr, beta1, beta2, eps;
     int64_t step;
 } ds_adam_args;

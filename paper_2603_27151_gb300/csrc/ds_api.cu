@@ -989,6 +989,8 @@ ds_status ds_raster_backward_adam(ds_ctx* c, int32_t soup_id, const ds_camera* c
     Soup* s = nullptr;
     DS_TRY(get_soup(c, soup_id, &s));
     if (s->fixed) return fail(DS_ERR_INVALID_ARG, "the soup is static (DS_STATIC): its texture cannot be updated");
+    if (tex_adam->n != (int64_t)s->tex_floats())
+        return fail(DS_ERR_INVALID_ARG, "m and v must hold " + std::to_string(s->tex_floats()) + " values");
     DS_TRY(check_views(cams, n_views, S));
     DS_TRY(check_gin(fwd, gin, n_views, grad_flags));
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -45,8 +45,8 @@ class ds_camera(ctypes.Structure):
 
 
 class ds_adam_args(ctypes.Structure):
-    _fields_ = [("m", ctypes.c_void_p), ("v", ctypes.c_void_p), ("lr", ctypes.c_float), ("beta1", ctypes.c_float),
-                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("step", ctypes.c_int64)]
+    _fields_ = [("m", ctypes.c_void_p), ("v", ctypes.c_void_p), ("n", ctypes.c_int64), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("step", ctypes.c_int64)]
 
 
 class ds_view_out(ctypes.Structure):
@@ -330,6 +330,8 @@ class Context:
         for t in (m, v):
             if t is None or t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous():
                 raise ValueError("m and v must be contiguous float32 CUDA tensors")
+        if m.numel() != v.numel():
+            raise ValueError("m and v must have the same size")
         n = len(cams)
         ca = cameras(cams)
         fwd = (ds_view_out * n)()
@@ -339,7 +341,8 @@ class Context:
             fwd[k].color = colors[k].data_ptr() if colors is not None else None
             gin[k].grad_color = grad_colors[k].data_ptr() if grad_colors is not None else None
             gin[k].score_w = score_ws[k].data_ptr() if score_ws is not None and score_ws[k] is not None else None
-        args = ds_adam_args(m.data_ptr(), v.data_ptr(), float(lr), float(beta1), float(beta2), float(eps), int(step))
+        args = ds_adam_args(m.data_ptr(), v.data_ptr(), m.numel(), float(lr), float(beta1), float(beta2), float(eps),
+                            int(step))
         _check(load().ds_raster_backward_adam(self.h, soup_id, ca, n, S, fwd, gin, flags, _ptr(grad_verts),
                                               ctypes.byref(args), _stream(stream)))
 

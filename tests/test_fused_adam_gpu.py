@@ -116,7 +116,10 @@ def test_fused_adam_invalid_arguments(ctx):
     fwd[0].gbuf = g[0].data_ptr()
     fwd[0].color = col[0].data_ptr()
     gin[0].grad_color = gc[0].data_ptr()
-    bad = N.ds_adam_args(None, v.data_ptr(), 0.01, 0.9, 0.999, 1e-8, 1)   # NULL m
+    with pytest.raises(N.DsError):   # m and v of the wrong size
+        ctx.raster_backward_adam(sid, sc.cams, 1, g, col, gc, None, N.DS_G_TEX, m[:-1].contiguous(),
+                                 v[:-1].contiguous(), 0.01, 1)
+    bad = N.ds_adam_args(None, v.data_ptr(), v.numel(), 0.01, 0.9, 0.999, 1e-8, 1)   # NULL m
     assert L.ds_raster_backward_adam(ctx.h, sid, N.cameras(sc.cams), 1, 1, fwd, gin, N.DS_G_TEX, None,
                                      ctypes.byref(bad), None) == -1
     assert L.ds_raster_backward_adam(ctx.h, sid, N.cameras(sc.cams), 1, 1, fwd, gin, N.DS_G_TEX, None,

@@ -646,6 +646,13 @@ def adam_step(params, grads, m, v, lr: float, step: int, dim: int = 1, beta1: fl
               eps: float = 1e-8, stream=None):
     """One Adam (dim = 1) or VectorAdam (dim = 3) step in place (ds_adam_step);
     float32 CUDA tensors, v with numel / dim entries."""
+    import torch
+    for name, t in (("params", params), ("grads", grads), ("m", m), ("v", v)):
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or t.device != params.device:
+            raise ValueError("%s must be a contiguous float32 CUDA tensor on the parameters' device" % name)
+    n = params.numel()
+    if grads.numel() != n or m.numel() != n or dim < 1 or n % dim != 0 or v.numel() != n // dim:
+        raise ValueError("grads and m must match params (%d values) and v hold one value per vector of %d" % (n, dim))
     _check(load().ds_adam_step(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), params.numel(), int(dim), float(lr),
                                float(beta1), float(beta2), float(eps), int(step), _stream(stream)))
 

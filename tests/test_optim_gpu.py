@@ -52,7 +52,16 @@ def test_adam_step_rejects_bad_arguments(dev):
     import torch
     from paper_2603_27151_gb300 import native as N
     x = torch.zeros(10, device=dev)
-    for kw in (dict(dim=3), dict(dim=5), dict(step=0), dict(beta1=1.0)):
+    # shapes are checked by the binding before the raw pointers go down
+    for kw in (dict(dim=3), dict(dim=5)):
+        args = dict(lr=0.1, step=1, dim=1)
+        args.update(kw)
+        with pytest.raises(ValueError):
+            N.adam_step(x, x, x, x, **args)
+    with pytest.raises(ValueError):
+        N.adam_step(x, torch.zeros(9, device=dev), x, x, lr=0.1, step=1)
+    # hyperparameters by the library
+    for kw in (dict(step=0), dict(beta1=1.0)):
         args = dict(lr=0.1, step=1, dim=1)
         args.update(kw)
         with pytest.raises(N.DsError):

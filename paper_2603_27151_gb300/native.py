@@ -234,6 +234,49 @@ class Context:
         _check(L.ds_create(ctypes.byref(h), int(device)))
         self.h = h
         self.device = device
+        self._soups = {}   # soup id -> (T, C, texture floats), for the buffer checks
+
+    def _check_views(self, soup_ids, sizes, S, gbufs=None, colors=None, n_fronts=None, grad_colors=None,
+                     score_ws=None, targets=None, grad_verts=None, grad_tex=None):
+        """Host-side checks of the per-view buffers (the C ABI sees raw
+        pointers): sizes[v] = (W, H); gbufs int32 [S,H,W,4], n_fronts int32
+        [S,H,W], score weights float32 [S,H,W], and, for a soup uploaded
+        through this object, colours and colour gradients float32
+        [S,C-1,H,W], targets [C-1,H,W], grad_verts 9T and grad_tex the
+        texture's size; all contiguous CUDA tensors."""
+        import torch
+        n = len(sizes)
+        if S < 1:
+            return   # the library rejects the sample count itself
+
+        def need(t, shape, dt, what):
+            if t is None:
+                return
+            if not (t.is_cuda and t.is_contiguous() and t.dtype == dt and (shape is None or tuple(t.shape) == shape)):
+                raise ValueError("%s must be a contiguous %s CUDA tensor%s" % (what, dt, "" if shape is None else
+                                                                                " of shape %s" % (shape,)))
+        for name, lst in (("gbufs", gbufs), ("colors", colors), ("n_fronts", n_fronts), ("grad_colors", grad_colors),
+                          ("score_ws", score_ws), ("targets", targets)):
+            if lst is not None and len(lst) != n:
+                raise ValueError("%s: one buffer per view is required" % name)
+        for v, (W, H) in enumerate(sizes):
+            meta = self._soups.get(int(soup_ids[v]))
+            Co = meta[1] - 1 if meta else None
+            need(gbufs[v] if gbufs is not None else None, (S, H, W, 4), torch.int32, "gbufs[%d]" % v)
+            need(n_fronts[v] if n_fronts is not None else None, (S, H, W), torch.int32, "n_fronts[%d]" % v)
+            need(score_ws[v] if score_ws is not None else None, (S, H, W), torch.float32, "score_ws[%d]" % v)
+            for name, lst, shape in (("colors", colors, (S, Co, H, W)), ("grad_colors", grad_colors, (S, Co, H, W)),
+                                     ("targets", targets, (Co, H, W))):
+                if lst is not None:
+                    need(lst[v], shape if meta else None, torch.float32, "%s[%d]" % (name, v))
+        meta = self._soups.get(int(soup_ids[0])) if n else None
+        if meta is not None:
+            need(grad_verts, None, torch.float32, "grad_verts")
+            need(grad_tex, None, torch.float32, "grad_tex")
+            if grad_verts is not None and grad_verts.numel() != 9 * meta[0]:
+                raise ValueError("grad_verts must hold 9 T = %d values" % (9 * meta[0]))
+            if grad_tex is not None and grad_tex.numel() != meta[2]:
+                raise ValueError("grad_tex must hold the texture's %d values" % meta[2])
 
     def close(self):
         if self.h:
@@ -256,6 +299,7 @@ class Context:
         flags = (DS_BORROW if borrow else DS_COPY) | (DS_STATIC if static else 0)
         _check(load().ds_soup_upload(self.h, _ptr(verts), _ptr(tex), T, grid_n, C, flags, ctypes.byref(sid),
                                      _stream(stream)))
+        self._soups[sid.value] = (int(T), int(C), int(tex.numel()))
         return sid.value
 
     def soup_upload_levels(self, verts, tex_levels, T: int, r_min: int, r_max: int, C: int, borrow: bool = False,
@@ -269,16 +313,19 @@ class Context:
         flags = (DS_BORROW if borrow else DS_COPY) | (DS_STATIC if static else 0)
         _check(load().ds_soup_upload_levels(self.h, _ptr(verts), _ptr(tex_levels), T, r_min, r_max, C, flags,
                                             ctypes.byref(sid), _stream(stream)))
+        self._soups[sid.value] = (int(T), int(C), int(tex_levels.numel()))
         return sid.value
 
     def soup_free(self, soup_id: int):
         _check(load().ds_soup_free(self.h, soup_id))
+        self._soups.pop(int(soup_id), None)
 
     # -------------------------------------------------------------- passes
     def raster_forward(self, soup_id, cams, seeds, S, mode, bg, gbufs, colors, n_fronts=None, stream=None):
         """gbufs[v]: int32 [S,H,W,4] (tri_id, b1, b2, depth bit patterns);
         colors[v]: float32 [S,C-1,H,W]; n_fronts[v]: int32 [S,H,W] or None."""
         n = len(cams)
+        self._check_views([soup_id] * n, [(c.width, c.height) for c in cams], S, gbufs, colors, n_fronts)
         ca = cameras(cams)
         sd = (ctypes.c_uint64 * n)(*[int(x) for x in (seeds if seeds is not None else [0] * n)])
         bga = np.ascontiguousarray(bg, np.float32)
@@ -294,6 +341,7 @@ class Context:
         """Views of different soups in one launch (ds_raster_forward_multi):
         view v renders soup soup_ids[v]; outputs as raster_forward."""
         n = len(cams)
+        self._check_views(list(soup_ids), [(c.width, c.height) for c in cams], S, gbufs, colors, n_fronts)
         ids = (ctypes.c_int32 * n)(*[int(x) for x in soup_ids])
         ca = cameras(cams)
         sd = (ctypes.c_uint64 * n)(*[int(x) for x in (seeds if seeds is not None else [0] * n)])
@@ -309,6 +357,8 @@ class Context:
     def raster_backward(self, soup_id, cams, S, gbufs, colors, grad_colors, score_ws, flags,
                         grad_verts=None, grad_tex=None, stream=None):
         n = len(cams)
+        self._check_views([soup_id] * n, [(c.width, c.height) for c in cams], S, gbufs, colors, None, grad_colors,
+                          score_ws, grad_verts=grad_verts, grad_tex=grad_tex)
         ca = cameras(cams)
         fwd = (ds_view_out * n)()
         gin = (ds_view_gin * n)()
@@ -333,6 +383,8 @@ class Context:
         if m.numel() != v.numel():
             raise ValueError("m and v must have the same size")
         n = len(cams)
+        self._check_views([soup_id] * n, [(c.width, c.height) for c in cams], S, gbufs, colors, None, grad_colors,
+                          score_ws, grad_verts=grad_verts)
         ca = cameras(cams)
         fwd = (ds_view_out * n)()
         gin = (ds_view_gin * n)()
@@ -439,6 +491,8 @@ class Context:
                  loss, flags, grad_verts=None, grad_tex=None, stream=None):
         """ds_raster_train_l2: forward + L2 loss + backward in one call."""
         n = len(cams)
+        self._check_views([soup_id] * n, [(c.width, c.height) for c in cams], S, gbufs, colors, None, grad_colors,
+                          score_ws, targets, grad_verts, grad_tex)
         ca = cameras(cams)
         sd = (ctypes.c_uint64 * n)(*[int(x) for x in (seeds if seeds is not None else [0] * n)])
         bga = np.ascontiguousarray(bg, np.float32)

@@ -225,6 +225,18 @@ def test_invalid_arguments_launch_nothing(ctx):
     with pytest.raises(N.DsError) as e:
         ctx.raster_forward(12345, sc.cams, sc.seeds, 1, 0, sc.bg, g, col)
     assert e.value.code == -6
+    # buffers of the wrong shape are refused before any pointer reaches the library
+    with pytest.raises(ValueError):
+        ctx.raster_forward(sid, sc.cams, sc.seeds, 2, 0, sc.bg, g, col)          # allocated for S = 1
+    with pytest.raises(ValueError):
+        ctx.raster_forward(sid, sc.cams, sc.seeds, 1, 0, sc.bg, g, [c[:, :-1].contiguous() for c in col])
+    ctx.raster_forward(sid, sc.cams, sc.seeds, 1, 0, sc.bg, g, col)
+    with pytest.raises(ValueError):
+        ctx.raster_backward(sid, sc.cams, 1, g, col, [torch.zeros_like(c) for c in col], None, N.DS_G_TEX,
+                            None, torch.zeros(10, device="cuda"))                  # not the texture's size
+    with pytest.raises(ValueError):
+        ctx.raster_backward(sid, sc.cams, 1, g, col, [torch.zeros_like(c) for c in col], None, N.DS_G_INTERIOR,
+                            torch.zeros(9 * sc.T - 1, device="cuda"), None)        # not 9 T
 
 
 def test_no_sync_forward_matches_and_reports_capacity(ctx):

@@ -11,9 +11,9 @@ constexpr unsigned kFullMask = 0xffffffffu;
 
 // Resident CTAs per SM requested from the compiler for the tile kernels
 // (register budget 65536 / (256 x blocks)); set per kernel at build time.
-// The backward runs at five (48 registers): its waits on gathers hide
-// better with 40 warps than the spills cost; the forward and the edge
-// kernel are faster at four.
+// The backward and the fused training pass run at five (48 registers):
+// their waits on gathers hide better with 40 warps than the spills cost;
+// the forward and the edge kernel are faster at four.
 #ifndef DS_MINB_FWD
 #define DS_MINB_FWD 4
 #endif
@@ -24,7 +24,7 @@ constexpr unsigned kFullMask = 0xffffffffu;
 #define DS_MINB_EDGE 4
 #endif
 #ifndef DS_MINB_TRAIN
-#define DS_MINB_TRAIN 4
+#define DS_MINB_TRAIN 5
 #endif
 
 // Per-tile staged set-up.  h0..h2 hold what the per-pixel coverage test reads

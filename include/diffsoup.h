@@ -255,8 +255,10 @@ typedef struct ds_adam_args {
  * texture updated is the soup's own storage: the caller's tensor for a soup
  * uploaded with borrowing, the context's copy otherwise.  grad_verts as in
  * ds_raster_backward.  DS_ERR_INVALID_ARG for a NULL tex_adam, m or v, bad
- * hyperparameters, step < 1, no DS_G_TEX or DS_G_SCORE in grad_flags, or a
- * static soup (DS_STATIC). */
+ * hyperparameters, step < 1, no DS_G_TEX or DS_G_SCORE in grad_flags, a
+ * static soup (DS_STATIC), or, for a level soup, C not a multiple of 4 or a
+ * texture, m or v not 16-byte aligned (the update moves four values per
+ * access). */
 DS_API ds_status ds_raster_backward_adam(ds_ctx* ctx, int32_t soup_id, const ds_camera* cams,
                                          int32_t n_views, int32_t S, const ds_view_out* fwd,
                                          const ds_view_gin* gin, uint32_t grad_flags, float* grad_verts,

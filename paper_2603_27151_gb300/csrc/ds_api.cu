@@ -991,6 +991,9 @@ ds_status ds_raster_backward_adam(ds_ctx* c, int32_t soup_id, const ds_camera* c
     if (s->fixed) return fail(DS_ERR_INVALID_ARG, "the soup is static (DS_STATIC): its texture cannot be updated");
     if (tex_adam->n != (int64_t)s->tex_floats())
         return fail(DS_ERR_INVALID_ARG, "m and v must hold " + std::to_string(s->tex_floats()) + " values");
+    if (s->levels() && (s->C % 4 != 0 || (((uintptr_t)s->tex | (uintptr_t)tex_adam->m | (uintptr_t)tex_adam->v) & 15)))
+        return fail(DS_ERR_INVALID_ARG, "a level soup's fused Adam needs C a multiple of 4 and 16-byte-aligned "
+                                        "texture, m and v");
     DS_TRY(check_views(cams, n_views, S));
     DS_TRY(check_gin(fwd, gin, n_views, grad_flags));
     cudaStream_t st = static_cast<cudaStream_t>(stream);

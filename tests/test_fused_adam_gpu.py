@@ -132,3 +132,26 @@ def test_fused_adam_invalid_arguments(ctx):
     ctx.soup_free(sid)
     torch.cuda.synchronize()
     ctx.status()
+
+
+def test_fused_adam_level_soup_needs_four_channel_groups(ctx):
+    """The level soups' fused update moves four values per access: a level
+    soup whose channel count is not a multiple of 4 is refused up front."""
+    import torch
+    from paper_2603_27151_gb300 import native as N
+    rng = np.random.default_rng(8)
+    T, C = 50, 3
+    verts = torch.from_numpy(I.box_soup(T, 0.3, rng)).cuda()
+    tex = torch.from_numpy(np.concatenate([l.reshape(-1) for l in I.level_logits(T, 0, 2, C, rng)])).cuda()
+    sid = ctx.soup_upload_levels(verts, tex, T, 0, 2, C, borrow=True)
+    cams = [I.look_at([0.0, 0.0, 3.0], 32, 32)]
+    g, col, _ = N.alloc_outputs(cams, 1, C, "cuda")
+    ctx.raster_forward(sid, cams, [1], 1, 0, np.zeros(C - 1, np.float32), g, col)
+    m, v = torch.zeros_like(tex), torch.zeros_like(tex)
+    with pytest.raises(N.DsError) as e:
+        ctx.raster_backward_adam(sid, cams, 1, g, col, [torch.ones_like(c) for c in col], None, N.DS_G_TEX, m, v,
+                                 0.01, 1)
+    assert e.value.code == -1
+    ctx.soup_free(sid)
+    torch.cuda.synchronize()
+    ctx.status()

@@ -518,7 +518,7 @@ DS_API ds_status ds_raster_forward_multi(ds_ctx* ctx, const int32_t* soup_ids, c
  * back (one synchronisation of `stream`) and returns DS_ERR_CAPACITY above
  * 524288 pairs; every call therefore synchronises `stream` once.  The
  * first call on each device looks up the array's device address with that
- * device current; make that first call before any stream capture.  Every
+ * device current.  Every
  * call in the process shares the one array and leaves its contents behind
  * (the call clears what must start at zero): calls whose work overlaps on the
  * GPU, from several streams or host threads, race and must be serialised by

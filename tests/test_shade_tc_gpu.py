@@ -72,6 +72,21 @@ def test_tensor_core_forward_matches_the_oracle_and_the_cuda_cores(ctx, S):
         assert np.abs(tc[v] - cc[v]).max() <= 1e-5, v
 
 
+def test_tensor_core_forward_tiny_views(ctx):
+    """Views smaller than one tile of 128 pixels (1x1, 5x3) beside a normal
+    one: every tile partial, S = 2."""
+    from paper_2603_27151_gb300 import native as N
+    eyes = I.sphere_eyes(3, 3.0, np.random.default_rng(6))
+    cams = [I.look_at(eyes[0], 1, 1), I.look_at(eyes[1], 5, 3), I.look_at(eyes[2], 40, 20)]
+    rng = np.random.default_rng(3)
+    feats = [rng.uniform(0, 1, (2, 7, c.height, c.width)).astype(np.float32) for c in cams]
+    params = _params(17)
+    tc = _shade(ctx, N.DS_SHADE_TENSOR_CORES, cams, params, feats)
+    for v, c in enumerate(cams):
+        ref = SH.shade(feats[v], c, params)
+        assert np.abs(tc[v] - ref).max() <= 1e-5, v
+
+
 def test_tensor_core_forward_special_cases(ctx):
     """A = 1 returns the feature colour exactly; all-zero features give the
     MLP of the view direction alone; large weights and biases (ReLU on both

@@ -449,15 +449,16 @@ __global__ void __launch_bounds__(kThreads) k_shade_finish(const float* __restri
 // keeps 10 mantissa bits, so every operand is split into hi = the TF32
 // truncation and lo = the remainder (exact in FP32) and each product is taken
 // as x_lo w_hi + x_hi w_lo + x_hi w_hi (the x_lo w_lo term, about 2^-21 of the
-// product, is dropped): six MMAs per layer, issued by one thread and
-// completed on an mbarrier.
+// product, is dropped): six MMAs per layer, and a seventh adds the bias (a
+// constant K-chunk (1, 1, 0, ...) times the bias tile (b hi, b lo)), issued
+// by one thread and completed on an mbarrier.
 //
 // The layer inputs (operand A) live in tensor memory beside the FP32
 // accumulator: each thread writes its row with tcgen05.st and the MMAs read A
-// from there, so shared memory carries only the 6 KB of weight tiles (B).
-// With A in shared memory every MMA re-read 4 KB of it, and the shared-memory
-// bandwidth, not the tensor cores, set the kernel's speed.  Per layer the 128
-// threads read their accumulator row (tcgen05.ld), add the bias, apply the
+// from there, so shared memory carries only the weight and bias tiles (B, 9
+// KB).  With A in shared memory every MMA re-read 4 KB of it, and the
+// shared-memory bandwidth, not the tensor cores, set the kernel's speed.  Per
+// layer the 128 threads read their accumulator row (tcgen05.ld), apply the
 // activation and write the next layer's hi/lo row.
 namespace tc {
 

@@ -5,9 +5,12 @@
 // MLP (ReLU, ReLU, sigmoid); the first four features, read as RGBA, are
 // blended with the MLP colour: rgb = A * feat_rgb + (1 - A) * mlp.
 //
-// FP32 on the CUDA cores.  The MLP is ALU-bound (560 multiply-adds per
-// pixel-sample against 40 bytes of traffic), so the kernels are organised to
-// issue few instructions besides the FFMAs:
+// Two forwards: on the tensor cores (k_shade_fwd_tc, tcgen05 kind::tf32 with
+// a hi/lo split, described further down; the faster one and the default)
+// and in FP32 on the CUDA cores (k_shade_fwd); the backward runs on the
+// CUDA cores.  On the CUDA cores the MLP is ALU-bound (560 multiply-adds per
+// pixel-sample against 40 bytes of traffic), so those kernels are organised
+// to issue few instructions besides the FFMAs:
 //  - the SH half of the first layer does not depend on the mask sample: it is
 //    evaluated once per pixel and reused for all S samples;
 //  - the parameters sit in shared memory and are read as float4 broadcasts,

@@ -20,6 +20,10 @@
 //    twin and, with weight 1/2, the midpoints of its six incident edges.  One
 //    CTA per triangle, levels in shared memory, FP32 from the FP64
 //    accumulator of the finest grid;
+//  - k_restrict_staged: the same adjoint with all of a triangle's level
+//    gradients staged in shared memory and written as float4 streams
+//    (overwrite mode), or applied there as the levels' Adam step (the
+//    backward with a fused texture optimiser);
 //  - k_resample: one level's grid sampled at another level's vertices.
 #include <cuda_fp16.h>
 

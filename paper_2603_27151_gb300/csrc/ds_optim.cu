@@ -5,6 +5,8 @@
 //   m <- b1 m + (1 - b1) g,  v <- b2 v + (1 - b2) |g|^2,
 //   x <- x - lr (m c1) / (sqrt(v c2) + eps),  c1 = 1/(1 - b1^t), c2 = 1/(1 - b2^t).
 // HBM-bound: one read of x, g, m, v and one write of x, m, v per value.
+// Every value's update is adam_apply (ds_common.cuh), shared with the fused
+// gradient finishes, so both give the same bits for the same gradient.
 #include <cmath>
 
 #include "ds_internal.h"

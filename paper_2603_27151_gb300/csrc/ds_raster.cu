@@ -16,7 +16,7 @@ namespace ds {
 // kMulti: the views are of different soups (ViewDesc s_act, s_act_a,
 // rec_base; the soups share N, C and V, given by s).
 template <int SG, int TW, bool kLoss, bool kMulti>
-__global__ void __launch_bounds__(kTilePix, DS_MINB_FWD)
+__global__ void __launch_bounds__(kTilePix, SG == 4 ? DS_MINB_FWD : DS_MINB_FWD_SMALL)
     k_raster_fwd(const __grid_constant__ ViewTable vt, const SoupDev soup, const SetupRec* __restrict__ recs,
                  const uint32_t* __restrict__ keys, const uint32_t* __restrict__ vals,
                  const uint2* __restrict__ ranges, int DB, uint32_t mode, const Bg bg, float scale,

@@ -13,9 +13,13 @@ constexpr unsigned kFullMask = 0xffffffffu;
 // (register budget 65536 / (256 x blocks)); set per kernel at build time.
 // The backward and the fused training pass run at five (48 registers):
 // their waits on gathers hide better with 40 warps than the spills cost;
-// the forward and the edge kernel are faster at four.
+// the edge kernel and the forward of 4-sample groups are faster at four,
+// the forward of smaller groups (fewer registers per pixel) at five.
 #ifndef DS_MINB_FWD
 #define DS_MINB_FWD 4
+#endif
+#ifndef DS_MINB_FWD_SMALL
+#define DS_MINB_FWD_SMALL 5
 #endif
 #ifndef DS_MINB_BWD
 #define DS_MINB_BWD 5
